@@ -1,0 +1,175 @@
+"""Tucker-format reference operations (arXiv:1912.04582, Sections 4-5), numpy FP64.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).  Each function restates one
+operation of the paper from its mathematics; library primitives used as steps are
+``numpy.linalg.svd`` and ``numpy.einsum``.
+
+A Tucker tensor is a tuple ``(G, (U1, U2, U3))`` with core ``G`` of shape
+(r1, r2, r3) and factors ``U_a`` of shape (N_a, r_a):
+    A(i1,i2,i3) = sum_k G(k1,k2,k3) U1(i1,k1) U2(i2,k2) U3(i3,k3)   (Section 4, Tucker format).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def full(t):
+    """Expand a Tucker tensor to the full N1 x N2 x N3 array (Section 4)."""
+    G, (U1, U2, U3) = t
+    return np.einsum("abc,ia,jb,kc->ijk", G, U1, U2, U3, optimize=True)
+
+
+def ranks(t):
+    return tuple(int(s) for s in t[0].shape)
+
+
+def unfold(A, mode):
+    """Mode-a unfolding: rows indexed by i_a, columns by the other two indices."""
+    return np.moveaxis(A, mode, 0).reshape(A.shape[mode], -1)
+
+
+def truncation_rank(sigma, eps, cap, total_sq):
+    """Smallest r with sum_{k>r} sigma_k^2 <= (eps^2/3) ||A||_F^2, then r <- min(r, cap),
+    r >= 1 (the per-mode rule that makes ||A - B||_F <= eps ||A||_F for HOSVD, Section 4
+    item 1)."""
+    s2 = np.asarray(sigma, dtype=np.float64) ** 2
+    tail = np.concatenate([np.cumsum(s2[::-1])[::-1][1:], [0.0]])  # tail[r-1] = sum_{k>r}
+    thr = eps * eps / 3.0 * total_sq
+    r = len(s2)
+    for cand in range(1, len(s2) + 1):
+        if tail[cand - 1] <= thr:
+            r = cand
+            break
+    if cap is not None:
+        r = min(r, int(cap))
+    return max(1, r)
+
+
+def hosvd(A, eps, cap=None):
+    """Truncated higher-order SVD of a full tensor (Section 4 item 1, after De Lathauwer
+    et al.): factors are the leading left singular vectors of each unfolding, the core is
+    A x_1 U1^T x_2 U2^T x_3 U3^T.  Returns the Tucker tensor and the singular values."""
+    total = float(np.sum(A * A))
+    Us, sig = [], []
+    for a in range(3):
+        Ua, sa, _ = np.linalg.svd(unfold(A, a), full_matrices=False)
+        r = truncation_rank(sa, eps, cap, total)
+        Us.append(Ua[:, :r])
+        sig.append(sa)
+    G = np.einsum("ijk,ia,jb,kc->abc", A, Us[0], Us[1], Us[2], optimize=True)
+    return (G, tuple(Us)), sig
+
+
+def round_reference(t, eps, cap=None):
+    """Reference rounding of a Tucker tensor: expand to full, then truncated HOSVD.
+    (The fast route of Section 4 item 4 — QR of the factors, SVD of the small core — gives
+    the same subspaces; this reference takes the definition directly.)"""
+    return hosvd(full(t), eps, cap)[0]
+
+
+def add(a, b):
+    """Element-wise sum (Section 4 item 2, element_wise_sum): block-diagonal core,
+    concatenated factors; ranks add."""
+    Ga, Ua = a
+    Gb, Ub = b
+    ra, rb = Ga.shape, Gb.shape
+    G = np.zeros(tuple(ra[k] + rb[k] for k in range(3)))
+    G[:ra[0], :ra[1], :ra[2]] = Ga
+    G[ra[0]:, ra[1]:, ra[2]:] = Gb
+    U = tuple(np.concatenate([Ua[k], Ub[k]], axis=1) for k in range(3))
+    return G, U
+
+
+def scale(a, s):
+    G, U = a
+    return G * s, U
+
+
+def hadamard(a, b):
+    """Element-wise product (Section 4 item 3): Kronecker product of the cores and
+    row-wise Kronecker products of the factors; with 1-based k = (kA-1) rB + kB."""
+    Ga, Ua = a
+    Gb, Ub = b
+    G = np.kron(Ga, Gb)
+    U = tuple(np.einsum("ia,ib->iab", Ua[k], Ub[k]).reshape(Ua[k].shape[0], -1)
+              for k in range(3))
+    return G, U
+
+
+def convolve(t, w1, w2, w3):
+    """Weighted convolution S = sum_i A(i) w1(i1) w2(i2) w3(i3) in O(n r^3)
+    (Section 4 item 5): S_a = U_a^T w_a, then contract the core."""
+    G, (U1, U2, U3) = t
+    return float(np.einsum("abc,a,b,c->", G, U1.T @ w1, U2.T @ w2, U3.T @ w3))
+
+
+def maxwellian_rank1(xi, n, u, T):
+    """Rank-1 Tucker Maxwellian (Section 5): U_a(i) = n^{1/3} (2 pi R_g T)^{-1/2}
+    exp(-(xi_{a,i} - u_a)^2 / (2 R_g T)), with R_g = 1/2."""
+    Rg = 0.5
+    U = tuple((n ** (1.0 / 3.0) / math.sqrt(2 * math.pi * Rg * T)
+               * np.exp(-(xi[a] - u[a]) ** 2 / (2 * Rg * T)))[:, None] for a in range(3))
+    return np.ones((1, 1, 1)), U
+
+
+def lemma1(w1, w2, w3):
+    """Lemma 1: w1(i1) + w2(i2) + w3(i3) in Tucker format with ranks 2: core zero except
+    G(1,2,2) = G(2,1,2) = G(2,2,1) = 1 (1-based), factors [w_a, 1]."""
+    G = np.zeros((2, 2, 2))
+    G[0, 1, 1] = G[1, 0, 1] = G[1, 1, 0] = 1.0
+    U = tuple(np.stack([w, np.ones_like(w)], axis=1) for w in (w1, w2, w3))
+    return G, U
+
+
+def shakhov_coefficient(n, T, Pr):
+    """A in f^S = f^M [1 + A (q.v)(v^2/T - 5/2)] with R_g = 1/2, m = 1:
+    (2/5)(1-Pr)/(p R_g T), p = n R_g T  =>  A = (8/5)(1-Pr)/(n T^2)."""
+    Rg = 0.5
+    p = n * Rg * T
+    return 0.4 * (1.0 - Pr) / (p * Rg * T)
+
+
+def shakhov_rank5(xi, a, Pr):
+    """f^S built as in Proposition 1 (fshakhov_structure):
+    f^M o (1 + (sum_a c_a v_a) o (b v^2 - 1)), with Lemma 1 for both rank-2 factors,
+    Hadamard products and one sum — Tucker ranks 1 + 2*2 = 5."""
+    n, u, T, q = a[0], a[1:4], a[4], a[5:8]
+    A = shakhov_coefficient(n, T, Pr)
+    v = [xi[k] - u[k] for k in range(3)]
+    # (sum_a c_a v_a) o (b v^2 - 1) with c_a = A q_a * (5/2),  b = 2/(5T)
+    c = [2.5 * A * q[k] for k in range(3)]
+    b = 2.0 / (5.0 * T)
+    lin = lemma1(c[0] * v[0], c[1] * v[1], c[2] * v[2])
+    quad = lemma1(b * v[0] ** 2 - 1.0, b * v[1] ** 2, b * v[2] ** 2)
+    one = (np.ones((1, 1, 1)), tuple(np.ones((len(xi[k]), 1)) for k in range(3)))
+    bracket = add(one, hadamard(lin, quad))
+    return hadamard(maxwellian_rank1(xi, n, u, T), bracket)
+
+
+def shakhov_rank4(xi, a, Pr):
+    """f^S with per-mode basis {1, v, v^2, v^3} x Maxwellian factor: the bracket
+    1 + A (q.v)(v^2/T - 5/2) is a cubic polynomial in (v1, v2, v3), so a 4x4x4 core
+    with 13 non-zeros represents it exactly (ranks 4 <= 5 of Proposition 1)."""
+    n, u, T, q = a[0], a[1:4], a[4], a[5:8]
+    A = shakhov_coefficient(n, T, Pr)
+    G = np.zeros((4, 4, 4))
+    G[0, 0, 0] = 1.0
+    e = np.eye(3, dtype=int)
+    for al in range(3):
+        lin = tuple(e[al])                       # v_al
+        G[lin] += -2.5 * A * q[al]
+        for be in range(3):                      # v_al * v_be^2 / T
+            idx = [int(e[al][k]) + 2 * int(e[be][k]) for k in range(3)]
+            G[tuple(idx)] += A * q[al] / T
+    _, M = maxwellian_rank1(xi, n, u, T)
+    U = tuple(M[k][:, 0:1] * np.stack([(xi[k] - u[k]) ** p for p in range(4)], axis=1)
+              for k in range(3))
+    return G, U
+
+
+def compression(r, N):
+    """C = (r1 r2 r3 + N (r1 + r2 + r3)) / N^3 (Section 7)."""
+    r1, r2, r3 = r
+    return (r1 * r2 * r3 + N * (r1 + r2 + r3)) / float(N) ** 3

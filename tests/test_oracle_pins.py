@@ -1,0 +1,300 @@
+"""Pins of the FP64 full-grid oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed-form moments of
+Maxwellians and Maxwellian mixtures, the Poisson-summation quadrature defect, the
+Shakhov heat-flux relaxation property, exact geometry of lattices and parallelepipeds,
+the textbook upwind scheme in the free-molecular limit, steadiness of a uniform free
+stream, conservation in closed boxes, and invariance under renumbering.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+
+def _mixture_closed_form(comps):
+    """Moments of a sum of Maxwellians M(n_k, u_k, T_k) with R_g = 1/2, m = 1.
+
+    Each component has per-axis variance T_k/2.  With d_k = u_k - u:
+      n = sum n_k;  n u = sum n_k u_k;
+      (3/2) n T = sum n_k (|d_k|^2 + 3 T_k / 2);
+      q = 1/2 sum n_k d_k (|d_k|^2 + 5 T_k / 2).
+    """
+    n = sum(c[0] for c in comps)
+    u = sum(c[0] * np.asarray(c[1]) for c in comps) / n
+    e = 0.0
+    q = np.zeros(3)
+    for nk, uk, Tk in comps:
+        d = np.asarray(uk) - u
+        e += nk * (d @ d + 1.5 * Tk)
+        q += 0.5 * nk * d * (d @ d + 2.5 * Tk)
+    T = e / (1.5 * n)
+    return n, u, T, q
+
+
+def _one_cell(N=40, vmax=8.0, Pr=2.0 / 3.0, Kn=0.1):
+    wl = W.specular_box(shape=(1, 1, 1), N=N, vmax=vmax, Kn=Kn)
+    wl.Pr = Pr
+    return wl
+
+
+def test_grid_nodes_and_symmetry(oracle_lib):
+    wl = W.sod_row(N=12)
+    o = oracle_lib.FullGridOracle(wl)
+    xs = o.nodes()
+    for x in xs:
+        ref = -5.0 + np.arange(12) * (10.0 / 11.0)
+        assert np.max(np.abs(x - ref)) < 1e-14
+        assert np.array_equal(x[::-1], -x)          # exactly symmetric grid
+    assert abs(o.weight() - (10.0 / 11.0) ** 3) < 1e-15
+
+
+def test_geometry_lattice_exact_and_closed(oracle_lib):
+    wl = W.cavity(nside=3, N=4, seed=5)
+    o = oracle_lib.FullGridOracle(wl)
+    vol, fcell, fgeo = o.geometry()
+    assert np.allclose(vol, (1.0 / 3.0) ** 3, rtol=0, atol=1e-16)
+    assert np.allclose(fgeo[:, 0], (1.0 / 3.0) ** 2, rtol=1e-15)
+    # 3*3*3 cubes: 3*4*9 = 108 faces, 6*9 = 54 on the boundary
+    assert fcell.shape[0] == 108 and np.sum(fcell[:, 1] < 0) == 54
+    # each normal is a signed unit axis
+    assert np.allclose(np.sort(np.abs(fgeo[:, 1:]), axis=1), [0, 0, 1], atol=0)
+
+
+def _closure(o, n_cell):
+    vol, fcell, fgeo = o.geometry()
+    s = np.zeros((n_cell, 3))
+    for j in range(fcell.shape[0]):
+        a = fgeo[j, 0] * fgeo[j, 1:]
+        s[fcell[j, 0]] += a
+        if fcell[j, 1] >= 0:
+            s[fcell[j, 1]] -= a
+    return vol, s
+
+
+def test_geometry_jittered_closure_and_total_volume(oracle_lib):
+    wl = W.closed_freestream_box(shape=(4, 3, 3), jitter=0.25, seed=7)
+    o = oracle_lib.FullGridOracle(wl)
+    vol, s = _closure(o, wl.n_cell)
+    assert np.max(np.abs(s)) < 1e-15                # sum_l A_l e_l = 0 per closed cell
+    assert abs(vol.sum() - 1.0) < 1e-14             # cells tile the unit box
+    assert vol.min() > 0
+
+
+def test_geometry_parallelepiped_volume_is_determinant(oracle_lib):
+    # one hex that is the image of the unit cube under an affine map x -> M x + b
+    M = np.array([[1.0, 0.3, -0.2], [0.1, 0.9, 0.25], [-0.15, 0.05, 1.2]])
+    corners = np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, 1, 0],
+                        [0, 0, 1], [1, 0, 1], [1, 1, 1], [0, 1, 1]], float)
+    xyz = corners @ M.T + np.array([0.2, -0.1, 0.4])
+    wl = W.closed_freestream_box(shape=(1, 1, 1), jitter=0.0)
+    wl.xyz = xyz
+    wl.hex8 = np.arange(8, dtype=np.int64)[None, :]
+    wl.bface = np.array([[0, l] for l in range(6)], dtype=np.int64)
+    wl.bgroup = np.zeros(6, dtype=np.int32)
+    wl.n0, wl.u0, wl.T0 = np.ones(1), np.zeros((1, 3)), np.ones(1)
+    o = oracle_lib.FullGridOracle(wl)
+    vol, fcell, fgeo = o.geometry()
+    assert abs(vol[0] - np.linalg.det(M)) < 1e-14
+    # face x- of the image: area vector = -(M e2) x (M e3)
+    A = -np.cross(M[:, 1], M[:, 2])
+    j = [k for k in range(6) if fcell[k, 0] == 0][0]
+    got = [fgeo[k, 0] * fgeo[k, 1:] for k in range(6)]
+    assert min(np.max(np.abs(g - A)) for g in got) < 1e-14
+
+
+def test_mesh_rejects_unlisted_boundary(oracle_lib):
+    wl = W.cavity(nside=2, N=4)
+    wl.bface = wl.bface[1:]
+    wl.bgroup = wl.bgroup[1:]
+    with pytest.raises(ValueError):
+        oracle_lib.FullGridOracle(wl)
+
+
+@pytest.mark.parametrize("u,T", [((0.0, 0.0, 0.0), 1.0), ((0.7, -0.4, 0.2), 1.3),
+                                 ((2.7386, 0.0, 0.0), 1.0)])
+def test_maxwellian_moments_closed_form(oracle_lib, u, T):
+    """Discrete Maxwellian on a fine, wide grid: n, u, T recovered, q = 0 (Section 2)."""
+    wl = _one_cell(N=48, vmax=9.0)
+    o = oracle_lib.FullGridOracle(wl)
+    f = o.maxwellian(1.7, u, T)
+    _, a = o.shakhov_of(f)
+    assert abs(a[0] - 1.7) < 1e-13
+    assert np.max(np.abs(a[1:4] - u)) < 1e-13
+    assert abs(a[4] - T) < 1e-12
+    assert np.max(np.abs(a[5:8])) < 1e-12
+
+
+def test_mixture_moments_closed_form(oracle_lib):
+    """Sum of two Maxwellians: T and the heat flux q have closed forms; a dropped term,
+    a wrong sign or the wrong 1/2 in q would show here."""
+    wl = _one_cell(N=56, vmax=10.0)
+    o = oracle_lib.FullGridOracle(wl)
+    comps = [(0.8, (0.9, -0.3, 0.1), 0.9), (0.5, (-0.6, 0.5, -0.4), 1.6)]
+    f = sum(o.maxwellian(n, u, T) for n, u, T in comps)
+    _, a = o.shakhov_of(f)
+    n, u, T, q = _mixture_closed_form(comps)
+    assert abs(a[0] - n) < 1e-13
+    assert np.max(np.abs(a[1:4] - u)) < 1e-13
+    assert abs(a[4] - T) < 1e-12
+    assert np.max(np.abs(a[5:8] - q)) < 1e-12
+    assert np.max(np.abs(q)) > 0.05
+
+
+def test_quadrature_defect_poisson_summation(oracle_lib):
+    """Coarse grid (N=12 on [-5,5], even N so the nodes sit at half-steps around 0):
+    the discrete density of a unit Maxwellian at rest is (1 + 2 sum_m (-1)^m
+    exp(-pi^2 m^2 T / dxi^2))^3 (Poisson summation of the node sum, Section 3)."""
+    wl = W.sod_row(N=12)
+    o = oracle_lib.FullGridOracle(wl)
+    dxi = 10.0 / 11.0
+    for T in (0.6, 0.8, 1.0):        # box truncation below 1e-15 for these T
+        f = o.maxwellian(1.0, (0, 0, 0), T)
+        n_disc = o.weight() * f.sum()
+        s = 1.0 + 2.0 * sum((-1) ** m * math.exp(-math.pi ** 2 * m * m * T / dxi ** 2)
+                            for m in range(1, 6))
+        assert abs(n_disc - s ** 3) < 1e-12
+        assert abs(n_disc - 1.0) > 1e-6              # the defect is visible at this size
+
+
+def test_shakhov_heat_flux_identity(oracle_lib):
+    """f^S keeps n, u, T of f and carries heat flux (1 - Pr) q (S-model property,
+    Section 2 shakhov_integral, coefficient reading (2/5)(1-Pr)/(p R_g T))."""
+    wl = _one_cell(N=40, vmax=8.0)
+    o = oracle_lib.FullGridOracle(wl)
+    a = np.array([1.3, 0.3, -0.2, 0.1, 1.1, 0.15, -0.08, 0.05])
+    fs = o.shakhov_from_macro(a)
+    _, b = o.shakhov_of(fs)
+    assert np.max(np.abs(b[:5] - a[:5])) < 1e-12
+    assert np.max(np.abs(b[5:8] - (1.0 - 2.0 / 3.0) * a[5:8])) < 1e-12
+
+
+def test_shakhov_reduces_to_maxwellian_without_heat_flux(oracle_lib):
+    wl = _one_cell(N=16, vmax=6.0)
+    o = oracle_lib.FullGridOracle(wl)
+    a = np.array([0.9, 0.2, 0.1, -0.3, 1.2, 0.0, 0.0, 0.0])
+    assert np.array_equal(o.shakhov_from_macro(a), o.maxwellian(0.9, a[1:4], 1.2))
+
+
+def test_collision_frequency_law(oracle_lib):
+    """nu = p / mu(T), p = n T / 2, mu = (Kn / sqrt(pi)) T^omega (nondimensional)."""
+    wl = _one_cell(N=4, vmax=4.0, Kn=0.37)
+    o = oracle_lib.FullGridOracle(wl)
+    for n, T in ((1.0, 1.0), (0.4, 2.3)):
+        p = 0.5 * n * T
+        mu = 0.37 / math.sqrt(math.pi) * T ** 0.81
+        assert abs(o.nu(n, T) - p / mu) < 1e-13 * (p / mu)
+
+
+def test_free_molecular_row_is_textbook_upwind(oracle_lib):
+    """Kn -> infinity on the 1D row: each velocity node follows the first-order upwind
+    scheme f_i - dt/h [xi+ (f_i - f_{i-1}) + xi- (f_{i+1} - f_i)] with zero-gradient
+    ends; symmetry sides cancel for a mirror-symmetric state (Section 3)."""
+    wl = W.sod_row(N=12, Kn=1e12, seed=4)
+    o = oracle_lib.FullGridOracle(wl)
+    f0 = o.f()
+    order = np.argsort(wl.cell_ijk[:, 0])
+    g = f0[order]                                   # lattice order along x
+    xi1 = o.nodes()[0][None, :, None, None]
+    dt = 1.0e-3
+    h = 1.0 / 16
+    gm = np.concatenate([g[:1], g[:-1]])            # f_{i-1} (zero gradient at the left)
+    gp = np.concatenate([g[1:], g[-1:]])            # f_{i+1}
+    exp = g - dt / h * (np.maximum(xi1, 0) * (g - gm) + np.minimum(xi1, 0) * (gp - g))
+    o.step(1, dt)
+    got = o.f()[order]
+    assert np.max(np.abs(got - exp)) < 1e-13 * np.max(np.abs(g))
+
+
+def test_uniform_free_stream_is_steady_on_jittered_mesh(oracle_lib):
+    wl = W.closed_freestream_box(shape=(3, 3, 2), jitter=0.3, Kn=1e12)
+    o = oracle_lib.FullGridOracle(wl)
+    f0 = o.f()
+    o.step(5, o.dt())
+    assert np.max(np.abs(o.f() - f0)) < 1e-14 * np.max(f0)
+
+
+def test_uniform_maxwellian_fixed_point_with_collisions(oracle_lib):
+    """J = nu (f^S - f) vanishes for a Maxwellian (q = 0): on a fine grid the uniform
+    free stream stays put to the quadrature defect, and the residual is ~0."""
+    wl = W.closed_freestream_box(shape=(2, 2, 2), N=28, vmax=5.5, jitter=0.2, Kn=0.05,
+                                 u=(0.2, 0.1, -0.1))
+    o = oracle_lib.FullGridOracle(wl)
+    f0 = o.f()
+    res = o.step(3, o.dt())
+    assert np.max(np.abs(o.f() - f0)) < 1e-13 * np.max(f0)
+    assert res < 1e-10
+
+
+def test_renumbering_invariance(oracle_lib):
+    """Shuffled cell, face and local-vertex numbering gives the same solution."""
+    out = []
+    for seed in (None, 1, 9):
+        wl = W.sod_row(N=8, seed=seed)
+        o = oracle_lib.FullGridOracle(wl)
+        o.step(20, 2e-3)
+        m = o.macro()
+        out.append(m[np.argsort(wl.cell_ijk[:, 0])])
+    assert np.max(np.abs(out[0] - out[1])) < 1e-13
+    assert np.max(np.abs(out[0] - out[2])) < 1e-13
+
+
+def _totals(o, wl):
+    vol, _, _ = o.geometry()
+    f = o.f()
+    xs = o.nodes()
+    w = o.weight()
+    x2 = xs[0][:, None, None] ** 2 + xs[1][None, :, None] ** 2 + xs[2][None, None, :] ** 2
+    mass = np.sum(vol * w * f.reshape(f.shape[0], -1).sum(1))
+    energy = np.sum(vol * w * (f * x2[None]).reshape(f.shape[0], -1).sum(1))
+    return mass, energy
+
+
+def test_specular_box_conserves_mass_and_energy(oracle_lib):
+    """Symmetry planes on every side: no mass or energy crosses them; the collision term
+    conserves both up to the quadrature defect (negligible on this fine grid)."""
+    wl = W.specular_box(shape=(2, 2, 1), N=32, vmax=6.2, jitter=0.0)
+    o = oracle_lib.FullGridOracle(wl)
+    m0, e0 = _totals(o, wl)
+    o.step(10, o.dt())
+    m1, e1 = _totals(o, wl)
+    assert abs(m1 - m0) < 1e-13 * m0
+    assert abs(e1 - e0) < 1e-12 * e0
+
+
+def test_diffuse_wall_is_impermeable(oracle_lib):
+    """Diffuse walls: n_w from the impermeability condition makes the wall mass flux zero,
+    so the total mass in a closed box is conserved (energy is not: walls exchange heat)."""
+    wl = W.specular_box(shape=(2, 1, 1), N=32, vmax=6.2, wall_group=0)
+    o = oracle_lib.FullGridOracle(wl)
+    m0, _ = _totals(o, wl)
+    o.step(10, o.dt())
+    m1, _ = _totals(o, wl)
+    assert abs(m1 - m0) < 1e-13 * m0
+
+
+def test_wall_density_equals_gas_density_at_equilibrium(oracle_lib):
+    """Gas at rest in equilibrium with a wall at the same temperature: the reflected
+    density n_w equals the gas density (Section 2, impermeability)."""
+    wl = W.cavity(nside=2, N=12, vmax=6.0, lid=0.0)
+    wl.n0 = np.full(wl.n_cell, 0.7)
+    o = oracle_lib.FullGridOracle(wl)
+    o.step(1, 1e-3)
+    nw = o.wall_density()
+    _, fcell, _ = o.geometry()
+    wall = fcell[:, 1] < 0
+    assert np.max(np.abs(nw[wall] - 0.7)) < 1e-14
+
+
+def test_time_step_rule(oracle_lib):
+    """dt = CFL / max_i [nu_i + sum_l |A_l| xi_max / (2 |V_i|)]; for cubes of side h:
+    sum |A| / (2 V) = 3 / h."""
+    wl = W.sod_row(N=12)
+    o = oracle_lib.FullGridOracle(wl)
+    m = o.macro()
+    h = 1.0 / 16
+    xi_max = math.sqrt(3) * 5.0
+    rates = [o.nu(m[c, 0], m[c, 4]) + 3.0 * xi_max / h for c in range(wl.n_cell)]
+    assert abs(o.dt(0.5) - 0.5 / max(rates)) < 1e-15
