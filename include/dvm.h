@@ -1,0 +1,193 @@
+/*
+ * dvm.h — C ABI of the GB300 S-model discrete velocity solver.
+ *
+ * Method: Chikitkin, Kornev & Titarev, "Numerical solution of the Boltzmann
+ * equation with S-model collision integral using tensor decompositions"
+ * (arXiv:1912.04582).  One explicit time step of the discrete velocity method
+ * (Section 3, Algorithms 1 and 2) on every hexahedral cell of an unstructured
+ * mesh, with the distribution function of each cell stored on a structured
+ * N1 x N2 x N3 velocity grid either as a full tensor or in Tucker format
+ * (Sections 4 and 5).
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ * Units      nondimensional: R_g = 1/2, molecular mass m = 1, so that
+ *            f^M = n (pi T)^{-3/2} exp(-|xi - u|^2 / T), p = n T / 2 and
+ *            nu = p / mu(T) with mu = (Kn / sqrt(pi)) T^omega
+ *            (Section 2, shakhov_integral).
+ * Grid       xi_{a,i} = ((N_a-1-i) lo_a + i hi_a) / (N_a-1), i = 0..N_a-1
+ *            (Section 3: uniform nodes xi_min + (i-1) dxi, endpoints included);
+ *            every node has quadrature weight dxi_1 dxi_2 dxi_3.
+ * Layout     a full tensor f of one cell is N1*N2*N3 doubles, i3 fastest:
+ *            f[(i1*N2 + i2)*N3 + i3].  Arrays over cells are cell-major.
+ * Macro      per cell [n, u1, u2, u3, T, q1, q2, q3] (Section 2), with
+ *            q = (1/2) sum_nodes w v |v|^2 f.
+ * Mesh       hex8 lists vertex ids in VTK order (unit-cube corners
+ *            (0,0,0) (1,0,0) (1,1,0) (0,1,0) (0,0,1) (1,0,1) (1,1,1) (0,1,1));
+ *            local face l is the quad {0,4,7,3}, {1,2,6,5}, {0,1,5,4},
+ *            {3,7,6,2}, {0,3,2,1}, {4,5,6,7} (outward by the right-hand
+ *            rule).  Faces shared by two cells are found by vertex sets; every
+ *            other (cell, local face) must be listed as a boundary face with a
+ *            group id.
+ * Errors     every call returns a status: DVM_OK (0), a warning (> 0) or an
+ *            error (< 0); dvm_last_error() gives a message for the calling
+ *            thread.  No exception crosses the ABI.
+ * Ownership  the library copies every input array; the caller keeps its
+ *            buffers.  The context owns all device memory it allocates.
+ * Streams    all device work of a context is issued on opts.cuda_stream
+ *            (NULL = the legacy default stream).  Calls that return host data
+ *            synchronise that stream.
+ */
+#ifndef DVM_GB300_H
+#define DVM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define DVM_OK 0
+#define DVM_NOT_CONVERGED 1
+#define DVM_ERR_INVALID_ARG (-1)
+#define DVM_ERR_OOM (-2)
+#define DVM_ERR_CUDA (-3)
+#define DVM_ERR_TIMEOUT (-4)
+#define DVM_ERR_NONPHYSICAL (-5)
+#define DVM_ERR_UNSUPPORTED (-6)
+#define DVM_ERR_STATE (-7)
+#define DVM_ERR_IO (-8)
+
+/* boundary condition types (Section 2; Section 6 lists 'in'/'out' = free
+ * stream, 'wall', and symmetry 'sym-y'/'sym-z') */
+#define DVM_BC_FREESTREAM 0 /* Maxwellian with prescribed n, u, T           */
+#define DVM_BC_ZEROGRAD 1   /* ghost value = interior value                  */
+#define DVM_BC_SYMMETRY 2   /* f(xi) = f(xi - 2 (xi.e) e), coordinate plane  */
+#define DVM_BC_WALL 3       /* diffuse reflection, full accommodation        */
+
+/* storage formats and arithmetic */
+#define DVM_FORMAT_FULL 0
+#define DVM_FORMAT_TUCKER 1
+#define DVM_PREC_FP64 0
+#define DVM_PREC_MIXED 1
+
+typedef struct dvm_ctx dvm_ctx;
+
+typedef struct {
+  int64_t n_vert;             /* number of vertices                          */
+  const double *xyz;          /* [n_vert][3]                                 */
+  int64_t n_cell;             /* number of hexahedra (1 .. 2^31-1)           */
+  const int64_t *hex8;        /* [n_cell][8] vertex ids, VTK order           */
+  int64_t n_bface;            /* number of boundary faces                    */
+  const int64_t *bface;       /* [n_bface][2] = (cell, local face 0..5)      */
+  const int32_t *bface_group; /* [n_bface] group id 0 .. 4095                */
+} dvm_mesh;
+
+typedef struct {
+  int32_t N[3];  /* nodes per axis, 2 .. 128                                 */
+  double lo[3];  /* smallest node per axis                                   */
+  double hi[3];  /* largest node per axis (hi > lo)                          */
+} dvm_vgrid;
+
+typedef struct {
+  double Pr;     /* Prandtl number (Section 2: 2/3)                          */
+  double omega;  /* viscosity exponent, mu ~ T^omega                         */
+  double Kn;     /* Knudsen number (mean-free-path definition)               */
+} dvm_gas;
+
+typedef struct {
+  int32_t format;     /* DVM_FORMAT_FULL or DVM_FORMAT_TUCKER                */
+  int32_t precision;  /* DVM_PREC_FP64 or DVM_PREC_MIXED                     */
+  int32_t rank_cap;   /* Tucker: maximal rank per mode (1 .. min(N, 64))     */
+  double tol;         /* Tucker: relative rounding tolerance eps             */
+  double cfl;         /* CFL number for the fixed time step (default 0.5)    */
+  double dt;          /* if > 0, use this time step instead of the CFL rule  */
+  void *cuda_stream;  /* cudaStream_t for all device work (may be NULL)      */
+} dvm_opts;
+
+/* Create a solver context on the current CUDA device.  Builds the face list
+ * (interior faces by shared vertex sets, boundary faces from mesh->bface),
+ * face area vectors (1/2)(p2-p0)x(p3-p1) and cell volumes, and allocates the
+ * state.  Section 3 (ode_system: |V_i|, |A_j|, e_j, sign(i,l)); Section 6
+ * (Mesh, Solution).  Errors: INVALID_ARG (bad sizes, unmatched faces,
+ * non-positive volumes), OOM, CUDA. */
+int dvm_create(dvm_ctx **out, const dvm_mesh *mesh, const dvm_vgrid *vgrid,
+               const dvm_gas *gas, const dvm_opts *opts);
+
+/* Assign a boundary condition to a group (Section 2; Section 6 Problem).
+ * params[8] = [n, u1, u2, u3, T, 0, 0, 0]: free stream uses all five; a wall
+ * uses u (its velocity, tangential) and T (its temperature), its density n_w
+ * comes from the impermeability condition; zero-gradient and symmetry ignore
+ * params.  Symmetry needs a coordinate-plane face and lo = -hi on that axis
+ * (else UNSUPPORTED at init).  Must precede the init call. */
+int dvm_set_bc(dvm_ctx *ctx, int32_t group, int32_t type, const double params[8]);
+
+/* Initial state from per-cell Maxwellians (Section 6, f_init): host arrays
+ * n[n_cell], u[n_cell][3], T[n_cell].  Computes the moments, the time step
+ * (opts.dt, or dt = CFL / max_i [nu_i + sum_l |A_l| xi_max / (2 |V_i|)]) and,
+ * for the Tucker format, the rank-1 Tucker form (Section 5).  Errors:
+ * INVALID_ARG, STATE (a boundary group without a condition), UNSUPPORTED. */
+int dvm_init_maxwellian(dvm_ctx *ctx, const double *n, const double *u, const double *T);
+
+/* Initial state from full tensors f[n_cell][N1*N2*N3]; on_device != 0 means f
+ * is a device pointer.  Tucker contexts compress each cell by truncated HOSVD
+ * at opts.tol / opts.rank_cap (Section 4, item 1). */
+int dvm_init_f(dvm_ctx *ctx, const double *f, int32_t on_device);
+
+/* Advance nsteps explicit Euler steps (Section 3, Algorithm 1 with
+ * Algorithm 2 inside; Tucker: Section 5 with one rounding per cell and step).
+ * If residual_out is not NULL the call synchronises and stores the residual
+ * of the last step, ||U^{n+1}-U^n||_{2,V} / (dt ||U^n||_{2,V}) with
+ * U = (n, n u, sum w |xi|^2 f) per cell; with NULL the call only enqueues.
+ * Errors: NONPHYSICAL (n <= 0 or T <= 0 seen in a cell), CUDA. */
+int dvm_step(dvm_ctx *ctx, int32_t nsteps, double *residual_out);
+
+/* Macroparameters of every cell (Section 2): host arrays out[n_cell][8] =
+ * [n, u1, u2, u3, T, q1, q2, q3]. */
+int dvm_moments(dvm_ctx *ctx, double *out);
+
+/* Run steps until the residual is <= tol or max_steps were made; the residual
+ * is checked every check_every steps (>= 1).  Returns DVM_NOT_CONVERGED (1)
+ * if max_steps is hit.  steps_out / res_out may be NULL. */
+int dvm_solve(dvm_ctx *ctx, double tol, int64_t max_steps, int32_t check_every,
+              int64_t *steps_out, double *res_out);
+
+/* Full tensors of cells [cell0, cell0 + ncell) into host out[ncell][N^3]
+ * (Tucker cells are expanded). */
+int dvm_get_f(dvm_ctx *ctx, int64_t cell0, int64_t ncell, double *out);
+
+/* Scalars: the fixed time step, the number of steps made, the number of faces. */
+int dvm_get_dt(dvm_ctx *ctx, double *dt);
+int dvm_get_step_count(dvm_ctx *ctx, int64_t *steps);
+int dvm_get_num_faces(dvm_ctx *ctx, int64_t *n_face);
+
+/* Geometry as the solver sees it: vol[n_cell]; per face (owner, neighbour or
+ * -1, group or -1) into fcell[n_face][3] and (|A|, e1, e2, e3) into
+ * fgeo[n_face][4].  Any pointer may be NULL. */
+int dvm_get_geometry(dvm_ctx *ctx, double *vol, int64_t *fcell, double *fgeo);
+
+/* Tucker ranks per cell into r[n_cell][3] (full format: N1, N2, N3). */
+int dvm_get_ranks(dvm_ctx *ctx, int32_t *r);
+
+/* Bytes of device memory held for the distribution function in its current
+ * representation (Tucker: sum over cells of r1 r2 r3 + N1 r1 + N2 r2 + N3 r3
+ * values, Section 7), and the total bytes the context allocated. */
+int dvm_memory(dvm_ctx *ctx, size_t *f_bytes, size_t *total_bytes);
+
+/* Checkpoint / restart of the state (Section 6: init_type 'restart'): the
+ * distribution function (full tensors or cores + factors), the step counter
+ * and the time step.  Restarting gives bitwise the same continuation. */
+int dvm_save(dvm_ctx *ctx, const char *path);
+int dvm_load(dvm_ctx *ctx, const char *path);
+
+void dvm_destroy(dvm_ctx *ctx);
+
+/* Message of the last failed call made by this thread ("" if none). */
+const char *dvm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DVM_GB300_H */

@@ -1,0 +1,573 @@
+// Full-grid FP64 kernels of the S-model DVM step (arXiv:1912.04582, Section 3).
+//
+// One CTA owns one spatial cell.  Thread t owns the velocity "columns"
+// p = (i2, i3) = t, t + B, ... of the cell and walks i1 = 0..N1-1, so that for
+// a fixed i1 a warp reads 32 consecutive doubles of f (i3 fastest): every load
+// and store of f is a coalesced 256-byte transaction.  Per-cell data that
+// depends on i1 only (the first Maxwellian factor, the Shakhov polynomial
+// pieces, the upwind weights of faces normal to axis 1) sits in shared memory;
+// data that depends on (i2, i3) only is kept in registers for the whole i1
+// walk.  This makes the per-node work of the fused step
+//   f^{n+1} = c0(xi) f + dt nu f^S + sum_l m_l(xi) g_l
+// (Algorithm 1 with Algorithm 2 inside, CIR flux written as
+// xi_n^+ f_L + xi_n^- f_R, exact-flux equation) one FP64 FMA per face plus a
+// handful of FMAs for f^S and the update, with no exp per node: f^M is the
+// product of three 1D factors (Section 5, rank-1 Maxwellian).
+//
+// The epilogue accumulates the moment sums of f^{n+1} about the cell's current
+// velocity u^n (so the heat flux of the next step needs no second pass and no
+// large cancellation), plus the wall outflow sums that fix the wall density of
+// the next step (impermeability condition, Section 2).
+#include <cmath>
+
+#include "dvm_internal.h"
+
+namespace dvm {
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+struct CellMacro {
+  double n, u[3], T, q[3];
+  bool bad;
+};
+
+// Macroparameters from raw moment sums taken about the reference velocity r
+// (Section 2 definitions with R_g = 1/2, m = 1):
+//   n = w S0, u = r + M / S0, T = (2/3) (E / S0 - |u - r|^2),
+//   q_a = (w/2) sum (xi_a - u_a) |xi - u|^2 f expanded about r.
+__host__ __device__ inline void macro_from_sums(const double *S, double w, CellMacro &m) {
+  const double S0 = S[3];
+  const double ut0 = S[4] / S0, ut1 = S[5] / S0, ut2 = S[6] / S0;
+  const double S11 = S[7], S22 = S[8], S33 = S[9], S12 = S[10], S13 = S[11], S23 = S[12];
+  const double Et = S11 + S22 + S33;
+  const double uu = ut0 * ut0 + ut1 * ut1 + ut2 * ut2;
+  const double um = ut0 * S[4] + ut1 * S[5] + ut2 * S[6];
+  m.n = w * S0;
+  m.u[0] = S[0] + ut0;
+  m.u[1] = S[1] + ut1;
+  m.u[2] = S[2] + ut2;
+  m.T = (2.0 / 3.0) * (Et / S0 - uu);
+  const double us[3] = {ut0, ut1, ut2};
+  const double Sab[3][3] = {{S11, S12, S13}, {S12, S22, S23}, {S13, S23, S33}};
+  for (int a = 0; a < 3; ++a) {
+    const double su = Sab[a][0] * ut0 + Sab[a][1] * ut1 + Sab[a][2] * ut2;
+    m.q[a] = 0.5 * w *
+             (S[13 + a] - 2.0 * su + uu * S[4 + a] - us[a] * Et + 2.0 * us[a] * um -
+              us[a] * uu * S0);
+  }
+  m.bad = !(m.n > 0.0) || !(m.T > 0.0) || !isfinite(m.n) || !isfinite(m.T);
+}
+
+// conserved moments U = (n, n u, sum w |xi|^2 f) from sums about r
+__device__ inline void conserved_from_sums(const double *S, double w, double U[5]) {
+  const double S0 = S[3];
+  const double r0 = S[0], r1 = S[1], r2 = S[2];
+  const double Et = S[7] + S[8] + S[9];
+  U[0] = w * S0;
+  U[1] = w * (S[4] + r0 * S0);
+  U[2] = w * (S[5] + r1 * S0);
+  U[3] = w * (S[6] + r2 * S0);
+  U[4] = w * (Et + 2.0 * (r0 * S[4] + r1 * S[5] + r2 * S[6]) + (r0 * r0 + r1 * r1 + r2 * r2) * S0);
+}
+
+template <int B>
+__device__ inline void warp_block_reduce(double (&v)[kRawSums], double (*s_red)[kRawSums],
+                                         double *s_tot) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < kRawSums; ++k) {
+    double x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    v[k] = x;
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < kRawSums; ++k) s_red[warp][k] = v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < kRawSums) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < B / 32; ++q) t += s_red[q][threadIdx.x];
+    s_tot[threadIdx.x] = t;
+  }
+  __syncthreads();
+}
+
+// Fold the i1-walk partial sums P_k = sum_{i1} v1^k g (k = 0..3) of one column
+// (i2, i3) into the 13 moment sums about r (v = xi - r).
+__device__ __forceinline__ void fold_column(double (&acc)[kRawSums], double P0, double P1,
+                                            double P2, double P3, double v2, double v3) {
+  const double v22 = v2 * v2, v33 = v3 * v3, s23 = v22 + v33;
+  acc[0] += P0;
+  acc[1] += P1;
+  acc[2] = fma(v2, P0, acc[2]);
+  acc[3] = fma(v3, P0, acc[3]);
+  acc[4] += P2;
+  acc[5] = fma(v22, P0, acc[5]);
+  acc[6] = fma(v33, P0, acc[6]);
+  acc[7] = fma(v2, P1, acc[7]);
+  acc[8] = fma(v3, P1, acc[8]);
+  acc[9] = fma(v2 * v3, P0, acc[9]);
+  acc[10] += fma(s23, P1, P3);
+  acc[11] += fma(v2, P2, v2 * s23 * P0);
+  acc[12] += fma(v3, P2, v3 * s23 * P0);
+}
+
+// ------------------------------------------------------------------------
+// Fused explicit step: f^{n+1} and the moment sums of f^{n+1}.
+template <int B, bool ALL_AXIS>
+__global__ void __launch_bounds__(B) full_step_kernel(const FullParams P) {
+  extern __shared__ double tab[];
+  __shared__ SlotDev s_slot[6];
+  __shared__ double s_par[12];
+  __shared__ double s_scale[6];
+  __shared__ double s_red[B / 32][kRawSums];
+  __shared__ double s_tot[kRawSums];
+
+  const int64_t c = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int N1 = P.N1, N2 = P.N2, N3 = P.N3;
+  const int NP = N2 * N3;
+  const int64_t nn = (int64_t)N1 * NP;
+
+  double *tF1 = tab;           // dt nu n^{1/3} (pi T)^{-1/2} exp(-v1^2/T)
+  double *tA1 = tF1 + N1;      // A q1 v1
+  double *tT1 = tA1 + N1;      // v1^2 / T
+  double *tV1 = tT1 + N1;      // v1
+  double *tV2 = tV1 + N1;      // v1^2
+  double *tV3 = tV2 + N1;      // v1^3
+  double *tC1 = tV3 + N1;      // 1 - dt nu - sum_{axis-1 faces} c max(s xi1, 0)
+  double *tX1 = tC1 + N1;      // xi1
+  double *tM = tX1 + N1;       // [6][N1] upwind weight of axis-1 faces (scaled by n_w)
+  double *tO = tM + 6 * N1;    // [6][N1] wall outflow weight of axis-1 wall faces
+  double *tF2 = tO + 6 * N1;   // n^{1/3} (pi T)^{-1/2} exp(-v2^2/T)
+  double *tF3 = tF2 + N2;
+
+  const double *S = P.sums + c * kSums;
+  if (tid < 6) {
+    s_slot[tid] = P.slot[c * 6 + tid];
+    const SlotDev &sl = s_slot[tid];
+    s_scale[tid] = (sl.kind == kWall) ? -S[16 + tid] / sl.wall_den : 1.0;
+  }
+  if (tid == 0) {
+    CellMacro m;
+    macro_from_sums(S, P.w, m);
+    if (m.bad) atomicOr(P.flag, 1);
+    const double nu = P.delta * m.n * pow(m.T, 1.0 - P.omega);
+    s_par[0] = m.n;
+    s_par[1] = m.u[0];
+    s_par[2] = m.u[1];
+    s_par[3] = m.u[2];
+    s_par[4] = m.T;
+    s_par[5] = m.q[0];
+    s_par[6] = m.q[1];
+    s_par[7] = m.q[2];
+    s_par[8] = nu;
+    s_par[9] = 1.6 * (1.0 - P.Pr) / (m.n * m.T * m.T);  // Shakhov A (R_g = 1/2, m = 1)
+    s_par[10] = cbrt(m.n) / sqrt(kPi * m.T);            // per-axis Maxwellian amplitude
+    s_par[11] = P.dt * nu;
+  }
+  __syncthreads();
+
+  const double T = s_par[4], invT = 1.0 / T, A = s_par[9], amp = s_par[10], dtnu = s_par[11];
+  const double u0 = s_par[1], u1 = s_par[2], u2 = s_par[3];
+  const double q0 = s_par[5], q1 = s_par[6], q2 = s_par[7];
+
+  for (int i = tid; i < N1; i += B) {
+    const double x = P.xi[0][i];
+    const double v = x - u0;
+    tF1[i] = dtnu * amp * exp(-v * v * invT);
+    tA1[i] = A * q0 * v;
+    tT1[i] = v * v * invT;
+    tV1[i] = v;
+    tV2[i] = v * v;
+    tV3[i] = v * v * v;
+    tX1[i] = x;
+    double c0 = 1.0 - dtnu;
+#pragma unroll
+    for (int l = 0; l < 6; ++l) {
+      const SlotDev &sl = s_slot[l];
+      double m = 0.0, o = 0.0;
+      if (sl.axis == 0) {
+        const double sx = sl.sgn * x;
+        c0 -= sl.c * fmax(sx, 0.0);
+        m = sl.c * fmin(sx, 0.0) * s_scale[l];
+        o = fmax(sx, 0.0);
+      }
+      tM[l * N1 + i] = m;
+      tO[l * N1 + i] = o;
+    }
+    tC1[i] = c0;
+  }
+  for (int i = tid; i < N2; i += B) {
+    const double v = P.xi[1][i] - u1;
+    tF2[i] = amp * exp(-v * v * invT);
+  }
+  for (int i = tid; i < N3; i += B) {
+    const double v = P.xi[2][i] - u2;
+    tF3[i] = amp * exp(-v * v * invT);
+  }
+  __syncthreads();
+
+  double acc[kRawSums];
+#pragma unroll
+  for (int k = 0; k < kRawSums; ++k) acc[k] = 0.0;
+
+  const double *__restrict__ fown = P.f + c * nn;
+  double *__restrict__ fout = P.fnew + c * nn;
+
+  for (int p = tid; p < NP; p += B) {
+    const int i2 = p / N3, i3 = p - i2 * N3;
+    const double x2 = P.xi[1][i2], x3 = P.xi[2][i3];
+    const double v2 = x2 - u1, v3 = x3 - u2;
+    const double G = tF2[i2] * tF3[i3];
+    const double bq = A * (q1 * v2 + q2 * v3);
+    const double cp = (v2 * v2 + v3 * v3) * invT - 2.5;
+    double C23 = 0.0;
+    const double *src[6];
+    double pf[6];   // axis-2/3 faces: upwind weight; generic faces: e2 xi2 + e3 xi3
+    double ow[6];   // axis-2/3 wall faces: outflow weight
+    int flip1 = 0;  // bit l: mirror i1 for face l
+#pragma unroll
+    for (int l = 0; l < 6; ++l) {
+      const SlotDev &sl = s_slot[l];
+      pf[l] = 0.0;
+      ow[l] = 0.0;
+      if (sl.axis == 1 || sl.axis == 2) {
+        const double sx = sl.sgn * (sl.axis == 1 ? x2 : x3);
+        C23 -= sl.c * fmax(sx, 0.0);
+        pf[l] = sl.c * fmin(sx, 0.0) * s_scale[l];
+        ow[l] = fmax(sx, 0.0);
+      } else if (!ALL_AXIS && sl.axis < 0) {
+        pf[l] = sl.e[1] * x2 + sl.e[2] * x3;
+      }
+      int pp = p;
+      const double *base;
+      switch (sl.kind) {
+        case kInterior: base = P.f + (int64_t)sl.src * nn; break;
+        case kFreeStream:
+        case kWall: base = P.ghost + (int64_t)sl.src * nn; break;
+        case kSymmetry:
+          base = fown;
+          if (sl.flip == 0) flip1 |= 1 << l;
+          else if (sl.flip == 1) pp = (N2 - 1 - i2) * N3 + i3;
+          else pp = i2 * N3 + (N3 - 1 - i3);
+          break;
+        default: base = fown; break;  // zero gradient
+      }
+      src[l] = base + pp;
+    }
+
+    double P0 = 0.0, P1 = 0.0, P2 = 0.0, P3 = 0.0;
+    double O[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll 2
+    for (int i1 = 0; i1 < N1; ++i1) {
+      const int64_t off = (int64_t)i1 * NP;
+      const int64_t offm = (int64_t)(N1 - 1 - i1) * NP;
+      const double fc = __ldg(fown + off + p);
+      const double fM = tF1[i1] * G;
+      const double poly = fma(tA1[i1] + bq, tT1[i1] + cp, 1.0);
+      double a = fM * poly;
+      double c0 = tC1[i1] + C23;
+#pragma unroll
+      for (int l = 0; l < 6; ++l) {
+        const SlotDev &sl = s_slot[l];
+        const double g = __ldg(src[l] + ((flip1 >> l) & 1 ? offm : off));
+        if (sl.axis == 0) {
+          a = fma(tM[l * N1 + i1], g, a);
+        } else if (ALL_AXIS || sl.axis > 0) {
+          a = fma(pf[l], g, a);
+        } else {
+          const double xu = fma(sl.e[0], tX1[i1], pf[l]);
+          const double x = sl.c * xu;
+          a = fma(fmin(x, 0.0) * s_scale[l], g, a);
+          c0 -= fmax(x, 0.0);
+        }
+      }
+      const double fn = fma(c0, fc, a);
+      fout[off + p] = fn;
+      P0 += fn;
+      P1 = fma(tV1[i1], fn, P1);
+      P2 = fma(tV2[i1], fn, P2);
+      P3 = fma(tV3[i1], fn, P3);
+#pragma unroll
+      for (int l = 0; l < 6; ++l) {
+        const SlotDev &sl = s_slot[l];
+        if (sl.kind == kWall) {
+          if (sl.axis == 0) {
+            O[l] = fma(tO[l * N1 + i1], fn, O[l]);
+          } else if (!ALL_AXIS && sl.axis < 0) {
+            O[l] = fma(fmax(fma(sl.e[0], tX1[i1], pf[l]), 0.0), fn, O[l]);
+          }
+        }
+      }
+    }
+    fold_column(acc, P0, P1, P2, P3, v2, v3);
+#pragma unroll
+    for (int l = 0; l < 6; ++l) acc[13 + l] += O[l] + ow[l] * P0;
+  }
+
+  warp_block_reduce<B>(acc, s_red, s_tot);
+
+  if (tid == 0) {
+    double *Sn = P.sums_new + c * kSums;
+    Sn[0] = u0;
+    Sn[1] = u1;
+    Sn[2] = u2;
+    for (int k = 0; k < kRawSums; ++k) Sn[3 + k] = s_tot[k];
+    Sn[22] = 0.0;
+    Sn[23] = 0.0;
+    if (P.respart) {
+      double U0[5], U1[5];
+      conserved_from_sums(S, P.w, U0);
+      conserved_from_sums(Sn, P.w, U1);
+      double num = 0.0, den = 0.0;
+      for (int k = 0; k < 5; ++k) {
+        num += (U1[k] - U0[k]) * (U1[k] - U0[k]);
+        den += U0[k] * U0[k];
+      }
+      P.respart[2 * c] = P.vol[c] * num;
+      P.respart[2 * c + 1] = P.vol[c] * den;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------
+// Moment sums of f about a reference velocity (no update).
+template <int B>
+__global__ void __launch_bounds__(B) full_moments_kernel(const MomentParams P) {
+  extern __shared__ double tab[];
+  __shared__ SlotDev s_slot[6];
+  __shared__ double s_red[B / 32][kRawSums];
+  __shared__ double s_tot[kRawSums];
+  const int64_t c = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int N1 = P.N1, N2 = P.N2, N3 = P.N3;
+  const int NP = N2 * N3;
+  const int64_t nn = (int64_t)N1 * NP;
+  double *tV1 = tab, *tV2 = tV1 + N1, *tV3 = tV2 + N1, *tX1 = tV3 + N1;
+  const double r0 = P.uref ? P.uref[3 * c] : 0.0;
+  const double r1 = P.uref ? P.uref[3 * c + 1] : 0.0;
+  const double r2 = P.uref ? P.uref[3 * c + 2] : 0.0;
+  if (tid < 6) s_slot[tid] = P.slot[c * 6 + tid];
+  for (int i = tid; i < N1; i += B) {
+    const double x = P.xi[0][i], v = x - r0;
+    tV1[i] = v;
+    tV2[i] = v * v;
+    tV3[i] = v * v * v;
+    tX1[i] = x;
+  }
+  __syncthreads();
+  double acc[kRawSums];
+#pragma unroll
+  for (int k = 0; k < kRawSums; ++k) acc[k] = 0.0;
+  const double *fc = P.f + c * nn;
+  for (int p = tid; p < NP; p += B) {
+    const int i2 = p / N3, i3 = p - i2 * N3;
+    const double x2 = P.xi[1][i2], x3 = P.xi[2][i3];
+    double P0 = 0.0, P1 = 0.0, P2 = 0.0, P3 = 0.0;
+    double O[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int i1 = 0; i1 < N1; ++i1) {
+      const double g = __ldg(fc + (int64_t)i1 * NP + p);
+      P0 += g;
+      P1 = fma(tV1[i1], g, P1);
+      P2 = fma(tV2[i1], g, P2);
+      P3 = fma(tV3[i1], g, P3);
+#pragma unroll
+      for (int l = 0; l < 6; ++l) {
+        const SlotDev &sl = s_slot[l];
+        if (sl.kind == kWall) {
+          const double x = sl.e[0] * tX1[i1] + sl.e[1] * x2 + sl.e[2] * x3;
+          O[l] = fma(fmax(x, 0.0), g, O[l]);
+        }
+      }
+    }
+    fold_column(acc, P0, P1, P2, P3, x2 - r1, x3 - r2);
+#pragma unroll
+    for (int l = 0; l < 6; ++l) acc[13 + l] += O[l];
+  }
+  warp_block_reduce<B>(acc, s_red, s_tot);
+  if (tid == 0) {
+    double *Sn = P.sums + c * kSums;
+    Sn[0] = r0;
+    Sn[1] = r1;
+    Sn[2] = r2;
+    for (int k = 0; k < kRawSums; ++k) Sn[3 + k] = s_tot[k];
+    Sn[22] = 0.0;
+    Sn[23] = 0.0;
+  }
+}
+
+__global__ void macro_kernel(const double *sums, double *macro, int64_t nc, double w) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  CellMacro m;
+  macro_from_sums(sums + c * kSums, w, m);
+  double *o = macro + 8 * c;
+  o[0] = m.n;
+  o[1] = m.u[0];
+  o[2] = m.u[1];
+  o[3] = m.u[2];
+  o[4] = m.T;
+  o[5] = m.q[0];
+  o[6] = m.q[1];
+  o[7] = m.q[2];
+}
+
+__global__ void residual_reduce_kernel(const double *respart, int64_t nc, double dt,
+                                       double *out) {
+  __shared__ double s_a[1024], s_b[1024];
+  double a = 0.0, b = 0.0;
+  for (int64_t c = threadIdx.x; c < nc; c += blockDim.x) {
+    a += respart[2 * c];
+    b += respart[2 * c + 1];
+  }
+  s_a[threadIdx.x] = a;
+  s_b[threadIdx.x] = b;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) {
+      s_a[threadIdx.x] += s_a[threadIdx.x + s];
+      s_b[threadIdx.x] += s_b[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = sqrt(s_a[0]) / (dt * sqrt(s_b[0]));
+}
+
+__global__ void maxwellian_fill_kernel(double *out, const double *xi0, const double *xi1,
+                                       const double *xi2, int N1, int N2, int N3, double n,
+                                       double ux, double uy, double uz, double T) {
+  const int64_t nn = (int64_t)N1 * N2 * N3;
+  const double cst = n / pow(kPi * T, 1.5);
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < nn;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i3 = (int)(idx % N3);
+    const int i2 = (int)((idx / N3) % N2);
+    const int i1 = (int)(idx / ((int64_t)N2 * N3));
+    const double v1 = xi0[i1] - ux, v2 = xi1[i2] - uy, v3 = xi2[i3] - uz;
+    out[idx] = cst * exp(-(v1 * v1 + v2 * v2 + v3 * v3) / T);
+  }
+}
+
+__global__ void cell_maxwellians_kernel(double *f, const double *n, const double *u,
+                                        const double *T, const double *xi0, const double *xi1,
+                                        const double *xi2, int N1, int N2, int N3) {
+  const int64_t c = blockIdx.y;
+  const int64_t nn = (int64_t)N1 * N2 * N3;
+  const double Tc = T[c];
+  const double cst = n[c] / pow(kPi * Tc, 1.5);
+  const double ux = u[3 * c], uy = u[3 * c + 1], uz = u[3 * c + 2];
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < nn;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i3 = (int)(idx % N3);
+    const int i2 = (int)((idx / N3) % N2);
+    const int i1 = (int)(idx / ((int64_t)N2 * N3));
+    const double v1 = xi0[i1] - ux, v2 = xi1[i2] - uy, v3 = xi2[i3] - uz;
+    f[c * nn + idx] = cst * exp(-(v1 * v1 + v2 * v2 + v3 * v3) / Tc);
+  }
+}
+
+__global__ void inflow_sum_kernel(const double *g, const double *xi0, const double *xi1,
+                                  const double *xi2, int N1, int N2, int N3, double e0,
+                                  double e1, double e2, double *out) {
+  __shared__ double s[256];
+  const int64_t nn = (int64_t)N1 * N2 * N3;
+  double a = 0.0;
+  for (int64_t idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+    const int i3 = (int)(idx % N3);
+    const int i2 = (int)((idx / N3) % N2);
+    const int i1 = (int)(idx / ((int64_t)N2 * N3));
+    const double x = e0 * xi0[i1] + e1 * xi1[i2] + e2 * xi2[i3];
+    if (x < 0.0) a = fma(x, g[idx], a);
+  }
+  s[threadIdx.x] = a;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if ((int)threadIdx.x < k) s[threadIdx.x] += s[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = s[0];
+}
+
+size_t step_smem_bytes(int N1, int N2, int N3) {
+  return sizeof(double) * (size_t)(20 * N1 + N2 + N3);
+}
+
+template <int B>
+void launch_step_B(const FullParams &p, bool all_axis, cudaStream_t s) {
+  const size_t smem = step_smem_bytes(p.N1, p.N2, p.N3);
+  if (all_axis)
+    full_step_kernel<B, true><<<(unsigned)p.nc, B, smem, s>>>(p);
+  else
+    full_step_kernel<B, false><<<(unsigned)p.nc, B, smem, s>>>(p);
+}
+
+}  // namespace
+
+// block size: 256 threads, fewer for small velocity grids
+static int pick_block(int NP) {
+  if (NP >= 256) return 256;
+  if (NP > 64) return 128;
+  return 64;
+}
+
+void launch_full_step(const FullParams &p, cudaStream_t s) {
+  const bool all_axis = p.all_axis != 0;
+  switch (pick_block(p.N2 * p.N3)) {
+    case 256: launch_step_B<256>(p, all_axis, s); break;
+    case 128: launch_step_B<128>(p, all_axis, s); break;
+    default: launch_step_B<64>(p, all_axis, s); break;
+  }
+}
+
+void launch_full_moments(const MomentParams &p, cudaStream_t s) {
+  const int NP = p.N2 * p.N3;
+  const size_t smem = sizeof(double) * 4 * (size_t)p.N1;
+  switch (pick_block(NP)) {
+    case 256: full_moments_kernel<256><<<(unsigned)p.nc, 256, smem, s>>>(p); break;
+    case 128: full_moments_kernel<128><<<(unsigned)p.nc, 128, smem, s>>>(p); break;
+    default: full_moments_kernel<64><<<(unsigned)p.nc, 64, smem, s>>>(p); break;
+  }
+}
+
+void launch_macro_from_sums(const double *sums, double *macro, int64_t nc, double w,
+                            cudaStream_t s) {
+  const int B = 128;
+  macro_kernel<<<(unsigned)((nc + B - 1) / B), B, 0, s>>>(sums, macro, nc, w);
+}
+
+void launch_residual_reduce(const double *respart, int64_t nc, double dt, double *out,
+                            cudaStream_t s) {
+  residual_reduce_kernel<<<1, 1024, 0, s>>>(respart, nc, dt, out);
+}
+
+void launch_maxwellian_fill(double *out, const double *xi0, const double *xi1,
+                            const double *xi2, int N1, int N2, int N3, double n,
+                            const double u[3], double T, cudaStream_t s) {
+  const int64_t nn = (int64_t)N1 * N2 * N3;
+  const int B = 256;
+  const unsigned g = (unsigned)((nn + B - 1) / B);
+  maxwellian_fill_kernel<<<g, B, 0, s>>>(out, xi0, xi1, xi2, N1, N2, N3, n, u[0], u[1], u[2],
+                                         T);
+}
+
+void launch_cell_maxwellians(double *f, const double *n, const double *u, const double *T,
+                             const double *xi0, const double *xi1, const double *xi2,
+                             int64_t nc, int N1, int N2, int N3, cudaStream_t s) {
+  const int64_t nn = (int64_t)N1 * N2 * N3;
+  const int B = 256;
+  dim3 grid((unsigned)((nn + B - 1) / B), (unsigned)nc);
+  cell_maxwellians_kernel<<<grid, B, 0, s>>>(f, n, u, T, xi0, xi1, xi2, N1, N2, N3);
+}
+
+void launch_inflow_sum(const double *ghost, const double *xi0, const double *xi1,
+                       const double *xi2, int N1, int N2, int N3, const double e[3],
+                       double *out, cudaStream_t s) {
+  inflow_sum_kernel<<<1, 256, 0, s>>>(ghost, xi0, xi1, xi2, N1, N2, N3, e[0], e[1], e[2], out);
+}
+
+}  // namespace dvm
