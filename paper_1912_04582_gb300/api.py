@@ -9,7 +9,7 @@ import ctypes
 
 import numpy as np
 
-from . import _native as N
+from . import _native as _n
 
 
 def _dp(a):
@@ -44,16 +44,16 @@ def dvm_create(xyz, hex8, bface, bface_group, N, lo, hi, Pr, omega, Kn, format=0
     hex8 = np.ascontiguousarray(hex8, dtype=np.int64)
     bface = np.ascontiguousarray(bface, dtype=np.int64).reshape(-1, 2)
     bgroup = np.ascontiguousarray(bface_group, dtype=np.int32)
-    mesh = N.dvm_mesh(xyz.shape[0], _dp(xyz), hex8.shape[0], _i64p(hex8), bface.shape[0],
+    mesh = _n.dvm_mesh(xyz.shape[0], _dp(xyz), hex8.shape[0], _i64p(hex8), bface.shape[0],
                       _i64p(bface), _i32p(bgroup))
-    vg = N.dvm_vgrid((ctypes.c_int32 * 3)(*[int(v) for v in N_tuple(N)]),
+    vg = _n.dvm_vgrid((ctypes.c_int32 * 3)(*[int(v) for v in N_tuple(N)]),
                      (ctypes.c_double * 3)(*[float(v) for v in lo]),
                      (ctypes.c_double * 3)(*[float(v) for v in hi]))
-    gas = N.dvm_gas(float(Pr), float(omega), float(Kn))
-    opts = N.dvm_opts(int(format), int(precision), int(rank_cap), float(tol), float(cfl),
+    gas = _n.dvm_gas(float(Pr), float(omega), float(Kn))
+    opts = _n.dvm_opts(int(format), int(precision), int(rank_cap), float(tol), float(cfl),
                       float(dt), ctypes.c_void_p(int(stream)))
     out = ctypes.c_void_p()
-    N.check(L.dvm_create(ctypes.byref(out), ctypes.byref(mesh), ctypes.byref(vg),
+    _n.check(L.dvm_create(ctypes.byref(out), ctypes.byref(mesh), ctypes.byref(vg),
                          ctypes.byref(gas), ctypes.byref(opts)), "dvm_create")
     h = Handle(out, (xyz, hex8, bface, bgroup))
     h.n_cell = int(hex8.shape[0])
@@ -66,19 +66,19 @@ def N_tuple(N):
 
 
 def N_lib():
-    return N.load()
+    return _n.load()
 
 
 def dvm_set_bc(h, group, bc_type, params=None):
     p = np.zeros(8) if params is None else np.ascontiguousarray(params, dtype=np.float64)
-    return N.check(N_lib().dvm_set_bc(h.ptr, int(group), int(bc_type), _dp(p)), "dvm_set_bc")
+    return _n.check(N_lib().dvm_set_bc(h.ptr, int(group), int(bc_type), _dp(p)), "dvm_set_bc")
 
 
 def dvm_init_maxwellian(h, n, u, T):
     n = np.ascontiguousarray(n, dtype=np.float64)
     u = np.ascontiguousarray(u, dtype=np.float64)
     T = np.ascontiguousarray(T, dtype=np.float64)
-    return N.check(N_lib().dvm_init_maxwellian(h.ptr, _dp(n), _dp(u), _dp(T)),
+    return _n.check(N_lib().dvm_init_maxwellian(h.ptr, _dp(n), _dp(u), _dp(T)),
                    "dvm_init_maxwellian")
 
 
@@ -86,56 +86,56 @@ def dvm_init_f(h, f=None, device_ptr=None):
     """Initial full tensors from a host array ``f`` or a device pointer (int)."""
     L = N_lib()
     if device_ptr is not None:
-        return N.check(L.dvm_init_f(h.ptr, ctypes.cast(ctypes.c_void_p(int(device_ptr)),
+        return _n.check(L.dvm_init_f(h.ptr, ctypes.cast(ctypes.c_void_p(int(device_ptr)),
                                                        ctypes.POINTER(ctypes.c_double)), 1),
                        "dvm_init_f")
     f = np.ascontiguousarray(f, dtype=np.float64)
-    return N.check(L.dvm_init_f(h.ptr, _dp(f), 0), "dvm_init_f")
+    return _n.check(L.dvm_init_f(h.ptr, _dp(f), 0), "dvm_init_f")
 
 
 def dvm_step(h, nsteps=1, residual=True):
     r = ctypes.c_double(0.0)
-    N.check(N_lib().dvm_step(h.ptr, int(nsteps), ctypes.byref(r) if residual else None),
+    _n.check(N_lib().dvm_step(h.ptr, int(nsteps), ctypes.byref(r) if residual else None),
             "dvm_step")
     return r.value if residual else None
 
 
 def dvm_moments(h):
     out = np.empty((h.n_cell, 8))
-    N.check(N_lib().dvm_moments(h.ptr, _dp(out)), "dvm_moments")
+    _n.check(N_lib().dvm_moments(h.ptr, _dp(out)), "dvm_moments")
     return out
 
 
 def dvm_solve(h, tol, max_steps, check_every=10):
     steps = ctypes.c_int64(0)
     res = ctypes.c_double(0.0)
-    rc = N.check(N_lib().dvm_solve(h.ptr, float(tol), int(max_steps), int(check_every),
+    rc = _n.check(N_lib().dvm_solve(h.ptr, float(tol), int(max_steps), int(check_every),
                                    ctypes.byref(steps), ctypes.byref(res)), "dvm_solve")
-    return rc == N.DVM_OK, int(steps.value), float(res.value)
+    return rc == _n.DVM_OK, int(steps.value), float(res.value)
 
 
 def dvm_get_f(h, cell0=0, ncell=None):
     ncell = h.n_cell - cell0 if ncell is None else ncell
     out = np.empty((ncell,) + tuple(h.N))
-    N.check(N_lib().dvm_get_f(h.ptr, int(cell0), int(ncell), _dp(out)), "dvm_get_f")
+    _n.check(N_lib().dvm_get_f(h.ptr, int(cell0), int(ncell), _dp(out)), "dvm_get_f")
     return out
 
 
 def dvm_get_dt(h):
     v = ctypes.c_double(0.0)
-    N.check(N_lib().dvm_get_dt(h.ptr, ctypes.byref(v)), "dvm_get_dt")
+    _n.check(N_lib().dvm_get_dt(h.ptr, ctypes.byref(v)), "dvm_get_dt")
     return v.value
 
 
 def dvm_get_step_count(h):
     v = ctypes.c_int64(0)
-    N.check(N_lib().dvm_get_step_count(h.ptr, ctypes.byref(v)), "dvm_get_step_count")
+    _n.check(N_lib().dvm_get_step_count(h.ptr, ctypes.byref(v)), "dvm_get_step_count")
     return v.value
 
 
 def dvm_get_num_faces(h):
     v = ctypes.c_int64(0)
-    N.check(N_lib().dvm_get_num_faces(h.ptr, ctypes.byref(v)), "dvm_get_num_faces")
+    _n.check(N_lib().dvm_get_num_faces(h.ptr, ctypes.byref(v)), "dvm_get_num_faces")
     return v.value
 
 
@@ -144,30 +144,30 @@ def dvm_get_geometry(h):
     vol = np.empty(h.n_cell)
     fcell = np.empty((nf, 3), dtype=np.int64)
     fgeo = np.empty((nf, 4))
-    N.check(N_lib().dvm_get_geometry(h.ptr, _dp(vol), _i64p(fcell), _dp(fgeo)),
+    _n.check(N_lib().dvm_get_geometry(h.ptr, _dp(vol), _i64p(fcell), _dp(fgeo)),
             "dvm_get_geometry")
     return vol, fcell, fgeo
 
 
 def dvm_get_ranks(h):
     r = np.empty((h.n_cell, 3), dtype=np.int32)
-    N.check(N_lib().dvm_get_ranks(h.ptr, _i32p(r)), "dvm_get_ranks")
+    _n.check(N_lib().dvm_get_ranks(h.ptr, _i32p(r)), "dvm_get_ranks")
     return r
 
 
 def dvm_memory(h):
     fb = ctypes.c_size_t(0)
     tb = ctypes.c_size_t(0)
-    N.check(N_lib().dvm_memory(h.ptr, ctypes.byref(fb), ctypes.byref(tb)), "dvm_memory")
+    _n.check(N_lib().dvm_memory(h.ptr, ctypes.byref(fb), ctypes.byref(tb)), "dvm_memory")
     return int(fb.value), int(tb.value)
 
 
 def dvm_save(h, path):
-    return N.check(N_lib().dvm_save(h.ptr, str(path).encode()), "dvm_save")
+    return _n.check(N_lib().dvm_save(h.ptr, str(path).encode()), "dvm_save")
 
 
 def dvm_load(h, path):
-    return N.check(N_lib().dvm_load(h.ptr, str(path).encode()), "dvm_load")
+    return _n.check(N_lib().dvm_load(h.ptr, str(path).encode()), "dvm_load")
 
 
 def dvm_destroy(h):
@@ -183,7 +183,7 @@ def dvm_last_error():
 class Solver:
     """One solve on one workload (``workloads.Workload``): create, set BCs, init."""
 
-    def __init__(self, wl, format=N.DVM_FORMAT_FULL, precision=N.DVM_PREC_FP64,
+    def __init__(self, wl, format=_n.DVM_FORMAT_FULL, precision=_n.DVM_PREC_FP64,
                  rank_cap=None, tol=None, dt=0.0, stream=0, init=True):
         self.wl = wl
         self.h = dvm_create(wl.xyz, wl.hex8, wl.bface, wl.bgroup, wl.N, wl.lo, wl.hi, wl.Pr,

@@ -8,7 +8,8 @@
 // pieces, the upwind weights of faces normal to axis 1) sits in shared memory;
 // data that depends on (i2, i3) only is kept in registers for the whole i1
 // walk.  This makes the per-node work of the fused step
-//   f^{n+1} = c0(xi) f + dt nu f^S + sum_l m_l(xi) g_l
+//   f^{n+1} = c0(xi) f + dt nu f^S + sum_l m_l(xi) g_l,
+//   c0 = 1 - dt nu - sum_l c_l xi_n,l^+,   m_l = -c_l xi_n,l^-,   c_l = dt |A_l| / |V|
 // (Algorithm 1 with Algorithm 2 inside, CIR flux written as
 // xi_n^+ f_L + xi_n^- f_R, exact-flux equation) one FP64 FMA per face plus a
 // handful of FMAs for f^S and the update, with no exp per node: f^M is the
@@ -141,7 +142,7 @@ __global__ void __launch_bounds__(B) full_step_kernel(const FullParams P) {
   double *tV3 = tV2 + N1;      // v1^3
   double *tC1 = tV3 + N1;      // 1 - dt nu - sum_{axis-1 faces} c max(s xi1, 0)
   double *tX1 = tC1 + N1;      // xi1
-  double *tM = tX1 + N1;       // [6][N1] upwind weight of axis-1 faces (scaled by n_w)
+  double *tM = tX1 + N1;       // [6][N1] inflow weight -c min(xi_n, 0) of axis-1 faces (x n_w)
   double *tO = tM + 6 * N1;    // [6][N1] wall outflow weight of axis-1 wall faces
   double *tF2 = tO + 6 * N1;   // n^{1/3} (pi T)^{-1/2} exp(-v2^2/T)
   double *tF3 = tF2 + N2;
@@ -194,8 +195,8 @@ __global__ void __launch_bounds__(B) full_step_kernel(const FullParams P) {
       if (sl.axis == 0) {
         const double sx = sl.sgn * x;
         c0 -= sl.c * fmax(sx, 0.0);
-        m = sl.c * fmin(sx, 0.0) * s_scale[l];
-        o = fmax(sx, 0.0);
+        m = -sl.c * fmin(sx, 0.0) * s_scale[l];  // inflow: -c xi_n^- (>= 0)
+        o = sl.kind == kWall ? fmax(sx, 0.0) : 0.0;
       }
       tM[l * N1 + i] = m;
       tO[l * N1 + i] = o;
@@ -239,8 +240,8 @@ __global__ void __launch_bounds__(B) full_step_kernel(const FullParams P) {
       if (sl.axis == 1 || sl.axis == 2) {
         const double sx = sl.sgn * (sl.axis == 1 ? x2 : x3);
         C23 -= sl.c * fmax(sx, 0.0);
-        pf[l] = sl.c * fmin(sx, 0.0) * s_scale[l];
-        ow[l] = fmax(sx, 0.0);
+        pf[l] = -sl.c * fmin(sx, 0.0) * s_scale[l];
+        ow[l] = sl.kind == kWall ? fmax(sx, 0.0) : 0.0;
       } else if (!ALL_AXIS && sl.axis < 0) {
         pf[l] = sl.e[1] * x2 + sl.e[2] * x3;
       }
@@ -283,7 +284,7 @@ __global__ void __launch_bounds__(B) full_step_kernel(const FullParams P) {
         } else {
           const double xu = fma(sl.e[0], tX1[i1], pf[l]);
           const double x = sl.c * xu;
-          a = fma(fmin(x, 0.0) * s_scale[l], g, a);
+          a = fma(-fmin(x, 0.0) * s_scale[l], g, a);
           c0 -= fmax(x, 0.0);
         }
       }
