@@ -133,7 +133,9 @@ int dvm_init_maxwellian(dvm_ctx *ctx, const double *n, const double *u, const do
 
 /* Initial state from full tensors f[n_cell][N1*N2*N3]; on_device != 0 means f
  * is a device pointer.  Tucker contexts compress each cell by truncated HOSVD
- * at opts.tol / opts.rank_cap (Section 4, item 1). */
+ * at opts.tol / opts.rank_cap (Section 4, item 1).  May be called again on an
+ * initialised context to replace the state; the time step of the solve is
+ * then kept. */
 int dvm_init_f(dvm_ctx *ctx, const double *f, int32_t on_device);
 
 /* Advance nsteps explicit Euler steps (Section 3, Algorithm 1 with

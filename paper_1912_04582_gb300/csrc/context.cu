@@ -95,10 +95,6 @@ void ctx_free(dvm_ctx *C) {
 // Validate boundary conditions, build ghost tensors and the per-slot table (the
 // time-step dependent coefficient c is filled in once dt is known).
 int ctx_prepare_boundaries(dvm_ctx *C) {
-  if (C->initialized) {
-    set_error("context already initialised");
-    return DVM_ERR_STATE;
-  }
   if (C->prepared) return DVM_OK;
   const int64_t nc = C->nc;
   C->group_ghost.assign(kMaxGroups, -1);
