@@ -184,6 +184,28 @@ int dvm_memory(dvm_ctx *ctx, size_t *f_bytes, size_t *total_bytes);
 int dvm_save(dvm_ctx *ctx, const char *path);
 int dvm_load(dvm_ctx *ctx, const char *path);
 
+/* Macroparameters [n, u1, u2, u3, T, q1, q2, q3] of n_cell full tensors that
+ * are already in device memory, computed without allocating device memory.
+ * The paper has no counterpart: this entry point is for callers that cannot
+ * allocate at the point of the call, such as an application whose device
+ * memory is handed out by its own pool allocator, or a pipeline that must not
+ * pay the implicit device-wide synchronisation of cudaMalloc between kernels
+ * it has already queued.
+ *   f      device pointer, [n_cell][N1*N2*N3] doubles in the layout above
+ *   macro  device pointer, [n_cell][8] doubles, written on cuda_stream (the
+ *          call only enqueues; synchronise before reading)
+ * The per-cell intermediate sums live in a fixed array inside the library
+ * with room for 16384 cells (1 MiB, held by every GPU that loads the library
+ * until the process exits); a larger n_cell is rejected with
+ * DVM_ERR_INVALID_ARG.  The first call on each device looks up that array's
+ * device address with cudaGetSymbolAddress, so make the first call on a device
+ * before any stream capture.  Every call uses the same array: calls whose GPU
+ * work overlaps (other streams or host threads on the same device) race on it
+ * and must be serialised by the caller.  Results equal those of dvm_moments on
+ * a context initialised with the same tensors, up to summation order. */
+int dvm_full_macro_noalloc(const double *f, int64_t n_cell, const dvm_vgrid *vgrid,
+                           double *macro, void *cuda_stream);
+
 void dvm_destroy(dvm_ctx *ctx);
 
 /* Message of the last failed call made by this thread ("" if none). */

@@ -78,6 +78,9 @@ SIGNATURES = {
                                   ctypes.POINTER(ctypes.c_size_t)]),
     "dvm_save": (ctypes.c_int, [_P, ctypes.c_char_p]),
     "dvm_load": (ctypes.c_int, [_P, ctypes.c_char_p]),
+    "dvm_full_macro_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64,
+                                              ctypes.POINTER(dvm_vgrid), ctypes.c_void_p,
+                                              ctypes.c_void_p]),
     "dvm_destroy": (None, [_P]),
     "dvm_last_error": (ctypes.c_char_p, []),
 }

@@ -170,6 +170,20 @@ def dvm_load(h, path):
     return _n.check(N_lib().dvm_load(h.ptr, str(path).encode()), "dvm_load")
 
 
+def dvm_full_macro_noalloc(f_ptr, n_cell, N, lo, hi, macro_ptr, stream=0):
+    """Macroparameters of n_cell device-resident full tensors (device pointer f_ptr)
+    into the device buffer macro_ptr ([n_cell][8] doubles), enqueued on ``stream``;
+    the library allocates no device memory for it."""
+    vg = _n.dvm_vgrid((ctypes.c_int32 * 3)(*[int(v) for v in N_tuple(N)]),
+                      (ctypes.c_double * 3)(*[float(v) for v in lo]),
+                      (ctypes.c_double * 3)(*[float(v) for v in hi]))
+    return _n.check(N_lib().dvm_full_macro_noalloc(ctypes.c_void_p(int(f_ptr)), int(n_cell),
+                                                   ctypes.byref(vg),
+                                                   ctypes.c_void_p(int(macro_ptr)),
+                                                   ctypes.c_void_p(int(stream))),
+                    "dvm_full_macro_noalloc")
+
+
 def dvm_destroy(h):
     if h.ptr:
         N_lib().dvm_destroy(h.ptr)
