@@ -301,17 +301,8 @@ int ctx_init_from_maxwellians(dvm_ctx *C, const double *n, const double *u, cons
                             C->d_xi[2], nc, C->N[0], C->N[1], C->N[2], C->stream);
     rc = sync_and_check(C);
   } else {
-    // expand the Maxwellians in a temporary full buffer, then compress
-    double *d_full = nullptr;
-    rc = ctx_malloc(C, reinterpret_cast<void **>(&d_full), sizeof(double) * (size_t)nc * C->nn);
-    if (rc == DVM_OK) {
-      launch_cell_maxwellians(d_full, d_in, d_in + nc, d_in + 4 * nc, C->d_xi[0], C->d_xi[1],
-                              C->d_xi[2], nc, C->N[0], C->N[1], C->N[2], C->stream);
-      rc = sync_and_check(C);
-      if (rc == DVM_OK) rc = tucker_init_from_full(C, d_full);
-      cudaFree(d_full);
-      C->bytes -= sizeof(double) * (size_t)nc * C->nn;
-    }
+    // a Maxwellian is exactly rank 1 in Tucker format (Section 5)
+    rc = tucker_init_maxwellians(C, d_in, d_in + nc, d_in + 4 * nc);
   }
   cudaFree(d_in);
   C->bytes -= sizeof(double) * 5 * nc;

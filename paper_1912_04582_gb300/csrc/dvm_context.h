@@ -74,6 +74,7 @@ int ctx_memory(dvm_ctx *C, size_t *f_bytes, size_t *total_bytes);
 int ctx_save(dvm_ctx *C, const char *path);
 int ctx_load(dvm_ctx *C, const char *path);
 int ctx_malloc(dvm_ctx *C, void **p, size_t bytes);
+int ctx_finalize_dt_from_macro(dvm_ctx *C, const std::vector<double> &macro);
 
 namespace dvm {
 int build_topology(dvm_ctx *C, const dvm_mesh *m);
@@ -83,6 +84,7 @@ int build_topology(dvm_ctx *C, const dvm_mesh *m);
 int tucker_alloc(dvm_ctx *C);
 void tucker_free(dvm_ctx *C);
 int tucker_init_from_full(dvm_ctx *C, const double *d_f_full);
+int tucker_init_maxwellians(dvm_ctx *C, const double *d_n, const double *d_u, const double *d_T);
 int tucker_step(dvm_ctx *C, int32_t nsteps, double *residual_out);
 int tucker_moments(dvm_ctx *C, double *d_macro);
 int tucker_get_f(dvm_ctx *C, int64_t cell0, int64_t ncell, double *d_out);

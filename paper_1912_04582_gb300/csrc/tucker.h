@@ -1,0 +1,63 @@
+// Tucker-format device structures and launchers (internal).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include "dvm_internal.h"
+
+namespace dvm {
+
+// One set of Tucker tensors, one per cell, FP64, capacity R per mode.
+struct TuckerDev {
+  double *core;   // [nc][R*R*R], compact r1 x r2 x r3 (k3 fastest)
+  double *fac[3]; // [nc][N_a*R], row i at offset i*R, first r_a columns used
+  int *rank;      // [nc][3]
+};
+
+struct TuckerStepParams {
+  TuckerDev cur;         // state at t^n (read)
+  TuckerDev nxt;         // state at t^{n+1} (written)
+  const double *sums;    // [nc][kSums] moment sums of cur
+  const SlotDev *slot;   // [nc][6]
+  const double *ghostf;  // [nghost][3][Nmax] rank-1 ghost Maxwellian factors
+  const double *xi[3];
+  const double *finit;   // mode 1: [nc][N^3] tensors to compress
+  double *err;           // [nc] relative truncation error of the last rounding (may be null)
+  int *flag;
+  void *scratch;         // per-CTA work space
+  size_t scratch_stride; // elements (of the kernel's scalar type) per CTA
+  int64_t nc;
+  int N1, N2, N3, R, Nmax;
+  int mode;              // 0 = time step, 1 = compress finit
+  double w, dt, Pr, omega, delta, tol;
+};
+
+struct TuckerMomentParams {
+  TuckerDev T;
+  const double *uref;    // reference velocity, uref[c*uref_stride + k] (may be null)
+  int uref_stride;
+  const SlotDev *slot;
+  const double *xi[3];
+  double *sums;          // [nc][kSums] out
+  const double *sums_prev;  // [nc][kSums] of the previous state (residual) or null
+  double *respart;       // [nc][2] or null
+  const double *vol;
+  int *flag;
+  int64_t nc;
+  int N1, N2, N3, R;
+  double w;
+};
+
+size_t tucker_scratch_elems(int N1, int N2, int N3, int R);
+size_t tucker_smem_bytes(int Nmax, int R, bool fp64);
+int launch_tucker_step(const TuckerStepParams &p, int grid, bool fp64, cudaStream_t s);
+int launch_tucker_expand(const TuckerDev &T, int64_t c0, int64_t ncell, int N1, int N2, int N3,
+                         int R, int Nmax, void *scratch, size_t stride, double *out, int grid,
+                         bool fp64, cudaStream_t s);
+void launch_tucker_moments(const TuckerMomentParams &p, cudaStream_t s);
+void launch_tucker_maxwellians(TuckerDev T, const double *n, const double *u, const double *Tc,
+                               const double *xi0, const double *xi1, const double *xi2, int64_t nc,
+                               int N1, int N2, int N3, int R, cudaStream_t s);
+
+}  // namespace dvm

@@ -1,21 +1,360 @@
-// Tucker-format driver (placeholder until the Tucker kernels land).
+// Tucker-format driver: state allocation, initialisation (rank-1 Maxwellians or
+// HOSVD of full tensors), time stepping, moments, inspection and checkpoints.
+// Kernels: tucker_kernels.cu.
+#include <algorithm>
+#include <cmath>
 #include <cstdio>
+#include <string>
+#include <vector>
 
 #include "dvm_context.h"
+#include "tucker.h"
 
 using namespace dvm;
 
-static int unsupported() {
-  set_error("Tucker format not available in this build");
-  return DVM_ERR_UNSUPPORTED;
+struct TuckerState {
+  TuckerDev buf[2]{};
+  int cur = 0;
+  int scur = 0;        // index of the moment-sum buffer of the current state
+  int R = 0;
+  int Nmax = 0;
+  bool fp64 = true;
+  void *scratch = nullptr;
+  size_t stride = 0;   // scratch elements per CTA
+  int grid = 0;
+  double *ghostf = nullptr;  // [nghost][3][Nmax]
+  double *err = nullptr;     // [nc]
+};
+
+int ctx_finalize_dt_from_macro(dvm_ctx *C, const std::vector<double> &macro);
+
+namespace {
+
+int sync_check(dvm_ctx *C) {
+  DVM_CUDA_TRY(cudaGetLastError());
+  DVM_CUDA_TRY(cudaStreamSynchronize(C->stream));
+  return DVM_OK;
 }
-int tucker_alloc(dvm_ctx *) { return unsupported(); }
-void tucker_free(dvm_ctx *) {}
-int tucker_init_from_full(dvm_ctx *, const double *) { return unsupported(); }
-int tucker_step(dvm_ctx *, int32_t, double *) { return unsupported(); }
-int tucker_moments(dvm_ctx *, double *) { return unsupported(); }
-int tucker_get_f(dvm_ctx *, int64_t, int64_t, double *) { return unsupported(); }
-int tucker_get_ranks(dvm_ctx *, int32_t *) { return unsupported(); }
-int tucker_memory(dvm_ctx *, size_t *) { return unsupported(); }
-int tucker_save(dvm_ctx *, FILE *) { return unsupported(); }
-int tucker_load(dvm_ctx *, FILE *) { return unsupported(); }
+
+TuckerStepParams step_params(dvm_ctx *C) {
+  TuckerState *S = C->tucker;
+  TuckerStepParams p{};
+  p.slot = C->d_slot;
+  p.ghostf = S->ghostf;
+  for (int a = 0; a < 3; ++a) p.xi[a] = C->d_xi[a];
+  p.err = S->err;
+  p.flag = C->d_flag;
+  p.scratch = S->scratch;
+  p.scratch_stride = S->stride;
+  p.nc = C->nc;
+  p.N1 = C->N[0];
+  p.N2 = C->N[1];
+  p.N3 = C->N[2];
+  p.R = S->R;
+  p.Nmax = S->Nmax;
+  p.w = C->w;
+  p.dt = C->dt;
+  p.Pr = C->gas.Pr;
+  p.omega = C->gas.omega;
+  p.delta = std::sqrt(3.14159265358979323846) / (2.0 * C->gas.Kn);
+  p.tol = C->opts.tol;
+  return p;
+}
+
+TuckerMomentParams moment_params(dvm_ctx *C, const TuckerDev &T, double *sums) {
+  TuckerMomentParams m{};
+  m.T = T;
+  m.slot = C->d_slot;
+  for (int a = 0; a < 3; ++a) m.xi[a] = C->d_xi[a];
+  m.sums = sums;
+  m.vol = C->d_vol;
+  m.flag = C->d_flag;
+  m.nc = C->nc;
+  m.N1 = C->N[0];
+  m.N2 = C->N[1];
+  m.N3 = C->N[2];
+  m.R = C->tucker->R;
+  m.w = C->w;
+  return m;
+}
+
+// moments of the current state about its own velocity: pass 1 about 0, pass 2
+// about the pass-1 velocity; macro to host
+int two_pass_moments(dvm_ctx *C, std::vector<double> &macro) {
+  TuckerState *S = C->tucker;
+  const int64_t nc = C->nc;
+  TuckerMomentParams m = moment_params(C, S->buf[S->cur], C->d_sums[S->scur]);
+  launch_tucker_moments(m, C->stream);
+  launch_macro_from_sums(C->d_sums[S->scur], C->d_macro, nc, C->w, C->stream);
+  m.uref = C->d_macro + 1;
+  m.uref_stride = 8;
+  m.sums = C->d_sums[1 - S->scur];
+  launch_tucker_moments(m, C->stream);
+  S->scur = 1 - S->scur;
+  launch_macro_from_sums(C->d_sums[S->scur], C->d_macro, nc, C->w, C->stream);
+  macro.resize(8 * nc);
+  DVM_CUDA_TRY(cudaMemcpyAsync(macro.data(), C->d_macro, sizeof(double) * 8 * nc,
+                               cudaMemcpyDeviceToHost, C->stream));
+  return sync_check(C);
+}
+
+int build_ghost_factors(dvm_ctx *C) {
+  TuckerState *S = C->tucker;
+  if (S->ghostf) {
+    cudaFree(S->ghostf);
+    S->ghostf = nullptr;
+  }
+  const int ng = std::max(C->nghost, 1);
+  std::vector<double> h((size_t)ng * 3 * S->Nmax, 0.0);
+  const double pi = 3.14159265358979323846;
+  for (int g = 0; g < kMaxGroups; ++g) {
+    const int k = C->group_ghost.empty() ? -1 : C->group_ghost[g];
+    if (k < 0) continue;
+    const auto &p = C->bc_par[g];
+    const double n = C->bc_type[g] == DVM_BC_WALL ? 1.0 : p[0];
+    const double T = p[4];
+    const double amp = std::cbrt(n) / std::sqrt(pi * T);
+    for (int a = 0; a < 3; ++a)
+      for (int i = 0; i < C->N[a]; ++i) {
+        const double v = C->xi[a][i] - p[1 + a];
+        h[((size_t)k * 3 + a) * S->Nmax + i] = amp * std::exp(-v * v / T);
+      }
+  }
+  int rc = ctx_malloc(C, reinterpret_cast<void **>(&S->ghostf), sizeof(double) * h.size());
+  if (rc != DVM_OK) return rc;
+  DVM_CUDA_TRY(cudaMemcpyAsync(S->ghostf, h.data(), sizeof(double) * h.size(),
+                               cudaMemcpyHostToDevice, C->stream));
+  return sync_check(C);
+}
+
+int check_tucker_faces(dvm_ctx *C) {
+  for (int64_t s = 0; s < 6 * C->nc; ++s)
+    if (C->slot[s].kind == kWall && C->slot[s].axis < 0) {
+      set_error("Tucker format: diffuse walls must lie on coordinate planes");
+      return DVM_ERR_UNSUPPORTED;
+    }
+  return DVM_OK;
+}
+
+int finish_init(dvm_ctx *C) {
+  int rc = check_tucker_faces(C);
+  if (rc != DVM_OK) return rc;
+  rc = build_ghost_factors(C);
+  if (rc != DVM_OK) return rc;
+  std::vector<double> macro;
+  rc = two_pass_moments(C, macro);
+  if (rc != DVM_OK) return rc;
+  if (!C->initialized) {
+    rc = ctx_finalize_dt_from_macro(C, macro);
+    if (rc != DVM_OK) return rc;
+    C->steps = 0;
+  }
+  for (int64_t c = 0; c < C->nc; ++c)
+    if (!(macro[8 * c] > 0.0) || !(macro[8 * c + 4] > 0.0)) {
+      set_error("non-physical initial state (n or T <= 0)");
+      return DVM_ERR_NONPHYSICAL;
+    }
+  return DVM_OK;
+}
+
+}  // namespace
+
+int tucker_alloc(dvm_ctx *C) {
+  TuckerState *S = new TuckerState();
+  C->tucker = S;
+  S->R = C->opts.rank_cap;
+  S->Nmax = std::max(C->N[0], std::max(C->N[1], C->N[2]));
+  S->fp64 = C->opts.precision == DVM_PREC_FP64;
+  if (S->Nmax > 64) {
+    set_error("Tucker format supports at most 64 velocity nodes per axis");
+    return DVM_ERR_UNSUPPORTED;
+  }
+  const int64_t nc = C->nc;
+  const int R = S->R;
+  for (int b = 0; b < 2; ++b) {
+    TuckerDev &T = S->buf[b];
+    int rc = ctx_malloc(C, reinterpret_cast<void **>(&T.core), sizeof(double) * nc * R * R * R);
+    if (rc != DVM_OK) return rc;
+    for (int a = 0; a < 3; ++a) {
+      rc = ctx_malloc(C, reinterpret_cast<void **>(&T.fac[a]),
+                      sizeof(double) * nc * (int64_t)C->N[a] * R);
+      if (rc != DVM_OK) return rc;
+      DVM_CUDA_TRY(cudaMemset(T.fac[a], 0, sizeof(double) * nc * (int64_t)C->N[a] * R));
+    }
+    rc = ctx_malloc(C, reinterpret_cast<void **>(&T.rank), sizeof(int) * 3 * nc);
+    if (rc != DVM_OK) return rc;
+    DVM_CUDA_TRY(cudaMemset(T.core, 0, sizeof(double) * nc * R * R * R));
+    DVM_CUDA_TRY(cudaMemset(T.rank, 0, sizeof(int) * 3 * nc));
+  }
+  int sms = 1;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, C->device);
+  const size_t smem = tucker_smem_bytes(S->Nmax, R, S->fp64);
+  int per_sm = (int)std::max<size_t>(1, std::min<size_t>(2, (200 * 1024) / (smem + 1024)));
+  S->grid = (int)std::min<int64_t>(nc, (int64_t)sms * per_sm);
+  S->stride = tucker_scratch_elems(C->N[0], C->N[1], C->N[2], R);
+  S->stride = (S->stride + 63) & ~size_t(63);
+  const size_t es = S->fp64 ? sizeof(double) : sizeof(float);
+  int rc = ctx_malloc(C, &S->scratch, es * S->stride * S->grid);
+  if (rc != DVM_OK) return rc;
+  rc = ctx_malloc(C, reinterpret_cast<void **>(&S->err), sizeof(double) * nc);
+  if (rc != DVM_OK) return rc;
+  DVM_CUDA_TRY(cudaMemset(S->err, 0, sizeof(double) * nc));
+  return DVM_OK;
+}
+
+void tucker_free(dvm_ctx *C) {
+  TuckerState *S = C->tucker;
+  if (!S) return;
+  for (int b = 0; b < 2; ++b) {
+    if (S->buf[b].core) cudaFree(S->buf[b].core);
+    for (int a = 0; a < 3; ++a)
+      if (S->buf[b].fac[a]) cudaFree(S->buf[b].fac[a]);
+    if (S->buf[b].rank) cudaFree(S->buf[b].rank);
+  }
+  if (S->scratch) cudaFree(S->scratch);
+  if (S->ghostf) cudaFree(S->ghostf);
+  if (S->err) cudaFree(S->err);
+  delete S;
+  C->tucker = nullptr;
+}
+
+int tucker_init_maxwellians(dvm_ctx *C, const double *d_n, const double *d_u, const double *d_T) {
+  TuckerState *S = C->tucker;
+  launch_tucker_maxwellians(S->buf[S->cur], d_n, d_u, d_T, C->d_xi[0], C->d_xi[1], C->d_xi[2],
+                            C->nc, C->N[0], C->N[1], C->N[2], S->R, C->stream);
+  int rc = sync_check(C);
+  if (rc != DVM_OK) return rc;
+  return finish_init(C);
+}
+
+int tucker_init_from_full(dvm_ctx *C, const double *d_f_full) {
+  TuckerState *S = C->tucker;
+  TuckerStepParams p = step_params(C);
+  p.mode = 1;
+  p.finit = d_f_full;
+  p.nxt = S->buf[S->cur];
+  if (launch_tucker_step(p, S->grid, S->fp64, C->stream) != 0) {
+    set_error("Tucker kernel needs more shared memory than the device allows");
+    return DVM_ERR_UNSUPPORTED;
+  }
+  int rc = sync_check(C);
+  if (rc != DVM_OK) return rc;
+  return finish_init(C);
+}
+
+int tucker_step(dvm_ctx *C, int32_t nsteps, double *residual_out) {
+  (void)residual_out;
+  TuckerState *S = C->tucker;
+  TuckerStepParams p = step_params(C);
+  for (int32_t s = 0; s < nsteps; ++s) {
+    p.mode = 0;
+    p.cur = S->buf[S->cur];
+    p.nxt = S->buf[1 - S->cur];
+    p.sums = C->d_sums[S->scur];
+    if (launch_tucker_step(p, S->grid, S->fp64, C->stream) != 0) {
+      set_error("Tucker kernel needs more shared memory than the device allows");
+      return DVM_ERR_UNSUPPORTED;
+    }
+    S->cur = 1 - S->cur;
+    // moments of the new state about the previous velocity (+ residual parts)
+    launch_macro_from_sums(C->d_sums[S->scur], C->d_macro, C->nc, C->w, C->stream);
+    TuckerMomentParams m = moment_params(C, S->buf[S->cur], C->d_sums[1 - S->scur]);
+    m.uref = C->d_macro + 1;
+    m.uref_stride = 8;
+    m.sums_prev = C->d_sums[S->scur];
+    m.respart = C->d_respart;
+    launch_tucker_moments(m, C->stream);
+    S->scur = 1 - S->scur;
+    C->steps++;
+  }
+  DVM_CUDA_TRY(cudaGetLastError());
+  return DVM_OK;
+}
+
+int tucker_moments(dvm_ctx *C, double *d_macro) {
+  launch_macro_from_sums(C->d_sums[C->tucker->scur], d_macro, C->nc, C->w, C->stream);
+  DVM_CUDA_TRY(cudaGetLastError());
+  return DVM_OK;
+}
+
+int tucker_get_f(dvm_ctx *C, int64_t cell0, int64_t ncell, double *d_out) {
+  TuckerState *S = C->tucker;
+  const int grid = (int)std::min<int64_t>(ncell, S->grid);
+  if (launch_tucker_expand(S->buf[S->cur], cell0, ncell, C->N[0], C->N[1], C->N[2], S->R, S->Nmax,
+                           S->scratch, S->stride, d_out, grid, S->fp64, C->stream) != 0) {
+    set_error("Tucker kernel needs more shared memory than the device allows");
+    return DVM_ERR_UNSUPPORTED;
+  }
+  DVM_CUDA_TRY(cudaGetLastError());
+  return DVM_OK;
+}
+
+int tucker_get_ranks(dvm_ctx *C, int32_t *r) {
+  TuckerState *S = C->tucker;
+  DVM_CUDA_TRY(cudaMemcpyAsync(r, S->buf[S->cur].rank, sizeof(int) * 3 * C->nc,
+                               cudaMemcpyDeviceToHost, C->stream));
+  return sync_check(C);
+}
+
+int tucker_memory(dvm_ctx *C, size_t *f_bytes) {
+  std::vector<int32_t> r(3 * C->nc);
+  int rc = tucker_get_ranks(C, r.data());
+  if (rc != DVM_OK) return rc;
+  size_t vals = 0;
+  for (int64_t c = 0; c < C->nc; ++c)
+    vals += (size_t)r[3 * c] * r[3 * c + 1] * r[3 * c + 2] + (size_t)C->N[0] * r[3 * c] +
+            (size_t)C->N[1] * r[3 * c + 1] + (size_t)C->N[2] * r[3 * c + 2];
+  *f_bytes = vals * sizeof(double);
+  return DVM_OK;
+}
+
+namespace {
+template <typename T>
+bool io_dev(FILE *fp, T *d, size_t n, bool write) {
+  std::vector<T> h(n);
+  if (write) {
+    if (cudaMemcpy(h.data(), d, sizeof(T) * n, cudaMemcpyDeviceToHost) != cudaSuccess) return false;
+    return std::fwrite(h.data(), sizeof(T), n, fp) == n;
+  }
+  if (std::fread(h.data(), sizeof(T), n, fp) != n) return false;
+  return cudaMemcpy(d, h.data(), sizeof(T) * n, cudaMemcpyHostToDevice) == cudaSuccess;
+}
+
+bool io_state(dvm_ctx *C, FILE *fp, bool write) {
+  TuckerState *S = C->tucker;
+  const int64_t nc = C->nc;
+  const int R = S->R;
+  TuckerDev &T = S->buf[S->cur];
+  if (!io_dev(fp, T.rank, 3 * nc, write)) return false;
+  if (!io_dev(fp, T.core, (size_t)nc * R * R * R, write)) return false;
+  for (int a = 0; a < 3; ++a)
+    if (!io_dev(fp, T.fac[a], (size_t)nc * C->N[a] * R, write)) return false;
+  return io_dev(fp, C->d_sums[S->scur], (size_t)nc * kSums, write);
+}
+}  // namespace
+
+int tucker_save(dvm_ctx *C, FILE *fp) {
+  int32_t R = C->tucker->R;
+  if (std::fwrite(&R, sizeof R, 1, fp) != 1 || !io_state(C, fp, true)) {
+    set_error("checkpoint write failed");
+    return DVM_ERR_IO;
+  }
+  return DVM_OK;
+}
+
+int tucker_load(dvm_ctx *C, FILE *fp) {
+  int32_t R = 0;
+  if (std::fread(&R, sizeof R, 1, fp) != 1 || R != C->tucker->R) {
+    set_error("checkpoint rank capacity does not match this context");
+    return DVM_ERR_IO;
+  }
+  int rc = check_tucker_faces(C);
+  if (rc != DVM_OK) return rc;
+  rc = build_ghost_factors(C);
+  if (rc != DVM_OK) return rc;
+  if (!io_state(C, fp, false)) {
+    set_error("checkpoint read failed");
+    return DVM_ERR_IO;
+  }
+  return DVM_OK;
+}

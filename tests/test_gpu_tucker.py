@@ -1,0 +1,170 @@
+"""Tucker-format CUDA path through the C ABI vs the FP64 full-grid oracle and the numpy
+Tucker reference.
+
+* Compression of given tensors (Section 4 item 1): the rounding error bound
+  ||A - B|| <= eps ||A|| per cell, exact recovery of low-rank tensors.
+* A Maxwellian initial state is rank 1 (Section 5).
+* Time steps (Section 5): with a tight tolerance and a rank cap equal to N the Tucker
+  step reproduces the full-grid oracle to round-off of the rounding; at the working
+  tolerance the difference is O(eps) per step.
+Tucker factors are unique only up to rotations, so expanded tensors and
+macroparameters are compared, never raw factors.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import tucker as tk
+
+pytestmark = pytest.mark.gpu
+
+FP64 = 0
+MIXED = 1
+
+
+@pytest.fixture(scope="module")
+def dvm():
+    import paper_1912_04582_gb300 as P
+    from paper_1912_04582_gb300 import _native
+    _native.load()
+    return P
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+def macro_err(mg, mo):
+    err = {"n": rel_l2(mg[:, 0], mo[:, 0]), "T": rel_l2(mg[:, 4], mo[:, 4])}
+    un = max(np.linalg.norm(mo[:, 1:4]), 1e-3 * np.sqrt(mo.shape[0]))
+    err["u"] = float(np.linalg.norm(mg[:, 1:4] - mo[:, 1:4]) / un)
+    qn = max(np.linalg.norm(mo[:, 5:8]), 1e-6 * np.sqrt(mo.shape[0]))
+    err["q"] = float(np.linalg.norm(mg[:, 5:8] - mo[:, 5:8]) / qn)
+    return err
+
+
+def tucker_solver(dvm, wl, cap, tol, precision=FP64, init=True):
+    return dvm.Solver(wl, format=1, precision=precision, rank_cap=cap, tol=tol, init=init)
+
+
+def test_maxwellian_initial_state_is_rank_one(dvm, oracle_lib):
+    wl = W.cavity(nside=3, N=12, seed=1)
+    rng = np.random.default_rng(5)
+    wl.n0 = rng.uniform(0.5, 1.5, wl.n_cell)
+    wl.u0 = rng.uniform(-0.3, 0.3, (wl.n_cell, 3))
+    wl.T0 = rng.uniform(0.7, 1.4, wl.n_cell)
+    s = tucker_solver(dvm, wl, 6, 1e-6)
+    assert np.all(dvm.dvm_get_ranks(s.h) == 1)
+    o = oracle_lib.FullGridOracle(wl)
+    assert rel_l2(s.f(), o.f()) < 1e-14
+    for k, v in macro_err(s.moments(), o.macro()).items():
+        assert v < 1e-12, (k, v)
+    fb, _ = dvm.dvm_memory(s.h)
+    assert fb == wl.n_cell * (1 + 3 * 12) * 8
+
+
+@pytest.mark.parametrize("precision,tol_rel", [(FP64, 1e-13), (MIXED, 2e-6)])
+def test_compression_recovers_low_rank_tensors(dvm, oracle_lib, precision, tol_rel):
+    """Sum of two Maxwellians per cell: Tucker ranks exactly 2."""
+    wl = W.specular_box(shape=(2, 2, 1), N=16, vmax=5.0)
+    o = oracle_lib.FullGridOracle(wl)
+    rng = np.random.default_rng(3)
+    f = np.stack([o.maxwellian(rng.uniform(0.5, 1), rng.uniform(-1, 1, 3), rng.uniform(0.6, 1.2))
+                  + o.maxwellian(rng.uniform(0.2, 0.5), rng.uniform(-1, 1, 3), rng.uniform(0.6, 1.2))
+                  for _ in range(wl.n_cell)])
+    s = tucker_solver(dvm, wl, 8, 1e-9, precision=precision, init=False)
+    dvm.dvm_init_f(s.h, f)
+    r = dvm.dvm_get_ranks(s.h)
+    assert np.all(r == 2), r
+    assert rel_l2(s.f(), f) < tol_rel
+
+
+@pytest.mark.parametrize("eps", [1e-2, 1e-4, 1e-6])
+def test_rounding_respects_error_bound(dvm, oracle_lib, eps):
+    """Random decaying-spectrum tensors: ||A - round(A)|| <= eps ||A|| per cell (cap
+    inactive), and ranks no larger than the reference HOSVD's (Section 4 items 1, 4)."""
+    N = 14
+    wl = W.specular_box(shape=(3, 1, 1), N=N, vmax=5.0)
+    rng = np.random.default_rng(9)
+    f = []
+    for _ in range(wl.n_cell):
+        G = rng.standard_normal((N, N, N)) * np.exp(-0.7 * np.add.outer(np.add.outer(
+            np.arange(N), np.arange(N)), np.arange(N)))
+        Q = [np.linalg.qr(rng.standard_normal((N, N)))[0] for _ in range(3)]
+        f.append(np.abs(tk.full((G, tuple(Q)))) + 0.0)
+    f = np.stack(f)
+    s = tucker_solver(dvm, wl, N, eps, init=False)
+    dvm.dvm_init_f(s.h, f)
+    g = s.f()
+    ranks = dvm.dvm_get_ranks(s.h)
+    for c in range(wl.n_cell):
+        assert np.linalg.norm(g[c] - f[c]) <= eps * np.linalg.norm(f[c]) * (1 + 1e-8)
+        ref, _ = tk.hosvd(f[c], eps)
+        assert np.all(ranks[c] <= np.array(tk.ranks(ref)) + 1)
+
+
+def test_step_matches_oracle_with_tight_tolerance(dvm, oracle_lib):
+    """Cap = N and eps = 1e-12: the Tucker step is the full-grid step plus rounding at
+    1e-12, so 20 steps agree with the FP64 oracle to ~1e-10."""
+    wl = W.sod_row(N=12, seed=2)
+    s = tucker_solver(dvm, wl, 12, 1e-12)
+    o = oracle_lib.FullGridOracle(wl)
+    assert abs(s.dt - o.dt()) <= 1e-14 * o.dt()
+    s.step(20)
+    o.step(20, o.dt())
+    assert rel_l2(s.f(), o.f()) < 1e-9
+    for k, v in macro_err(s.moments(), o.macro()).items():
+        assert v < 1e-9, (k, v)
+
+
+@pytest.mark.parametrize("precision,bound", [(FP64, 1e-4), (MIXED, 1e-4)])
+def test_cavity_walls_lid_working_tolerance(dvm, oracle_lib, precision, bound):
+    """Small cavity (diffuse walls, moving lid), eps = 1e-5, cap 8, 40 steps."""
+    wl = W.cavity(nside=4, N=16, seed=4)
+    s = tucker_solver(dvm, wl, 8, 1e-5, precision=precision)
+    o = oracle_lib.FullGridOracle(wl)
+    s.step(40)
+    o.step(40, o.dt())
+    e = rel_l2(s.f(), o.f())
+    me = macro_err(s.moments(), o.macro())
+    assert e < bound, e
+    for k, v in me.items():
+        assert v < bound, (k, v)
+
+
+def test_non_axis_faces_use_exact_flux(dvm, oracle_lib):
+    """Jittered interior faces: the Tucker assembly applies the exact upwind weight, so with
+    a tight tolerance it agrees with the full-grid oracle."""
+    wl = W.closed_freestream_box(shape=(3, 2, 2), N=10, jitter=0.25, Kn=0.3,
+                                 u=(0.4, -0.3, 0.2))
+    rng = np.random.default_rng(1)
+    wl.n0 = rng.uniform(0.6, 1.4, wl.n_cell)
+    wl.T0 = rng.uniform(0.8, 1.3, wl.n_cell)
+    s = tucker_solver(dvm, wl, 10, 1e-12)
+    o = oracle_lib.FullGridOracle(wl)
+    s.step(8)
+    o.step(8, o.dt())
+    assert rel_l2(s.f(), o.f()) < 1e-9
+
+
+def test_tucker_restart_is_bitwise(dvm, tmp_path):
+    wl = W.cavity(nside=3, N=12, seed=6)
+    a = tucker_solver(dvm, wl, 6, 1e-5)
+    a.step(4)
+    p = str(tmp_path / "tk.bin")
+    dvm.dvm_save(a.h, p)
+    a.step(3)
+    b = tucker_solver(dvm, wl, 6, 1e-5, init=False)
+    dvm.dvm_load(b.h, p)
+    b.step(3)
+    assert np.array_equal(a.f(), b.f())
+    assert np.array_equal(dvm.dvm_get_ranks(a.h), dvm.dvm_get_ranks(b.h))
+
+
+def test_tucker_memory_is_compressed(dvm):
+    wl = W.cavity(nside=4, N=16, seed=4)
+    s = tucker_solver(dvm, wl, 8, 1e-5)
+    s.step(10)
+    fb, _ = dvm.dvm_memory(s.h)
+    assert fb <= wl.n_cell * (8 ** 3 + 3 * 16 * 8) * 8
+    assert fb < 0.6 * wl.n_cell * 16 ** 3 * 8
