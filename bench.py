@@ -41,6 +41,9 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--path", default="full", choices=["full", "tucker"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--rank-cap", type=int, default=None)
+    ap.add_argument("--tol", type=float, default=None)
     ap.add_argument("--workload", default="cavity")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -203,7 +206,9 @@ def run_gpu(args, rank, world):
     stream = torch.cuda.current_stream()
     wl = make_workload(args.workload)
     fmt = NAT.DVM_FORMAT_TUCKER if args.path == "tucker" else NAT.DVM_FORMAT_FULL
-    s = P.Solver(wl, format=fmt, stream=stream.cuda_stream)
+    prec = NAT.DVM_PREC_MIXED if args.precision == "mixed" else NAT.DVM_PREC_FP64
+    s = P.Solver(wl, format=fmt, precision=prec, stream=stream.cuda_stream,
+                 rank_cap=args.rank_cap, tol=args.tol)
     upd = wl.n_cell * wl.nodes_per_cell
 
     for _ in range(args.warmup):

@@ -356,7 +356,7 @@ __device__ int choose_rank(Smem<Real> &sm, int n, double thr, int cap, double *d
     }
     double tail = 0.0;
     int r = n;
-    for (int k = n - 1; k >= 1; --k) {
+    for (int k = n - 1; k >= 1 && thr > 0.0; --k) {  // eps = 0: no truncation
       const double l = fmax((double)sm.A[sm.perm[k] * n + sm.perm[k]], 0.0);
       if (tail + l > thr) break;
       tail += l;
