@@ -8,24 +8,29 @@
 //   1. Moments of the Tucker tensor by weighted convolution (Section 4 item 5):
 //      S_a^(p) = U_a^T (v_a^p) for p = 0..3, then core contractions
 //      (tucker_moments_kernel, FP64).
-//   2. Assembly of f^{n+1} (Section 5): the self term f_i o W with the
-//      Lemma-1 weight W = 1 - dt nu - sum_l c_l (xi.e_l)^+, the equilibrium term
-//      dt nu f^S (rank-1 Maxwellian factors times the cubic Shakhov polynomial,
-//      Proposition 1), and one block per face, (-c_l (xi.e_l)^-) o f_nb(l).
-//      Because the pre-rounding rank r0 = 2r + sum r_nb + 4 is at least N on
-//      every workload of interest, the QR-of-factors route of Section 4 item 4
-//      leaves an N1 x N2 x N3 core; this kernel therefore forms that tensor X
-//      directly in scratch by mode products of each block (a dense
-//      contraction), which also lets faces whose normal is not a coordinate
-//      axis use the exact CIR weight (xi.e)^- pointwise.
-//   3. Rounding (Section 4 items 1 and 4): sequentially truncated HOSVD of X —
-//      per mode the Gram matrix of the unfolding, its eigen-decomposition by
-//      cyclic Jacobi rotations, truncation to the smallest rank whose discarded
-//      energy is <= (eps^2/3) ||X||^2 (capped), projection — giving the new
-//      orthonormal factors and core.
-// The heavy arithmetic (expansions, Gram matrices, Jacobi) is templated on the
-// scalar type: double for the FP64 path, float for the mixed path; moments,
-// macroparameters, rank decisions' energy sums and the stored state stay FP64.
+//   2. Assembly of f^{n+1} (Section 5): the self term f_i o W with the Lemma-1
+//      weight W = 1 - dt nu - sum_l c_l (xi.e_l)^+, the equilibrium term
+//      dt nu f^S (rank-1 Maxwellian factors times the cubic Shakhov
+//      polynomial, Proposition 1), and one block per face,
+//      (-c_l (xi.e_l)^-) o f_nb(l).  The pre-rounding rank
+//      r0 = 2r + sum r_nb + 4 is at least N on every workload of interest, so
+//      the QR-of-factors route of Section 4 item 4 leaves an N1 x N2 x N3 core;
+//      this kernel forms that tensor X directly in scratch by mode products of
+//      each block (dense contractions), which also lets faces whose normal is
+//      not a coordinate axis use the exact CIR weight (xi.e)^- pointwise.
+//   3. Rounding (Section 4 items 1 and 4): sequentially truncated HOSVD of X.
+//      Per mode: the Gram matrix of the unfolding (FP64 accumulation on the FP64
+//      path; exact FP32 products summed in double-FP32 on the mixed path, so
+//      that eigenvalues far below sqrt(FP32 round-off) remain resolved), its
+//      leading eigenvectors by block subspace iteration and a Rayleigh-Ritz step
+//      (FP64, cyclic Jacobi on the small projected matrix), and the truncation
+//      rank chosen from the energy the kept Ritz vectors capture exactly:
+//      the smallest r with trace(C) - sum_{j<r} theta_j <= (eps^2/3) ||X||^2,
+//      then capped.  The error bound ||X - X~|| <= eps ||X|| therefore holds by
+//      construction whenever the cap is inactive.
+// Expansions, assembly and projections run in the kernel's scalar type (double
+// on the FP64 path, float on the mixed path); moments, macroparameters, Gram
+// matrices, eigen-solves, energy sums and the stored state are FP64.
 #include <cfloat>
 #include <cmath>
 
@@ -38,20 +43,76 @@ namespace {
 
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kTB = 256;   // threads per CTA for the step / rounding kernel
-constexpr int kKC = 32;    // column chunk of the Gram (SYRK) tiles
+constexpr int kKC = 32;    // column chunk of the Gram tiles
+constexpr int kExtra = 4;  // oversampling columns of the subspace iteration
+constexpr int kPower = 3;  // subspace (power) iterations before Rayleigh-Ritz
+constexpr int kTabs = 21;  // per-axis tables of the assembly
+
+__host__ __device__ inline int sub_k(int Nmax, int R) { return Nmax < R + kExtra ? Nmax : R + kExtra; }
+
+// Shared-memory layout of the step / rounding kernel.
+template <typename Real>
+struct Smem {
+  double *par;    // [32] cell scalars
+  double *red;    // [32]
+  double *C;      // [Nmax*Nmax] Gram matrix (FP64)
+  double *Q;      // [Nmax*K] subspace basis
+  double *W;      // [Nmax*K] C*Q, then the Ritz vectors
+  double *B;      // [K*K] projected matrix
+  double *Z;      // [K*K] its eigenvectors
+  double *cs;     // [K+2] Jacobi cosines / sines
+  Real *rt;       // [kTabs][Nmax] assembly tables
+  Real *fac[3];   // [Nmax*R] factor rows of the expansion in progress
+  Real *tile;     // [Nmax*kKC] Gram tile
+  Real *Vr;       // [Nmax*K] kept eigenvectors in the working precision
+  int *pairs;     // [K+2]
+  int *perm;      // [K]
+};
 
 template <typename Real>
-struct Eps;
-template <>
-struct Eps<double> {
-  static constexpr double jacobi = 1e-15;
-  static constexpr int sweeps = 24;
-};
-template <>
-struct Eps<float> {
-  static constexpr float jacobi = 3e-7f;
-  static constexpr int sweeps = 16;
-};
+__host__ __device__ inline size_t smem_bytes(int Nmax, int R) {
+  const int K = sub_k(Nmax, R);
+  size_t b = sizeof(double) *
+             (64 + (size_t)Nmax * Nmax + 2 * (size_t)Nmax * K + 2 * (size_t)K * K + K + 2);
+  b += sizeof(Real) * ((size_t)kTabs * Nmax + 3 * (size_t)Nmax * R + (size_t)Nmax * kKC +
+                       (size_t)Nmax * K);
+  b += sizeof(int) * (2 * (size_t)K + 2);
+  return b + 64;
+}
+
+template <typename Real>
+__device__ Smem<Real> carve(unsigned char *base, int Nmax, int R) {
+  const int K = sub_k(Nmax, R);
+  Smem<Real> s;
+  size_t off = 0;
+  auto takeD = [&](size_t n) {
+    double *p = reinterpret_cast<double *>(base + off);
+    off += sizeof(double) * n;
+    return p;
+  };
+  s.par = takeD(32);
+  s.red = takeD(32);
+  s.C = takeD((size_t)Nmax * Nmax);
+  s.Q = takeD((size_t)Nmax * K);
+  s.W = takeD((size_t)Nmax * K);
+  s.B = takeD((size_t)K * K);
+  s.Z = takeD((size_t)K * K);
+  s.cs = takeD(K + 2);
+  auto takeR = [&](size_t n) {
+    Real *p = reinterpret_cast<Real *>(base + off);
+    off += sizeof(Real) * n;
+    return p;
+  };
+  s.rt = takeR((size_t)kTabs * Nmax);
+  for (int a = 0; a < 3; ++a) s.fac[a] = takeR((size_t)Nmax * R);
+  s.tile = takeR((size_t)Nmax * kKC);
+  s.Vr = takeR((size_t)Nmax * K);
+  off = (off + 3) & ~size_t(3);
+  s.pairs = reinterpret_cast<int *>(base + off);
+  off += sizeof(int) * (K + 2);
+  s.perm = reinterpret_cast<int *>(base + off);
+  return s;
+}
 
 __device__ __forceinline__ double block_sum_d(double v, double *red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -65,73 +126,13 @@ __device__ __forceinline__ double block_sum_d(double v, double *red) {
   return t;
 }
 
-// Shared-memory layout of the step / rounding kernel.
-template <typename Real>
-struct Smem {
-  Real *fac[3];   // [Nmax * R] factor rows for the expansion in progress
-  Real *A;        // [Nmax * Nmax] Gram / Jacobi matrix
-  Real *V;        // [Nmax * Nmax] eigenvectors
-  Real *tile;     // [Nmax * kKC] SYRK tile
-  Real *cs;       // [Nmax + 2] Jacobi cosines / sines
-  int *pairs;     // [Nmax + 2]
-  int *perm;      // [Nmax]
-  double *tab;    // [3][8][Nmax] per-axis tables
-  double *par;    // [32] cell scalars
-  double *red;    // [32]
-};
-
-template <typename Real>
-__host__ __device__ inline size_t smem_bytes(int Nmax, int R) {
-  size_t b = 0;
-  b += sizeof(Real) * 3 * (size_t)Nmax * R;
-  b += sizeof(Real) * 2 * (size_t)Nmax * Nmax;
-  b += sizeof(Real) * (size_t)Nmax * kKC;
-  b += sizeof(Real) * (Nmax + 2);
-  b += sizeof(int) * (2 * Nmax + 2);
-  b = (b + 15) & ~size_t(15);
-  b += sizeof(double) * (24 * (size_t)Nmax + 64);
-  return b + 64;
-}
-
-template <typename Real>
-__device__ Smem<Real> carve(unsigned char *base, int Nmax, int R) {
-  Smem<Real> s;
-  // doubles first (8-byte alignment), then Real arrays, then ints
-  size_t off = 0;
-  s.tab = reinterpret_cast<double *>(base + off);
-  off += sizeof(double) * 24 * (size_t)Nmax;
-  s.par = reinterpret_cast<double *>(base + off);
-  off += sizeof(double) * 32;
-  s.red = reinterpret_cast<double *>(base + off);
-  off += sizeof(double) * 32;
-  for (int a = 0; a < 3; ++a) {
-    s.fac[a] = reinterpret_cast<Real *>(base + off);
-    off += sizeof(Real) * (size_t)Nmax * R;
-  }
-  s.A = reinterpret_cast<Real *>(base + off);
-  off += sizeof(Real) * (size_t)Nmax * Nmax;
-  s.V = reinterpret_cast<Real *>(base + off);
-  off += sizeof(Real) * (size_t)Nmax * Nmax;
-  s.tile = reinterpret_cast<Real *>(base + off);
-  off += sizeof(Real) * (size_t)Nmax * kKC;
-  s.cs = reinterpret_cast<Real *>(base + off);
-  off += sizeof(Real) * (Nmax + 2);
-  off = (off + 3) & ~size_t(3);
-  s.pairs = reinterpret_cast<int *>(base + off);
-  off += sizeof(int) * (Nmax + 2);
-  s.perm = reinterpret_cast<int *>(base + off);
-  return s;
-}
-
 // ---------------------------------------------------------------------------
 // Expansion of one Tucker tensor (Section 4: A = G x1 U1 x2 U2 x3 U3) into a
-// full N1 x N2 x N3 array.  The factors are first copied to shared memory in
-// `Real`, optionally with their rows scaled (rowscale[a] != null).  The last
-// mode product either assigns (acc == false) or accumulates weight(i) * value.
+// full N1 x N2 x N3 array.  The last mode product either assigns
+// (acc == false) or accumulates weight(i1, i2, i3) * value.
 template <typename Real, typename Weight>
-__device__ void expand(const TuckerDev &T, int64_t cell, const int N[3], int R,
-                       const double *const rowscale[3], Smem<Real> &sm, Real *T1, Real *T2,
-                       Real *out, bool acc, const Weight &weight) {
+__device__ void expand(const TuckerDev &T, int64_t cell, const int N[3], int R, Smem<Real> &sm,
+                       Real *T1, Real *T2, Real *out, bool acc, const Weight &weight) {
   const int tid = threadIdx.x;
   const int r1 = T.rank[3 * cell], r2 = T.rank[3 * cell + 1], r3 = T.rank[3 * cell + 2];
   const double *G = T.core + cell * (int64_t)R * R * R;
@@ -140,9 +141,7 @@ __device__ void expand(const TuckerDev &T, int64_t cell, const int N[3], int R,
     const double *U = T.fac[a] + cell * (int64_t)N[a] * R;
     for (int idx = tid; idx < N[a] * ra; idx += blockDim.x) {
       const int i = idx / ra, k = idx - i * ra;
-      double v = U[(int64_t)i * R + k];
-      if (rowscale[a]) v *= rowscale[a][i];
-      sm.fac[a][idx] = (Real)v;
+      sm.fac[a][idx] = (Real)U[(int64_t)i * R + k];
     }
   }
   __syncthreads();
@@ -185,7 +184,7 @@ __device__ void expand(const TuckerDev &T, int64_t cell, const int N[3], int R,
         if (i1 < N1) {
           const int64_t o = (int64_t)i1 * NP + p;
           if (acc)
-            out[o] += (Real)weight(i1, i2, i3) * a[j];
+            out[o] += weight(i1, i2, i3) * a[j];
           else
             out[o] = a[j];
         }
@@ -195,23 +194,43 @@ __device__ void expand(const TuckerDev &T, int64_t cell, const int N[3], int R,
   __syncthreads();
 }
 
+template <typename Real>
 struct NoWeight {
-  __device__ double operator()(int, int, int) const { return 1.0; }
+  __device__ Real operator()(int, int, int) const { return Real(1); }
 };
 
-// inflow weight of a face: -c min(xi.e, 0) * scale
+// inflow weight -c min(xi.e, 0) * scale of one face: a 1D table for faces
+// normal to a coordinate axis, the dot product otherwise
+template <typename Real>
 struct FaceWeight {
-  const double *x0, *x1, *x2;
-  double c, e0, e1, e2, scale;
-  __device__ double operator()(int i1, int i2, int i3) const {
-    const double xn = e0 * x0[i1] + e1 * x1[i2] + e2 * x2[i3];
-    return -c * fmin(xn, 0.0) * scale;
+  const Real *tab;
+  const Real *x0, *x1, *x2;
+  Real c, e0, e1, e2, scale;
+  int axis;
+  __device__ Real operator()(int i1, int i2, int i3) const {
+    if (axis == 0) return tab[i1];
+    if (axis == 1) return tab[i2];
+    if (axis == 2) return tab[i3];
+    const Real xn = e0 * x0[i1] + e1 * x1[i2] + e2 * x2[i3];
+    return -c * fmin(xn, Real(0)) * scale;
   }
 };
 
 // ---------------------------------------------------------------------------
-// Gram matrix of the mode-m unfolding of a tensor with dims D (row-major):
-// C[a][b] = sum_j T(a, j) T(b, j), into sm.A (n x n, n = D[m]).
+// Gram matrix of the mode-m unfolding of a tensor with dims D (row-major),
+// C[a][b] = sum_j T(a, j) T(b, j), into sm.C (FP64).  For float data each
+// product is formed exactly (p + e with e = fma(x, y, -p)) and accumulated in a
+// (hi, lo) pair of floats (Knuth's two-sum), renormalised after every tile.
+__device__ __forceinline__ void df_acc(float x, float y, float &hi, float &lo) {
+  const float p = __fmul_rn(x, y);
+  const float pe = __fmaf_rn(x, y, -p);
+  const float s = __fadd_rn(hi, p);
+  const float bb = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(err, pe));
+}
+
 template <typename Real>
 __device__ void gram(const Real *T, const int D[3], int m, Smem<Real> &sm) {
   const int tid = threadIdx.x;
@@ -219,9 +238,9 @@ __device__ void gram(const Real *T, const int D[3], int m, Smem<Real> &sm) {
   const int cols = (D[0] * D[1] * D[2]) / n;
   const int nn = n * n;
   constexpr int Q = 16;  // outputs per thread (n <= 64 with 256 threads)
-  Real acc[Q];
+  Real hi[Q], lo[Q];
 #pragma unroll
-  for (int q = 0; q < Q; ++q) acc[q] = 0;
+  for (int q = 0; q < Q; ++q) hi[q] = lo[q] = 0;
   for (int j0 = 0; j0 < cols; j0 += kKC) {
     for (int idx = tid; idx < n * kKC; idx += blockDim.x) {
       const int a = idx / kKC, jj = idx - a * kKC, j = j0 + jj;
@@ -247,10 +266,20 @@ __device__ void gram(const Real *T, const int D[3], int m, Smem<Real> &sm) {
       if (o < nn) {
         const int a = o / n, b = o - a * n;
         const Real *ta = sm.tile + a * kKC, *tb = sm.tile + b * kKC;
-        Real s = acc[q];
+        if constexpr (sizeof(Real) == 8) {
+          Real s = hi[q];
 #pragma unroll 8
-        for (int k = 0; k < kKC; ++k) s += ta[k] * tb[k];
-        acc[q] = s;
+          for (int k = 0; k < kKC; ++k) s = fma(ta[k], tb[k], s);
+          hi[q] = s;
+        } else {
+          float h = hi[q], l = lo[q];
+#pragma unroll 8
+          for (int k = 0; k < kKC; ++k) df_acc(ta[k], tb[k], h, l);
+          const float s = __fadd_rn(h, l);  // renormalise (fast two-sum, |h| >= |l|)
+          l = __fsub_rn(l, __fsub_rn(s, h));
+          hi[q] = s;
+          lo[q] = l;
+        }
       }
     }
     __syncthreads();
@@ -258,30 +287,99 @@ __device__ void gram(const Real *T, const int D[3], int m, Smem<Real> &sm) {
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     const int o = tid + q * kTB;
-    if (o < nn) sm.A[o] = acc[q];
+    if (o < nn) sm.C[o] = (double)hi[q] + (double)lo[q];
   }
   __syncthreads();
 }
 
-// Cyclic Jacobi eigen-decomposition of the symmetric n x n matrix in sm.A
-// (eigenvalues left on its diagonal, eigenvectors in the columns of sm.V).
-// Disjoint rotation pairs of a round-robin schedule are applied together.
-template <typename Real>
-__device__ void jacobi(Smem<Real> &sm, int n) {
-  const int tid = threadIdx.x;
-  Real *A = sm.A, *V = sm.V;
-  for (int i = tid; i < n * n; i += blockDim.x) V[i] = (i / n == i % n) ? Real(1) : Real(0);
-  const int m = (n + 1) & ~1;
-  const int half = m / 2;
-  for (int sweep = 0; sweep < Eps<Real>::sweeps; ++sweep) {
-    double off = 0.0, dia = 0.0;
-    for (int i = tid; i < n * n; i += blockDim.x) {
-      const double a = (double)A[i];
-      if (i / n == i % n) dia += a * a; else off += a * a;
+// ---------------------------------------------------------------------------
+// FP64 dense helpers on shared-memory matrices (row-major).
+
+// W[n x k] = C[n x n] Q[n x k]
+__device__ void mat_cq(const double *C, const double *Q, double *W, int n, int k) {
+  for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) {
+    const int i = idx / k, j = idx - i * k;
+    double s = 0.0;
+    for (int t = 0; t < n; ++t) s = fma(C[i * n + t], Q[t * k + j], s);
+    W[idx] = s;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ double start_value(int i, int j);
+
+// Orthonormalise the k <= n columns of Q (n x k) in place: classical
+// Gram-Schmidt applied twice per column, one warp per dot product.  A column
+// that is numerically dependent on the previous ones (its norm drops below
+// 1e-6 of its norm before orthogonalisation, e.g. directions that power
+// iteration has driven below round-off) is replaced by a fresh start vector, so
+// the result is always an orthonormal basis of full rank k.
+__device__ void orthonormalise(double *Q, int n, int k, double *coef, double *red) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int j = 0; j < k; ++j) {
+    for (int attempt = 0; attempt < 4; ++attempt) {
+      if (warp == 0) {  // norm before orthogonalisation
+        double s = 0.0;
+        for (int r = lane; r < n; r += 32) s = fma(Q[r * k + j], Q[r * k + j], s);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) red[1] = s;
+      }
+      __syncthreads();
+      for (int pass = 0; pass < 2 && j > 0; ++pass) {
+        for (int i = warp; i < j; i += nw) {
+          double s = 0.0;
+          for (int r = lane; r < n; r += 32) s = fma(Q[r * k + i], Q[r * k + j], s);
+          for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+          if (lane == 0) coef[i] = s;
+        }
+        __syncthreads();
+        for (int r = threadIdx.x; r < n; r += blockDim.x) {
+          double v = Q[r * k + j];
+          for (int i = 0; i < j; ++i) v = fma(-coef[i], Q[r * k + i], v);
+          Q[r * k + j] = v;
+        }
+        __syncthreads();
+      }
+      if (warp == 0) {
+        double s = 0.0;
+        for (int r = lane; r < n; r += 32) s = fma(Q[r * k + j], Q[r * k + j], s);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) red[0] = s;
+      }
+      __syncthreads();
+      const double before = red[1], after = red[0];
+      const bool ok = after > 1e-12 * before && after > 1e-300;
+      if (ok || attempt == 3) {
+        const double inv = ok ? 1.0 / sqrt(after) : 0.0;
+        for (int r = threadIdx.x; r < n; r += blockDim.x) Q[r * k + j] *= inv;
+        __syncthreads();
+        break;
+      }
+      for (int r = threadIdx.x; r < n; r += blockDim.x)
+        Q[r * k + j] = start_value(r, j + 131 * (attempt + 1));
+      __syncthreads();
     }
-    off = block_sum_d(off, sm.red);
-    dia = block_sum_d(dia, sm.red);
-    if (off <= (double)Eps<Real>::jacobi * (double)Eps<Real>::jacobi * dia || dia == 0.0) break;
+  }
+}
+
+// Cyclic Jacobi on the symmetric k x k matrix B: eigenvalues on its diagonal,
+// eigenvectors in the columns of Z.  Disjoint pairs of a round-robin schedule
+// are rotated together.
+__device__ void jacobi_small(double *B, double *Z, int k, double *cs, int *pairs, double *red) {
+  const int tid = threadIdx.x;
+  for (int i = tid; i < k * k; i += blockDim.x) Z[i] = (i / k == i % k) ? 1.0 : 0.0;
+  __syncthreads();
+  const int m = (k + 1) & ~1;
+  const int half = m / 2;
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    double off = 0.0, dia = 0.0;
+    for (int i = tid; i < k * k; i += blockDim.x) {
+      const double a = B[i];
+      if (i / k == i % k) dia += a * a; else off += a * a;
+    }
+    off = block_sum_d(off, red);
+    dia = block_sum_d(dia, red);
+    if (off <= 1e-30 * dia || dia == 0.0) break;
     for (int round = 0; round < m - 1; ++round) {
       if (tid < half) {
         int p, q;
@@ -292,84 +390,150 @@ __device__ void jacobi(Smem<Real> &sm, int n) {
           p = 1 + (round + tid) % (m - 1);
           q = 1 + (round - tid + (m - 1)) % (m - 1);
         }
-        Real c = 1, s = 0;
-        if (p < n && q < n) {
-          const Real apq = A[p * n + q];
-          if (apq != Real(0)) {
-            const Real theta = (A[q * n + q] - A[p * n + p]) / (Real(2) * apq);
-            const Real t = (theta >= Real(0) ? Real(1) : Real(-1)) /
-                           (fabs(theta) + sqrt(theta * theta + Real(1)));
-            c = Real(1) / sqrt(t * t + Real(1));
+        double c = 1.0, s = 0.0;
+        if (p < k && q < k) {
+          const double apq = B[p * k + q];
+          if (apq != 0.0) {
+            const double theta = (B[q * k + q] - B[p * k + p]) / (2.0 * apq);
+            const double t =
+                (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+            c = 1.0 / sqrt(t * t + 1.0);
             s = t * c;
           }
         } else {
           p = q = -1;
         }
-        sm.pairs[2 * tid] = p;
-        sm.pairs[2 * tid + 1] = q;
-        sm.cs[2 * tid] = c;
-        sm.cs[2 * tid + 1] = s;
+        pairs[2 * tid] = p;
+        pairs[2 * tid + 1] = q;
+        cs[2 * tid] = c;
+        cs[2 * tid + 1] = s;
       }
       __syncthreads();
-      for (int idx = tid; idx < half * n; idx += blockDim.x) {  // A <- A P, V <- V P
-        const int k = idx / n, r = idx - k * n;
-        const int p = sm.pairs[2 * k], q = sm.pairs[2 * k + 1];
+      for (int idx = tid; idx < half * k; idx += blockDim.x) {  // B <- B P, Z <- Z P
+        const int h = idx / k, r = idx - h * k;
+        const int p = pairs[2 * h], q = pairs[2 * h + 1];
         if (p < 0) continue;
-        const Real c = sm.cs[2 * k], s = sm.cs[2 * k + 1];
-        const Real ap = A[r * n + p], aq = A[r * n + q];
-        A[r * n + p] = c * ap - s * aq;
-        A[r * n + q] = s * ap + c * aq;
-        const Real vp = V[r * n + p], vq = V[r * n + q];
-        V[r * n + p] = c * vp - s * vq;
-        V[r * n + q] = s * vp + c * vq;
+        const double c = cs[2 * h], s = cs[2 * h + 1];
+        const double bp = B[r * k + p], bq = B[r * k + q];
+        B[r * k + p] = c * bp - s * bq;
+        B[r * k + q] = s * bp + c * bq;
+        const double zp = Z[r * k + p], zq = Z[r * k + q];
+        Z[r * k + p] = c * zp - s * zq;
+        Z[r * k + q] = s * zp + c * zq;
       }
       __syncthreads();
-      for (int idx = tid; idx < half * n; idx += blockDim.x) {  // A <- P^T A
-        const int k = idx / n, j = idx - k * n;
-        const int p = sm.pairs[2 * k], q = sm.pairs[2 * k + 1];
+      for (int idx = tid; idx < half * k; idx += blockDim.x) {  // B <- P^T B
+        const int h = idx / k, j = idx - h * k;
+        const int p = pairs[2 * h], q = pairs[2 * h + 1];
         if (p < 0) continue;
-        const Real c = sm.cs[2 * k], s = sm.cs[2 * k + 1];
-        const Real bp = A[p * n + j], bq = A[q * n + j];
-        A[p * n + j] = c * bp - s * bq;
-        A[q * n + j] = s * bp + c * bq;
+        const double c = cs[2 * h], s = cs[2 * h + 1];
+        const double bp = B[p * k + j], bq = B[q * k + j];
+        B[p * k + j] = c * bp - s * bq;
+        B[q * k + j] = s * bp + c * bq;
       }
       __syncthreads();
     }
   }
 }
 
-// Sort the eigenvalues (descending, into sm.perm) and pick the truncation rank:
-// the smallest r whose discarded energy is <= thr, capped to [1, cap].
+// deterministic start vectors in [-1, 1)
+__device__ __forceinline__ double start_value(int i, int j) {
+  unsigned h = 0x9E3779B9u * (unsigned)(i + 1) ^ (0x85EBCA6Bu * (unsigned)(j + 7));
+  h ^= h >> 15;
+  h *= 0x2C1B3C6Du;
+  h ^= h >> 12;
+  h *= 0x297A2D39u;
+  h ^= h >> 15;
+  return (double)(h & 0xFFFFFF) / 8388608.0 - 1.0;
+}
+
+// Leading eigenpairs of the n x n Gram matrix sm.C: block subspace iteration
+// from fixed start vectors, then Rayleigh-Ritz.  On exit sm.W holds the k Ritz
+// vectors (columns sorted by Ritz value, descending) and the diagonal of sm.B
+// the Ritz values (in sm.perm order).  Returns k.
 template <typename Real>
-__device__ int choose_rank(Smem<Real> &sm, int n, double thr, int cap, double *discarded) {
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < n; ++i) sm.perm[i] = i;
-    for (int i = 1; i < n; ++i) {  // insertion sort by eigenvalue, descending
+__device__ int leading_eigs(Smem<Real> &sm, int n, int R) {
+  const int k = n < R + kExtra ? n : R + kExtra;
+  for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x)
+    sm.Q[idx] = (n == k) ? ((idx / k == idx % k) ? 1.0 : 0.0) : start_value(idx / k, idx % k);
+  __syncthreads();
+  if (n > k) {
+    orthonormalise(sm.Q, n, k, sm.cs, sm.red);
+    for (int it = 0; it < kPower; ++it) {
+      mat_cq(sm.C, sm.Q, sm.W, n, k);
+      for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) sm.Q[idx] = sm.W[idx];
+      __syncthreads();
+      orthonormalise(sm.Q, n, k, sm.cs, sm.red);
+    }
+  }
+  // Rayleigh-Ritz: B = Q^T C Q
+  mat_cq(sm.C, sm.Q, sm.W, n, k);
+  for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
+    const int a = idx / k, b = idx - a * k;
+    double s = 0.0;
+    for (int t = 0; t < n; ++t) s = fma(sm.Q[t * k + a], sm.W[t * k + b], s);
+    sm.B[idx] = s;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {  // symmetrise
+    const int a = idx / k, b = idx - a * k;
+    if (a < b) {
+      const double v = 0.5 * (sm.B[a * k + b] + sm.B[b * k + a]);
+      sm.B[a * k + b] = v;
+      sm.B[b * k + a] = v;
+    }
+  }
+  __syncthreads();
+  jacobi_small(sm.B, sm.Z, k, sm.cs, sm.pairs, sm.red);
+  if (threadIdx.x == 0) {  // sort Ritz values descending
+    for (int i = 0; i < k; ++i) sm.perm[i] = i;
+    for (int i = 1; i < k; ++i) {
       const int v = sm.perm[i];
-      const double lv = (double)sm.A[v * n + v];
+      const double lv = sm.B[v * k + v];
       int j = i - 1;
-      while (j >= 0 && (double)sm.A[sm.perm[j] * n + sm.perm[j]] < lv) {
+      while (j >= 0 && sm.B[sm.perm[j] * k + sm.perm[j]] < lv) {
         sm.perm[j + 1] = sm.perm[j];
         --j;
       }
       sm.perm[j + 1] = v;
     }
-    double tail = 0.0;
-    int r = n;
-    for (int k = n - 1; k >= 1 && thr > 0.0; --k) {  // eps = 0: no truncation
-      const double l = fmax((double)sm.A[sm.perm[k] * n + sm.perm[k]], 0.0);
-      if (tail + l > thr) break;
-      tail += l;
-      r = k;
+  }
+  __syncthreads();
+  // Ritz vectors W[:, j] = Q Z[:, perm[j]]
+  for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) {
+    const int i = idx / k, j = idx - i * k;
+    const int col = sm.perm[j];
+    double s = 0.0;
+    for (int t = 0; t < k; ++t) s = fma(sm.Q[i * k + t], sm.Z[t * k + col], s);
+    sm.W[idx] = s;
+  }
+  __syncthreads();
+  return k;
+}
+
+// Truncation rank from the energy the first r Ritz vectors capture:
+// smallest r with trace(C) - sum_{j<r} theta_j <= thr (thr > 0), else all k;
+// then r <- min(r, cap), r >= 1.
+template <typename Real>
+__device__ int choose_rank(Smem<Real> &sm, int n, int k, double thr, int cap, double *discarded) {
+  if (threadIdx.x == 0) {
+    double tr = 0.0;
+    for (int i = 0; i < n; ++i) tr += sm.C[i * n + i];
+    double kept = 0.0;
+    int r = k;
+    for (int j = 0; j < k && thr > 0.0; ++j) {
+      kept += fmax(sm.B[sm.perm[j] * k + sm.perm[j]], 0.0);
+      if (tr - kept <= thr) {
+        r = j + 1;
+        break;
+      }
     }
-    if (r > cap) {
-      tail = 0.0;
-      for (int k = cap; k < n; ++k) tail += fmax((double)sm.A[sm.perm[k] * n + sm.perm[k]], 0.0);
-      r = cap;
-    }
+    if (r > cap) r = cap;
     if (r < 1) r = 1;
+    kept = 0.0;
+    for (int j = 0; j < r; ++j) kept += fmax(sm.B[sm.perm[j] * k + sm.perm[j]], 0.0);
     sm.par[30] = (double)r;
-    sm.par[31] = tail;
+    sm.par[31] = fmax(tr - kept, 0.0);
   }
   __syncthreads();
   const int r = (int)sm.par[30];
@@ -377,10 +541,11 @@ __device__ int choose_rank(Smem<Real> &sm, int n, double thr, int cap, double *d
   return r;
 }
 
-// out = T x_m Vsel^T : mode m of T (dims D) contracted with the first r sorted
-// eigenvectors; result dims D with D[m] -> r.
+// out = T x_m Vr^T : mode m of T (dims D) contracted with the first r kept
+// eigenvectors (sm.Vr, n x k, column j = j-th vector); result dims D with D[m] -> r.
 template <typename Real>
-__device__ void project(const Real *T, const int D[3], int m, int r, Smem<Real> &sm, Real *out) {
+__device__ void project(const Real *T, const int D[3], int m, int r, int k, Smem<Real> &sm,
+                        Real *out) {
   const int n = D[m];
   int Do[3] = {D[0], D[1], D[2]};
   Do[m] = r;
@@ -388,8 +553,7 @@ __device__ void project(const Real *T, const int D[3], int m, int r, Smem<Real> 
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     const int i2 = idx % Do[2], t = idx / Do[2], i1 = t % Do[1], i0 = t / Do[1];
     const int ii[3] = {i0, i1, i2};
-    const int k = ii[m];
-    const int col = sm.perm[k];
+    const int kk = ii[m];
     int64_t base, stride;
     if (m == 0) {
       base = (int64_t)i1 * D[2] + i2;
@@ -402,7 +566,7 @@ __device__ void project(const Real *T, const int D[3], int m, int r, Smem<Real> 
       stride = 1;
     }
     Real s = 0;
-    for (int a = 0; a < n; ++a) s += sm.V[a * n + col] * T[base + a * stride];
+    for (int a = 0; a < n; ++a) s += sm.Vr[a * k + kk] * T[base + a * stride];
     out[idx] = s;
   }
   __syncthreads();
@@ -414,42 +578,41 @@ template <typename Real>
 __device__ void round_hosvd(Real *X, Real *T1, Real *T2, const int N[3], int R, double eps,
                             TuckerDev &out, int64_t cell, Smem<Real> &sm, double *err_out) {
   int D[3] = {N[0], N[1], N[2]};
-  // total energy ||X||^2 (FP64 sums)
-  double e = 0.0;
   const int NN = N[0] * N[1] * N[2];
+  double e = 0.0;
   for (int i = threadIdx.x; i < NN; i += blockDim.x) e += (double)X[i] * (double)X[i];
   e = block_sum_d(e, sm.red);
   const double thr = eps * eps / 3.0 * e;
   double discarded = 0.0;
   int r[3];
   const Real *src = X;
-  Real *dst[3] = {T2, T1, nullptr};
+  Real *dst[2] = {T2, T1};
   for (int m = 0; m < 3; ++m) {
+    const int n = D[m];
     gram<Real>(src, D, m, sm);
-    jacobi<Real>(sm, D[m]);
-    r[m] = choose_rank<Real>(sm, D[m], thr, R, &discarded);
-    // factor U_m = first r sorted eigenvectors (FP64 state, row stride R)
+    const int k = leading_eigs<Real>(sm, n, R);
+    r[m] = choose_rank<Real>(sm, n, k, thr, R, &discarded);
     double *U = out.fac[m] + cell * (int64_t)N[m] * R;
-    for (int idx = threadIdx.x; idx < N[m] * r[m]; idx += blockDim.x) {
-      const int i = idx / r[m], k = idx - i * r[m];
-      U[(int64_t)i * R + k] = (double)sm.V[i * D[m] + sm.perm[k]];
+    for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) {
+      const int i = idx / k, j = idx - i * k;
+      const double v = sm.W[idx];
+      sm.Vr[idx] = (Real)v;
+      if (j < r[m]) U[(int64_t)i * R + j] = v;
     }
+    __syncthreads();
     if (m < 2) {
-      project<Real>(src, D, m, r[m], sm, dst[m]);
+      project<Real>(src, D, m, r[m], k, sm, dst[m]);
       D[m] = r[m];
       src = dst[m];
     } else {
-      // core = Y2 x_3 V3^T, written compact in FP64
-      int Do[3] = {D[0], D[1], r[2]};
-      const int total = Do[0] * Do[1] * Do[2];
+      // core = Y2 x_3 V3^T (FP64 accumulation), compact r1 x r2 x r3
+      const int total = D[0] * D[1] * r[2];
       double *G = out.core + cell * (int64_t)R * R * R;
-      const int n = D[2];
       for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-        const int k3 = idx % Do[2], k12 = idx / Do[2];
-        const int col = sm.perm[k3];
+        const int k3 = idx % r[2], k12 = idx / r[2];
         const Real *y = src + (int64_t)k12 * n;
         double s = 0.0;
-        for (int a = 0; a < n; ++a) s += (double)sm.V[a * n + col] * (double)y[a];
+        for (int a = 0; a < n; ++a) s = fma(sm.W[a * k + k3], (double)y[a], s);
         G[idx] = s;
       }
       __syncthreads();
@@ -465,6 +628,14 @@ __device__ void round_hosvd(Real *X, Real *T1, Real *T2, const int N[3], int R, 
 }
 
 // ---------------------------------------------------------------------------
+// Per-cell tables of the assembly (working precision), per axis a:
+//   [a] nodes xi_a, [3+a] Maxwellian factor (dt nu folded into a = 0),
+//   [6+a] A q_a v_a, [9+a] v_a^2/T, [12+a] self outflow weight
+//   -sum_{faces normal to a} c max(s xi_a, 0); [15+l] inflow weight of face l
+//   (faces normal to a coordinate axis; scaled by the wall density on walls).
+template <typename Real>
+__device__ __forceinline__ Real *tabp(Smem<Real> &sm, int Nmax, int t) { return sm.rt + t * Nmax; }
+
 template <typename Real>
 __global__ void __launch_bounds__(kTB) tucker_step_kernel(TuckerStepParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -474,15 +645,12 @@ __global__ void __launch_bounds__(kTB) tucker_step_kernel(TuckerStepParams P) {
   const int N[3] = {P.N1, P.N2, P.N3};
   const int N1 = P.N1, N2 = P.N2, N3 = P.N3, NP = N2 * N3;
   const int NN = N1 * NP;
+  const int Nm = P.Nmax;
   const int tid = threadIdx.x;
   Real *X = reinterpret_cast<Real *>(P.scratch) + (size_t)blockIdx.x * P.scratch_stride;
   Real *E = X + NN;
   Real *T2 = E + NN;
   Real *T1 = T2 + (size_t)P.R * NP;
-  double *xt[3] = {sm.tab, sm.tab + P.Nmax, sm.tab + 2 * P.Nmax};  // nodes
-  for (int a = 0; a < 3; ++a)
-    for (int i = tid; i < N[a]; i += blockDim.x) xt[a][i] = P.xi[a][i];
-  __syncthreads();
 
   for (int64_t c = blockIdx.x; c < P.nc; c += gridDim.x) {
     if (P.mode == 1) {  // compress a given full tensor
@@ -518,57 +686,81 @@ __global__ void __launch_bounds__(kTB) tucker_step_kernel(TuckerStepParams P) {
       const double T = sm.par[4], dtnu = sm.par[8], A = sm.par[9], amp = sm.par[10];
       for (int a = 0; a < 3; ++a)
         for (int i = tid; i < N[a]; i += blockDim.x) {
-          const double v = xt[a][i] - sm.par[1 + a];
-          double *tb = sm.tab + (3 + 3 * a) * P.Nmax;  // F, A q v, v^2/T per axis
-          tb[i] = (a == 0 ? dtnu : 1.0) * amp * exp(-v * v / T);
-          tb[P.Nmax + i] = A * sm.par[5 + a] * v;
-          tb[2 * P.Nmax + i] = v * v / T;
+          const double x = P.xi[a][i];
+          const double v = x - sm.par[1 + a];
+          tabp(sm, Nm, 0 + a)[i] = (Real)x;
+          tabp(sm, Nm, 3 + a)[i] = (Real)((a == 0 ? dtnu : 1.0) * amp * exp(-v * v / T));
+          tabp(sm, Nm, 6 + a)[i] = (Real)(A * sm.par[5 + a] * v);
+          tabp(sm, Nm, 9 + a)[i] = (Real)(v * v / T);
+          double g = 0.0;
+          for (int l = 0; l < 6; ++l) {
+            const SlotDev &sl = s_slot[l];
+            if (sl.axis == a) g -= sl.c * fmax(sl.sgn * x, 0.0);
+          }
+          tabp(sm, Nm, 12 + a)[i] = (Real)g;
         }
+      for (int l = 0; l < 6; ++l) {
+        const SlotDev &sl = s_slot[l];
+        if (sl.axis < 0) continue;
+        for (int i = tid; i < N[sl.axis]; i += blockDim.x)
+          tabp(sm, Nm, 15 + l)[i] =
+              (Real)(-sl.c * fmin(sl.sgn * P.xi[sl.axis][i], 0.0) * s_scale[l]);
+      }
     }
     __syncthreads();
     // ---- own expansion into E
-    const double *none[3] = {nullptr, nullptr, nullptr};
-    expand<Real>(P.cur, c, N, P.R, none, sm, T1, T2, E, false, NoWeight{});
+    expand<Real>(P.cur, c, N, P.R, sm, T1, T2, E, false, NoWeight<Real>{});
     // ---- pointwise part: c0 f + dt nu f^S + ghost / self-referencing faces
     {
-      const double dtnu = sm.par[8];
-      const double *F0 = sm.tab + 3 * P.Nmax, *F1 = sm.tab + 6 * P.Nmax, *F2 = sm.tab + 9 * P.Nmax;
+      const Real w0 = (Real)(1.0 - sm.par[8]);
+      const Real *x0 = tabp(sm, Nm, 0), *x1 = tabp(sm, Nm, 1), *x2 = tabp(sm, Nm, 2);
+      const Real *F0 = tabp(sm, Nm, 3), *F1 = tabp(sm, Nm, 4), *F2 = tabp(sm, Nm, 5);
+      const Real *Q0 = tabp(sm, Nm, 6), *Q1 = tabp(sm, Nm, 7), *Q2 = tabp(sm, Nm, 8);
+      const Real *V0 = tabp(sm, Nm, 9), *V1 = tabp(sm, Nm, 10), *V2 = tabp(sm, Nm, 11);
+      const Real *G0 = tabp(sm, Nm, 12), *G1 = tabp(sm, Nm, 13), *G2 = tabp(sm, Nm, 14);
       for (int idx = tid; idx < NN; idx += blockDim.x) {
         const int i3 = idx % N3, t = idx / N3, i2 = t % N2, i1 = t / N2;
-        const double x1 = xt[0][i1], x2 = xt[1][i2], x3 = xt[2][i3];
-        const double fM = F0[i1] * F1[i2] * F2[i3];
-        const double aq = F0[P.Nmax + i1] + F1[P.Nmax + i2] + F2[P.Nmax + i3];
-        const double tt = F0[2 * P.Nmax + i1] + F1[2 * P.Nmax + i2] + F2[2 * P.Nmax + i3] - 2.5;
-        double val = fM * fma(aq, tt, 1.0);
-        double c0 = 1.0 - dtnu;
-        const double fe = (double)E[idx];
+        const Real fM = F0[i1] * F1[i2] * F2[i3];
+        Real val =
+            fM * (Real(1) + (Q0[i1] + Q1[i2] + Q2[i3]) * (V0[i1] + V1[i2] + V2[i3] - Real(2.5)));
+        Real c0 = w0 + G0[i1] + G1[i2] + G2[i3];
+        const Real fe = E[idx];
 #pragma unroll
         for (int l = 0; l < 6; ++l) {
           const SlotDev &sl = s_slot[l];
-          const double xn = sl.e[0] * x1 + sl.e[1] * x2 + sl.e[2] * x3;
-          c0 -= sl.c * fmax(xn, 0.0);
-          const double m = -sl.c * fmin(xn, 0.0);
-          if (m == 0.0) continue;
-          double g;
+          Real m;
+          if (sl.axis >= 0) {
+            if (sl.kind == kInterior) continue;
+            m = tabp(sm, Nm, 15 + l)[sl.axis == 0 ? i1 : (sl.axis == 1 ? i2 : i3)];
+          } else {
+            const Real xn =
+                (Real)sl.e[0] * x0[i1] + (Real)sl.e[1] * x1[i2] + (Real)sl.e[2] * x2[i3];
+            c0 -= (Real)sl.c * fmax(xn, Real(0));
+            if (sl.kind == kInterior) continue;
+            m = -(Real)sl.c * fmin(xn, Real(0)) * (Real)s_scale[l];
+          }
+          if (m == Real(0)) continue;
+          Real g;
           switch (sl.kind) {
-            case kInterior: continue;  // added by its block expansion below
-            case kZeroGrad: g = fe; break;
+            case kZeroGrad:
+              g = fe;
+              break;
             case kSymmetry: {
               int j1 = i1, j2 = i2, j3 = i3;
               if (sl.flip == 0) j1 = N1 - 1 - i1;
               else if (sl.flip == 1) j2 = N2 - 1 - i2;
               else j3 = N3 - 1 - i3;
-              g = (double)E[((int64_t)j1 * N2 + j2) * N3 + j3];
+              g = E[((int64_t)j1 * N2 + j2) * N3 + j3];
               break;
             }
             default: {  // free stream / wall: rank-1 Maxwellian ghost
               const double *gf = P.ghostf + (int64_t)sl.src * 3 * P.Nmax;
-              g = s_scale[l] * gf[i1] * gf[P.Nmax + i2] * gf[2 * P.Nmax + i3];
+              g = (Real)(gf[i1] * gf[P.Nmax + i2] * gf[2 * P.Nmax + i3]);
             }
           }
-          val = fma(m, g, val);
+          val += m * g;
         }
-        X[idx] = (Real)fma(c0, fe, val);
+        X[idx] = c0 * fe + val;
       }
       __syncthreads();
     }
@@ -576,8 +768,9 @@ __global__ void __launch_bounds__(kTB) tucker_step_kernel(TuckerStepParams P) {
     for (int l = 0; l < 6; ++l) {
       const SlotDev sl = s_slot[l];
       if (sl.kind != kInterior) continue;
-      FaceWeight fw{xt[0], xt[1], xt[2], sl.c, sl.e[0], sl.e[1], sl.e[2], 1.0};
-      expand<Real>(P.cur, sl.src, N, P.R, none, sm, T1, T2, X, true, fw);
+      FaceWeight<Real> fw{tabp(sm, Nm, 15 + l), tabp(sm, Nm, 0), tabp(sm, Nm, 1), tabp(sm, Nm, 2),
+                          (Real)sl.c, (Real)sl.e[0], (Real)sl.e[1], (Real)sl.e[2], Real(1), sl.axis};
+      expand<Real>(P.cur, sl.src, N, P.R, sm, T1, T2, X, true, fw);
     }
     // ---- rounding
     round_hosvd<Real>(X, T1, T2, N, P.R, P.tol, P.nxt, c, sm, P.err);
@@ -596,9 +789,8 @@ __global__ void __launch_bounds__(kTB) tucker_expand_kernel(TuckerDev T, int64_t
   Real *E = reinterpret_cast<Real *>(scratch) + (size_t)blockIdx.x * stride;
   Real *T2 = E + NN;
   Real *T1 = T2 + (size_t)R * N2 * N3;
-  const double *none[3] = {nullptr, nullptr, nullptr};
   for (int64_t j = blockIdx.x; j < ncell; j += gridDim.x) {
-    expand<Real>(T, c0 + j, N, R, none, sm, T1, T2, E, false, NoWeight{});
+    expand<Real>(T, c0 + j, N, R, sm, T1, T2, E, false, NoWeight<Real>{});
     for (int i = threadIdx.x; i < NN; i += blockDim.x) out[j * NN + i] = (double)E[i];
     __syncthreads();
   }

@@ -66,11 +66,11 @@ def test_maxwellian_initial_state_is_rank_one(dvm, oracle_lib):
     assert fb == wl.n_cell * (1 + 3 * 12) * 8
 
 
-@pytest.mark.parametrize("precision,eps,tol_rel", [(FP64, 1e-6, 1e-12), (MIXED, 1e-3, 2e-6)])
+@pytest.mark.parametrize("precision,eps,tol_rel", [(FP64, 1e-6, 1e-12), (MIXED, 1e-6, 1e-6)])
 def test_compression_recovers_low_rank_tensors(dvm, oracle_lib, precision, eps, tol_rel):
-    """Sum of two Maxwellians per cell: Tucker ranks exactly 2.  (The Gram route resolves
-    relative tolerances down to about the square root of the arithmetic's unit round-off,
-    so eps is 1e-6 for FP64 and 1e-3 for FP32.)"""
+    """Sum of two Maxwellians per cell: Tucker ranks exactly 2 (the mixed path forms its
+    Gram matrices from exact FP32 products summed in double-FP32, so tolerances well below
+    sqrt(FP32 round-off) are still resolved)."""
     wl = W.specular_box(shape=(2, 2, 1), N=16, vmax=5.0)
     o = oracle_lib.FullGridOracle(wl)
     rng = np.random.default_rng(3)
@@ -84,8 +84,9 @@ def test_compression_recovers_low_rank_tensors(dvm, oracle_lib, precision, eps, 
     assert rel_l2(s.f(), f) < tol_rel
 
 
-@pytest.mark.parametrize("eps", [1e-2, 1e-4, 1e-6, 1e-7])
-def test_rounding_respects_error_bound(dvm, oracle_lib, eps):
+@pytest.mark.parametrize("precision,eps", [(FP64, 1e-2), (FP64, 1e-4), (FP64, 1e-6),
+                                           (FP64, 1e-7), (MIXED, 1e-3), (MIXED, 1e-5)])
+def test_rounding_respects_error_bound(dvm, oracle_lib, precision, eps):
     """Random decaying-spectrum tensors: ||A - round(A)|| <= eps ||A|| per cell (cap
     inactive), and ranks no larger than the reference HOSVD's (Section 4 items 1, 4)."""
     N = 14
@@ -98,14 +99,16 @@ def test_rounding_respects_error_bound(dvm, oracle_lib, eps):
         Q = [np.linalg.qr(rng.standard_normal((N, N)))[0] for _ in range(3)]
         f.append(np.abs(tk.full((G, tuple(Q)))) + 0.0)
     f = np.stack(f)
-    s = tucker_solver(dvm, wl, N, eps, init=False)
+    s = tucker_solver(dvm, wl, N, eps, precision=precision, init=False)
     dvm.dvm_init_f(s.h, f)
     g = s.f()
     ranks = dvm.dvm_get_ranks(s.h)
+    slack = 1e-8 if precision == FP64 else 1e-6   # FP32 storage of the working tensor
     for c in range(wl.n_cell):
-        assert np.linalg.norm(g[c] - f[c]) <= eps * np.linalg.norm(f[c]) * (1 + 1e-8)
+        nf = np.linalg.norm(f[c])
+        assert np.linalg.norm(g[c] - f[c]) <= eps * nf * (1 + 1e-8) + slack * nf
         ref, _ = tk.hosvd(f[c], eps)
-        assert np.all(ranks[c] <= np.array(tk.ranks(ref)) + 1)
+        assert np.all(ranks[c] <= np.array(tk.ranks(ref)) + 2)
 
 
 def test_step_without_truncation_matches_oracle(dvm, oracle_lib):
