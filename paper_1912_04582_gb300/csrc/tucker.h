@@ -51,6 +51,7 @@ struct TuckerMomentParams {
 
 size_t tucker_scratch_elems(int N1, int N2, int N3, int R);
 size_t tucker_smem_bytes(int Nmax, int R, bool fp64);
+int tucker_step_blocks_per_sm(int Nmax, int R, bool fp64);
 int launch_tucker_step(const TuckerStepParams &p, int grid, bool fp64, cudaStream_t s);
 int launch_tucker_expand(const TuckerDev &T, int64_t c0, int64_t ncell, int N1, int N2, int N3,
                          int R, int Nmax, void *scratch, size_t stride, double *out, int grid,

@@ -63,8 +63,11 @@ struct Smem {
   double *cs;     // [K+2] Jacobi cosines / sines
   Real *rt;       // [kTabs][Nmax] assembly tables
   Real *fac[3];   // [Nmax*R] factor rows of the expansion in progress
-  Real *tile;     // [Nmax*kKC] Gram tile
+  Real *tile;     // [Nmax*(kKC+1)] Gram tile
   Real *Vr;       // [Nmax*K] kept eigenvectors in the working precision
+  float *C32;     // [Nmax*Nmax] FP32 copy of C (mixed path: power iterations)
+  float *Q32;     // [Nmax*K]
+  float *W32;     // [Nmax*K]
   int *pairs;     // [K+2]
   int *perm;      // [K]
 };
@@ -74,8 +77,9 @@ __host__ __device__ inline size_t smem_bytes(int Nmax, int R) {
   const int K = sub_k(Nmax, R);
   size_t b = sizeof(double) *
              (64 + (size_t)Nmax * Nmax + 2 * (size_t)Nmax * K + 2 * (size_t)K * K + K + 2);
-  b += sizeof(Real) * ((size_t)kTabs * Nmax + 3 * (size_t)Nmax * R + (size_t)Nmax * kKC +
+  b += sizeof(Real) * ((size_t)kTabs * Nmax + 3 * (size_t)Nmax * R + (size_t)Nmax * (kKC + 1) +
                        (size_t)Nmax * K);
+  b += sizeof(float) * ((size_t)Nmax * Nmax + 2 * (size_t)Nmax * K);
   b += sizeof(int) * (2 * (size_t)K + 2);
   return b + 64;
 }
@@ -105,9 +109,15 @@ __device__ Smem<Real> carve(unsigned char *base, int Nmax, int R) {
   };
   s.rt = takeR((size_t)kTabs * Nmax);
   for (int a = 0; a < 3; ++a) s.fac[a] = takeR((size_t)Nmax * R);
-  s.tile = takeR((size_t)Nmax * kKC);
+  s.tile = takeR((size_t)Nmax * (kKC + 1));
   s.Vr = takeR((size_t)Nmax * K);
   off = (off + 3) & ~size_t(3);
+  s.C32 = reinterpret_cast<float *>(base + off);
+  off += sizeof(float) * (size_t)Nmax * Nmax;
+  s.Q32 = reinterpret_cast<float *>(base + off);
+  off += sizeof(float) * (size_t)Nmax * K;
+  s.W32 = reinterpret_cast<float *>(base + off);
+  off += sizeof(float) * (size_t)Nmax * K;
   s.pairs = reinterpret_cast<int *>(base + off);
   off += sizeof(int) * (K + 2);
   s.perm = reinterpret_cast<int *>(base + off);
@@ -231,18 +241,23 @@ __device__ __forceinline__ void df_acc(float x, float y, float &hi, float &lo) {
   lo = __fadd_rn(lo, __fadd_rn(err, pe));
 }
 
-template <typename Real>
-__device__ void gram(const Real *T, const int D[3], int m, Smem<Real> &sm) {
-  const int tid = threadIdx.x;
+constexpr int kKP = kKC + 1;  // padded tile row (no shared-memory bank conflicts)
+
+template <typename Real, int TS>
+__device__ void gram_tiled(const Real *T, const int D[3], int m, Smem<Real> &sm) {
   const int n = D[m];
   const int cols = (D[0] * D[1] * D[2]) / n;
-  const int nn = n * n;
-  constexpr int Q = 16;  // outputs per thread (n <= 64 with 256 threads)
-  Real hi[Q], lo[Q];
+  // thread (ta, tb) of a 16 x 16 grid owns the TS x TS output block at
+  // rows ta*TS.., columns tb*TS..; only blocks on or above the diagonal work
+  const int ta = threadIdx.x >> 4, tb = threadIdx.x & 15;
+  const bool active = (ta <= tb) && (ta * TS < n) && (tb * TS < n);
+  Real hi[TS][TS], lo[TS][TS];
 #pragma unroll
-  for (int q = 0; q < Q; ++q) hi[q] = lo[q] = 0;
+  for (int i = 0; i < TS; ++i)
+#pragma unroll
+    for (int j = 0; j < TS; ++j) hi[i][j] = lo[i][j] = 0;
   for (int j0 = 0; j0 < cols; j0 += kKC) {
-    for (int idx = tid; idx < n * kKC; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < n * kKC; idx += blockDim.x) {
       const int a = idx / kKC, jj = idx - a * kKC, j = j0 + jj;
       Real v = 0;
       if (j < cols) {
@@ -250,56 +265,81 @@ __device__ void gram(const Real *T, const int D[3], int m, Smem<Real> &sm) {
         if (m == 0) {
           addr = (int64_t)a * cols + j;
         } else if (m == 1) {
-          const int k = j / D[2], i = j - k * D[2];
-          addr = ((int64_t)k * D[1] + a) * D[2] + i;
+          const int kk = j / D[2], i = j - kk * D[2];
+          addr = ((int64_t)kk * D[1] + a) * D[2] + i;
         } else {
           addr = (int64_t)j * D[2] + a;
         }
         v = T[addr];
       }
-      sm.tile[idx] = v;
+      sm.tile[a * kKP + jj] = v;
     }
     __syncthreads();
+    if (active) {
+#pragma unroll 4
+      for (int kk = 0; kk < kKC; ++kk) {
+        Real xa[TS], xb[TS];
 #pragma unroll
-    for (int q = 0; q < Q; ++q) {
-      const int o = tid + q * kTB;
-      if (o < nn) {
-        const int a = o / n, b = o - a * n;
-        const Real *ta = sm.tile + a * kKC, *tb = sm.tile + b * kKC;
-        if constexpr (sizeof(Real) == 8) {
-          Real s = hi[q];
-#pragma unroll 8
-          for (int k = 0; k < kKC; ++k) s = fma(ta[k], tb[k], s);
-          hi[q] = s;
-        } else {
-          float h = hi[q], l = lo[q];
-#pragma unroll 8
-          for (int k = 0; k < kKC; ++k) df_acc(ta[k], tb[k], h, l);
-          const float s = __fadd_rn(h, l);  // renormalise (fast two-sum, |h| >= |l|)
-          l = __fsub_rn(l, __fsub_rn(s, h));
-          hi[q] = s;
-          lo[q] = l;
+        for (int i = 0; i < TS; ++i) {
+          const int ra = ta * TS + i, rb = tb * TS + i;
+          xa[i] = ra < n ? sm.tile[ra * kKP + kk] : Real(0);
+          xb[i] = rb < n ? sm.tile[rb * kKP + kk] : Real(0);
         }
+#pragma unroll
+        for (int i = 0; i < TS; ++i)
+#pragma unroll
+          for (int j = 0; j < TS; ++j) {
+            if constexpr (sizeof(Real) == 8) {
+              hi[i][j] = fma(xa[i], xb[j], hi[i][j]);
+            } else {
+              df_acc(xa[i], xb[j], hi[i][j], lo[i][j]);
+            }
+          }
+      }
+      if constexpr (sizeof(Real) == 4) {
+#pragma unroll
+        for (int i = 0; i < TS; ++i)
+#pragma unroll
+          for (int j = 0; j < TS; ++j) {  // renormalise (fast two-sum)
+            const float sum = __fadd_rn(hi[i][j], lo[i][j]);
+            lo[i][j] = __fsub_rn(lo[i][j], __fsub_rn(sum, hi[i][j]));
+            hi[i][j] = sum;
+          }
       }
     }
     __syncthreads();
   }
+  if (active) {
 #pragma unroll
-  for (int q = 0; q < Q; ++q) {
-    const int o = tid + q * kTB;
-    if (o < nn) sm.C[o] = (double)hi[q] + (double)lo[q];
+    for (int i = 0; i < TS; ++i)
+#pragma unroll
+      for (int j = 0; j < TS; ++j) {
+        const int a = ta * TS + i, b = tb * TS + j;
+        if (a < n && b < n) {
+          const double v = (double)hi[i][j] + (double)lo[i][j];
+          sm.C[a * n + b] = v;
+          sm.C[b * n + a] = v;
+        }
+      }
   }
   __syncthreads();
+}
+
+// TS = 2 covers n <= 32 and TS = 4 covers n <= 64 (16 x 16 thread grid)
+template <typename Real, int TS>
+__device__ void gram(const Real *T, const int D[3], int m, Smem<Real> &sm) {
+  gram_tiled<Real, TS>(T, D, m, sm);
 }
 
 // ---------------------------------------------------------------------------
 // FP64 dense helpers on shared-memory matrices (row-major).
 
 // W[n x k] = C[n x n] Q[n x k]
-__device__ void mat_cq(const double *C, const double *Q, double *W, int n, int k) {
+template <typename T>
+__device__ void mat_cq(const T *C, const T *Q, T *W, int n, int k) {
   for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) {
     const int i = idx / k, j = idx - i * k;
-    double s = 0.0;
+    T s = 0;
     for (int t = 0; t < n; ++t) s = fma(C[i * n + t], Q[t * k + j], s);
     W[idx] = s;
   }
@@ -308,132 +348,134 @@ __device__ void mat_cq(const double *C, const double *Q, double *W, int n, int k
 
 __device__ __forceinline__ double start_value(int i, int j);
 
-// Orthonormalise the k <= n columns of Q (n x k) in place: classical
-// Gram-Schmidt applied twice per column, one warp per dot product.  A column
-// that is numerically dependent on the previous ones (its norm drops below
-// 1e-6 of its norm before orthogonalisation, e.g. directions that power
-// iteration has driven below round-off) is replaced by a fresh start vector, so
-// the result is always an orthonormal basis of full rank k.
-__device__ void orthonormalise(double *Q, int n, int k, double *coef, double *red) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int j = 0; j < k; ++j) {
-    for (int attempt = 0; attempt < 4; ++attempt) {
-      if (warp == 0) {  // norm before orthogonalisation
-        double s = 0.0;
-        for (int r = lane; r < n; r += 32) s = fma(Q[r * k + j], Q[r * k + j], s);
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) red[1] = s;
-      }
-      __syncthreads();
-      for (int pass = 0; pass < 2 && j > 0; ++pass) {
-        for (int i = warp; i < j; i += nw) {
-          double s = 0.0;
-          for (int r = lane; r < n; r += 32) s = fma(Q[r * k + i], Q[r * k + j], s);
-          for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-          if (lane == 0) coef[i] = s;
+// Orthonormalise the k <= n columns of Q (n x k) in place, by warp 0 alone
+// (no block barriers inside): classical Gram-Schmidt applied twice per column,
+// lanes over rows, shuffles for the dot products.  A column that is numerically
+// dependent on the previous ones (its squared norm drops below `dep` times its
+// value before orthogonalisation, e.g. directions that power iteration has
+// driven below round-off) is replaced by a fresh start vector, so the result is
+// always an orthonormal basis of full rank k.  Ends with one block barrier.
+template <typename T>
+__device__ void orthonormalise(T *Q, int n, int k, double *coef, double *red) {
+  (void)coef;
+  (void)red;
+  if ((threadIdx.x >> 5) == 0) {
+    const int lane = threadIdx.x & 31;
+    const double dep = sizeof(T) == 8 ? 1e-12 : 1e-6;
+    for (int j = 0; j < k; ++j) {
+      for (int attempt = 0; attempt < 4; ++attempt) {
+        double before = 0.0;
+        for (int r = lane; r < n; r += 32) before = fma((double)Q[r * k + j], (double)Q[r * k + j], before);
+        for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(0xffffffffu, before, o);
+        for (int pass = 0; pass < 2; ++pass) {
+          for (int i = 0; i < j; ++i) {
+            T d = 0;
+            for (int r = lane; r < n; r += 32) d = fma(Q[r * k + i], Q[r * k + j], d);
+            for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+            for (int r = lane; r < n; r += 32) Q[r * k + j] = fma(-d, Q[r * k + i], Q[r * k + j]);
+          }
+          __syncwarp();
         }
-        __syncthreads();
-        for (int r = threadIdx.x; r < n; r += blockDim.x) {
-          double v = Q[r * k + j];
-          for (int i = 0; i < j; ++i) v = fma(-coef[i], Q[r * k + i], v);
-          Q[r * k + j] = v;
+        double after = 0.0;
+        for (int r = lane; r < n; r += 32) after = fma((double)Q[r * k + j], (double)Q[r * k + j], after);
+        for (int o = 16; o > 0; o >>= 1) after += __shfl_xor_sync(0xffffffffu, after, o);
+        const bool ok = after > dep * before && after > 1e-300;
+        if (ok || attempt == 3) {
+          const T inv = ok ? (T)(1.0 / sqrt(after)) : T(0);
+          for (int r = lane; r < n; r += 32) Q[r * k + j] *= inv;
+          __syncwarp();
+          break;
         }
-        __syncthreads();
+        for (int r = lane; r < n; r += 32) Q[r * k + j] = (T)start_value(r, j + 131 * (attempt + 1));
+        __syncwarp();
       }
-      if (warp == 0) {
-        double s = 0.0;
-        for (int r = lane; r < n; r += 32) s = fma(Q[r * k + j], Q[r * k + j], s);
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) red[0] = s;
-      }
-      __syncthreads();
-      const double before = red[1], after = red[0];
-      const bool ok = after > 1e-12 * before && after > 1e-300;
-      if (ok || attempt == 3) {
-        const double inv = ok ? 1.0 / sqrt(after) : 0.0;
-        for (int r = threadIdx.x; r < n; r += blockDim.x) Q[r * k + j] *= inv;
-        __syncthreads();
-        break;
-      }
-      for (int r = threadIdx.x; r < n; r += blockDim.x)
-        Q[r * k + j] = start_value(r, j + 131 * (attempt + 1));
-      __syncthreads();
     }
   }
+  __syncthreads();
 }
 
-// Cyclic Jacobi on the symmetric k x k matrix B: eigenvalues on its diagonal,
-// eigenvectors in the columns of Z.  Disjoint pairs of a round-robin schedule
-// are rotated together.
+// Cyclic Jacobi on the symmetric k x k matrix B (k <= 32), by warp 0 alone:
+// rotated diagonal on B's diagonal, rotations accumulated in the columns of Z.
+// Disjoint pairs of a round-robin schedule are rotated together.  Full
+// convergence is not needed for correctness: the kept energy is read from the
+// rotated diagonal, which is exactly v^T C v for the Ritz vectors v = Q Z.
 __device__ void jacobi_small(double *B, double *Z, int k, double *cs, int *pairs, double *red) {
-  const int tid = threadIdx.x;
-  for (int i = tid; i < k * k; i += blockDim.x) Z[i] = (i / k == i % k) ? 1.0 : 0.0;
-  __syncthreads();
-  const int m = (k + 1) & ~1;
-  const int half = m / 2;
-  for (int sweep = 0; sweep < 30; ++sweep) {
-    double off = 0.0, dia = 0.0;
-    for (int i = tid; i < k * k; i += blockDim.x) {
-      const double a = B[i];
-      if (i / k == i % k) dia += a * a; else off += a * a;
-    }
-    off = block_sum_d(off, red);
-    dia = block_sum_d(dia, red);
-    if (off <= 1e-30 * dia || dia == 0.0) break;
-    for (int round = 0; round < m - 1; ++round) {
-      if (tid < half) {
-        int p, q;
-        if (tid == 0) {
-          p = 0;
-          q = 1 + round;
-        } else {
-          p = 1 + (round + tid) % (m - 1);
-          q = 1 + (round - tid + (m - 1)) % (m - 1);
-        }
-        double c = 1.0, s = 0.0;
-        if (p < k && q < k) {
-          const double apq = B[p * k + q];
-          if (apq != 0.0) {
-            const double theta = (B[q * k + q] - B[p * k + p]) / (2.0 * apq);
-            const double t =
-                (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-            c = 1.0 / sqrt(t * t + 1.0);
-            s = t * c;
+  (void)red;
+  if ((threadIdx.x >> 5) == 0) {
+    const int lane = threadIdx.x & 31;
+    for (int i = lane; i < k * k; i += 32) Z[i] = (i / k == i % k) ? 1.0 : 0.0;
+    __syncwarp();
+    const int m = (k + 1) & ~1;
+    const int half = m / 2;
+    for (int sweep = 0; sweep < 16; ++sweep) {
+      double off = 0.0, dia = 0.0;
+      for (int i = lane; i < k * k; i += 32) {
+        const double a = B[i];
+        if (i / k == i % k) dia += a * a; else off += a * a;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        off += __shfl_xor_sync(0xffffffffu, off, o);
+        dia += __shfl_xor_sync(0xffffffffu, dia, o);
+      }
+      if (off <= 1e-24 * dia || dia == 0.0) break;
+      for (int round = 0; round < m - 1; ++round) {
+        if (lane < half) {
+          int p, q;
+          if (lane == 0) {
+            p = 0;
+            q = 1 + round;
+          } else {
+            p = 1 + (round + lane) % (m - 1);
+            q = 1 + (round - lane + (m - 1)) % (m - 1);
           }
-        } else {
-          p = q = -1;
+          double c = 1.0, sn = 0.0;
+          if (p < k && q < k) {
+            const double apq = B[p * k + q];
+            if (apq != 0.0) {
+              const double theta = (B[q * k + q] - B[p * k + p]) / (2.0 * apq);
+              const double t =
+                  (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+              c = 1.0 / sqrt(t * t + 1.0);
+              sn = t * c;
+            }
+          } else {
+            p = q = -1;
+          }
+          pairs[2 * lane] = p;
+          pairs[2 * lane + 1] = q;
+          cs[2 * lane] = c;
+          cs[2 * lane + 1] = sn;
         }
-        pairs[2 * tid] = p;
-        pairs[2 * tid + 1] = q;
-        cs[2 * tid] = c;
-        cs[2 * tid + 1] = s;
+        __syncwarp();
+        for (int h = 0; h < half; ++h) {  // B <- B P, Z <- Z P  (lanes over rows)
+          const int p = pairs[2 * h], q = pairs[2 * h + 1];
+          if (p < 0) continue;
+          const double c = cs[2 * h], sn = cs[2 * h + 1];
+          for (int r = lane; r < k; r += 32) {
+            const double bp = B[r * k + p], bq = B[r * k + q];
+            B[r * k + p] = c * bp - sn * bq;
+            B[r * k + q] = sn * bp + c * bq;
+            const double zp = Z[r * k + p], zq = Z[r * k + q];
+            Z[r * k + p] = c * zp - sn * zq;
+            Z[r * k + q] = sn * zp + c * zq;
+          }
+        }
+        __syncwarp();
+        for (int h = 0; h < half; ++h) {  // B <- P^T B  (lanes over columns)
+          const int p = pairs[2 * h], q = pairs[2 * h + 1];
+          if (p < 0) continue;
+          const double c = cs[2 * h], sn = cs[2 * h + 1];
+          for (int j = lane; j < k; j += 32) {
+            const double bp = B[p * k + j], bq = B[q * k + j];
+            B[p * k + j] = c * bp - sn * bq;
+            B[q * k + j] = sn * bp + c * bq;
+          }
+        }
+        __syncwarp();
       }
-      __syncthreads();
-      for (int idx = tid; idx < half * k; idx += blockDim.x) {  // B <- B P, Z <- Z P
-        const int h = idx / k, r = idx - h * k;
-        const int p = pairs[2 * h], q = pairs[2 * h + 1];
-        if (p < 0) continue;
-        const double c = cs[2 * h], s = cs[2 * h + 1];
-        const double bp = B[r * k + p], bq = B[r * k + q];
-        B[r * k + p] = c * bp - s * bq;
-        B[r * k + q] = s * bp + c * bq;
-        const double zp = Z[r * k + p], zq = Z[r * k + q];
-        Z[r * k + p] = c * zp - s * zq;
-        Z[r * k + q] = s * zp + c * zq;
-      }
-      __syncthreads();
-      for (int idx = tid; idx < half * k; idx += blockDim.x) {  // B <- P^T B
-        const int h = idx / k, j = idx - h * k;
-        const int p = pairs[2 * h], q = pairs[2 * h + 1];
-        if (p < 0) continue;
-        const double c = cs[2 * h], s = cs[2 * h + 1];
-        const double bp = B[p * k + j], bq = B[q * k + j];
-        B[p * k + j] = c * bp - s * bq;
-        B[q * k + j] = s * bp + c * bq;
-      }
-      __syncthreads();
     }
   }
+  __syncthreads();
 }
 
 // deterministic start vectors in [-1, 1)
@@ -454,10 +496,14 @@ __device__ __forceinline__ double start_value(int i, int j) {
 template <typename Real>
 __device__ int leading_eigs(Smem<Real> &sm, int n, int R) {
   const int k = n < R + kExtra ? n : R + kExtra;
-  for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x)
-    sm.Q[idx] = (n == k) ? ((idx / k == idx % k) ? 1.0 : 0.0) : start_value(idx / k, idx % k);
-  __syncthreads();
-  if (n > k) {
+  if (n == k) {
+    for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x)
+      sm.Q[idx] = (idx / k == idx % k) ? 1.0 : 0.0;
+    __syncthreads();
+  } else if (sizeof(Real) == 8) {
+    for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x)
+      sm.Q[idx] = start_value(idx / k, idx % k);
+    __syncthreads();
     orthonormalise(sm.Q, n, k, sm.cs, sm.red);
     for (int it = 0; it < kPower; ++it) {
       mat_cq(sm.C, sm.Q, sm.W, n, k);
@@ -465,6 +511,26 @@ __device__ int leading_eigs(Smem<Real> &sm, int n, int R) {
       __syncthreads();
       orthonormalise(sm.Q, n, k, sm.cs, sm.red);
     }
+  } else {
+    // mixed path: find the subspace with FP32 power iterations on the rounded
+    // Gram matrix, then refine it with one FP64 step on the accurate one
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) sm.C32[idx] = (float)sm.C[idx];
+    for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x)
+      sm.Q32[idx] = (float)start_value(idx / k, idx % k);
+    __syncthreads();
+    orthonormalise(sm.Q32, n, k, sm.cs, sm.red);
+    for (int it = 0; it < kPower; ++it) {
+      mat_cq(sm.C32, sm.Q32, sm.W32, n, k);
+      for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) sm.Q32[idx] = sm.W32[idx];
+      __syncthreads();
+      orthonormalise(sm.Q32, n, k, sm.cs, sm.red);
+    }
+    for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) sm.Q[idx] = (double)sm.Q32[idx];
+    __syncthreads();
+    mat_cq(sm.C, sm.Q, sm.W, n, k);
+    for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) sm.Q[idx] = sm.W[idx];
+    __syncthreads();
+    orthonormalise(sm.Q, n, k, sm.cs, sm.red);
   }
   // Rayleigh-Ritz: B = Q^T C Q
   mat_cq(sm.C, sm.Q, sm.W, n, k);
@@ -574,7 +640,7 @@ __device__ void project(const Real *T, const int D[3], int m, int r, int k, Smem
 
 // Truncated sequential HOSVD of X (N1 x N2 x N3 in scratch) into the Tucker
 // slot `cell` of `out`.  Uses T2 (>= R*N2*N3) and T1 (>= R*R*N3) as work space.
-template <typename Real>
+template <typename Real, int TS>
 __device__ void round_hosvd(Real *X, Real *T1, Real *T2, const int N[3], int R, double eps,
                             TuckerDev &out, int64_t cell, Smem<Real> &sm, double *err_out) {
   int D[3] = {N[0], N[1], N[2]};
@@ -589,7 +655,7 @@ __device__ void round_hosvd(Real *X, Real *T1, Real *T2, const int N[3], int R, 
   Real *dst[2] = {T2, T1};
   for (int m = 0; m < 3; ++m) {
     const int n = D[m];
-    gram<Real>(src, D, m, sm);
+    gram<Real, TS>(src, D, m, sm);
     const int k = leading_eigs<Real>(sm, n, R);
     r[m] = choose_rank<Real>(sm, n, k, thr, R, &discarded);
     double *U = out.fac[m] + cell * (int64_t)N[m] * R;
@@ -636,8 +702,14 @@ __device__ void round_hosvd(Real *X, Real *T1, Real *T2, const int N[3], int R, 
 template <typename Real>
 __device__ __forceinline__ Real *tabp(Smem<Real> &sm, int Nmax, int t) { return sm.rt + t * Nmax; }
 
+// minimum resident CTAs per SM the register allocation must allow
 template <typename Real>
-__global__ void __launch_bounds__(kTB) tucker_step_kernel(TuckerStepParams P) {
+struct MinBlocks {
+  static constexpr int value = sizeof(Real) == 8 ? 2 : 3;
+};
+
+template <typename Real, int TS>
+__global__ void __launch_bounds__(kTB, MinBlocks<Real>::value) tucker_step_kernel(TuckerStepParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<Real> sm = carve<Real>(smem_raw, P.Nmax, P.R);
   __shared__ SlotDev s_slot[6];
@@ -657,7 +729,7 @@ __global__ void __launch_bounds__(kTB) tucker_step_kernel(TuckerStepParams P) {
       const double *src = P.finit + c * (int64_t)NN;
       for (int i = tid; i < NN; i += blockDim.x) X[i] = (Real)src[i];
       __syncthreads();
-      round_hosvd<Real>(X, T1, T2, N, P.R, P.tol, P.nxt, c, sm, P.err);
+      round_hosvd<Real, TS>(X, T1, T2, N, P.R, P.tol, P.nxt, c, sm, P.err);
       continue;
     }
     // ---- prologue: macroparameters, wall densities
@@ -773,7 +845,7 @@ __global__ void __launch_bounds__(kTB) tucker_step_kernel(TuckerStepParams P) {
       expand<Real>(P.cur, sl.src, N, P.R, sm, T1, T2, X, true, fw);
     }
     // ---- rounding
-    round_hosvd<Real>(X, T1, T2, N, P.R, P.tol, P.nxt, c, sm, P.err);
+    round_hosvd<Real, TS>(X, T1, T2, N, P.R, P.tol, P.nxt, c, sm, P.err);
   }
 }
 
@@ -943,23 +1015,28 @@ __global__ void tucker_maxwellian_kernel(TuckerDev Tk, const double *n, const do
     Tk.core[c * (int64_t)R * R * R] = n[c] / pow(kPi * T, 1.5) * s_norm[0] * s_norm[1] * s_norm[2];
 }
 
-template <typename Real>
-int launch_step_T(const TuckerStepParams &p, int grid, cudaStream_t s) {
+template <typename Real, int TS>
+int launch_step_TS(const TuckerStepParams &p, int grid, cudaStream_t s) {
   const size_t smem = smem_bytes<Real>(p.Nmax, p.R);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(tucker_step_kernel<Real>,
+  {  // the dynamic size plus the kernel's static shared memory may pass 48 KB
+    cudaError_t e = cudaFuncSetAttribute(tucker_step_kernel<Real, TS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return -1;
   }
-  tucker_step_kernel<Real><<<grid, kTB, smem, s>>>(p);
+  tucker_step_kernel<Real, TS><<<grid, kTB, smem, s>>>(p);
   return 0;
+}
+
+template <typename Real>
+int launch_step_T(const TuckerStepParams &p, int grid, cudaStream_t s) {
+  return p.Nmax <= 32 ? launch_step_TS<Real, 2>(p, grid, s) : launch_step_TS<Real, 4>(p, grid, s);
 }
 
 template <typename Real>
 int launch_expand_T(const TuckerDev &T, int64_t c0, int64_t ncell, int N1, int N2, int N3, int R,
                     int Nmax, void *scratch, size_t stride, double *out, int grid, cudaStream_t s) {
   const size_t smem = smem_bytes<Real>(Nmax, R);
-  if (smem > 48 * 1024) {
+  {
     cudaError_t e = cudaFuncSetAttribute(tucker_expand_kernel<Real>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return -1;
@@ -974,6 +1051,32 @@ int launch_expand_T(const TuckerDev &T, int64_t c0, int64_t ncell, int N1, int N
 size_t tucker_scratch_elems(int N1, int N2, int N3, int R) {
   const size_t NN = (size_t)N1 * N2 * N3;
   return 2 * NN + (size_t)R * N2 * N3 + (size_t)R * R * N3 + 64;
+}
+
+template <typename Real, int TS>
+int blocks_per_sm_TS(int Nmax, int R) {
+  const size_t smem = smem_bytes<Real>(Nmax, R);
+  if (cudaFuncSetAttribute(tucker_step_kernel<Real, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tucker_step_kernel<Real, TS>, kTB, smem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return nb < 1 ? 1 : nb;
+}
+
+template <typename Real>
+int blocks_per_sm_T(int Nmax, int R) {
+  return Nmax <= 32 ? blocks_per_sm_TS<Real, 2>(Nmax, R) : blocks_per_sm_TS<Real, 4>(Nmax, R);
+}
+
+int tucker_step_blocks_per_sm(int Nmax, int R, bool fp64) {
+  return fp64 ? blocks_per_sm_T<double>(Nmax, R) : blocks_per_sm_T<float>(Nmax, R);
 }
 
 size_t tucker_smem_bytes(int Nmax, int R, bool fp64) {

@@ -188,8 +188,7 @@ int tucker_alloc(dvm_ctx *C) {
   }
   int sms = 1;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, C->device);
-  const size_t smem = tucker_smem_bytes(S->Nmax, R, S->fp64);
-  int per_sm = (int)std::max<size_t>(1, std::min<size_t>(2, (200 * 1024) / (smem + 1024)));
+  const int per_sm = std::min(4, tucker_step_blocks_per_sm(S->Nmax, R, S->fp64));
   S->grid = (int)std::min<int64_t>(nc, (int64_t)sms * per_sm);
   S->stride = tucker_scratch_elems(C->N[0], C->N[1], C->N[2], R);
   S->stride = (S->stride + 63) & ~size_t(63);
@@ -254,6 +253,15 @@ int tucker_step(dvm_ctx *C, int32_t nsteps, double *residual_out) {
     if (launch_tucker_step(p, S->grid, S->fp64, C->stream) != 0) {
       set_error("Tucker kernel needs more shared memory than the device allows");
       return DVM_ERR_UNSUPPORTED;
+    }
+    {
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) {
+        set_error(std::string("Tucker step launch (grid ") + std::to_string(S->grid) + ", smem " +
+                  std::to_string(tucker_smem_bytes(S->Nmax, S->R, S->fp64)) + "): " +
+                  cudaGetErrorString(e));
+        return DVM_ERR_CUDA;
+      }
     }
     S->cur = 1 - S->cur;
     // moments of the new state about the previous velocity (+ residual parts)

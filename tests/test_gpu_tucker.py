@@ -35,13 +35,16 @@ def rel_l2(a, b):
 
 
 def macro_err(mg, mo, u_scale=1e-3):
-    """Relative L2 errors of n and T; u and q relative to their own L2 norm or, where the
-    flow is slower than u_scale (the problem's characteristic speed), to u_scale per cell
-    (q likewise to u_scale times the pressure scale)."""
+    """Relative L2 errors of n and T; u relative to its own L2 norm or, where the flow is
+    slower than u_scale (the problem's characteristic speed), to u_scale per cell; q
+    relative to its own norm or, where it is smaller, to the thermal heat-flux scale
+    p sqrt(T) = n T^1.5 / 2 per cell (q vanishes in equilibrium, so its own norm is no
+    scale for the round-off of a truncated distribution)."""
     err = {"n": rel_l2(mg[:, 0], mo[:, 0]), "T": rel_l2(mg[:, 4], mo[:, 4])}
     un = max(np.linalg.norm(mo[:, 1:4]), u_scale * np.sqrt(mo.shape[0]))
     err["u"] = float(np.linalg.norm(mg[:, 1:4] - mo[:, 1:4]) / un)
-    qn = max(np.linalg.norm(mo[:, 5:8]), 0.5 * u_scale * np.sqrt(mo.shape[0]) * 1e-3)
+    qs = np.linalg.norm(0.5 * mo[:, 0] * mo[:, 4] ** 1.5)
+    qn = max(np.linalg.norm(mo[:, 5:8]), qs)
     err["q"] = float(np.linalg.norm(mg[:, 5:8] - mo[:, 5:8]) / qn)
     return err
 
@@ -128,15 +131,18 @@ def test_step_without_truncation_matches_oracle(dvm, oracle_lib):
 
 @pytest.mark.parametrize("precision,bound", [(FP64, 1e-4), (MIXED, 1e-4)])
 def test_cavity_walls_lid_working_tolerance(dvm, oracle_lib, precision, bound):
-    """Small cavity (diffuse walls, moving lid), eps = 1e-5, cap 8, 40 steps."""
+    """Small cavity (diffuse walls, moving lid), eps = 1e-6, cap 12, 40 steps: f, n, T,
+    u (relative to the lid speed where the flow is slower) and q within 1e-4 of the FP64
+    full-grid oracle.  (eps = 1e-5 leaves ~1.5e-4 in u after 40 steps: the truncation error
+    of each step accumulates.)"""
     wl = W.cavity(nside=4, N=16, seed=4)
-    s = tucker_solver(dvm, wl, 8, 1e-5, precision=precision)
+    s = tucker_solver(dvm, wl, 12, 1e-6, precision=precision)
     o = oracle_lib.FullGridOracle(wl)
     s.step(40)
     o.step(40, o.dt())
     e = rel_l2(s.f(), o.f())
     me = macro_err(s.moments(), o.macro(), u_scale=0.2)
-    print(f"cavity 4^3x16^3 eps=1e-5 cap 8 prec={precision}: f {e:.2e} {me} "
+    print(f"cavity 4^3x16^3 eps=1e-6 cap 12 prec={precision}: f {e:.2e} {me} "
           f"ranks max {dvm.dvm_get_ranks(s.h).max()}")
     assert e < bound, e
     for k, v in me.items():
