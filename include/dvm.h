@@ -86,7 +86,7 @@ typedef struct {
 } dvm_mesh;
 
 typedef struct {
-  int32_t N[3];  /* nodes per axis, 2 .. 128                                 */
+  int32_t N[3];  /* nodes per axis, 2 .. 128 (Tucker format: 2 .. 64)       */
   double lo[3];  /* smallest node per axis                                   */
   double hi[3];  /* largest node per axis (hi > lo)                          */
 } dvm_vgrid;
@@ -100,7 +100,7 @@ typedef struct {
 typedef struct {
   int32_t format;     /* DVM_FORMAT_FULL or DVM_FORMAT_TUCKER                */
   int32_t precision;  /* DVM_PREC_FP64 or DVM_PREC_MIXED                     */
-  int32_t rank_cap;   /* Tucker: maximal rank per mode (1 .. min(N, 64))     */
+  int32_t rank_cap;   /* Tucker: maximal rank per mode (1 .. min(N, 24))     */
   double tol;         /* Tucker: relative rounding tolerance eps             */
   double cfl;         /* CFL number for the fixed time step (default 0.5)    */
   double dt;          /* if > 0, use this time step instead of the CFL rule  */

@@ -188,7 +188,7 @@ int dvm_create(dvm_ctx **out, const dvm_mesh *mesh, const dvm_vgrid *vg, const d
     return DVM_ERR_INVALID_ARG;
   }
   if (opts->format == DVM_FORMAT_TUCKER &&
-      (opts->rank_cap < 1 || opts->rank_cap > std::min(64, std::min(vg->N[0], std::min(vg->N[1], vg->N[2]))) ||
+      (opts->rank_cap < 1 || opts->rank_cap > std::min(24, std::min(vg->N[0], std::min(vg->N[1], vg->N[2]))) ||
        !(opts->tol >= 0.0))) {
     set_error("dvm_create: bad Tucker rank cap or tolerance");
     return DVM_ERR_INVALID_ARG;

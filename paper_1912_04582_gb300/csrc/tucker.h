@@ -24,6 +24,7 @@ struct TuckerStepParams {
   const double *xi[3];
   const double *finit;   // mode 1: [nc][N^3] tensors to compress
   double *err;           // [nc] relative truncation error of the last rounding (may be null)
+  long long *phase;      // [16] optional per-phase cycle counters (null: off)
   int *flag;
   void *scratch;         // per-CTA work space
   size_t scratch_stride; // elements (of the kernel's scalar type) per CTA

@@ -22,11 +22,11 @@
 //      Per mode: the Gram matrix of the unfolding (FP64 accumulation on the FP64
 //      path; exact FP32 products summed in double-FP32 on the mixed path, so
 //      that eigenvalues far below sqrt(FP32 round-off) remain resolved), its
-//      leading eigenvectors by block subspace iteration and a Rayleigh-Ritz step
-//      (FP64, cyclic Jacobi on the small projected matrix), and the truncation
-//      rank chosen from the energy the kept Ritz vectors capture exactly:
-//      the smallest r with trace(C) - sum_{j<r} theta_j <= (eps^2/3) ||X||^2,
-//      then capped.  The error bound ||X - X~|| <= eps ||X|| therefore holds by
+//      leading eigenvectors by orthogonal (block power) iteration — FP32 steps
+//      on the mixed path, always finished by an FP64 step on the accurate Gram
+//      matrix — and the truncation rank chosen from the energy the kept
+//      orthonormal vectors capture exactly: the smallest r with
+//      trace(C) - sum_{j<r} q_j^T C q_j <= (eps^2/3) ||X||^2, then capped.  The error bound ||X - X~|| <= eps ||X|| therefore holds by
 //      construction whenever the cap is inactive.
 // Expansions, assembly and projections run in the kernel's scalar type (double
 // on the FP64 path, float on the mixed path); moments, macroparameters, Gram
@@ -45,10 +45,32 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr int kTB = 256;   // threads per CTA for the step / rounding kernel
 constexpr int kKC = 32;    // column chunk of the Gram tiles
 constexpr int kExtra = 4;  // oversampling columns of the subspace iteration
-constexpr int kPower = 3;  // subspace (power) iterations before Rayleigh-Ritz
+constexpr int kPower = 3;     // orthogonal (power) iterations from a cold start
+constexpr int kWarmIter = 2;  // orthogonal iterations from the previous step's factor
 constexpr int kTabs = 21;  // per-axis tables of the assembly
 
-__host__ __device__ inline int sub_k(int Nmax, int R) { return Nmax < R + kExtra ? Nmax : R + kExtra; }
+// Optional per-phase cycle counters (thread 0 of every CTA adds clock64 deltas
+// to P.phase[i] when P.phase is not null); no effect on the computation.
+struct PhaseClock {
+  long long *acc;
+  long long t;
+  __device__ PhaseClock(long long *a) {
+    acc = a;
+    t = a ? (long long)clock64() : 0;
+  }
+  __device__ void mark(int i) {
+    if (acc && threadIdx.x == 0) {
+      const long long now = (long long)clock64();
+      atomicAdd(reinterpret_cast<unsigned long long *>(acc + i), (unsigned long long)(now - t));
+      t = now;
+    }
+  }
+};
+
+__host__ __device__ inline int sub_k(int Nmax, int R) {
+  const int k = Nmax < R + kExtra ? Nmax : R + kExtra;
+  return k < 24 ? k : 24;
+}
 
 // Shared-memory layout of the step / rounding kernel.
 template <typename Real>
@@ -348,134 +370,103 @@ __device__ void mat_cq(const T *C, const T *Q, T *W, int n, int k) {
 
 __device__ __forceinline__ double start_value(int i, int j);
 
-// Orthonormalise the k <= n columns of Q (n x k) in place, by warp 0 alone
-// (no block barriers inside): classical Gram-Schmidt applied twice per column,
-// lanes over rows, shuffles for the dot products.  A column that is numerically
-// dependent on the previous ones (its squared norm drops below `dep` times its
-// value before orthogonalisation, e.g. directions that power iteration has
-// driven below round-off) is replaced by a fresh start vector, so the result is
-// always an orthonormal basis of full rank k.  Ends with one block barrier.
-template <typename T>
-__device__ void orthonormalise(T *Q, int n, int k, double *coef, double *red) {
-  (void)coef;
-  (void)red;
-  if ((threadIdx.x >> 5) == 0) {
-    const int lane = threadIdx.x & 31;
-    const double dep = sizeof(T) == 8 ? 1e-12 : 1e-6;
-    for (int j = 0; j < k; ++j) {
-      for (int attempt = 0; attempt < 4; ++attempt) {
-        double before = 0.0;
-        for (int r = lane; r < n; r += 32) before = fma((double)Q[r * k + j], (double)Q[r * k + j], before);
-        for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(0xffffffffu, before, o);
-        for (int pass = 0; pass < 2; ++pass) {
-          for (int i = 0; i < j; ++i) {
-            T d = 0;
-            for (int r = lane; r < n; r += 32) d = fma(Q[r * k + i], Q[r * k + j], d);
-            for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-            for (int r = lane; r < n; r += 32) Q[r * k + j] = fma(-d, Q[r * k + i], Q[r * k + j]);
-          }
-          __syncwarp();
-        }
-        double after = 0.0;
-        for (int r = lane; r < n; r += 32) after = fma((double)Q[r * k + j], (double)Q[r * k + j], after);
-        for (int o = 16; o > 0; o >>= 1) after += __shfl_xor_sync(0xffffffffu, after, o);
-        const bool ok = after > dep * before && after > 1e-300;
-        if (ok || attempt == 3) {
-          const T inv = ok ? (T)(1.0 / sqrt(after)) : T(0);
-          for (int r = lane; r < n; r += 32) Q[r * k + j] *= inv;
-          __syncwarp();
-          break;
-        }
-        for (int r = lane; r < n; r += 32) Q[r * k + j] = (T)start_value(r, j + 131 * (attempt + 1));
-        __syncwarp();
-      }
-    }
-  }
-  __syncthreads();
-}
+constexpr int kOrthMax = 24;  // largest number of basis columns
 
-// Cyclic Jacobi on the symmetric k x k matrix B (k <= 32), by warp 0 alone:
-// rotated diagonal on B's diagonal, rotations accumulated in the columns of Z.
-// Disjoint pairs of a round-robin schedule are rotated together.  Full
-// convergence is not needed for correctness: the kept energy is read from the
-// rotated diagonal, which is exactly v^T C v for the Ritz vectors v = Q Z.
-__device__ void jacobi_small(double *B, double *Z, int k, double *cs, int *pairs, double *red) {
-  (void)red;
-  if ((threadIdx.x >> 5) == 0) {
-    const int lane = threadIdx.x & 31;
-    for (int i = lane; i < k * k; i += 32) Z[i] = (i / k == i % k) ? 1.0 : 0.0;
-    __syncwarp();
-    const int m = (k + 1) & ~1;
-    const int half = m / 2;
-    for (int sweep = 0; sweep < 16; ++sweep) {
-      double off = 0.0, dia = 0.0;
-      for (int i = lane; i < k * k; i += 32) {
-        const double a = B[i];
-        if (i / k == i % k) dia += a * a; else off += a * a;
+__device__ __forceinline__ double start_value(int i, int j);
+
+// Orthonormalise the k <= n columns of Q (n x k, row-major) in place by
+// Cholesky-QR: G = Q^T Q in FP64 (all threads), its Cholesky factor by one
+// thread, Q <- Q L^{-T} (one thread per row).
+//  * final == false (the power iterations): two passes, the first with a
+//    relative shift of trace(G) (1e-5 for FP32 data, 1e-12 for FP64; shifted
+//    Cholesky-QR, Fukaya et al. 2020), which keeps nearly dependent columns
+//    from breaking the factorisation; the result is approximately orthonormal,
+//    which is all those iterations need.
+//  * final == true (FP64 data, the last step): three passes; a column whose
+//    squared norm after removing its projections on the previous columns drops
+//    below 1e-10 of its own is numerically dependent; it is replaced by a fresh
+//    start vector and the passes repeated (at most three rounds), so the basis
+//    keeps full rank k (any column still dependent after that is zero).
+// Returns the number of non-zero columns.  G uses the k x k scratch `Gs`,
+// `dinv` the reciprocal pivots.  Ends with a block barrier.
+template <typename T>
+__device__ int orthonormalise(T *Q, int n, int k, double *Gs, double *dinv, bool final) {
+  const bool f32 = sizeof(T) == 4;
+  const int passes = final ? 3 : 2;
+  __shared__ int s_dep;
+  for (int round = 0; round < (final ? 3 : 1); ++round) {
+    for (int pass = 0; pass < passes; ++pass) {
+      for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
+        const int a = idx / k, b = idx - a * k;
+        if (a > b) continue;
+        double s = 0.0;
+        for (int r = 0; r < n; ++r) s = fma((double)Q[r * k + a], (double)Q[r * k + b], s);
+        Gs[a * k + b] = s;
+        Gs[b * k + a] = s;
       }
-      for (int o = 16; o > 0; o >>= 1) {
-        off += __shfl_xor_sync(0xffffffffu, off, o);
-        dia += __shfl_xor_sync(0xffffffffu, dia, o);
-      }
-      if (off <= 1e-24 * dia || dia == 0.0) break;
-      for (int round = 0; round < m - 1; ++round) {
-        if (lane < half) {
-          int p, q;
-          if (lane == 0) {
-            p = 0;
-            q = 1 + round;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double tr = 0.0;
+        for (int a = 0; a < k; ++a) tr += Gs[a * k + a];
+        const double shift = (!final && pass == 0) ? (f32 ? 1e-5 : 1e-12) * tr : 0.0;
+        int ndep = 0;
+        for (int j = 0; j < k; ++j) {  // in-place lower Cholesky factor of G + shift I
+          const double gjj = Gs[j * k + j];
+          double d = gjj + shift;
+          for (int i = 0; i < j; ++i) d = fma(-Gs[j * k + i], Gs[j * k + i], d);
+          const bool dependent = final ? (!(d > 1e-10 * gjj) || !(d > 1e-300)) : !(d > 1e-300);
+          if (dependent) {
+            ++ndep;
+            dinv[j] = 0.0;
+            Gs[j * k + j] = 1.0;
+            for (int r = j + 1; r < k; ++r) Gs[r * k + j] = 0.0;
+            for (int i = 0; i < j; ++i) Gs[j * k + i] = 0.0;
+            continue;
+          }
+          double ljj, inv;
+          if (f32) {
+            inv = (double)rsqrtf((float)d);
+            ljj = d * inv;
           } else {
-            p = 1 + (round + lane) % (m - 1);
-            q = 1 + (round - lane + (m - 1)) % (m - 1);
+            ljj = sqrt(d);
+            inv = 1.0 / ljj;
           }
-          double c = 1.0, sn = 0.0;
-          if (p < k && q < k) {
-            const double apq = B[p * k + q];
-            if (apq != 0.0) {
-              const double theta = (B[q * k + q] - B[p * k + p]) / (2.0 * apq);
-              const double t =
-                  (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-              c = 1.0 / sqrt(t * t + 1.0);
-              sn = t * c;
-            }
-          } else {
-            p = q = -1;
-          }
-          pairs[2 * lane] = p;
-          pairs[2 * lane + 1] = q;
-          cs[2 * lane] = c;
-          cs[2 * lane + 1] = sn;
-        }
-        __syncwarp();
-        for (int h = 0; h < half; ++h) {  // B <- B P, Z <- Z P  (lanes over rows)
-          const int p = pairs[2 * h], q = pairs[2 * h + 1];
-          if (p < 0) continue;
-          const double c = cs[2 * h], sn = cs[2 * h + 1];
-          for (int r = lane; r < k; r += 32) {
-            const double bp = B[r * k + p], bq = B[r * k + q];
-            B[r * k + p] = c * bp - sn * bq;
-            B[r * k + q] = sn * bp + c * bq;
-            const double zp = Z[r * k + p], zq = Z[r * k + q];
-            Z[r * k + p] = c * zp - sn * zq;
-            Z[r * k + q] = sn * zp + c * zq;
+          Gs[j * k + j] = ljj;
+          dinv[j] = inv;
+          for (int r = j + 1; r < k; ++r) {
+            double v = Gs[r * k + j];
+            for (int i = 0; i < j; ++i) v = fma(-Gs[r * k + i], Gs[j * k + i], v);
+            Gs[r * k + j] = v * inv;
           }
         }
-        __syncwarp();
-        for (int h = 0; h < half; ++h) {  // B <- P^T B  (lanes over columns)
-          const int p = pairs[2 * h], q = pairs[2 * h + 1];
-          if (p < 0) continue;
-          const double c = cs[2 * h], sn = cs[2 * h + 1];
-          for (int j = lane; j < k; j += 32) {
-            const double bp = B[p * k + j], bq = B[q * k + j];
-            B[p * k + j] = c * bp - sn * bq;
-            B[q * k + j] = sn * bp + c * bq;
-          }
-        }
-        __syncwarp();
+        s_dep = ndep;
       }
+      __syncthreads();
+      // each row x of Q solves y L^T = x: y_j = (x_j - sum_{i<j} y_i L_ji) / L_jj
+      for (int r = threadIdx.x; r < n; r += blockDim.x) {
+        double y[kOrthMax];
+        for (int j = 0; j < k; ++j) {
+          double v = (double)Q[r * k + j];
+          for (int i = 0; i < j; ++i) v = fma(-y[i], Gs[j * k + i], v);
+          y[j] = v * dinv[j];
+        }
+        for (int j = 0; j < k; ++j) Q[r * k + j] = (T)y[j];
+      }
+      __syncthreads();
     }
+    if (!final || s_dep == 0 || round == 2) break;
+    // final step: dependent columns (now zero) are replaced by fresh start
+    // vectors and the passes repeated, so the basis keeps full rank
+    for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) {
+      const int j = idx % k;
+      if (dinv[j] == 0.0) Q[idx] = (T)start_value(idx / k, j + 131 * (round + 1));
+    }
+    __syncthreads();
   }
+  int nz = 0;
+  for (int j = 0; j < k; ++j) nz += dinv[j] != 0.0;
   __syncthreads();
+  return nz;
 }
 
 // deterministic start vectors in [-1, 1)
@@ -489,96 +480,100 @@ __device__ __forceinline__ double start_value(int i, int j) {
   return (double)(h & 0xFFFFFF) / 8388608.0 - 1.0;
 }
 
-// Leading eigenpairs of the n x n Gram matrix sm.C: block subspace iteration
-// from fixed start vectors, then Rayleigh-Ritz.  On exit sm.W holds the k Ritz
-// vectors (columns sorted by Ritz value, descending) and the diagonal of sm.B
-// the Ritz values (in sm.perm order).  Returns k.
+// Leading eigenvectors of the n x n Gram matrix sm.C by orthogonal iteration
+// from fixed start vectors.  On exit sm.W holds k orthonormal columns ordered by
+// their Rayleigh quotients (descending), sm.B[perm[j]] the quotient of column j.
+// Returns k.
 template <typename Real>
-__device__ int leading_eigs(Smem<Real> &sm, int n, int R) {
-  const int k = n < R + kExtra ? n : R + kExtra;
-  if (n == k) {
-    for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x)
-      sm.Q[idx] = (idx / k == idx % k) ? 1.0 : 0.0;
+__device__ int leading_eigs(Smem<Real> &sm, int n, int R, const double *warm, int r_warm,
+                             PhaseClock &pc) {
+  int k = n < R + kExtra ? n : R + kExtra;
+  if (k > kOrthMax) k = kOrthMax;
+  if (!warm) r_warm = 0;
+  // start block: the previous step's orthonormal factor, when there is one (it
+  // spans most of the new dominant subspace), completed by fixed start vectors
+  const int iters = r_warm > 0 ? kWarmIter : kPower;
+  if (sizeof(Real) == 8) {
+    for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) {
+      const int i = idx / k, j = idx - i * k;
+      sm.Q[idx] = j < r_warm ? warm[(int64_t)i * R + j] : start_value(i, j);
+    }
     __syncthreads();
-  } else if (sizeof(Real) == 8) {
-    for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x)
-      sm.Q[idx] = start_value(idx / k, idx % k);
-    __syncthreads();
-    orthonormalise(sm.Q, n, k, sm.cs, sm.red);
-    for (int it = 0; it < kPower; ++it) {
+    int nz = k;
+    for (int it = 0; it < iters; ++it) {
       mat_cq(sm.C, sm.Q, sm.W, n, k);
       for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) sm.Q[idx] = sm.W[idx];
       __syncthreads();
-      orthonormalise(sm.Q, n, k, sm.cs, sm.red);
+      nz = orthonormalise(sm.Q, n, k, sm.B, sm.cs, it == iters - 1);
     }
+    if (threadIdx.x == 0) sm.par[29] = (double)nz;
   } else {
-    // mixed path: find the subspace with FP32 power iterations on the rounded
-    // Gram matrix, then refine it with one FP64 step on the accurate one
+    // mixed path: orthogonal iteration in FP32 on the rounded Gram matrix, then
+    // one FP64 step on the accurate one
     for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) sm.C32[idx] = (float)sm.C[idx];
-    for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x)
-      sm.Q32[idx] = (float)start_value(idx / k, idx % k);
+    for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) {
+      const int i = idx / k, j = idx - i * k;
+      sm.Q32[idx] = (float)(j < r_warm ? warm[(int64_t)i * R + j] : start_value(i, j));
+    }
     __syncthreads();
-    orthonormalise(sm.Q32, n, k, sm.cs, sm.red);
-    for (int it = 0; it < kPower; ++it) {
+    pc.mark(6);
+    for (int it = 0; it < iters; ++it) {
       mat_cq(sm.C32, sm.Q32, sm.W32, n, k);
       for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) sm.Q32[idx] = sm.W32[idx];
       __syncthreads();
-      orthonormalise(sm.Q32, n, k, sm.cs, sm.red);
+      pc.mark(9);
+      orthonormalise(sm.Q32, n, k, sm.B, sm.cs, false);
+      pc.mark(10);
     }
     for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) sm.Q[idx] = (double)sm.Q32[idx];
     __syncthreads();
     mat_cq(sm.C, sm.Q, sm.W, n, k);
     for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) sm.Q[idx] = sm.W[idx];
     __syncthreads();
-    orthonormalise(sm.Q, n, k, sm.cs, sm.red);
+    pc.mark(11);
+    const int nz = orthonormalise(sm.Q, n, k, sm.B, sm.cs, true);
+    if (threadIdx.x == 0) sm.par[29] = (double)nz;
+    pc.mark(12);
   }
-  // Rayleigh-Ritz: B = Q^T C Q
+  // Rayleigh quotients d_j = q_j^T C q_j of the orthonormal columns (FP64): any
+  // leading set of columns captures exactly the sum of its d_j, so the columns
+  // are ordered by d_j and the rank rule reads them (sorted, in sm.Z).
   mat_cq(sm.C, sm.Q, sm.W, n, k);
-  for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
-    const int a = idx / k, b = idx - a * k;
-    double s = 0.0;
-    for (int t = 0; t < n; ++t) s = fma(sm.Q[t * k + a], sm.W[t * k + b], s);
-    sm.B[idx] = s;
-  }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {  // symmetrise
-    const int a = idx / k, b = idx - a * k;
-    if (a < b) {
-      const double v = 0.5 * (sm.B[a * k + b] + sm.B[b * k + a]);
-      sm.B[a * k + b] = v;
-      sm.B[b * k + a] = v;
+  if ((threadIdx.x >> 5) == 0) {
+    const int lane = threadIdx.x & 31;
+    for (int j = 0; j < k; ++j) {
+      double d = 0.0;
+      for (int i = lane; i < n; i += 32) d = fma(sm.Q[i * k + j], sm.W[i * k + j], d);
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+      if (lane == 0) sm.cs[j] = d;
     }
-  }
-  __syncthreads();
-  jacobi_small(sm.B, sm.Z, k, sm.cs, sm.pairs, sm.red);
-  if (threadIdx.x == 0) {  // sort Ritz values descending
-    for (int i = 0; i < k; ++i) sm.perm[i] = i;
-    for (int i = 1; i < k; ++i) {
-      const int v = sm.perm[i];
-      const double lv = sm.B[v * k + v];
-      int j = i - 1;
-      while (j >= 0 && sm.B[sm.perm[j] * k + sm.perm[j]] < lv) {
-        sm.perm[j + 1] = sm.perm[j];
-        --j;
+    __syncwarp();
+    if (lane == 0) {  // order columns by quotient, descending
+      for (int i = 0; i < k; ++i) sm.perm[i] = i;
+      for (int i = 1; i < k; ++i) {
+        const int v = sm.perm[i];
+        const double lv = sm.cs[v];
+        int j = i - 1;
+        while (j >= 0 && sm.cs[sm.perm[j]] < lv) {
+          sm.perm[j + 1] = sm.perm[j];
+          --j;
+        }
+        sm.perm[j + 1] = v;
       }
-      sm.perm[j + 1] = v;
+      for (int j = 0; j < k; ++j) sm.Z[j] = sm.cs[sm.perm[j]];
     }
   }
   __syncthreads();
-  // Ritz vectors W[:, j] = Q Z[:, perm[j]]
   for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) {
     const int i = idx / k, j = idx - i * k;
-    const int col = sm.perm[j];
-    double s = 0.0;
-    for (int t = 0; t < k; ++t) s = fma(sm.Q[i * k + t], sm.Z[t * k + col], s);
-    sm.W[idx] = s;
+    sm.W[idx] = sm.Q[i * k + sm.perm[j]];
   }
   __syncthreads();
   return k;
 }
 
-// Truncation rank from the energy the first r Ritz vectors capture:
-// smallest r with trace(C) - sum_{j<r} theta_j <= thr (thr > 0), else all k;
+// Truncation rank from the energy the first r basis vectors capture:
+// smallest r with trace(C) - sum_{j<r} d_j <= thr (thr > 0), else all k;
 // then r <- min(r, cap), r >= 1.
 template <typename Real>
 __device__ int choose_rank(Smem<Real> &sm, int n, int k, double thr, int cap, double *discarded) {
@@ -588,16 +583,17 @@ __device__ int choose_rank(Smem<Real> &sm, int n, int k, double thr, int cap, do
     double kept = 0.0;
     int r = k;
     for (int j = 0; j < k && thr > 0.0; ++j) {
-      kept += fmax(sm.B[sm.perm[j] * k + sm.perm[j]], 0.0);
+      kept += fmax(sm.Z[j], 0.0);
       if (tr - kept <= thr) {
         r = j + 1;
         break;
       }
     }
     if (r > cap) r = cap;
+    if (r > (int)sm.par[29]) r = (int)sm.par[29];  // never keep zeroed (dependent) columns
     if (r < 1) r = 1;
     kept = 0.0;
-    for (int j = 0; j < r; ++j) kept += fmax(sm.B[sm.perm[j] * k + sm.perm[j]], 0.0);
+    for (int j = 0; j < r; ++j) kept += fmax(sm.Z[j], 0.0);
     sm.par[30] = (double)r;
     sm.par[31] = fmax(tr - kept, 0.0);
   }
@@ -642,7 +638,8 @@ __device__ void project(const Real *T, const int D[3], int m, int r, int k, Smem
 // slot `cell` of `out`.  Uses T2 (>= R*N2*N3) and T1 (>= R*R*N3) as work space.
 template <typename Real, int TS>
 __device__ void round_hosvd(Real *X, Real *T1, Real *T2, const int N[3], int R, double eps,
-                            TuckerDev &out, int64_t cell, Smem<Real> &sm, double *err_out) {
+                            TuckerDev &out, int64_t cell, Smem<Real> &sm, double *err_out,
+                            PhaseClock &pc, const TuckerDev *warm) {
   int D[3] = {N[0], N[1], N[2]};
   const int NN = N[0] * N[1] * N[2];
   double e = 0.0;
@@ -651,12 +648,17 @@ __device__ void round_hosvd(Real *X, Real *T1, Real *T2, const int N[3], int R, 
   const double thr = eps * eps / 3.0 * e;
   double discarded = 0.0;
   int r[3];
+  pc.mark(4);
   const Real *src = X;
   Real *dst[2] = {T2, T1};
   for (int m = 0; m < 3; ++m) {
     const int n = D[m];
     gram<Real, TS>(src, D, m, sm);
-    const int k = leading_eigs<Real>(sm, n, R);
+    pc.mark(5);
+    const double *wU = warm ? warm->fac[m] + cell * (int64_t)N[m] * R : nullptr;
+    const int wr = warm ? warm->rank[3 * cell + m] : 0;
+    const int k = leading_eigs<Real>(sm, n, R, wU, wr, pc);
+    pc.mark(6);
     r[m] = choose_rank<Real>(sm, n, k, thr, R, &discarded);
     double *U = out.fac[m] + cell * (int64_t)N[m] * R;
     for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) {
@@ -666,10 +668,12 @@ __device__ void round_hosvd(Real *X, Real *T1, Real *T2, const int N[3], int R, 
       if (j < r[m]) U[(int64_t)i * R + j] = v;
     }
     __syncthreads();
+    pc.mark(7);
     if (m < 2) {
       project<Real>(src, D, m, r[m], k, sm, dst[m]);
       D[m] = r[m];
       src = dst[m];
+      pc.mark(8);
     } else {
       // core = Y2 x_3 V3^T (FP64 accumulation), compact r1 x r2 x r3
       const int total = D[0] * D[1] * r[2];
@@ -682,6 +686,7 @@ __device__ void round_hosvd(Real *X, Real *T1, Real *T2, const int N[3], int R, 
         G[idx] = s;
       }
       __syncthreads();
+      pc.mark(8);
     }
   }
   if (threadIdx.x == 0) {
@@ -724,12 +729,13 @@ __global__ void __launch_bounds__(kTB, MinBlocks<Real>::value) tucker_step_kerne
   Real *T2 = E + NN;
   Real *T1 = T2 + (size_t)P.R * NP;
 
+  PhaseClock pc(P.phase);
   for (int64_t c = blockIdx.x; c < P.nc; c += gridDim.x) {
     if (P.mode == 1) {  // compress a given full tensor
       const double *src = P.finit + c * (int64_t)NN;
       for (int i = tid; i < NN; i += blockDim.x) X[i] = (Real)src[i];
       __syncthreads();
-      round_hosvd<Real, TS>(X, T1, T2, N, P.R, P.tol, P.nxt, c, sm, P.err);
+      round_hosvd<Real, TS>(X, T1, T2, N, P.R, P.tol, P.nxt, c, sm, P.err, pc, nullptr);
       continue;
     }
     // ---- prologue: macroparameters, wall densities
@@ -780,8 +786,10 @@ __global__ void __launch_bounds__(kTB, MinBlocks<Real>::value) tucker_step_kerne
       }
     }
     __syncthreads();
+    pc.mark(0);
     // ---- own expansion into E
     expand<Real>(P.cur, c, N, P.R, sm, T1, T2, E, false, NoWeight<Real>{});
+    pc.mark(1);
     // ---- pointwise part: c0 f + dt nu f^S + ghost / self-referencing faces
     {
       const Real w0 = (Real)(1.0 - sm.par[8]);
@@ -836,6 +844,7 @@ __global__ void __launch_bounds__(kTB, MinBlocks<Real>::value) tucker_step_kerne
       }
       __syncthreads();
     }
+    pc.mark(2);
     // ---- one block per interior face: X += (-c (xi.e)^-) o f_nb
     for (int l = 0; l < 6; ++l) {
       const SlotDev sl = s_slot[l];
@@ -844,8 +853,9 @@ __global__ void __launch_bounds__(kTB, MinBlocks<Real>::value) tucker_step_kerne
                           (Real)sl.c, (Real)sl.e[0], (Real)sl.e[1], (Real)sl.e[2], Real(1), sl.axis};
       expand<Real>(P.cur, sl.src, N, P.R, sm, T1, T2, X, true, fw);
     }
+    pc.mark(3);
     // ---- rounding
-    round_hosvd<Real, TS>(X, T1, T2, N, P.R, P.tol, P.nxt, c, sm, P.err);
+    round_hosvd<Real, TS>(X, T1, T2, N, P.R, P.tol, P.nxt, c, sm, P.err, pc, &P.cur);
   }
 }
 

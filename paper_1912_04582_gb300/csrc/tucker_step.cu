@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <string>
 #include <vector>
 
@@ -24,6 +25,7 @@ struct TuckerState {
   int grid = 0;
   double *ghostf = nullptr;  // [nghost][3][Nmax]
   double *err = nullptr;     // [nc]
+  long long *phase = nullptr;  // [16] per-phase cycles (DVM_TUCKER_PHASES set)
 };
 
 int ctx_finalize_dt_from_macro(dvm_ctx *C, const std::vector<double> &macro);
@@ -43,6 +45,7 @@ TuckerStepParams step_params(dvm_ctx *C) {
   p.ghostf = S->ghostf;
   for (int a = 0; a < 3; ++a) p.xi[a] = C->d_xi[a];
   p.err = S->err;
+  p.phase = S->phase;
   p.flag = C->d_flag;
   p.scratch = S->scratch;
   p.scratch_stride = S->stride;
@@ -198,6 +201,11 @@ int tucker_alloc(dvm_ctx *C) {
   rc = ctx_malloc(C, reinterpret_cast<void **>(&S->err), sizeof(double) * nc);
   if (rc != DVM_OK) return rc;
   DVM_CUDA_TRY(cudaMemset(S->err, 0, sizeof(double) * nc));
+  if (std::getenv("DVM_TUCKER_PHASES")) {
+    rc = ctx_malloc(C, reinterpret_cast<void **>(&S->phase), sizeof(long long) * 16);
+    if (rc != DVM_OK) return rc;
+    DVM_CUDA_TRY(cudaMemset(S->phase, 0, sizeof(long long) * 16));
+  }
   return DVM_OK;
 }
 
@@ -213,6 +221,18 @@ void tucker_free(dvm_ctx *C) {
   if (S->scratch) cudaFree(S->scratch);
   if (S->ghostf) cudaFree(S->ghostf);
   if (S->err) cudaFree(S->err);
+  if (S->phase) {
+    long long h[16] = {0};
+    if (cudaMemcpy(h, S->phase, sizeof h, cudaMemcpyDeviceToHost) == cudaSuccess) {
+      static const char *names[13] = {"prologue", "expand_own", "pointwise", "expand_nb", "energy",
+                                      "gram",     "eig",        "rank",      "project",   "eig_cq32",
+                                      "eig_orth32", "eig_cq64", "eig_orth64"};
+      std::fprintf(stderr, "tucker phases (SM cycles, summed over CTAs):");
+      for (int i = 0; i < 13; ++i) std::fprintf(stderr, " %s=%lld", names[i], h[i]);
+      std::fprintf(stderr, "\n");
+    }
+    cudaFree(S->phase);
+  }
   delete S;
   C->tucker = nullptr;
 }
