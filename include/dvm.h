@@ -184,6 +184,72 @@ int dvm_memory(dvm_ctx *ctx, size_t *f_bytes, size_t *total_bytes);
 int dvm_save(dvm_ctx *ctx, const char *path);
 int dvm_load(dvm_ctx *ctx, const char *path);
 
+/* ---------------------------------------------------------------------------
+ * Serving: continuous batching of steady-state solves (one request = one
+ * mesh / velocity grid / gas / boundary conditions / initial state, run to a
+ * residual; Section 3: the steady problem, n the iteration index).
+ * A server admits queued requests while the summed device-memory estimate of
+ * the running ones stays within its budget and a slot is free, creates each
+ * admitted context on its own CUDA stream (so the kernels of different solves
+ * overlap on the device), advances every running solve by a few steps per
+ * round, and retires a solve when its residual reaches the request's
+ * tolerance or its step limit.  A solve's arithmetic depends on its own data
+ * only, so its result is the same alone and in a mix.
+ */
+typedef struct dvm_server dvm_server;
+
+typedef struct {
+  dvm_mesh mesh;
+  dvm_vgrid vgrid;
+  dvm_gas gas;
+  dvm_opts opts;            /* opts.cuda_stream is ignored: the server owns streams */
+  int32_t n_bc;             /* boundary conditions: groups[n_bc], types[n_bc],      */
+  const int32_t *bc_group;  /* params[n_bc][8] (as for dvm_set_bc)                  */
+  const int32_t *bc_type;
+  const double *bc_params;
+  const double *n0;         /* initial Maxwellians, as for dvm_init_maxwellian      */
+  const double *u0;
+  const double *T0;
+  double tol;               /* residual to reach                                    */
+  int64_t max_steps;        /* step limit                                           */
+  int32_t check_every;      /* steps between residual checks (>= 1)                 */
+} dvm_request;
+
+/* request states reported by dvm_server_poll */
+#define DVM_REQ_QUEUED 0
+#define DVM_REQ_RUNNING 1
+#define DVM_REQ_CONVERGED 2
+#define DVM_REQ_NOT_CONVERGED 3
+#define DVM_REQ_FAILED 4
+
+/* Device-memory estimate of one request's context (bytes). */
+int dvm_estimate_memory(const dvm_request *req, size_t *bytes);
+
+/* Create a server with a device-memory budget (bytes) and at most max_slots
+ * concurrently running solves, on the current device. */
+int dvm_server_create(dvm_server **out, size_t hbm_budget, int32_t max_slots);
+
+/* Queue a request (every array is copied); its ticket is returned.  Requests
+ * whose estimate exceeds the whole budget are rejected (INVALID_ARG). */
+int dvm_server_submit(dvm_server *srv, const dvm_request *req, int64_t *ticket);
+
+/* Run the admission / stepping / retirement loop until every queued request
+ * has finished or max_seconds of wall time have passed.  Returns the number
+ * of requests still queued or running in *pending (may be NULL). */
+int dvm_server_run(dvm_server *srv, double max_seconds, int64_t *pending);
+
+/* State of a request: state (DVM_REQ_*), steps made, last residual, latency
+ * from submission to retirement in seconds (0 while unfinished).  Any output
+ * pointer may be NULL. */
+int dvm_server_poll(dvm_server *srv, int64_t ticket, int32_t *state, int64_t *steps,
+                    double *residual, double *latency_s);
+
+/* Macroparameters [n_cell][8] of a finished request (kept after its device
+ * memory was released). */
+int dvm_server_result(dvm_server *srv, int64_t ticket, double *macro);
+
+void dvm_server_destroy(dvm_server *srv);
+
 /* Macroparameters [n, u1, u2, u3, T, q1, q2, q3] of n_cell full tensors that
  * are already in device memory, computed without allocating device memory.
  * The paper has no counterpart: this entry point is for callers that cannot

@@ -55,6 +55,16 @@ class dvm_opts(ctypes.Structure):
                 ("cuda_stream", ctypes.c_void_p)]
 
 
+class dvm_request(ctypes.Structure):
+    _fields_ = [("mesh", dvm_mesh), ("vgrid", dvm_vgrid), ("gas", dvm_gas), ("opts", dvm_opts),
+                ("n_bc", ctypes.c_int32), ("bc_group", _c_i32p), ("bc_type", _c_i32p),
+                ("bc_params", _c_dp), ("n0", _c_dp), ("u0", _c_dp), ("T0", _c_dp),
+                ("tol", ctypes.c_double), ("max_steps", ctypes.c_int64),
+                ("check_every", ctypes.c_int32)]
+
+
+DVM_REQ_QUEUED, DVM_REQ_RUNNING, DVM_REQ_CONVERGED, DVM_REQ_NOT_CONVERGED, DVM_REQ_FAILED = range(5)
+
 _P = ctypes.c_void_p
 _PP = ctypes.POINTER(ctypes.c_void_p)
 # name -> (restype, argtypes); the exported names of include/dvm.h
@@ -81,6 +91,14 @@ SIGNATURES = {
     "dvm_full_macro_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64,
                                               ctypes.POINTER(dvm_vgrid), ctypes.c_void_p,
                                               ctypes.c_void_p]),
+    "dvm_estimate_memory": (ctypes.c_int, [ctypes.POINTER(dvm_request),
+                                           ctypes.POINTER(ctypes.c_size_t)]),
+    "dvm_server_create": (ctypes.c_int, [_PP, ctypes.c_size_t, ctypes.c_int32]),
+    "dvm_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(dvm_request), _c_i64p]),
+    "dvm_server_run": (ctypes.c_int, [_P, ctypes.c_double, _c_i64p]),
+    "dvm_server_poll": (ctypes.c_int, [_P, ctypes.c_int64, _c_i32p, _c_i64p, _c_dp, _c_dp]),
+    "dvm_server_result": (ctypes.c_int, [_P, ctypes.c_int64, _c_dp]),
+    "dvm_server_destroy": (None, [_P]),
     "dvm_destroy": (None, [_P]),
     "dvm_last_error": (ctypes.c_char_p, []),
 }

@@ -231,3 +231,121 @@ class Solver:
     @property
     def dt(self):
         return dvm_get_dt(self.h)
+
+
+# --------------------------------------------------------------------------
+# Serving (continuous batching of steady-state solves)
+
+def _request(wl, format, precision, rank_cap, tol, res_tol, max_steps, check_every, keep):
+    xyz = np.ascontiguousarray(wl.xyz, dtype=np.float64)
+    hex8 = np.ascontiguousarray(wl.hex8, dtype=np.int64)
+    bface = np.ascontiguousarray(wl.bface, dtype=np.int64).reshape(-1, 2)
+    bgroup = np.ascontiguousarray(wl.bgroup, dtype=np.int32)
+    groups = np.ascontiguousarray([g for g, _, _ in wl.bcs], dtype=np.int32)
+    types = np.ascontiguousarray([t for _, t, _ in wl.bcs], dtype=np.int32)
+    params = np.ascontiguousarray(np.stack([np.asarray(p, float) for _, _, p in wl.bcs]),
+                                  dtype=np.float64)
+    n0 = np.ascontiguousarray(wl.n0, dtype=np.float64)
+    u0 = np.ascontiguousarray(wl.u0, dtype=np.float64)
+    T0 = np.ascontiguousarray(wl.T0, dtype=np.float64)
+    keep.extend([xyz, hex8, bface, bgroup, groups, types, params, n0, u0, T0])
+    req = _n.dvm_request()
+    req.mesh = _n.dvm_mesh(xyz.shape[0], _dp(xyz), hex8.shape[0], _i64p(hex8), bface.shape[0],
+                           _i64p(bface), _i32p(bgroup))
+    req.vgrid = _n.dvm_vgrid((ctypes.c_int32 * 3)(*[int(v) for v in wl.N]),
+                             (ctypes.c_double * 3)(*[float(v) for v in wl.lo]),
+                             (ctypes.c_double * 3)(*[float(v) for v in wl.hi]))
+    req.gas = _n.dvm_gas(float(wl.Pr), float(wl.omega), float(wl.Kn))
+    req.opts = _n.dvm_opts(int(format), int(precision), int(rank_cap), float(tol), float(wl.cfl),
+                           0.0, None)
+    req.n_bc = len(wl.bcs)
+    req.bc_group, req.bc_type, req.bc_params = _i32p(groups), _i32p(types), _dp(params)
+    req.n0, req.u0, req.T0 = _dp(n0), _dp(u0), _dp(T0)
+    req.tol = float(res_tol)
+    req.max_steps = int(max_steps)
+    req.check_every = int(check_every)
+    return req
+
+
+def dvm_estimate_memory(wl, format=0, precision=0, rank_cap=8, tol=1e-5):
+    keep = []
+    req = _request(wl, format, precision, rank_cap, tol, 1e-6, 1, 1, keep)
+    b = ctypes.c_size_t(0)
+    _n.check(N_lib().dvm_estimate_memory(ctypes.byref(req), ctypes.byref(b)),
+             "dvm_estimate_memory")
+    return int(b.value)
+
+
+class Server:
+    """``dvm_server_*``: admits requests by device-memory budget and free slots, runs their
+    steps interleaved on separate streams, retires them at their residual target."""
+
+    def __init__(self, hbm_budget, max_slots):
+        self.ptr = ctypes.c_void_p()
+        _n.check(N_lib().dvm_server_create(ctypes.byref(self.ptr), int(hbm_budget),
+                                           int(max_slots)), "dvm_server_create")
+
+    def submit(self, wl, format=0, precision=0, rank_cap=8, tol=1e-5, res_tol=1e-6,
+               max_steps=10000, check_every=10):
+        keep = []
+        req = _request(wl, format, precision, rank_cap, tol, res_tol, max_steps, check_every,
+                       keep)
+        t = ctypes.c_int64(0)
+        _n.check(N_lib().dvm_server_submit(self.ptr, ctypes.byref(req), ctypes.byref(t)),
+                 "dvm_server_submit")
+        return int(t.value)
+
+    def run(self, max_seconds):
+        p = ctypes.c_int64(0)
+        _n.check(N_lib().dvm_server_run(self.ptr, float(max_seconds), ctypes.byref(p)),
+                 "dvm_server_run")
+        return int(p.value)
+
+    def poll(self, ticket):
+        st, steps = ctypes.c_int32(0), ctypes.c_int64(0)
+        res, lat = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        _n.check(N_lib().dvm_server_poll(self.ptr, int(ticket), ctypes.byref(st),
+                                         ctypes.byref(steps), ctypes.byref(res),
+                                         ctypes.byref(lat)), "dvm_server_poll")
+        return {"state": int(st.value), "steps": int(steps.value), "residual": float(res.value),
+                "latency_s": float(lat.value)}
+
+    def result(self, ticket, n_cell):
+        out = np.empty((n_cell, 8))
+        _n.check(N_lib().dvm_server_result(self.ptr, int(ticket), _dp(out)), "dvm_server_result")
+        return out
+
+    def close(self):
+        if self.ptr:
+            N_lib().dvm_server_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dvm_server_create(hbm_budget, max_slots):
+    return Server(hbm_budget, max_slots)
+
+
+def dvm_server_submit(srv, wl, **kw):
+    return srv.submit(wl, **kw)
+
+
+def dvm_server_run(srv, max_seconds):
+    return srv.run(max_seconds)
+
+
+def dvm_server_poll(srv, ticket):
+    return srv.poll(ticket)
+
+
+def dvm_server_result(srv, ticket, n_cell):
+    return srv.result(ticket, n_cell)
+
+
+def dvm_server_destroy(srv):
+    srv.close()

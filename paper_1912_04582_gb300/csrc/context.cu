@@ -551,3 +551,15 @@ int ctx_load(dvm_ctx *C, const char *path) {
   C->initialized = true;
   return DVM_OK;
 }
+
+// Enqueue the residual of the last step and the non-physical flag into
+// pinned host memory (out[0] = residual, low bytes of out[1] = flag) on the
+// context's stream, without synchronising.
+int ctx_enqueue_residual(dvm_ctx *C, double *pinned_out) {
+  launch_residual_reduce(C->d_respart, C->nc, C->dt, C->d_res, C->stream);
+  DVM_CUDA_TRY(cudaMemcpyAsync(pinned_out, C->d_res, sizeof(double), cudaMemcpyDeviceToHost,
+                               C->stream));
+  DVM_CUDA_TRY(cudaMemcpyAsync(pinned_out + 1, C->d_flag, sizeof(int), cudaMemcpyDeviceToHost,
+                               C->stream));
+  return DVM_OK;
+}
