@@ -173,6 +173,13 @@ int dvm_get_geometry(dvm_ctx *ctx, double *vol, int64_t *fcell, double *fgeo);
 /* Tucker ranks per cell into r[n_cell][3] (full format: N1, N2, N3). */
 int dvm_get_ranks(dvm_ctx *ctx, int32_t *r);
 
+/* Launch configuration of the Tucker step kernel (persistent, one cell per
+ * CTA at a time): the grid in CTAs chosen by the autotuner on the first step,
+ * and the step-kernel time in ms it measured for 1..4 resident CTAs per SM in
+ * tune_ms[1..4] (0 where not tried; tune_ms[0] unused).  Full format: grid =
+ * number of cells, tune_ms zeros.  Either pointer may be NULL. */
+int dvm_get_launch_config(dvm_ctx *ctx, int32_t *grid, float *tune_ms);
+
 /* Bytes of device memory held for the distribution function in its current
  * representation (Tucker: sum over cells of r1 r2 r3 + N1 r1 + N2 r2 + N3 r3
  * values, Section 7), and the total bytes the context allocated. */

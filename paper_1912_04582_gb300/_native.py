@@ -84,6 +84,7 @@ SIGNATURES = {
     "dvm_get_num_faces": (ctypes.c_int, [_P, _c_i64p]),
     "dvm_get_geometry": (ctypes.c_int, [_P, _c_dp, _c_i64p, _c_dp]),
     "dvm_get_ranks": (ctypes.c_int, [_P, _c_i32p]),
+    "dvm_get_launch_config": (ctypes.c_int, [_P, _c_i32p, ctypes.POINTER(ctypes.c_float)]),
     "dvm_memory": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t),
                                   ctypes.POINTER(ctypes.c_size_t)]),
     "dvm_save": (ctypes.c_int, [_P, ctypes.c_char_p]),

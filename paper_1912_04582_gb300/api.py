@@ -155,6 +155,13 @@ def dvm_get_ranks(h):
     return r
 
 
+def dvm_get_launch_config(h):
+    g = ctypes.c_int32(0)
+    t = (ctypes.c_float * 5)()
+    _n.check(N_lib().dvm_get_launch_config(h.ptr, ctypes.byref(g), t), "dvm_get_launch_config")
+    return int(g.value), [float(v) for v in t]
+
+
 def dvm_memory(h):
     fb = ctypes.c_size_t(0)
     tb = ctypes.c_size_t(0)

@@ -397,6 +397,15 @@ int dvm_get_ranks(dvm_ctx *C, int32_t *r) {
   return ctx_get_ranks(C, r);
 }
 
+int dvm_get_launch_config(dvm_ctx *C, int32_t *grid, float *tune_ms) {
+  if (!C) return DVM_ERR_INVALID_ARG;
+  if (C->opts.format == DVM_FORMAT_TUCKER && C->tucker) return tucker_launch_info(C, grid, tune_ms);
+  if (grid) *grid = (int32_t)C->nc;
+  if (tune_ms)
+    for (int i = 0; i < 5; ++i) tune_ms[i] = 0.f;
+  return DVM_OK;
+}
+
 int dvm_memory(dvm_ctx *C, size_t *f_bytes, size_t *total_bytes) {
   if (!C) return DVM_ERR_INVALID_ARG;
   return ctx_memory(C, f_bytes, total_bytes);

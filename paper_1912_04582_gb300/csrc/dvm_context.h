@@ -92,3 +92,4 @@ int tucker_get_ranks(dvm_ctx *C, int32_t *r);
 int tucker_memory(dvm_ctx *C, size_t *f_bytes);
 int tucker_save(dvm_ctx *C, FILE *fp);
 int tucker_load(dvm_ctx *C, FILE *fp);
+int tucker_launch_info(dvm_ctx *C, int32_t *grid, float *tune_ms);

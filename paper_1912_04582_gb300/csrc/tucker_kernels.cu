@@ -1028,7 +1028,11 @@ __global__ void tucker_maxwellian_kernel(TuckerDev Tk, const double *n, const do
 template <typename Real, int TS>
 int launch_step_TS(const TuckerStepParams &p, int grid, cudaStream_t s) {
   const size_t smem = smem_bytes<Real>(p.Nmax, p.R);
-  {  // the dynamic size plus the kernel's static shared memory may pass 48 KB
+  // the dynamic size plus the kernel's static shared memory may pass 48 KB; the
+  // opt-in is (re)raised outside stream captures
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cap);
+  if (cap == cudaStreamCaptureStatusNone) {
     cudaError_t e = cudaFuncSetAttribute(tucker_step_kernel<Real, TS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return -1;

@@ -26,6 +26,13 @@ struct TuckerState {
   double *ghostf = nullptr;  // [nghost][3][Nmax]
   double *err = nullptr;     // [nc]
   long long *phase = nullptr;  // [16] per-phase cycles (DVM_TUCKER_PHASES set)
+  int max_grid = 0;             // CTAs the scratch is sized for
+  bool tuned = false;           // grid picked by the autotuner
+  float tune_ms[5] = {0, 0, 0, 0, 0};  // step-kernel time per CTAs-per-SM candidate
+  cudaGraphExec_t graph = nullptr;     // two steps (returns to the same buffer parity)
+  int graph_parity = -1;               // S->cur / S->scur when the graph was captured
+  cudaStream_t gstream = nullptr;      // private stream the graph is captured on / replayed on
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;  // hand-offs with the caller's stream
 };
 
 int ctx_finalize_dt_from_macro(dvm_ctx *C, const std::vector<double> &macro);
@@ -193,6 +200,7 @@ int tucker_alloc(dvm_ctx *C) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, C->device);
   const int per_sm = std::min(4, tucker_step_blocks_per_sm(S->Nmax, R, S->fp64));
   S->grid = (int)std::min<int64_t>(nc, (int64_t)sms * per_sm);
+  S->max_grid = S->grid;
   S->stride = tucker_scratch_elems(C->N[0], C->N[1], C->N[2], R);
   S->stride = (S->stride + 63) & ~size_t(63);
   const size_t es = S->fp64 ? sizeof(double) : sizeof(float);
@@ -218,6 +226,10 @@ void tucker_free(dvm_ctx *C) {
       if (S->buf[b].fac[a]) cudaFree(S->buf[b].fac[a]);
     if (S->buf[b].rank) cudaFree(S->buf[b].rank);
   }
+  if (S->graph) cudaGraphExecDestroy(S->graph);
+  if (S->gstream) cudaStreamDestroy(S->gstream);
+  if (S->ev_in) cudaEventDestroy(S->ev_in);
+  if (S->ev_out) cudaEventDestroy(S->ev_out);
   if (S->scratch) cudaFree(S->scratch);
   if (S->ghostf) cudaFree(S->ghostf);
   if (S->err) cudaFree(S->err);
@@ -261,41 +273,144 @@ int tucker_init_from_full(dvm_ctx *C, const double *d_f_full) {
   return finish_init(C);
 }
 
+namespace {
+
+// one explicit step: step kernel (cur -> nxt), then the moments of the new
+// state about the previous velocity (with the residual parts)
+int enqueue_one_step(dvm_ctx *C, TuckerStepParams &p) {
+  TuckerState *S = C->tucker;
+  p.mode = 0;
+  p.cur = S->buf[S->cur];
+  p.nxt = S->buf[1 - S->cur];
+  p.sums = C->d_sums[S->scur];
+  if (launch_tucker_step(p, S->grid, S->fp64, C->stream) != 0) {
+    set_error("Tucker kernel needs more shared memory than the device allows");
+    return DVM_ERR_UNSUPPORTED;
+  }
+  S->cur = 1 - S->cur;
+  launch_macro_from_sums(C->d_sums[S->scur], C->d_macro, C->nc, C->w, C->stream);
+  TuckerMomentParams m = moment_params(C, S->buf[S->cur], C->d_sums[1 - S->scur]);
+  m.uref = C->d_macro + 1;
+  m.uref_stride = 8;
+  m.sums_prev = C->d_sums[S->scur];
+  m.respart = C->d_respart;
+  launch_tucker_moments(m, C->stream);
+  S->scur = 1 - S->scur;
+  return DVM_OK;
+}
+
+// Autotuner: time the step kernel once for each resident-CTAs-per-SM choice the
+// scratch allows (writing into the spare buffer, so the state is untouched; a
+// cell's arithmetic does not depend on which CTA runs it) and keep the fastest.
+int autotune(dvm_ctx *C) {
+  TuckerState *S = C->tucker;
+  S->tuned = true;
+  int sms = 1;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, C->device);
+  if (std::getenv("DVM_NO_AUTOTUNE") || C->nc <= sms) return DVM_OK;
+  TuckerStepParams p = step_params(C);
+  p.mode = 0;
+  p.cur = S->buf[S->cur];
+  p.nxt = S->buf[1 - S->cur];
+  p.sums = C->d_sums[S->scur];
+  p.phase = nullptr;
+  cudaEvent_t e0, e1;
+  DVM_CUDA_TRY(cudaEventCreate(&e0));
+  DVM_CUDA_TRY(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_grid = S->grid;
+  for (int per_sm = 1; per_sm <= 4; ++per_sm) {
+    const int grid = (int)std::min<int64_t>(C->nc, (int64_t)sms * per_sm);
+    if (grid > S->max_grid) break;
+    if (launch_tucker_step(p, grid, S->fp64, C->stream) != 0) break;  // warm-up
+    cudaEventRecord(e0, C->stream);
+    launch_tucker_step(p, grid, S->fp64, C->stream);
+    cudaEventRecord(e1, C->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    S->tune_ms[per_sm] = ms;
+    if (ms < best) {
+      best = ms;
+      best_grid = grid;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  S->grid = best_grid;
+  DVM_CUDA_TRY(cudaGetLastError());
+  return DVM_OK;
+}
+
+}  // namespace
+
 int tucker_step(dvm_ctx *C, int32_t nsteps, double *residual_out) {
   (void)residual_out;
   TuckerState *S = C->tucker;
+  if (!S->tuned) {
+    int rc = autotune(C);
+    if (rc != DVM_OK) return rc;
+  }
   TuckerStepParams p = step_params(C);
-  for (int32_t s = 0; s < nsteps; ++s) {
-    p.mode = 0;
-    p.cur = S->buf[S->cur];
-    p.nxt = S->buf[1 - S->cur];
-    p.sums = C->d_sums[S->scur];
-    if (launch_tucker_step(p, S->grid, S->fp64, C->stream) != 0) {
-      set_error("Tucker kernel needs more shared memory than the device allows");
-      return DVM_ERR_UNSUPPORTED;
+  int32_t s = 0;
+  // pairs of steps replay a captured CUDA graph (launch overhead paid once per
+  // pair); the graph is re-captured if the buffer parity differs
+  const bool use_graph = nsteps >= 2 && !S->phase && !std::getenv("DVM_NO_GRAPH");
+  if (use_graph) {
+    if (!S->gstream) {
+      DVM_CUDA_TRY(cudaStreamCreateWithFlags(&S->gstream, cudaStreamNonBlocking));
+      DVM_CUDA_TRY(cudaEventCreateWithFlags(&S->ev_in, cudaEventDisableTiming));
+      DVM_CUDA_TRY(cudaEventCreateWithFlags(&S->ev_out, cudaEventDisableTiming));
     }
-    {
-      cudaError_t e = cudaGetLastError();
-      if (e != cudaSuccess) {
-        set_error(std::string("Tucker step launch (grid ") + std::to_string(S->grid) + ", smem " +
-                  std::to_string(tucker_smem_bytes(S->Nmax, S->R, S->fp64)) + "): " +
-                  cudaGetErrorString(e));
-        return DVM_ERR_CUDA;
+    const int parity = S->cur * 2 + S->scur;
+    if (!S->graph || S->graph_parity != parity) {
+      if (S->graph) {
+        cudaGraphExecDestroy(S->graph);
+        S->graph = nullptr;
       }
+      cudaGraph_t g = nullptr;
+      cudaStream_t user = C->stream;
+      C->stream = S->gstream;  // capture the launches on the private stream
+      DVM_CUDA_TRY(cudaStreamBeginCapture(S->gstream, cudaStreamCaptureModeThreadLocal));
+      const int c0 = S->cur, s0 = S->scur;
+      int rc = enqueue_one_step(C, p);
+      if (rc == DVM_OK) rc = enqueue_one_step(C, p);
+      S->cur = c0;  // capture does not execute: restore the parity
+      S->scur = s0;
+      cudaError_t e = cudaStreamEndCapture(S->gstream, &g);
+      C->stream = user;
+      if (rc != DVM_OK) return rc;
+      DVM_CUDA_TRY(e);
+      e = cudaGraphInstantiate(&S->graph, g, 0);
+      cudaGraphDestroy(g);
+      DVM_CUDA_TRY(e);
+      S->graph_parity = parity;
     }
-    S->cur = 1 - S->cur;
-    // moments of the new state about the previous velocity (+ residual parts)
-    launch_macro_from_sums(C->d_sums[S->scur], C->d_macro, C->nc, C->w, C->stream);
-    TuckerMomentParams m = moment_params(C, S->buf[S->cur], C->d_sums[1 - S->scur]);
-    m.uref = C->d_macro + 1;
-    m.uref_stride = 8;
-    m.sums_prev = C->d_sums[S->scur];
-    m.respart = C->d_respart;
-    launch_tucker_moments(m, C->stream);
-    S->scur = 1 - S->scur;
+    // the graph runs on the private stream, ordered after and before the
+    // caller's stream by events
+    DVM_CUDA_TRY(cudaEventRecord(S->ev_in, C->stream));
+    DVM_CUDA_TRY(cudaStreamWaitEvent(S->gstream, S->ev_in, 0));
+    for (; s + 2 <= nsteps; s += 2) {
+      DVM_CUDA_TRY(cudaGraphLaunch(S->graph, S->gstream));
+      C->steps += 2;
+    }
+    DVM_CUDA_TRY(cudaEventRecord(S->ev_out, S->gstream));
+    DVM_CUDA_TRY(cudaStreamWaitEvent(C->stream, S->ev_out, 0));
+  }
+  for (; s < nsteps; ++s) {
+    int rc = enqueue_one_step(C, p);
+    if (rc != DVM_OK) return rc;
     C->steps++;
   }
   DVM_CUDA_TRY(cudaGetLastError());
+  return DVM_OK;
+}
+
+int tucker_launch_info(dvm_ctx *C, int32_t *grid, float *tune_ms) {
+  TuckerState *S = C->tucker;
+  if (grid) *grid = S->grid;
+  if (tune_ms)
+    for (int i = 0; i < 5; ++i) tune_ms[i] = S->tune_ms[i];
   return DVM_OK;
 }
 

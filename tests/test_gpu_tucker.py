@@ -197,3 +197,18 @@ def test_tucker_memory_is_compressed(dvm):
     fb, _ = dvm.dvm_memory(s.h)
     assert fb <= wl.n_cell * (8 ** 3 + 3 * 16 * 8) * 8
     assert fb < 0.6 * wl.n_cell * 16 ** 3 * 8
+
+
+def test_graph_replay_equals_single_steps(dvm):
+    """Multi-step calls replay a captured CUDA graph of two steps on a private stream;
+    the state must equal single-step calls bitwise (and the autotuner's choice of grid
+    must not change it)."""
+    wl = W.cavity(nside=6, N=12, seed=3)
+    a = tucker_solver(dvm, wl, 8, 1e-6, precision=MIXED)
+    b = tucker_solver(dvm, wl, 8, 1e-6, precision=MIXED)
+    for _ in range(7):
+        a.step(1, residual=False)
+    b.step(7, residual=False)
+    assert np.array_equal(a.f(), b.f())
+    grid, tune = dvm.dvm_get_launch_config(a.h)
+    assert grid >= 1 and len(tune) == 5
