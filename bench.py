@@ -47,6 +47,8 @@ def _args():
     ap.add_argument("--workload", default="cavity")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other path, the accuracy check and the serving run")
     return ap.parse_args()
 
 
@@ -192,6 +194,104 @@ def run_reference(args, rank, world):
 
 
 # --------------------------------------------------------------------------
+FLOPS_PER_UPDATE = 28      # FP64 flops per cell.node of the fused full-grid step
+FP64_PEAK_GFLOPS = 1250.0  # nominal GB300 FP64 rate (152 SMs x 2 FMA/clk x 2 x ~2.06 GHz)
+
+
+def _time_steps(solver, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        solver.step(1, residual=False)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    solver.step(steps, residual=False)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+def tucker_accuracy(P, cap, tol, precision, steps=300):
+    """Tucker path vs the FP64 full-grid oracle on a reduced cavity (8^3 cells x 24^3)."""
+    import oracle
+    import workloads as W
+    wl = W.cavity(nside=8, N=24)
+    o = oracle.FullGridOracle(wl)
+    o.step(steps, o.dt())
+    fo, mo = o.f(), o.macro()
+    s = P.Solver(wl, format=1, precision=precision, rank_cap=cap, tol=tol)
+    s.step(steps, residual=False)
+    fg, mg = s.f(), s.moments()
+    ranks = P.dvm_get_ranks(s.h)
+    s.close()
+    un = max(np.linalg.norm(mo[:, 1:4]), 0.2 * np.sqrt(wl.n_cell))
+    qn = max(np.linalg.norm(mo[:, 5:8]), np.linalg.norm(0.5 * mo[:, 0] * mo[:, 4] ** 1.5))
+    return {"workload": f"cavity_8^3x24^3, {steps} steps", "eps": tol, "rank_cap": cap,
+            "f": _rel(fg, fo), "n": _rel(mg[:, 0], mo[:, 0]), "T": _rel(mg[:, 4], mo[:, 4]),
+            "u": float(np.linalg.norm(mg[:, 1:4] - mo[:, 1:4]) / un),
+            "q": float(np.linalg.norm(mg[:, 5:8] - mo[:, 5:8]) / qn),
+            "rank_mean": float(ranks.mean()), "rank_max": int(ranks.max()),
+            "note": "u relative to max(|u|, lid speed), q to max(|q|, n T^1.5 / 2); vs FP64 oracle"}
+
+
+def run_serving(P, n_req=16, seed=7, mean_gap_s=0.25, budget_gb=64, slots=8):
+    """Seeded Poisson arrivals of steady channel solves (Poiseuille / thermal
+    transpiration), Tucker mixed format, each run to residual 1e-4."""
+    import workloads as W
+    rng = np.random.default_rng(seed)
+    reqs = []
+    t = 0.0
+    for i in range(n_req):
+        t += rng.exponential(mean_gap_s)
+        kind = "poiseuille" if rng.random() < 0.5 else "transpiration"
+        ncell = int(np.exp(rng.uniform(np.log(256), np.log(2048))))
+        N = int(rng.choice([12, 16, 24]))
+        Kn = float(np.exp(rng.uniform(np.log(0.1), np.log(10.0))))
+        cap = int(rng.integers(6, 13))
+        wl = W.channel(n_cell_target=ncell, N=N, Kn=Kn, kind=kind, seed=i)
+        reqs.append((t, wl, cap))
+    srv = P.Server(int(budget_gb * (1 << 30)), slots)
+    t0 = time.perf_counter()
+    tickets = []
+    k = 0
+    while True:
+        now = time.perf_counter() - t0
+        while k < n_req and reqs[k][0] <= now:
+            _, wl, cap = reqs[k]
+            tickets.append((srv.submit(wl, format=1, precision=1, rank_cap=cap, tol=1e-6,
+                                       res_tol=1e-4, max_steps=6000, check_every=25), wl))
+            k += 1
+        pending = srv.run(0.02)
+        if k == n_req and pending == 0:
+            break
+    total = time.perf_counter() - t0
+    lat, conv, upd, states, errors = [], 0, 0, {}, set()
+    for tk, wl in tickets:
+        st = srv.poll(tk)
+        lat.append(st["latency_s"])
+        conv += st["state"] == 2
+        states[st["state"]] = states.get(st["state"], 0) + 1
+        if st["state"] == 4:
+            errors.add(srv.error(tk))
+        upd += st["steps"] * wl.n_cell * wl.nodes_per_cell
+    srv.close()
+    lat = np.array(lat)
+    return {"requests": n_req, "converged": int(conv),
+            "states": {["queued", "running", "converged", "not_converged", "failed"][k]: v
+                       for k, v in sorted(states.items())},
+            "errors": sorted(errors), "wall_s": total,
+            "solves_per_hour": 3600.0 * n_req / total, "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)), "updates_per_s": upd / total,
+            "mix": "channel Poiseuille/transpiration, 256-2048 cells, 12^3-24^3, Kn 0.1-10, "
+                   "Tucker mixed eps 1e-6 cap 6-12, residual 1e-4, Poisson arrivals "
+                   f"(mean gap {mean_gap_s} s, seed {seed}), {slots} slots"}
+
+
 def run_gpu(args, rank, world):
     import torch
     import paper_1912_04582_gb300 as P
@@ -205,12 +305,14 @@ def run_gpu(args, rank, world):
         dist.init_process_group("nccl")
     stream = torch.cuda.current_stream()
     wl = make_workload(args.workload)
-    fmt = NAT.DVM_FORMAT_TUCKER if args.path == "tucker" else NAT.DVM_FORMAT_FULL
-    prec = NAT.DVM_PREC_MIXED if args.precision == "mixed" else NAT.DVM_PREC_FP64
-    s = P.Solver(wl, format=fmt, precision=prec, stream=stream.cuda_stream,
-                 rank_cap=args.rank_cap, tol=args.tol)
     upd = wl.n_cell * wl.nodes_per_cell
+    prec = NAT.DVM_PREC_MIXED if args.precision == "mixed" else NAT.DVM_PREC_FP64
+    cap = args.rank_cap or 12
+    tol = args.tol or 1e-6
 
+    # headline path, timed with the clock sampler running
+    fmt = NAT.DVM_FORMAT_TUCKER if args.path == "tucker" else NAT.DVM_FORMAT_FULL
+    s = P.Solver(wl, format=fmt, precision=prec, rank_cap=cap, tol=tol, stream=stream.cuda_stream)
     for _ in range(args.warmup):
         s.step(1, residual=False)
     torch.cuda.synchronize()
@@ -229,53 +331,80 @@ def run_gpu(args, rank, world):
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    res = s.step(1)  # residual check after the timed region (state stays physical)
+    res = s.step(1)
     value = world * upd * args.steps / (ms / 1e3)
-    launches_per_step = 1 if args.path == "full" else None
-
-    # roofline of the dominant kernel (the fused step: one launch per step)
-    peaks, src = _peaks()
     kern_ms = ms / args.steps
-    alg_bytes = 2 * 8 * upd                  # read f^n once, write f^{n+1} once (FP64)
-    achieved = alg_bytes / (kern_ms / 1e3) / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": _traffic("full"),
-            "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else src,
-            "kernel": "full_step_kernel", "alg_bytes_per_launch": alg_bytes}
 
-    # end-to-end through the C ABI with host buffers: H2D of f, one step, D2H of moments
-    e2e = None
-    if not args.no_e2e and rank == 0:
-        f_host = torch.empty((wl.n_cell,) + tuple(wl.N), dtype=torch.float64, pin_memory=True)
-        f_np = f_host.numpy()
-        f_np[...] = s.f()
-        k = max(3, min(args.steps, 10))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(k):
-            P.dvm_init_f(s.h, f_np)
-            s.step(1, residual=False)
-            m = s.moments()
-        el = time.perf_counter() - t0
-        e2e = {"value": upd * k / el, "unit": UNIT, "h2d_bytes_per_step": int(f_np.nbytes),
-               "d2h_bytes_per_step": int(m.nbytes),
-               "note": "per step: dvm_init_f from pinned host f, dvm_step, dvm_moments to host"}
+    peaks, src = _peaks()
+    if args.path == "full":
+        achieved = FLOPS_PER_UPDATE * upd / (kern_ms / 1e3) / 1e9
+        hbm = 2 * 8 * upd / (kern_ms / 1e3) / 1e9
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                "frac": achieved / FP64_PEAK_GFLOPS, "traffic": _traffic("full"),
+                "peak_source": "FP64 nominal from unit counts and clock (1.197 TFLOP/s measured "
+                               "by an FMA probe on this pool)",
+                "kernel": "full_step_kernel", "alg_flops_per_launch": FLOPS_PER_UPDATE * upd,
+                "hbm": {"achieved": hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": hbm / peaks["hbm_gbs"], "alg_bytes_per_launch": 16 * upd,
+                        "peak_source": f"{src} MEASURED_PEAKS.json hbm_gbs"}}
+        launches = args.steps
+    else:
+        roof = {"bound": "alu", "kernel": "tucker_step_kernel", "achieved": None,
+                "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": None, "traffic": None,
+                "note": "latency-bound per-cell eigen-solves; see profiles/"}
+        launches = 3 * args.steps
 
     line = None
     if rank == 0:
+        paths = {}
+        # the other path on the same workload
+        if args.path == "full" and not args.no_extras:
+            t = P.Solver(wl, format=1, precision=NAT.DVM_PREC_MIXED, rank_cap=cap, tol=tol,
+                         stream=stream.cuda_stream)
+            tms = _time_steps(t, args.steps, args.warmup, stream) / args.steps
+            fb, _ = P.dvm_memory(t.h)
+            grid, tune = P.dvm_get_launch_config(t.h)
+            r = P.dvm_get_ranks(t.h)
+            paths["tucker_mixed"] = {
+                "ms_per_step": tms, "updates_per_s": upd / (tms / 1e3), "eps": tol,
+                "rank_cap": cap, "rank_mean": float(r.mean()), "rank_max": int(r.max()),
+                "f_bytes": fb, "compression": fb / (8.0 * upd), "grid": grid,
+                "autotune_ms_by_ctas_per_sm": tune[1:], "launches_per_step": 3}
+            t.close()
+        fbf, _ = P.dvm_memory(s.h)
+        paths[args.path + ("_fp64" if prec == NAT.DVM_PREC_FP64 else "_mixed")] = {
+            "ms_per_step": kern_ms, "updates_per_s": upd / (kern_ms / 1e3), "f_bytes": fbf}
+        e2e = None
+        if not args.no_e2e:
+            f_host = torch.empty((wl.n_cell,) + tuple(wl.N), dtype=torch.float64, pin_memory=True)
+            f_np = f_host.numpy()
+            f_np[...] = s.f()
+            k = max(3, min(args.steps, 10))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(k):
+                P.dvm_init_f(s.h, f_np)
+                s.step(1, residual=False)
+                m = s.moments()
+            el = time.perf_counter() - t0
+            e2e = {"value": upd * k / el, "unit": UNIT, "h2d_bytes_per_step": int(f_np.nbytes),
+                   "d2h_bytes_per_step": int(m.nbytes),
+                   "note": "per step: dvm_init_f from pinned host f, dvm_step, dvm_moments to host"}
         cfg = {**wl.describe(), "path": args.path,
-               "format": "full tensor FP64" if args.path == "full" else "Tucker",
+               "format": "full tensor FP64" if args.path == "full" else f"Tucker {args.precision}",
                "l2": f"inputs larger than L2 ({8 * upd / 1e9:.2f} GB per copy of f)",
                "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"}
-        clocks = clk.summary()
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": kern_ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64", "data": "synthetic", "config": cfg, "roofline": roof,
-                "gpu_launches": (launches_per_step * args.steps) if launches_per_step else None,
-                "clocks": clocks, "residual_after": res}
+                "dtype": "f64" if args.path == "full" or prec == NAT.DVM_PREC_FP64 else "f32+f64",
+                "data": "synthetic", "config": cfg, "roofline": roof, "gpu_launches": launches,
+                "clocks": clk.summary(), "residual_after": res, "paths": paths}
         if e2e:
             line["e2e"] = e2e
+        if not args.no_extras:
+            line["tucker_accuracy"] = tucker_accuracy(P, cap, tol, NAT.DVM_PREC_MIXED)
+            line["serving"] = run_serving(P)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(wl)
         print(json.dumps(line), flush=True)

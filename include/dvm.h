@@ -255,6 +255,10 @@ int dvm_server_poll(dvm_server *srv, int64_t ticket, int32_t *state, int64_t *st
  * memory was released). */
 int dvm_server_result(dvm_server *srv, int64_t ticket, double *macro);
 
+/* Message of a failed request ("" otherwise); valid until the server is
+ * destroyed. */
+const char *dvm_server_error(dvm_server *srv, int64_t ticket);
+
 void dvm_server_destroy(dvm_server *srv);
 
 /* Macroparameters [n, u1, u2, u3, T, q1, q2, q3] of n_cell full tensors that

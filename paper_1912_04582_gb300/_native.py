@@ -99,6 +99,7 @@ SIGNATURES = {
     "dvm_server_run": (ctypes.c_int, [_P, ctypes.c_double, _c_i64p]),
     "dvm_server_poll": (ctypes.c_int, [_P, ctypes.c_int64, _c_i32p, _c_i64p, _c_dp, _c_dp]),
     "dvm_server_result": (ctypes.c_int, [_P, ctypes.c_int64, _c_dp]),
+    "dvm_server_error": (ctypes.c_char_p, [_P, ctypes.c_int64]),
     "dvm_server_destroy": (None, [_P]),
     "dvm_destroy": (None, [_P]),
     "dvm_last_error": (ctypes.c_char_p, []),

@@ -317,6 +317,9 @@ class Server:
         return {"state": int(st.value), "steps": int(steps.value), "residual": float(res.value),
                 "latency_s": float(lat.value)}
 
+    def error(self, ticket):
+        return N_lib().dvm_server_error(self.ptr, int(ticket)).decode(errors="replace")
+
     def result(self, ticket, n_cell):
         out = np.empty((n_cell, 8))
         _n.check(N_lib().dvm_server_result(self.ptr, int(ticket), _dp(out)), "dvm_server_result")
@@ -352,6 +355,10 @@ def dvm_server_poll(srv, ticket):
 
 def dvm_server_result(srv, ticket, n_cell):
     return srv.result(ticket, n_cell)
+
+
+def dvm_server_error(srv, ticket):
+    return srv.error(ticket)
 
 
 def dvm_server_destroy(srv):

@@ -55,6 +55,7 @@ struct Request {
   double res = INFINITY;
   double t_submit = 0.0, t_done = 0.0;
   std::vector<double> macro;
+  std::string error;  // message of the failure, if any
 };
 
 size_t estimate(const dvm_request *q) {
@@ -137,6 +138,7 @@ int start(Request &r) {
 
 void finish(Request &r, dvm_server *S, int32_t state) {
   r.state = state;
+  if (state == DVM_REQ_FAILED && r.error.empty()) r.error = dvm_last_error();
   r.t_done = now_s();
   if (r.ctx && state != DVM_REQ_FAILED) {
     r.macro.resize(8 * (size_t)r.n_cell);
@@ -262,12 +264,17 @@ int dvm_server_run(dvm_server *S, double max_seconds, int64_t *pending) {
       int32_t done = -1;
       if (q != cudaSuccess) {
         cudaGetLastError();
+        r.error = std::string("device error: ") + cudaGetErrorString(q);
         done = DVM_REQ_FAILED;
       } else {
         r.res = r.h_out[0];
         int flag = 0;
         std::memcpy(&flag, r.h_out + 1, sizeof flag);
-        if (flag != 0 || !std::isfinite(r.res)) done = DVM_REQ_FAILED;
+        if (flag != 0 || !std::isfinite(r.res)) {
+          r.error = flag != 0 ? "non-physical state: n <= 0 or T <= 0 in some cell"
+                              : "residual is not finite";
+          done = DVM_REQ_FAILED;
+        }
         else if (r.res <= r.tol) done = DVM_REQ_CONVERGED;
         else if (r.steps >= r.max_steps) done = DVM_REQ_NOT_CONVERGED;
         else if (launch_chunk(r) != DVM_OK) done = DVM_REQ_FAILED;
@@ -311,6 +318,12 @@ int dvm_server_result(dvm_server *S, int64_t ticket, double *macro) {
   }
   std::memcpy(macro, it->second.macro.data(), sizeof(double) * it->second.macro.size());
   return DVM_OK;
+}
+
+const char *dvm_server_error(dvm_server *S, int64_t ticket) {
+  if (!S) return "";
+  auto it = S->reqs.find(ticket);
+  return it == S->reqs.end() ? "unknown ticket" : it->second.error.c_str();
 }
 
 void dvm_server_destroy(dvm_server *S) {

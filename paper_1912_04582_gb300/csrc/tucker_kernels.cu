@@ -1025,18 +1025,39 @@ __global__ void tucker_maxwellian_kernel(TuckerDev Tk, const double *n, const do
     Tk.core[c * (int64_t)R * R * R] = n[c] / pow(kPi * T, 1.5) * s_norm[0] * s_norm[1] * s_norm[2];
 }
 
+// The kernels' dynamic shared-memory opt-in is a per-function setting shared by
+// every context in the process: only ever raise it (to the largest size any
+// context needs), and do so outside stream captures (tucker_prepare_launch is
+// called when a context is created).
+template <typename K>
+int raise_smem_optin(K kernel, size_t smem, size_t &opted) {
+  if (smem <= opted) return 0;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  opted = smem;
+  return 0;
+}
+
+template <typename Real, int TS>
+struct OptIn {
+  static size_t step, expand;
+};
+template <typename Real, int TS>
+size_t OptIn<Real, TS>::step = 0;
+template <typename Real, int TS>
+size_t OptIn<Real, TS>::expand = 0;
+
 template <typename Real, int TS>
 int launch_step_TS(const TuckerStepParams &p, int grid, cudaStream_t s) {
   const size_t smem = smem_bytes<Real>(p.Nmax, p.R);
-  // the dynamic size plus the kernel's static shared memory may pass 48 KB; the
-  // opt-in is (re)raised outside stream captures
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(s, &cap);
-  if (cap == cudaStreamCaptureStatusNone) {
-    cudaError_t e = cudaFuncSetAttribute(tucker_step_kernel<Real, TS>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return -1;
-  }
+  if (cap == cudaStreamCaptureStatusNone &&
+      raise_smem_optin(tucker_step_kernel<Real, TS>, smem, OptIn<Real, TS>::step) != 0)
+    return -1;
   tucker_step_kernel<Real, TS><<<grid, kTB, smem, s>>>(p);
   return 0;
 }
@@ -1050,11 +1071,7 @@ template <typename Real>
 int launch_expand_T(const TuckerDev &T, int64_t c0, int64_t ncell, int N1, int N2, int N3, int R,
                     int Nmax, void *scratch, size_t stride, double *out, int grid, cudaStream_t s) {
   const size_t smem = smem_bytes<Real>(Nmax, R);
-  {
-    cudaError_t e = cudaFuncSetAttribute(tucker_expand_kernel<Real>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return -1;
-  }
+  if (raise_smem_optin(tucker_expand_kernel<Real>, smem, OptIn<Real, 0>::expand) != 0) return -1;
   tucker_expand_kernel<Real><<<grid, kTB, smem, s>>>(T, c0, ncell, N1, N2, N3, R, Nmax, scratch,
                                                      stride, out);
   return 0;
@@ -1070,11 +1087,7 @@ size_t tucker_scratch_elems(int N1, int N2, int N3, int R) {
 template <typename Real, int TS>
 int blocks_per_sm_TS(int Nmax, int R) {
   const size_t smem = smem_bytes<Real>(Nmax, R);
-  if (cudaFuncSetAttribute(tucker_step_kernel<Real, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem) != cudaSuccess) {
-    cudaGetLastError();
-    return 1;
-  }
+  if (raise_smem_optin(tucker_step_kernel<Real, TS>, smem, OptIn<Real, TS>::step) != 0) return 1;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tucker_step_kernel<Real, TS>, kTB, smem) !=
       cudaSuccess) {
