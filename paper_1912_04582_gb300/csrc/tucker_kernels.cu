@@ -354,7 +354,7 @@ __device__ void gram(const Real *T, const int D[3], int m, Smem<Real> &sm) {
 }
 
 // ---------------------------------------------------------------------------
-// FP64 dense helpers on shared-memory matrices (row-major).
+// Dense helpers on shared-memory matrices (row-major).
 
 // W[n x k] = C[n x n] Q[n x k]
 template <typename T>
@@ -368,106 +368,7 @@ __device__ void mat_cq(const T *C, const T *Q, T *W, int n, int k) {
   __syncthreads();
 }
 
-__device__ __forceinline__ double start_value(int i, int j);
-
 constexpr int kOrthMax = 24;  // largest number of basis columns
-
-__device__ __forceinline__ double start_value(int i, int j);
-
-// Orthonormalise the k <= n columns of Q (n x k, row-major) in place by
-// Cholesky-QR: G = Q^T Q in FP64 (all threads), its Cholesky factor by one
-// thread, Q <- Q L^{-T} (one thread per row).
-//  * final == false (the power iterations): two passes, the first with a
-//    relative shift of trace(G) (1e-5 for FP32 data, 1e-12 for FP64; shifted
-//    Cholesky-QR, Fukaya et al. 2020), which keeps nearly dependent columns
-//    from breaking the factorisation; the result is approximately orthonormal,
-//    which is all those iterations need.
-//  * final == true (FP64 data, the last step): three passes; a column whose
-//    squared norm after removing its projections on the previous columns drops
-//    below 1e-10 of its own is numerically dependent; it is replaced by a fresh
-//    start vector and the passes repeated (at most three rounds), so the basis
-//    keeps full rank k (any column still dependent after that is zero).
-// Returns the number of non-zero columns.  G uses the k x k scratch `Gs`,
-// `dinv` the reciprocal pivots.  Ends with a block barrier.
-template <typename T>
-__device__ int orthonormalise(T *Q, int n, int k, double *Gs, double *dinv, bool final) {
-  const bool f32 = sizeof(T) == 4;
-  const int passes = final ? 3 : 2;
-  __shared__ int s_dep;
-  for (int round = 0; round < (final ? 3 : 1); ++round) {
-    for (int pass = 0; pass < passes; ++pass) {
-      for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
-        const int a = idx / k, b = idx - a * k;
-        if (a > b) continue;
-        double s = 0.0;
-        for (int r = 0; r < n; ++r) s = fma((double)Q[r * k + a], (double)Q[r * k + b], s);
-        Gs[a * k + b] = s;
-        Gs[b * k + a] = s;
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        double tr = 0.0;
-        for (int a = 0; a < k; ++a) tr += Gs[a * k + a];
-        const double shift = (!final && pass == 0) ? (f32 ? 1e-5 : 1e-12) * tr : 0.0;
-        int ndep = 0;
-        for (int j = 0; j < k; ++j) {  // in-place lower Cholesky factor of G + shift I
-          const double gjj = Gs[j * k + j];
-          double d = gjj + shift;
-          for (int i = 0; i < j; ++i) d = fma(-Gs[j * k + i], Gs[j * k + i], d);
-          const bool dependent = final ? (!(d > 1e-10 * gjj) || !(d > 1e-300)) : !(d > 1e-300);
-          if (dependent) {
-            ++ndep;
-            dinv[j] = 0.0;
-            Gs[j * k + j] = 1.0;
-            for (int r = j + 1; r < k; ++r) Gs[r * k + j] = 0.0;
-            for (int i = 0; i < j; ++i) Gs[j * k + i] = 0.0;
-            continue;
-          }
-          double ljj, inv;
-          if (f32) {
-            inv = (double)rsqrtf((float)d);
-            ljj = d * inv;
-          } else {
-            ljj = sqrt(d);
-            inv = 1.0 / ljj;
-          }
-          Gs[j * k + j] = ljj;
-          dinv[j] = inv;
-          for (int r = j + 1; r < k; ++r) {
-            double v = Gs[r * k + j];
-            for (int i = 0; i < j; ++i) v = fma(-Gs[r * k + i], Gs[j * k + i], v);
-            Gs[r * k + j] = v * inv;
-          }
-        }
-        s_dep = ndep;
-      }
-      __syncthreads();
-      // each row x of Q solves y L^T = x: y_j = (x_j - sum_{i<j} y_i L_ji) / L_jj
-      for (int r = threadIdx.x; r < n; r += blockDim.x) {
-        double y[kOrthMax];
-        for (int j = 0; j < k; ++j) {
-          double v = (double)Q[r * k + j];
-          for (int i = 0; i < j; ++i) v = fma(-y[i], Gs[j * k + i], v);
-          y[j] = v * dinv[j];
-        }
-        for (int j = 0; j < k; ++j) Q[r * k + j] = (T)y[j];
-      }
-      __syncthreads();
-    }
-    if (!final || s_dep == 0 || round == 2) break;
-    // final step: dependent columns (now zero) are replaced by fresh start
-    // vectors and the passes repeated, so the basis keeps full rank
-    for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) {
-      const int j = idx % k;
-      if (dinv[j] == 0.0) Q[idx] = (T)start_value(idx / k, j + 131 * (round + 1));
-    }
-    __syncthreads();
-  }
-  int nz = 0;
-  for (int j = 0; j < k; ++j) nz += dinv[j] != 0.0;
-  __syncthreads();
-  return nz;
-}
 
 // deterministic start vectors in [-1, 1)
 __device__ __forceinline__ double start_value(int i, int j) {
@@ -480,40 +381,184 @@ __device__ __forceinline__ double start_value(int i, int j) {
   return (double)(h & 0xFFFFFF) / 8388608.0 - 1.0;
 }
 
-// Leading eigenvectors of the n x n Gram matrix sm.C by orthogonal iteration
-// from fixed start vectors.  On exit sm.W holds k orthonormal columns ordered by
-// their Rayleigh quotients (descending), sm.B[perm[j]] the quotient of column j.
-// Returns k.
-template <typename Real>
-__device__ int leading_eigs(Smem<Real> &sm, int n, int R, const double *warm, int r_warm,
-                             PhaseClock &pc) {
-  int k = n < R + kExtra ? n : R + kExtra;
-  if (k > kOrthMax) k = kOrthMax;
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
+
+// G = Q^T Q for the k columns of Q (n x k), accumulated in A, both triangles.
+template <typename T, typename A>
+__device__ void gram_cols(const T *Q, int n, int k, A *Gs) {
+  for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
+    const int a = idx / k, b = idx - a * k;
+    if (a > b) continue;
+    A s = 0;
+    for (int r = 0; r < n; ++r) s = fma((A)Q[r * k + a], (A)Q[r * k + b], s);
+    Gs[a * k + b] = s;
+    Gs[b * k + a] = s;
+  }
+}
+
+// Cholesky factor of the k x k symmetric matrix Gs + shift I, by warp 0: lane i
+// keeps row i in registers; right-looking, the pivot and the new column entries
+// are broadcast by shuffles.  On exit the lower triangle of Gs holds L and
+// dinv[j] = 1 / L_jj.  Column j is dependent when its pivot is not positive or
+// not above rel * G_jj (the part of the column outside the span of the previous
+// ones has lost all accurate digits): dinv[j] = 0, so the solve below zeroes
+// it.  Returns the number of dependent columns (the same on every lane).
+// Called by warp 0 only; KM >= k bounds the register arrays.
+template <typename A, int KM>
+__device__ __noinline__ int chol_warp(A *Gs, A *dinv, int k, A shift, A rel) {
+  const int lane = threadIdx.x & 31;
+  const A tiny = (A)(sizeof(A) == 8 ? 1e-300 : 1e-30);
+  A g[KM];
+  A diag0 = 0;
+#pragma unroll
+  for (int c = 0; c < KM; ++c) {
+    A v = (lane < k && c < k) ? Gs[lane * k + c] : A(0);
+    if (c == lane) {
+      diag0 = v;
+      v += shift;
+    }
+    g[c] = v;
+  }
+  int ndep = 0;
+#pragma unroll
+  for (int j = 0; j < KM; ++j) {
+    if (j < k) {
+      const A d = __shfl_sync(0xffffffffu, g[j], j);
+      const A d0 = __shfl_sync(0xffffffffu, diag0, j);
+      const bool dep = !(d > tiny) || !(d > rel * d0);
+      const A inv = dep ? A(0) : rsqrt_t(d);
+      ndep += dep;
+      const A lij = lane > j ? g[j] * inv : A(0);
+#pragma unroll
+      for (int c = j + 1; c < KM; ++c)
+        if (c < k) g[c] = fma(-lij, __shfl_sync(0xffffffffu, lij, c), g[c]);
+      if (lane == j) {
+        g[j] = dep ? A(1) : d * inv;
+        dinv[j] = inv;
+      } else if (lane > j) {
+        g[j] = lij;
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < KM; ++c)
+    if (lane < k && c <= lane) Gs[lane * k + c] = g[c];
+  __syncwarp();
+  return ndep;
+}
+
+// Q <- Q L^{-T}: every row x of Q solves y L^T = x (forward substitution, one
+// thread per row, the row held in registers).
+template <typename T, typename A, int KM>
+__device__ __noinline__ void solve_rows(T *Q, int n, int k, const A *L, const A *dinv) {
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    A y[KM];
+#pragma unroll
+    for (int j = 0; j < KM; ++j) {
+      if (j < k) {
+        A v = (A)Q[r * k + j];
+#pragma unroll
+        for (int i = 0; i < j; ++i) v = fma(-y[i], L[j * k + i], v);
+        y[j] = v * dinv[j];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < KM; ++j)
+      if (j < k) Q[r * k + j] = (T)y[j];
+  }
+}
+
+// Orthonormalise the k <= n columns of Q (n x k, row-major) in place by
+// Cholesky-QR repeated `passes` times: G = Q^T Q, its Cholesky factor L, then
+// Q <- Q L^{-T}; arithmetic in A.  The first pass factors G + shift_rel *
+// trace(G) I instead (shifted Cholesky-QR, Fukaya et al. 2020): the shift keeps
+// the factorisation from breaking down on nearly dependent columns while leaving
+// span(Q) unchanged, and the following unshifted passes restore orthonormality
+// to the working precision.  With reseed (the last step of an eigen-solve, where
+// the basis must keep full rank), the unshifted passes also flag columns that
+// are numerically dependent (pivot <= 1e-10 G_jj); flagged columns are replaced
+// by fresh start vectors and two more passes run (at most two such rounds).
+// Without reseed a dependent column is zeroed.  Returns the number of non-zero
+// columns.  Gs (k x k) and dinv (k) are scratch in shared memory; ends with a
+// barrier.
+template <typename T, typename A>
+__device__ __noinline__ int orthonormalise(T *Q, int n, int k, A *Gs, A *dinv, int passes,
+                                           double shift_rel, bool reseed) {
+  __shared__ int s_dep;
+  for (int round = 0; round < 3; ++round) {
+    for (int pass = 0; pass < passes; ++pass) {
+      const bool shifted = round == 0 && pass == 0;
+      gram_cols<T, A>(Q, n, k, Gs);
+      __syncthreads();
+      if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        A tr = lane < k ? Gs[lane * k + lane] : A(0);
+        for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+        const A shift = shifted ? (A)shift_rel * tr : A(0);
+        const A rel = (reseed && !shifted) ? A(1e-10) : A(0);
+        const int ndep = k <= 16 ? chol_warp<A, 16>(Gs, dinv, k, shift, rel)
+                                 : chol_warp<A, kOrthMax>(Gs, dinv, k, shift, rel);
+        if (lane == 0) s_dep = ndep;
+      }
+      __syncthreads();
+      if (k <= 16)
+        solve_rows<T, A, 16>(Q, n, k, Gs, dinv);
+      else
+        solve_rows<T, A, kOrthMax>(Q, n, k, Gs, dinv);
+      __syncthreads();
+    }
+    if (!reseed || s_dep == 0 || round == 2) break;
+    for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) {
+      const int j = idx % k;
+      if (dinv[j] == A(0)) Q[idx] = (T)start_value(idx / k, j + 131 * (round + 1));
+    }
+    __syncthreads();
+    passes = 2;
+  }
+  const int nz = k - s_dep;
+  __syncthreads();
+  return nz;
+}
+
+// Leading eigenvectors of the n x n Gram matrix sm.C by orthogonal (block
+// power) iteration with k basis columns: the start block is the warm basis
+// (r_warm columns, row stride ldw: the previous step's orthonormal factor, which
+// spans most of the new dominant subspace) completed by fixed start vectors.
+// FP64 path: FP64 iterations.  Mixed path: FP32 iterations on the rounded Gram
+// matrix, then one FP64 step on the accurate one.  Every path ends with an FP64
+// shifted Cholesky-QR3, so the basis is orthonormal to FP64 round-off.  On exit
+// sm.W holds the k columns ordered by their Rayleigh quotients (descending), sm.Z
+// the sorted quotients, sm.par[29] the number of non-zero columns.  Returns k.
+template <typename Real, typename WT>
+__device__ __noinline__ int leading_eigs(Smem<Real> &sm, int n, int k, const WT *warm, int ldw, int r_warm,
+                            PhaseClock &pc) {
   if (!warm) r_warm = 0;
-  // start block: the previous step's orthonormal factor, when there is one (it
-  // spans most of the new dominant subspace), completed by fixed start vectors
+  if (r_warm > k) r_warm = k;
   const int iters = r_warm > 0 ? kWarmIter : kPower;
+  float *G32 = reinterpret_cast<float *>(sm.B), *d32 = reinterpret_cast<float *>(sm.cs);
   if (sizeof(Real) == 8) {
     for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) {
       const int i = idx / k, j = idx - i * k;
-      sm.Q[idx] = j < r_warm ? warm[(int64_t)i * R + j] : start_value(i, j);
+      sm.Q[idx] = j < r_warm ? (double)warm[(int64_t)i * ldw + j] : start_value(i, j);
     }
     __syncthreads();
-    int nz = k;
     for (int it = 0; it < iters; ++it) {
       mat_cq(sm.C, sm.Q, sm.W, n, k);
       for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) sm.Q[idx] = sm.W[idx];
       __syncthreads();
-      nz = orthonormalise(sm.Q, n, k, sm.B, sm.cs, it == iters - 1);
+      pc.mark(11);
+      const bool last = it == iters - 1;
+      const int nz = orthonormalise<double, double>(sm.Q, n, k, sm.B, sm.cs, last ? 3 : 2,
+                                                    last ? 1e-11 : 1e-12, last);
+      if (threadIdx.x == 0) sm.par[29] = (double)nz;
+      pc.mark(12);
     }
-    if (threadIdx.x == 0) sm.par[29] = (double)nz;
   } else {
-    // mixed path: orthogonal iteration in FP32 on the rounded Gram matrix, then
-    // one FP64 step on the accurate one
     for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) sm.C32[idx] = (float)sm.C[idx];
     for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) {
       const int i = idx / k, j = idx - i * k;
-      sm.Q32[idx] = (float)(j < r_warm ? warm[(int64_t)i * R + j] : start_value(i, j));
+      sm.Q32[idx] = (float)(j < r_warm ? (double)warm[(int64_t)i * ldw + j] : start_value(i, j));
     }
     __syncthreads();
     pc.mark(6);
@@ -522,7 +567,7 @@ __device__ int leading_eigs(Smem<Real> &sm, int n, int R, const double *warm, in
       for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) sm.Q32[idx] = sm.W32[idx];
       __syncthreads();
       pc.mark(9);
-      orthonormalise(sm.Q32, n, k, sm.B, sm.cs, false);
+      orthonormalise<float, float>(sm.Q32, n, k, G32, d32, 2, 1e-5, false);
       pc.mark(10);
     }
     for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) sm.Q[idx] = (double)sm.Q32[idx];
@@ -531,7 +576,7 @@ __device__ int leading_eigs(Smem<Real> &sm, int n, int R, const double *warm, in
     for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) sm.Q[idx] = sm.W[idx];
     __syncthreads();
     pc.mark(11);
-    const int nz = orthonormalise(sm.Q, n, k, sm.B, sm.cs, true);
+    const int nz = orthonormalise<double, double>(sm.Q, n, k, sm.B, sm.cs, 3, 1e-11, true);
     if (threadIdx.x == 0) sm.par[29] = (double)nz;
     pc.mark(12);
   }
@@ -572,35 +617,38 @@ __device__ int leading_eigs(Smem<Real> &sm, int n, int R, const double *warm, in
   return k;
 }
 
-// Truncation rank from the energy the first r basis vectors capture:
-// smallest r with trace(C) - sum_{j<r} d_j <= thr (thr > 0), else all k;
-// then r <- min(r, cap), r >= 1.
+// Truncation rank from the energy the first r basis vectors capture: the
+// smallest r with trace(C) - sum_{j<r} d_j <= thr (thr > 0), else all k; then
+// r <- min(r, cap, non-zero columns), r >= 1.  Returns r; *met tells whether
+// the threshold was reached within the k columns, sm.par[31] holds the energy
+// the r columns leave out.
 template <typename Real>
-__device__ int choose_rank(Smem<Real> &sm, int n, int k, double thr, int cap, double *discarded) {
+__device__ int choose_rank(Smem<Real> &sm, int n, int k, double thr, int cap, bool *met) {
   if (threadIdx.x == 0) {
     double tr = 0.0;
     for (int i = 0; i < n; ++i) tr += sm.C[i * n + i];
     double kept = 0.0;
-    int r = k;
+    int r = k, found = 0;
     for (int j = 0; j < k && thr > 0.0; ++j) {
       kept += fmax(sm.Z[j], 0.0);
       if (tr - kept <= thr) {
         r = j + 1;
+        found = 1;
         break;
       }
     }
     if (r > cap) r = cap;
-    if (r > (int)sm.par[29]) r = (int)sm.par[29];  // never keep zeroed (dependent) columns
+    if (r > (int)sm.par[29]) r = (int)sm.par[29];  // never keep zeroed columns
     if (r < 1) r = 1;
     kept = 0.0;
     for (int j = 0; j < r; ++j) kept += fmax(sm.Z[j], 0.0);
+    sm.par[28] = (double)found;
     sm.par[30] = (double)r;
     sm.par[31] = fmax(tr - kept, 0.0);
   }
   __syncthreads();
-  const int r = (int)sm.par[30];
-  if (discarded) *discarded += sm.par[31];
-  return r;
+  *met = sm.par[28] != 0.0;
+  return (int)sm.par[30];
 }
 
 // out = T x_m Vr^T : mode m of T (dims D) contracted with the first r kept
@@ -657,9 +705,27 @@ __device__ void round_hosvd(Real *X, Real *T1, Real *T2, const int N[3], int R, 
     pc.mark(5);
     const double *wU = warm ? warm->fac[m] + cell * (int64_t)N[m] * R : nullptr;
     const int wr = warm ? warm->rank[3 * cell + m] : 0;
-    const int k = leading_eigs<Real>(sm, n, R, wU, wr, pc);
+    // basis size: the previous rank plus kExtra columns (ranks grow by at most
+    // kExtra per step through this path); if the threshold is not reached
+    // within them, the solve is repeated with the full basis, warm-started from
+    // the columns just found
+    int kmax = n < R + kExtra ? n : R + kExtra;
+    if (kmax > kOrthMax) kmax = kOrthMax;
+    int k = (wU && wr > 0 && thr > 0.0 && wr + kExtra < kmax) ? wr + kExtra : kmax;
+    k = leading_eigs<Real, double>(sm, n, k, wU, R, wr, pc);
     pc.mark(6);
-    r[m] = choose_rank<Real>(sm, n, k, thr, R, &discarded);
+    bool met;
+    r[m] = choose_rank<Real>(sm, n, k, thr, R, &met);
+    if (!met && k < kmax) {
+      // the k columns found start the full solve (kept in sm.Vr, which the
+      // iteration does not touch)
+      for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) sm.Vr[idx] = (Real)sm.W[idx];
+      __syncthreads();
+      k = leading_eigs<Real, Real>(sm, n, kmax, sm.Vr, k, k, pc);
+      pc.mark(6);
+      r[m] = choose_rank<Real>(sm, n, k, thr, R, &met);
+    }
+    discarded += sm.par[31];
     double *U = out.fac[m] + cell * (int64_t)N[m] * R;
     for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) {
       const int i = idx / k, j = idx - i * k;
