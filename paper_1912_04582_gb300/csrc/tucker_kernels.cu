@@ -46,8 +46,14 @@ constexpr int kTB = 256;   // threads per CTA for the step / rounding kernel
 constexpr int kKC = 32;    // column chunk of the Gram tiles
 constexpr int kExtra = 4;  // oversampling columns of the subspace iteration
 constexpr int kPower = 3;     // orthogonal (power) iterations from a cold start
-constexpr int kWarmIter = 2;  // orthogonal iterations from the previous step's factor
+constexpr int kWarmIter = 1;  // orthogonal iterations from the previous step's factor
+constexpr int kF32Passes = 2; // Cholesky-QR passes per FP32 orthogonal iteration
 constexpr int kTabs = 21;  // per-axis tables of the assembly
+constexpr int kTerms = 7;  // distinct Tucker tensors of one cell's assembly: itself + 6 faces
+constexpr int kRows = 16;  // first-mode rows one thread assembles per pass
+
+// table / first-mode row length padded to a multiple of kRows (zero-filled)
+__host__ __device__ inline int padN(int n) { return (n + kRows - 1) / kRows * kRows; }
 
 // Optional per-phase cycle counters (thread 0 of every CTA adds clock64 deltas
 // to P.phase[i] when P.phase is not null); no effect on the computation.
@@ -75,6 +81,8 @@ __host__ __device__ inline int sub_k(int Nmax, int R) {
 // Shared-memory layout of the step / rounding kernel.
 template <typename Real>
 struct Smem {
+  int nmax;       // Nmax the layout was carved for
+  int kdim;       // K: columns of the eigen-solver blocks
   double *par;    // [32] cell scalars
   double *red;    // [32]
   double *C;      // [Nmax*Nmax] Gram matrix (FP64)
@@ -85,6 +93,8 @@ struct Smem {
   double *cs;     // [K+2] Jacobi cosines / sines
   Real *rt;       // [kTabs][Nmax] assembly tables
   Real *fac[3];   // [Nmax*R] factor rows of the expansion in progress
+  Real *u1;       // [kTerms+1][R][padN(Nmax)] first-mode factors of the assembly's terms,
+                  // transposed (column k contiguous), zero-padded
   Real *tile;     // [Nmax*(kKC+1)] Gram tile
   Real *Vr;       // [Nmax*K] kept eigenvectors in the working precision
   float *C32;     // [Nmax*Nmax] FP32 copy of C (mixed path: power iterations)
@@ -99,7 +109,9 @@ __host__ __device__ inline size_t smem_bytes(int Nmax, int R) {
   const int K = sub_k(Nmax, R);
   size_t b = sizeof(double) *
              (64 + (size_t)Nmax * Nmax + 2 * (size_t)Nmax * K + 2 * (size_t)K * K + K + 2);
-  b += sizeof(Real) * ((size_t)kTabs * Nmax + 3 * (size_t)Nmax * R + (size_t)Nmax * (kKC + 1) +
+  b += sizeof(Real) * ((size_t)kTabs * padN(Nmax) + 3 * (size_t)Nmax * R +
+                       (kTerms + 1) * (size_t)R * padN(Nmax) +
+                       (size_t)Nmax * (kKC + 1) +
                        (size_t)Nmax * K);
   b += sizeof(float) * ((size_t)Nmax * Nmax + 2 * (size_t)Nmax * K);
   b += sizeof(int) * (2 * (size_t)K + 2);
@@ -110,6 +122,8 @@ template <typename Real>
 __device__ Smem<Real> carve(unsigned char *base, int Nmax, int R) {
   const int K = sub_k(Nmax, R);
   Smem<Real> s;
+  s.nmax = Nmax;
+  s.kdim = K;
   size_t off = 0;
   auto takeD = [&](size_t n) {
     double *p = reinterpret_cast<double *>(base + off);
@@ -129,8 +143,9 @@ __device__ Smem<Real> carve(unsigned char *base, int Nmax, int R) {
     off += sizeof(Real) * n;
     return p;
   };
-  s.rt = takeR((size_t)kTabs * Nmax);
+  s.rt = takeR((size_t)kTabs * padN(Nmax));
   for (int a = 0; a < 3; ++a) s.fac[a] = takeR((size_t)Nmax * R);
+  s.u1 = takeR((size_t)(kTerms + 1) * R * padN(Nmax));
   s.tile = takeR((size_t)Nmax * (kKC + 1));
   s.Vr = takeR((size_t)Nmax * K);
   off = (off + 3) & ~size_t(3);
@@ -144,6 +159,12 @@ __device__ Smem<Real> carve(unsigned char *base, int Nmax, int R) {
   off += sizeof(int) * (K + 2);
   s.perm = reinterpret_cast<int *>(base + off);
   return s;
+}
+
+// doubles from sm.C to the end of sm.W (contiguous): work space of the assembly
+template <typename Real>
+__device__ __forceinline__ int asm_space_doubles(const Smem<Real> &sm) {
+  return sm.nmax * sm.nmax + 2 * sm.nmax * sm.kdim;
 }
 
 __device__ __forceinline__ double block_sum_d(double v, double *red) {
@@ -160,11 +181,10 @@ __device__ __forceinline__ double block_sum_d(double v, double *red) {
 
 // ---------------------------------------------------------------------------
 // Expansion of one Tucker tensor (Section 4: A = G x1 U1 x2 U2 x3 U3) into a
-// full N1 x N2 x N3 array.  The last mode product either assigns
-// (acc == false) or accumulates weight(i1, i2, i3) * value.
-template <typename Real, typename Weight>
+// full N1 x N2 x N3 array (inspection and check-pointing).
+template <typename Real>
 __device__ void expand(const TuckerDev &T, int64_t cell, const int N[3], int R, Smem<Real> &sm,
-                       Real *T1, Real *T2, Real *out, bool acc, const Weight &weight) {
+                       Real *T1, Real *T2, Real *out) {
   const int tid = threadIdx.x;
   const int r1 = T.rank[3 * cell], r2 = T.rank[3 * cell + 1], r3 = T.rank[3 * cell + 2];
   const double *G = T.core + cell * (int64_t)R * R * R;
@@ -213,40 +233,12 @@ __device__ void expand(const TuckerDev &T, int64_t cell, const int N[3], int R, 
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int i1 = i0 + j;
-        if (i1 < N1) {
-          const int64_t o = (int64_t)i1 * NP + p;
-          if (acc)
-            out[o] += weight(i1, i2, i3) * a[j];
-          else
-            out[o] = a[j];
-        }
+        if (i1 < N1) out[(int64_t)i1 * NP + p] = a[j];
       }
     }
   }
   __syncthreads();
 }
-
-template <typename Real>
-struct NoWeight {
-  __device__ Real operator()(int, int, int) const { return Real(1); }
-};
-
-// inflow weight -c min(xi.e, 0) * scale of one face: a 1D table for faces
-// normal to a coordinate axis, the dot product otherwise
-template <typename Real>
-struct FaceWeight {
-  const Real *tab;
-  const Real *x0, *x1, *x2;
-  Real c, e0, e1, e2, scale;
-  int axis;
-  __device__ Real operator()(int i1, int i2, int i3) const {
-    if (axis == 0) return tab[i1];
-    if (axis == 1) return tab[i2];
-    if (axis == 2) return tab[i3];
-    const Real xn = e0 * x0[i1] + e1 * x1[i2] + e2 * x2[i3];
-    return -c * fmin(xn, Real(0)) * scale;
-  }
-};
 
 // ---------------------------------------------------------------------------
 // Gram matrix of the mode-m unfolding of a tensor with dims D (row-major),
@@ -567,7 +559,7 @@ __device__ __noinline__ int leading_eigs(Smem<Real> &sm, int n, int k, const WT 
       for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) sm.Q32[idx] = sm.W32[idx];
       __syncthreads();
       pc.mark(9);
-      orthonormalise<float, float>(sm.Q32, n, k, G32, d32, 2, 1e-5, false);
+      orthonormalise<float, float>(sm.Q32, n, k, G32, d32, kF32Passes, 1e-5, false);
       pc.mark(10);
     }
     for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) sm.Q[idx] = (double)sm.Q32[idx];
@@ -687,12 +679,14 @@ __device__ void project(const Real *T, const int D[3], int m, int r, int k, Smem
 template <typename Real, int TS>
 __device__ void round_hosvd(Real *X, Real *T1, Real *T2, const int N[3], int R, double eps,
                             TuckerDev &out, int64_t cell, Smem<Real> &sm, double *err_out,
-                            PhaseClock &pc, const TuckerDev *warm) {
+                            PhaseClock &pc, const TuckerDev *warm, double e = -1.0) {
   int D[3] = {N[0], N[1], N[2]};
   const int NN = N[0] * N[1] * N[2];
-  double e = 0.0;
-  for (int i = threadIdx.x; i < NN; i += blockDim.x) e += (double)X[i] * (double)X[i];
-  e = block_sum_d(e, sm.red);
+  if (e < 0.0) {  // ||X||^2 unless the caller has it
+    e = 0.0;
+    for (int i = threadIdx.x; i < NN; i += blockDim.x) e += (double)X[i] * (double)X[i];
+    e = block_sum_d(e, sm.red);
+  }
   const double thr = eps * eps / 3.0 * e;
   double discarded = 0.0;
   int r[3];
@@ -771,7 +765,282 @@ __device__ void round_hosvd(Real *X, Real *T1, Real *T2, const int N[3], int R, 
 //   -sum_{faces normal to a} c max(s xi_a, 0); [15+l] inflow weight of face l
 //   (faces normal to a coordinate axis; scaled by the wall density on walls).
 template <typename Real>
-__device__ __forceinline__ Real *tabp(Smem<Real> &sm, int Nmax, int t) { return sm.rt + t * Nmax; }
+__device__ __forceinline__ Real *tabp(Smem<Real> &sm, int Nmax, int t) {
+  return sm.rt + t * padN(Nmax);
+}
+
+// ---------------------------------------------------------------------------
+// Fused assembly of f^{n+1} for one cell (Section 5, Lemma 1) into X, one pass.
+//
+// Every Tucker tensor the update needs (the cell's own f and the f of each
+// interior neighbour) is first contracted over modes 2 and 3:
+//   T2_t[k1][i2][i3] = sum_{k2,k3} G_t[k1][k2][k3] U2_t[i2][k2] U3_t[i3][k3]
+// (global scratch, compact, one block per distinct tensor), and its first-mode
+// rows U1_t are kept in shared memory.  Then one pass over the (i2, i3)
+// columns, kRows first-mode rows per thread, forms
+//   X = dt nu f^S + sum_{Maxwellian ghosts l} m_l g_l + W_self o f
+//       + sum_{interior / symmetry faces l} m_l o f_src(l)
+// with f = U1 T2 formed in registers, the Lemma-1 self weight
+//   W_self = 1 - dt nu - sum_l c_l (xi.e_l)^+ + sum_{zero-gradient faces l} m_l
+// and the inflow weights m_l = -c_l (xi.e_l)^- (times the wall density on
+// walls).  A symmetry face reuses the cell's own T2 with the mirrored index
+// (rows of U1 reversed, or the mirrored (i2, i3) column).  X is written once and
+// its squared norm returned (FP64, block-reduced).
+struct AsmTerm {
+  int off;      // T2 offset in the scratch block (elements)
+  int r1;       // first-mode rank
+  int u1;       // U1 row block in sm.u1 (elements)
+  int rev;      // 1: first-mode index mirrored
+  int reflect;  // 1 / 2: second / third-mode index mirrored; 0 none
+  int face;     // weight: -1 the Lemma-1 self weight, else m of face `face`
+};
+
+template <typename Real>
+__device__ __noinline__ void term_contract(const TuckerDev &T, int64_t cell, const int N[3], int R, int NP,
+                              Smem<Real> &sm, Real *u1dst, Real *T2dst, int *r1_out) {
+  const int tid = threadIdx.x;
+  const int r1 = T.rank[3 * cell], r2 = T.rank[3 * cell + 1], r3 = T.rank[3 * cell + 2];
+  const double *U1 = T.fac[0] + cell * (int64_t)N[0] * R;
+  const double *U2 = T.fac[1] + cell * (int64_t)N[1] * R;
+  const double *U3 = T.fac[2] + cell * (int64_t)N[2] * R;
+  const int N1P = padN(N[0]);
+  for (int idx = tid; idx < r1 * N1P; idx += blockDim.x) {
+    const int k = idx / N1P, i = idx - k * N1P;
+    u1dst[idx] = i < N[0] ? (Real)U1[(int64_t)i * R + k] : Real(0);
+  }
+  for (int idx = tid; idx < N[1] * r2; idx += blockDim.x) {
+    const int i = idx / r2, k = idx - i * r2;
+    sm.fac[1][idx] = (Real)U2[(int64_t)i * R + k];
+  }
+  for (int idx = tid; idx < N[2] * r3; idx += blockDim.x) {
+    const int i = idx / r3, k = idx - i * r3;
+    sm.fac[2][idx] = (Real)U3[(int64_t)i * R + k];
+  }
+  __syncthreads();
+  // mode-3 then mode-2 contraction, a slab of first-mode indices at a time,
+  // both stages in shared memory (the Gram / eigen-solver space, free during the
+  // assembly): Gs = G[k1 slab], T1s[kk][k2][i3] = sum_k3 Gs[kk][k2][k3] U3[i3][k3],
+  // T2[k1][i2][i3] = sum_k2 U2[i2][k2] T1s[kk][k2][i3]
+  const double *G = T.core + cell * (int64_t)R * R * R;
+  const int N2 = N[1], N3 = N[2];
+  const int slabG = r2 * r3, slabT = r2 * N3;
+  Real *Gs = reinterpret_cast<Real *>(sm.C);
+  const int cap = (int)(asm_space_doubles(sm) * sizeof(double) / sizeof(Real));
+  const int kc = max(1, cap / max(1, slabG + slabT));
+  for (int k1a = 0; k1a < r1; k1a += kc) {
+    const int kn = min(kc, r1 - k1a);
+    Real *T1s = Gs + kn * slabG;
+    for (int idx = tid; idx < kn * slabG; idx += blockDim.x) Gs[idx] = (Real)G[k1a * slabG + idx];
+    __syncthreads();
+    for (int idx = tid; idx < kn * slabT; idx += blockDim.x) {
+      const int i3 = idx % N3, t = idx / N3;  // t = kk * r2 + k2
+      const Real *g = Gs + t * r3;
+      const Real *u3 = sm.fac[2] + i3 * r3;
+      Real acc = 0;
+      for (int k3 = 0; k3 < r3; ++k3) acc = fma(g[k3], u3[k3], acc);
+      T1s[idx] = acc;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < kn * N2 * N3; idx += blockDim.x) {
+      const int i3 = idx % N3, t = idx / N3, i2 = t % N2, kk = t / N2;
+      const Real *u2 = sm.fac[1] + i2 * r2;
+      const Real *t1 = T1s + kk * slabT + i3;
+      Real acc = 0;
+      for (int k2 = 0; k2 < r2; ++k2) acc = fma(u2[k2], t1[k2 * N3], acc);
+      T2dst[(int64_t)(k1a + kk) * NP + i2 * N3 + i3] = acc;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) *r1_out = r1;
+  __syncthreads();
+}
+
+// The assembly pass proper (see above).  Returns ||X||^2 (FP64) on every thread.
+template <typename Real>
+__device__ __noinline__ double assemble(const TuckerStepParams &P, int64_t c, const int N[3],
+                                        Smem<Real> &sm, const SlotDev *s_slot,
+                                        const double *s_scale, Real *X, Real *T2buf,
+                                        PhaseClock &pc) {
+  __shared__ AsmTerm s_term[1 + 2 * 6];
+  __shared__ int s_r1[kTerms];
+  const int tid = threadIdx.x;
+  const int N1 = N[0], N2 = N[1], N3 = N[2], NP = N2 * N3, Nm = P.Nmax, R = P.R;
+  const int N1P = padN(N1), u1slot = R * padN(Nm);
+  // mode-2/3 contractions of the cell's own tensor and of each interior neighbour
+  int nsrc = 0, off = 0;
+  int src_off[kTerms], src_r1[kTerms];
+  bool mirror1 = false;  // a symmetry face mirrors the first-mode index
+  for (int l = -1; l < 6; ++l) {
+    if (l >= 0 && s_slot[l].kind == kSymmetry && s_slot[l].flip == 0) mirror1 = true;
+    if (l >= 0 && s_slot[l].kind != kInterior) continue;
+    const int64_t cell = l < 0 ? c : (int64_t)s_slot[l].src;
+    term_contract<Real>(P.cur, cell, N, R, NP, sm, sm.u1 + nsrc * u1slot, T2buf + off,
+                        &s_r1[nsrc]);
+    src_off[nsrc] = off;
+    src_r1[nsrc] = s_r1[nsrc];
+    off += s_r1[nsrc] * NP;
+    ++nsrc;
+  }
+  if (mirror1) {  // the cell's own first-mode factor with rows reversed, in the spare slot
+    Real *dst = sm.u1 + kTerms * u1slot;
+    for (int idx = tid; idx < src_r1[0] * N1P; idx += blockDim.x) {
+      const int k = idx / N1P, i = idx - k * N1P;
+      dst[idx] = i < N1 ? sm.u1[k * N1P + N1 - 1 - i] : Real(0);
+    }
+  }
+  // term list: self, interior faces, symmetry faces (the mirrored self)
+  int nterm = 0;
+  bool self_extra = false;  // faces that change the self weight pointwise
+  {
+    int q = 0;
+    for (int l = -1; l < 6; ++l) {
+      if (l >= 0) {
+        const SlotDev &sl = s_slot[l];
+        if (sl.axis < 0 || sl.kind == kZeroGrad) self_extra = true;
+        if (sl.kind != kInterior && sl.kind != kSymmetry) continue;
+      }
+      AsmTerm tm;
+      const bool sym = l >= 0 && s_slot[l].kind == kSymmetry;
+      const int qs = (l < 0 || sym) ? 0 : ++q;
+      tm.off = src_off[qs];
+      tm.r1 = src_r1[qs];
+      tm.rev = sym && s_slot[l].flip == 0;
+      tm.u1 = tm.rev ? kTerms * u1slot : qs * u1slot;
+      tm.reflect = sym ? (s_slot[l].flip == 1 ? 1 : (s_slot[l].flip == 2 ? 2 : 0)) : 0;
+      tm.face = l;
+      if (tid == 0) s_term[nterm] = tm;
+      ++nterm;
+    }
+  }
+  __syncthreads();
+  pc.mark(13);
+  const Real w0 = (Real)(1.0 - sm.par[8]);
+  const Real *x0 = tabp(sm, Nm, 0), *x1 = tabp(sm, Nm, 1), *x2 = tabp(sm, Nm, 2);
+  const Real *F0 = tabp(sm, Nm, 3), *F1 = tabp(sm, Nm, 4), *F2 = tabp(sm, Nm, 5);
+  const Real *Q0 = tabp(sm, Nm, 6), *Q1 = tabp(sm, Nm, 7), *Q2 = tabp(sm, Nm, 8);
+  const Real *V0 = tabp(sm, Nm, 9), *V1 = tabp(sm, Nm, 10), *V2 = tabp(sm, Nm, 11);
+  const Real *G0 = tabp(sm, Nm, 12), *G1 = tabp(sm, Nm, 13), *G2 = tabp(sm, Nm, 14);
+  const int nch = N1P / kRows;
+  double en = 0.0;
+  for (int item = tid; item < NP * nch; item += blockDim.x) {
+    const int p = item % NP, ch = item / NP;
+    const int i2 = p / N3, i3 = p - i2 * N3;
+    const int i10 = ch * kRows;  // rows i10 .. i10 + kRows - 1 (tables zero-padded)
+    Real acc[kRows], sv[kRows];
+    // equilibrium term dt nu f^S (Proposition 1: Maxwellian factors times the
+    // cubic Shakhov polynomial)
+    {
+      const Real fM12 = F1[i2] * F2[i3], Qp = Q1[i2] + Q2[i3], Vp = V1[i2] + V2[i3] - Real(2.5);
+      const Real *f0 = F0 + i10, *q0 = Q0 + i10, *v0 = V0 + i10;
+#pragma unroll
+      for (int j = 0; j < kRows; ++j) acc[j] = f0[j] * fM12 * (Real(1) + (q0[j] + Qp) * (v0[j] + Vp));
+    }
+    // rank-1 Maxwellian ghosts (free stream, diffuse wall)
+    for (int l = 0; l < 6; ++l) {
+      const SlotDev &sl = s_slot[l];
+      if (sl.kind != kFreeStream && sl.kind != kWall) continue;
+      const double *gf = P.ghostf + (int64_t)sl.src * 3 * Nm;
+      const Real g23 = (Real)(gf[Nm + i2] * gf[2 * Nm + i3]);
+      const Real *tab = tabp(sm, Nm, 15 + l);
+      const Real e0 = (Real)sl.e[0], cl = (Real)sl.c, sc = (Real)s_scale[l];
+      const Real xn23 = (Real)sl.e[1] * x1[i2] + (Real)sl.e[2] * x2[i3];
+      const Real m23 = sl.axis == 1 ? tab[i2] : (sl.axis == 2 ? tab[i3] : Real(0));
+#pragma unroll
+      for (int j = 0; j < kRows; ++j) {
+        const int i1 = i10 + j;
+        Real m;
+        if (sl.axis == 0) m = tab[i1];
+        else if (sl.axis > 0) m = m23;
+        else m = -cl * fmin(e0 * x0[i1] + xn23, Real(0)) * sc;
+        acc[j] = fma(m, (Real)gf[min(i1, N1 - 1)] * g23, acc[j]);
+      }
+    }
+    // Tucker terms: f = U1 T2 in registers, then the weight
+    for (int t = 0; t < nterm; ++t) {
+      const AsmTerm tm = s_term[t];
+      int pp = p;
+      if (tm.reflect == 1) pp = (N2 - 1 - i2) * N3 + i3;
+      else if (tm.reflect == 2) pp = i2 * N3 + (N3 - 1 - i3);
+      const Real *t2 = T2buf + tm.off + pp;
+      const Real *u1 = sm.u1 + tm.u1 + i10;
+#pragma unroll
+      for (int j = 0; j < kRows; ++j) sv[j] = 0;
+      for (int k1 = 0; k1 < tm.r1; k1 += 4) {  // four loads in flight
+        Real tv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tv[q] = k1 + q < tm.r1 ? t2[(int64_t)(k1 + q) * NP] : Real(0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (k1 + q < tm.r1) {
+            const Real *ur = u1 + (k1 + q) * N1P;
+#pragma unroll
+            for (int j = 0; j < kRows; ++j) sv[j] = fma(ur[j], tv[q], sv[j]);
+          }
+        }
+      }
+      if (tm.face < 0) {  // Lemma-1 self weight
+        const Real c0p = w0 + G1[i2] + G2[i3];
+        const Real *g0 = G0 + i10;
+#pragma unroll
+        for (int j = 0; j < kRows; ++j) acc[j] = fma(c0p + g0[j], sv[j], acc[j]);
+        // outflow of faces whose normal is not a coordinate axis, inflow of
+        // zero-gradient faces (their ghost is the cell itself)
+        for (int l = 0; self_extra && l < 6; ++l) {
+          const SlotDev &sl = s_slot[l];
+          const bool nonaxis = sl.axis < 0, zg = sl.kind == kZeroGrad;
+          if (!nonaxis && !zg) continue;
+          const Real e0 = (Real)sl.e[0], cl = (Real)sl.c, sc = (Real)s_scale[l];
+          const Real *tab = tabp(sm, Nm, 15 + l);
+          const Real xn23 = (Real)sl.e[1] * x1[i2] + (Real)sl.e[2] * x2[i3];
+          const Real m23 = sl.axis == 1 ? tab[i2] : (sl.axis == 2 ? tab[i3] : Real(0));
+#pragma unroll
+          for (int j = 0; j < kRows; ++j) {
+            const int i1 = i10 + j;
+            Real wadd;
+            if (nonaxis) {
+              const Real xn = e0 * x0[i1] + xn23;
+              wadd = -cl * fmax(xn, Real(0));
+              if (zg) wadd -= cl * fmin(xn, Real(0)) * sc;
+            } else {
+              wadd = sl.axis == 0 ? tab[i1] : m23;
+            }
+            acc[j] = fma(wadd, sv[j], acc[j]);
+          }
+        }
+      } else {
+        const SlotDev &sl = s_slot[tm.face];
+        const Real *tab = tabp(sm, Nm, 15 + tm.face);
+        if (sl.axis == 0) {
+          const Real *tr = tab + i10;
+#pragma unroll
+          for (int j = 0; j < kRows; ++j) acc[j] = fma(tr[j], sv[j], acc[j]);
+        } else if (sl.axis > 0) {
+          const Real m = sl.axis == 1 ? tab[i2] : tab[i3];
+#pragma unroll
+          for (int j = 0; j < kRows; ++j) acc[j] = fma(m, sv[j], acc[j]);
+        } else {
+          const Real e0 = (Real)sl.e[0], cl = (Real)sl.c, sc = (Real)s_scale[tm.face];
+          const Real xn23 = (Real)sl.e[1] * x1[i2] + (Real)sl.e[2] * x2[i3];
+          const Real *xr = x0 + i10;
+#pragma unroll
+          for (int j = 0; j < kRows; ++j) {
+            const Real xn = e0 * xr[j] + xn23;
+            acc[j] = fma(-cl * fmin(xn, Real(0)) * sc, sv[j], acc[j]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kRows; ++j) {
+      const int i1 = i10 + j;
+      if (i1 < N1) {
+        X[(int64_t)i1 * NP + p] = acc[j];
+        en += (double)acc[j] * (double)acc[j];
+      }
+    }
+  }
+  return block_sum_d(en, sm.red);
+}
 
 // minimum resident CTAs per SM the register allocation must allow
 template <typename Real>
@@ -791,8 +1060,8 @@ __global__ void __launch_bounds__(kTB, MinBlocks<Real>::value) tucker_step_kerne
   const int Nm = P.Nmax;
   const int tid = threadIdx.x;
   Real *X = reinterpret_cast<Real *>(P.scratch) + (size_t)blockIdx.x * P.scratch_stride;
-  Real *E = X + NN;
-  Real *T2 = E + NN;
+  Real *T2buf = X + NN;  // assembly: mode-2/3 contractions; rounding: its work space
+  Real *T2 = T2buf;
   Real *T1 = T2 + (size_t)P.R * NP;
 
   PhaseClock pc(P.phase);
@@ -828,8 +1097,13 @@ __global__ void __launch_bounds__(kTB, MinBlocks<Real>::value) tucker_step_kerne
     __syncthreads();
     {
       const double T = sm.par[4], dtnu = sm.par[8], A = sm.par[9], amp = sm.par[10];
+      const int NmP = padN(Nm);
       for (int a = 0; a < 3; ++a)
-        for (int i = tid; i < N[a]; i += blockDim.x) {
+        for (int i = tid; i < NmP; i += blockDim.x) {
+          if (i >= N[a]) {  // zero padding up to a multiple of kRows
+            for (int t = a; t < 15; t += 3) tabp(sm, Nm, t)[i] = Real(0);
+            continue;
+          }
           const double x = P.xi[a][i];
           const double v = x - sm.par[1 + a];
           tabp(sm, Nm, 0 + a)[i] = (Real)x;
@@ -846,82 +1120,20 @@ __global__ void __launch_bounds__(kTB, MinBlocks<Real>::value) tucker_step_kerne
       for (int l = 0; l < 6; ++l) {
         const SlotDev &sl = s_slot[l];
         if (sl.axis < 0) continue;
-        for (int i = tid; i < N[sl.axis]; i += blockDim.x)
+        for (int i = tid; i < NmP; i += blockDim.x)
           tabp(sm, Nm, 15 + l)[i] =
-              (Real)(-sl.c * fmin(sl.sgn * P.xi[sl.axis][i], 0.0) * s_scale[l]);
+              i < N[sl.axis]
+                  ? (Real)(-sl.c * fmin(sl.sgn * P.xi[sl.axis][i], 0.0) * s_scale[l])
+                  : Real(0);
       }
     }
     __syncthreads();
     pc.mark(0);
-    // ---- own expansion into E
-    expand<Real>(P.cur, c, N, P.R, sm, T1, T2, E, false, NoWeight<Real>{});
-    pc.mark(1);
-    // ---- pointwise part: c0 f + dt nu f^S + ghost / self-referencing faces
-    {
-      const Real w0 = (Real)(1.0 - sm.par[8]);
-      const Real *x0 = tabp(sm, Nm, 0), *x1 = tabp(sm, Nm, 1), *x2 = tabp(sm, Nm, 2);
-      const Real *F0 = tabp(sm, Nm, 3), *F1 = tabp(sm, Nm, 4), *F2 = tabp(sm, Nm, 5);
-      const Real *Q0 = tabp(sm, Nm, 6), *Q1 = tabp(sm, Nm, 7), *Q2 = tabp(sm, Nm, 8);
-      const Real *V0 = tabp(sm, Nm, 9), *V1 = tabp(sm, Nm, 10), *V2 = tabp(sm, Nm, 11);
-      const Real *G0 = tabp(sm, Nm, 12), *G1 = tabp(sm, Nm, 13), *G2 = tabp(sm, Nm, 14);
-      for (int idx = tid; idx < NN; idx += blockDim.x) {
-        const int i3 = idx % N3, t = idx / N3, i2 = t % N2, i1 = t / N2;
-        const Real fM = F0[i1] * F1[i2] * F2[i3];
-        Real val =
-            fM * (Real(1) + (Q0[i1] + Q1[i2] + Q2[i3]) * (V0[i1] + V1[i2] + V2[i3] - Real(2.5)));
-        Real c0 = w0 + G0[i1] + G1[i2] + G2[i3];
-        const Real fe = E[idx];
-#pragma unroll
-        for (int l = 0; l < 6; ++l) {
-          const SlotDev &sl = s_slot[l];
-          Real m;
-          if (sl.axis >= 0) {
-            if (sl.kind == kInterior) continue;
-            m = tabp(sm, Nm, 15 + l)[sl.axis == 0 ? i1 : (sl.axis == 1 ? i2 : i3)];
-          } else {
-            const Real xn =
-                (Real)sl.e[0] * x0[i1] + (Real)sl.e[1] * x1[i2] + (Real)sl.e[2] * x2[i3];
-            c0 -= (Real)sl.c * fmax(xn, Real(0));
-            if (sl.kind == kInterior) continue;
-            m = -(Real)sl.c * fmin(xn, Real(0)) * (Real)s_scale[l];
-          }
-          if (m == Real(0)) continue;
-          Real g;
-          switch (sl.kind) {
-            case kZeroGrad:
-              g = fe;
-              break;
-            case kSymmetry: {
-              int j1 = i1, j2 = i2, j3 = i3;
-              if (sl.flip == 0) j1 = N1 - 1 - i1;
-              else if (sl.flip == 1) j2 = N2 - 1 - i2;
-              else j3 = N3 - 1 - i3;
-              g = E[((int64_t)j1 * N2 + j2) * N3 + j3];
-              break;
-            }
-            default: {  // free stream / wall: rank-1 Maxwellian ghost
-              const double *gf = P.ghostf + (int64_t)sl.src * 3 * P.Nmax;
-              g = (Real)(gf[i1] * gf[P.Nmax + i2] * gf[2 * P.Nmax + i3]);
-            }
-          }
-          val += m * g;
-        }
-        X[idx] = c0 * fe + val;
-      }
-      __syncthreads();
-    }
-    pc.mark(2);
-    // ---- one block per interior face: X += (-c (xi.e)^-) o f_nb
-    for (int l = 0; l < 6; ++l) {
-      const SlotDev sl = s_slot[l];
-      if (sl.kind != kInterior) continue;
-      FaceWeight<Real> fw{tabp(sm, Nm, 15 + l), tabp(sm, Nm, 0), tabp(sm, Nm, 1), tabp(sm, Nm, 2),
-                          (Real)sl.c, (Real)sl.e[0], (Real)sl.e[1], (Real)sl.e[2], Real(1), sl.axis};
-      expand<Real>(P.cur, sl.src, N, P.R, sm, T1, T2, X, true, fw);
-    }
+    // ---- f^{n+1} before rounding, in one pass
+    const double eX = assemble<Real>(P, c, N, sm, s_slot, s_scale, X, T2buf, pc);
     pc.mark(3);
     // ---- rounding
-    round_hosvd<Real, TS>(X, T1, T2, N, P.R, P.tol, P.nxt, c, sm, P.err, pc, &P.cur);
+    round_hosvd<Real, TS>(X, T1, T2, N, P.R, P.tol, P.nxt, c, sm, P.err, pc, &P.cur, eX);
   }
 }
 
@@ -938,7 +1150,7 @@ __global__ void __launch_bounds__(kTB) tucker_expand_kernel(TuckerDev T, int64_t
   Real *T2 = E + NN;
   Real *T1 = T2 + (size_t)R * N2 * N3;
   for (int64_t j = blockIdx.x; j < ncell; j += gridDim.x) {
-    expand<Real>(T, c0 + j, N, R, sm, T1, T2, E, false, NoWeight<Real>{});
+    expand<Real>(T, c0 + j, N, R, sm, T1, T2, E);
     for (int i = threadIdx.x; i < NN; i += blockDim.x) out[j * NN + i] = (double)E[i];
     __syncthreads();
   }
@@ -1146,8 +1358,10 @@ int launch_expand_T(const TuckerDev &T, int64_t c0, int64_t ncell, int N1, int N
 }  // namespace
 
 size_t tucker_scratch_elems(int N1, int N2, int N3, int R) {
+  // X, then the assembly's compact mode-2/3 contractions (at most kTerms blocks
+  // of R x N2 x N3), which also hold the rounding's and the expansion's T2, T1
   const size_t NN = (size_t)N1 * N2 * N3;
-  return 2 * NN + (size_t)R * N2 * N3 + (size_t)R * R * N3 + 64;
+  return NN + (size_t)kTerms * R * N2 * N3 + 64;
 }
 
 template <typename Real, int TS>

@@ -236,11 +236,11 @@ void tucker_free(dvm_ctx *C) {
   if (S->phase) {
     long long h[16] = {0};
     if (cudaMemcpy(h, S->phase, sizeof h, cudaMemcpyDeviceToHost) == cudaSuccess) {
-      static const char *names[13] = {"prologue", "expand_own", "pointwise", "expand_nb", "energy",
+      static const char *names[14] = {"prologue", "-", "-", "assemble", "energy",
                                       "gram",     "eig",        "rank",      "project",   "eig_cq32",
-                                      "eig_orth32", "eig_cq64", "eig_orth64"};
+                                      "eig_orth32", "eig_cq64", "eig_orth64", "contract"};
       std::fprintf(stderr, "tucker phases (SM cycles, summed over CTAs):");
-      for (int i = 0; i < 13; ++i) std::fprintf(stderr, " %s=%lld", names[i], h[i]);
+      for (int i = 0; i < 14; ++i) std::fprintf(stderr, " %s=%lld", names[i], h[i]);
       std::fprintf(stderr, "\n");
     }
     cudaFree(S->phase);
