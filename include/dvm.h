@@ -105,7 +105,19 @@ typedef struct {
   double cfl;         /* CFL number for the fixed time step (default 0.5)    */
   double dt;          /* if > 0, use this time step instead of the CFL rule  */
   void *cuda_stream;  /* cudaStream_t for all device work (may be NULL)      */
+  int32_t variant;    /* Tucker step launch variant: DVM_VARIANT_AUTO (0,
+                       * the autotuner times both on the first step and keeps
+                       * the faster), DVM_VARIANT_FUSED (one persistent
+                       * kernel, one cell per CTA through all phases) or
+                       * DVM_VARIANT_PHASED (phase-major: assembly, then per
+                       * mode Gram / eigen-solve (one warp per cell) /
+                       * projection kernels over chunks of cells).  Both
+                       * compute the same values cell by cell.              */
 } dvm_opts;
+
+#define DVM_VARIANT_AUTO 0
+#define DVM_VARIANT_FUSED 1
+#define DVM_VARIANT_PHASED 2
 
 /* Create a solver context on the current CUDA device.  Builds the face list
  * (interior faces by shared vertex sets, boundary faces from mesh->bface),
@@ -173,11 +185,13 @@ int dvm_get_geometry(dvm_ctx *ctx, double *vol, int64_t *fcell, double *fgeo);
 /* Tucker ranks per cell into r[n_cell][3] (full format: N1, N2, N3). */
 int dvm_get_ranks(dvm_ctx *ctx, int32_t *r);
 
-/* Launch configuration of the Tucker step kernel (persistent, one cell per
- * CTA at a time): the grid in CTAs chosen by the autotuner on the first step,
- * and the step-kernel time in ms it measured for 1..4 resident CTAs per SM in
- * tune_ms[1..4] (0 where not tried; tune_ms[0] unused).  Full format: grid =
- * number of cells, tune_ms zeros.  Either pointer may be NULL. */
+/* Launch configuration of the Tucker step: the persistent grid in CTAs
+ * chosen by the autotuner on the first step (fused kernel, or the assembly
+ * kernel of the phase-major variant), the fused kernel's time in ms for 1..4
+ * resident CTAs per SM in tune_ms[1..4] and the phase-major step's in
+ * tune_ms[0] (0 where not tried); the variant in use is returned as a negative
+ * grid when it is the phase-major one.  Full format: grid = number of cells,
+ * tune_ms zeros.  Either pointer may be NULL. */
 int dvm_get_launch_config(dvm_ctx *ctx, int32_t *grid, float *tune_ms);
 
 /* Bytes of device memory held for the distribution function in its current

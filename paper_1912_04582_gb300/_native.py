@@ -27,6 +27,7 @@ DVM_ERR_IO = -8
 DVM_BC_FREESTREAM, DVM_BC_ZEROGRAD, DVM_BC_SYMMETRY, DVM_BC_WALL = 0, 1, 2, 3
 DVM_FORMAT_FULL, DVM_FORMAT_TUCKER = 0, 1
 DVM_PREC_FP64, DVM_PREC_MIXED = 0, 1
+DVM_VARIANT_AUTO, DVM_VARIANT_FUSED, DVM_VARIANT_PHASED = 0, 1, 2
 
 _c_dp = ctypes.POINTER(ctypes.c_double)
 _c_i64p = ctypes.POINTER(ctypes.c_int64)
@@ -52,7 +53,7 @@ class dvm_opts(ctypes.Structure):
     _fields_ = [("format", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("rank_cap", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("cfl", ctypes.c_double), ("dt", ctypes.c_double),
-                ("cuda_stream", ctypes.c_void_p)]
+                ("cuda_stream", ctypes.c_void_p), ("variant", ctypes.c_int32)]
 
 
 class dvm_request(ctypes.Structure):

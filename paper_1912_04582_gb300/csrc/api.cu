@@ -187,6 +187,10 @@ int dvm_create(dvm_ctx **out, const dvm_mesh *mesh, const dvm_vgrid *vg, const d
     set_error("dvm_create: unknown format");
     return DVM_ERR_INVALID_ARG;
   }
+  if (opts->variant < DVM_VARIANT_AUTO || opts->variant > DVM_VARIANT_PHASED) {
+    set_error("dvm_create: variant must be DVM_VARIANT_AUTO, _FUSED or _PHASED");
+    return DVM_ERR_INVALID_ARG;
+  }
   if (opts->format == DVM_FORMAT_TUCKER &&
       (opts->rank_cap < 1 || opts->rank_cap > std::min(24, std::min(vg->N[0], std::min(vg->N[1], vg->N[2]))) ||
        !(opts->tol >= 0.0))) {

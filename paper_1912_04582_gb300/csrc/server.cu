@@ -82,6 +82,9 @@ size_t estimate(const dvm_request *q) {
     const size_t grid = std::min<size_t>((size_t)nc, (size_t)sms * 4);
     b += grid * es * (tucker_scratch_elems(q->vgrid.N[0], q->vgrid.N[1], q->vgrid.N[2], (int)R) + 64);
     b += sizeof(double) * (size_t)nc + sizeof(double) * (size_t)(nghost + 1) * 3 * Nmax;
+    // work buffers of the phase-major step variant, if the autotuner keeps it
+    b += (size_t)nc * (tucker_split_bytes_per_cell(q->vgrid.N[0], q->vgrid.N[1], q->vgrid.N[2],
+                                                   (int)R, (int)Nmax, es == 8) + 64);
   }
   return b + b / 20 + (16u << 20);
 }

@@ -34,6 +34,17 @@ struct TuckerStepParams {
   double w, dt, Pr, omega, delta, tol;
 };
 
+// Work buffers of the phase-major step for a chunk of cells [c0, c0 + cn)
+struct TuckerSplitBufs {
+  void *X;       // [cn][N1*N2*N3] f^{n+1} before rounding (working precision)
+  void *Y1;      // [cn][R*N2*N3] after the first-mode projection
+  void *Y2;      // [cn][R*R*N3]  after the second-mode projection
+  double *C;     // [cn][Nmax*Nmax] Gram matrix of the current mode
+  double *e;     // [cn] ||X||^2
+  double *disc;  // [cn] energy left out so far
+  int64_t c0, cn;
+};
+
 struct TuckerMomentParams {
   TuckerDev T;
   const double *uref;    // reference velocity, uref[c*uref_stride + k] (may be null)
@@ -54,6 +65,14 @@ size_t tucker_scratch_elems(int N1, int N2, int N3, int R);
 size_t tucker_smem_bytes(int Nmax, int R, bool fp64);
 int tucker_step_blocks_per_sm(int Nmax, int R, bool fp64);
 int launch_tucker_step(const TuckerStepParams &p, int grid, bool fp64, cudaStream_t s);
+// phase-major step over chunks of `chunk` cells (buffers sized for one chunk);
+// asm_grid persistent CTAs for the assembly
+int launch_tucker_split_step(const TuckerStepParams &p, TuckerSplitBufs b, int64_t chunk,
+                             int asm_grid, bool fp64, cudaStream_t s);
+// bytes of TuckerSplitBufs per cell (working precision fp64 or float)
+size_t tucker_split_bytes_per_cell(int N1, int N2, int N3, int R, int Nmax, bool fp64);
+// raise the kernels' shared-memory opt-in for this size (outside stream captures)
+int tucker_prepare_launch(int Nmax, int R, bool fp64);
 int launch_tucker_expand(const TuckerDev &T, int64_t c0, int64_t ncell, int N1, int N2, int N3,
                          int R, int Nmax, void *scratch, size_t stride, double *out, int grid,
                          bool fp64, cudaStream_t s);

@@ -1042,10 +1042,75 @@ __device__ __noinline__ double assemble(const TuckerStepParams &P, int64_t c, co
   return block_sum_d(en, sm.red);
 }
 
+// Per-cell prologue of the assembly: slots, wall-density scales, the cell's
+// macroparameters (moments of f^n, Section 4 item 5) and the per-axis tables of
+// the Maxwellian, Shakhov and face weights (zero-padded to padN(Nmax)).
+template <typename Real>
+__device__ void cell_prologue(const TuckerStepParams &P, int64_t c, const int N[3], Smem<Real> &sm,
+                              SlotDev *s_slot, double *s_scale) {
+  const int tid = threadIdx.x;
+  const int Nm = P.Nmax;
+  // ---- prologue: macroparameters, wall densities
+  const double *S = P.sums + c * kSums;
+  if (tid < 6) {
+    s_slot[tid] = P.slot[c * 6 + tid];
+    s_scale[tid] = (s_slot[tid].kind == kWall) ? -S[16 + tid] / s_slot[tid].wall_den : 1.0;
+  }
+  if (tid == 0) {
+    CellMacro m;
+    macro_from_sums(S, P.w, m);
+    if (m.bad) atomicOr(P.flag, 1);
+    const double nu = P.delta * m.n * pow(m.T, 1.0 - P.omega);
+    sm.par[0] = m.n;
+    for (int a = 0; a < 3; ++a) {
+      sm.par[1 + a] = m.u[a];
+      sm.par[5 + a] = m.q[a];
+    }
+    sm.par[4] = m.T;
+    sm.par[8] = P.dt * nu;
+    sm.par[9] = 1.6 * (1.0 - P.Pr) / (m.n * m.T * m.T);
+    sm.par[10] = cbrt(m.n) / sqrt(kPi * m.T);
+  }
+  __syncthreads();
+  {
+    const double T = sm.par[4], dtnu = sm.par[8], A = sm.par[9], amp = sm.par[10];
+    const int NmP = padN(Nm);
+    for (int a = 0; a < 3; ++a)
+      for (int i = tid; i < NmP; i += blockDim.x) {
+        if (i >= N[a]) {  // zero padding up to a multiple of kRows
+          for (int t = a; t < 15; t += 3) tabp(sm, Nm, t)[i] = Real(0);
+          continue;
+        }
+        const double x = P.xi[a][i];
+        const double v = x - sm.par[1 + a];
+        tabp(sm, Nm, 0 + a)[i] = (Real)x;
+        tabp(sm, Nm, 3 + a)[i] = (Real)((a == 0 ? dtnu : 1.0) * amp * exp(-v * v / T));
+        tabp(sm, Nm, 6 + a)[i] = (Real)(A * sm.par[5 + a] * v);
+        tabp(sm, Nm, 9 + a)[i] = (Real)(v * v / T);
+        double g = 0.0;
+        for (int l = 0; l < 6; ++l) {
+          const SlotDev &sl = s_slot[l];
+          if (sl.axis == a) g -= sl.c * fmax(sl.sgn * x, 0.0);
+        }
+        tabp(sm, Nm, 12 + a)[i] = (Real)g;
+      }
+    for (int l = 0; l < 6; ++l) {
+      const SlotDev &sl = s_slot[l];
+      if (sl.axis < 0) continue;
+      for (int i = tid; i < NmP; i += blockDim.x)
+        tabp(sm, Nm, 15 + l)[i] =
+            i < N[sl.axis]
+                ? (Real)(-sl.c * fmin(sl.sgn * P.xi[sl.axis][i], 0.0) * s_scale[l])
+                : Real(0);
+    }
+  }
+  __syncthreads();
+}
+
 // minimum resident CTAs per SM the register allocation must allow
 template <typename Real>
 struct MinBlocks {
-  static constexpr int value = sizeof(Real) == 8 ? 2 : 3;
+  static constexpr int value = sizeof(Real) == 8 ? 2 : 4;
 };
 
 template <typename Real, int TS>
@@ -1073,67 +1138,211 @@ __global__ void __launch_bounds__(kTB, MinBlocks<Real>::value) tucker_step_kerne
       round_hosvd<Real, TS>(X, T1, T2, N, P.R, P.tol, P.nxt, c, sm, P.err, pc, nullptr);
       continue;
     }
-    // ---- prologue: macroparameters, wall densities
-    const double *S = P.sums + c * kSums;
-    if (tid < 6) {
-      s_slot[tid] = P.slot[c * 6 + tid];
-      s_scale[tid] = (s_slot[tid].kind == kWall) ? -S[16 + tid] / s_slot[tid].wall_den : 1.0;
-    }
-    if (tid == 0) {
-      CellMacro m;
-      macro_from_sums(S, P.w, m);
-      if (m.bad) atomicOr(P.flag, 1);
-      const double nu = P.delta * m.n * pow(m.T, 1.0 - P.omega);
-      sm.par[0] = m.n;
-      for (int a = 0; a < 3; ++a) {
-        sm.par[1 + a] = m.u[a];
-        sm.par[5 + a] = m.q[a];
-      }
-      sm.par[4] = m.T;
-      sm.par[8] = P.dt * nu;
-      sm.par[9] = 1.6 * (1.0 - P.Pr) / (m.n * m.T * m.T);
-      sm.par[10] = cbrt(m.n) / sqrt(kPi * m.T);
-    }
-    __syncthreads();
-    {
-      const double T = sm.par[4], dtnu = sm.par[8], A = sm.par[9], amp = sm.par[10];
-      const int NmP = padN(Nm);
-      for (int a = 0; a < 3; ++a)
-        for (int i = tid; i < NmP; i += blockDim.x) {
-          if (i >= N[a]) {  // zero padding up to a multiple of kRows
-            for (int t = a; t < 15; t += 3) tabp(sm, Nm, t)[i] = Real(0);
-            continue;
-          }
-          const double x = P.xi[a][i];
-          const double v = x - sm.par[1 + a];
-          tabp(sm, Nm, 0 + a)[i] = (Real)x;
-          tabp(sm, Nm, 3 + a)[i] = (Real)((a == 0 ? dtnu : 1.0) * amp * exp(-v * v / T));
-          tabp(sm, Nm, 6 + a)[i] = (Real)(A * sm.par[5 + a] * v);
-          tabp(sm, Nm, 9 + a)[i] = (Real)(v * v / T);
-          double g = 0.0;
-          for (int l = 0; l < 6; ++l) {
-            const SlotDev &sl = s_slot[l];
-            if (sl.axis == a) g -= sl.c * fmax(sl.sgn * x, 0.0);
-          }
-          tabp(sm, Nm, 12 + a)[i] = (Real)g;
-        }
-      for (int l = 0; l < 6; ++l) {
-        const SlotDev &sl = s_slot[l];
-        if (sl.axis < 0) continue;
-        for (int i = tid; i < NmP; i += blockDim.x)
-          tabp(sm, Nm, 15 + l)[i] =
-              i < N[sl.axis]
-                  ? (Real)(-sl.c * fmin(sl.sgn * P.xi[sl.axis][i], 0.0) * s_scale[l])
-                  : Real(0);
-      }
-    }
-    __syncthreads();
+    cell_prologue<Real>(P, c, N, sm, s_slot, s_scale);
     pc.mark(0);
     // ---- f^{n+1} before rounding, in one pass
     const double eX = assemble<Real>(P, c, N, sm, s_slot, s_scale, X, T2buf, pc);
     pc.mark(3);
     // ---- rounding
     round_hosvd<Real, TS>(X, T1, T2, N, P.R, P.tol, P.nxt, c, sm, P.err, pc, &P.cur, eX);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Phase-major variant of the step (same arithmetic as tucker_step_kernel, cell
+// for cell): each phase runs for a chunk of cells before the next starts, so
+// the short dependent chains of the eigen-solves (one warp per cell) overlap
+// across many cells instead of a few.
+//   asm      persistent CTAs: prologue + assembly -> X (global), ||X||^2
+//   gram(m)  one CTA per cell: Gram matrix of the mode-m unfolding -> C
+//   eig(m)   one warp per cell: basis, rank rule -> new factor U_m, rank
+//   proj(m)  one CTA per cell: X x_1 U1^T -> Y1, Y1 x_2 U2^T -> Y2,
+//            Y2 x_3 U3^T -> core (FP64 accumulation)
+
+template <typename Real>
+__global__ void __launch_bounds__(kTB, MinBlocks<Real>::value)
+    tucker_asm_kernel(TuckerStepParams P, TuckerSplitBufs B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem<Real> sm = carve<Real>(smem_raw, P.Nmax, P.R);
+  __shared__ SlotDev s_slot[6];
+  __shared__ double s_scale[6];
+  const int N[3] = {P.N1, P.N2, P.N3};
+  const int64_t NN = (int64_t)P.N1 * P.N2 * P.N3;
+  Real *T2buf = reinterpret_cast<Real *>(P.scratch) + (size_t)blockIdx.x * P.scratch_stride;
+  PhaseClock pc(nullptr);
+  for (int64_t j = blockIdx.x; j < B.cn; j += gridDim.x) {
+    const int64_t c = B.c0 + j;
+    cell_prologue<Real>(P, c, N, sm, s_slot, s_scale);
+    Real *X = reinterpret_cast<Real *>(B.X) + j * NN;
+    const double e = assemble<Real>(P, c, N, sm, s_slot, s_scale, X, T2buf, pc);
+    if (threadIdx.x == 0) {
+      B.e[j] = e;
+      B.disc[j] = 0.0;
+    }
+  }
+}
+
+// dims of the tensor whose mode-m unfolding the Gram / projection of mode m use
+__device__ __forceinline__ void split_dims(const TuckerSplitBufs &B, const TuckerDev &nxt,
+                                           int64_t c, int m, const int N[3], int D[3]) {
+  D[0] = m >= 1 ? nxt.rank[3 * c] : N[0];
+  D[1] = m >= 2 ? nxt.rank[3 * c + 1] : N[1];
+  D[2] = N[2];
+}
+
+template <typename Real>
+__device__ __forceinline__ const Real *split_src(const TuckerSplitBufs &B, int64_t j, int m, int R,
+                                                 const int N[3]) {
+  if (m == 0) return reinterpret_cast<const Real *>(B.X) + j * (int64_t)N[0] * N[1] * N[2];
+  if (m == 1) return reinterpret_cast<const Real *>(B.Y1) + j * (int64_t)R * N[1] * N[2];
+  return reinterpret_cast<const Real *>(B.Y2) + j * (int64_t)R * R * N[2];
+}
+
+// Gram matrix of the mode-m unfolding of cell j's tensor, into B.C[j] (n x n)
+template <typename Real, int TS>
+__global__ void __launch_bounds__(kTB) tucker_gram_kernel(TuckerStepParams P, TuckerSplitBufs B,
+                                                          int m) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int Nm = P.Nmax;
+  Smem<Real> sm{};
+  sm.C = reinterpret_cast<double *>(smem_raw);
+  sm.tile = reinterpret_cast<Real *>(smem_raw + sizeof(double) * Nm * Nm);
+  const int N[3] = {P.N1, P.N2, P.N3};
+  const int64_t j = blockIdx.x, c = B.c0 + j;
+  int D[3];
+  split_dims(B, P.nxt, c, m, N, D);
+  gram_tiled<Real, TS>(split_src<Real>(B, j, m, P.R, N), D, m, sm);
+  const int n = D[m];
+  double *out = B.C + j * (int64_t)Nm * Nm;
+  for (int i = threadIdx.x; i < n * n; i += blockDim.x) out[i] = sm.C[i];
+}
+
+template <typename Real>
+__host__ __device__ inline size_t smem_eig_bytes(int Nmax, int R) {
+  const int K = sub_k(Nmax, R);
+  size_t b = sizeof(double) *
+             (64 + (size_t)Nmax * Nmax + 2 * (size_t)Nmax * K + 2 * (size_t)K * K + K + 2);
+  b += sizeof(Real) * (size_t)Nmax * K;
+  b += sizeof(float) * ((size_t)Nmax * Nmax + 2 * (size_t)Nmax * K);
+  b += sizeof(int) * (2 * (size_t)K + 2);
+  return b + 64;
+}
+
+// Eigen-solve and rank rule of mode m for cell j: one warp per cell.  On exit
+// nxt.fac[m] holds the kept orthonormal columns, nxt.rank the new rank; the
+// energy left out accumulates in B.disc (the relative error is stored after
+// mode 3).
+template <typename Real>
+__global__ void __launch_bounds__(32) tucker_eig_kernel(TuckerStepParams P, TuckerSplitBufs B,
+                                                         int m) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int Nm = P.Nmax, R = P.R, K = sub_k(Nm, R);
+  Smem<Real> sm{};
+  sm.nmax = Nm;
+  sm.kdim = K;
+  {
+    size_t off = 0;
+    auto takeD = [&](size_t n) {
+      double *p = reinterpret_cast<double *>(smem_raw + off);
+      off += sizeof(double) * n;
+      return p;
+    };
+    sm.par = takeD(32);
+    sm.red = takeD(32);
+    sm.C = takeD((size_t)Nm * Nm);
+    sm.Q = takeD((size_t)Nm * K);
+    sm.W = takeD((size_t)Nm * K);
+    sm.B = takeD((size_t)K * K);
+    sm.Z = takeD((size_t)K * K);
+    sm.cs = takeD(K + 2);
+    sm.Vr = reinterpret_cast<Real *>(smem_raw + off);
+    off += sizeof(Real) * (size_t)Nm * K;
+    off = (off + 3) & ~size_t(3);
+    sm.C32 = reinterpret_cast<float *>(smem_raw + off);
+    off += sizeof(float) * (size_t)Nm * Nm;
+    sm.Q32 = reinterpret_cast<float *>(smem_raw + off);
+    off += sizeof(float) * (size_t)Nm * K;
+    sm.W32 = reinterpret_cast<float *>(smem_raw + off);
+    off += sizeof(float) * (size_t)Nm * K;
+    sm.pairs = reinterpret_cast<int *>(smem_raw + off);
+    off += sizeof(int) * (K + 2);
+    sm.perm = reinterpret_cast<int *>(smem_raw + off);
+  }
+  const int N[3] = {P.N1, P.N2, P.N3};
+  const int64_t j = blockIdx.x, c = B.c0 + j;
+  const int n = N[m];
+  const double *Cin = B.C + j * (int64_t)Nm * Nm;
+  for (int i = threadIdx.x; i < n * n; i += blockDim.x) sm.C[i] = Cin[i];
+  __syncthreads();
+  const double thr = P.tol * P.tol / 3.0 * B.e[j];
+  const double *wU = P.cur.fac[m] + c * (int64_t)n * R;
+  const int wr = P.cur.rank[3 * c + m];
+  int kmax = n < R + kExtra ? n : R + kExtra;
+  if (kmax > kOrthMax) kmax = kOrthMax;
+  PhaseClock pc(nullptr);
+  int k = (wr > 0 && thr > 0.0 && wr + kExtra < kmax) ? wr + kExtra : kmax;
+  k = leading_eigs<Real, double>(sm, n, k, wU, R, wr, pc);
+  bool met;
+  int r = choose_rank<Real>(sm, n, k, thr, R, &met);
+  if (!met && k < kmax) {
+    for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) sm.Vr[idx] = (Real)sm.W[idx];
+    __syncthreads();
+    k = leading_eigs<Real, Real>(sm, n, kmax, sm.Vr, k, k, pc);
+    r = choose_rank<Real>(sm, n, k, thr, R, &met);
+  }
+  double *U = P.nxt.fac[m] + c * (int64_t)n * R;
+  for (int idx = threadIdx.x; idx < n * r; idx += blockDim.x) {
+    const int i = idx / r, jj = idx - i * r;
+    U[(int64_t)i * R + jj] = sm.W[i * k + jj];
+  }
+  if (threadIdx.x == 0) {
+    P.nxt.rank[3 * c + m] = r;
+    const double d = B.disc[j] + sm.par[31];
+    B.disc[j] = d;
+    if (m == 2 && P.err) P.err[c] = B.e[j] > 0.0 ? sqrt(d / B.e[j]) : 0.0;
+  }
+}
+
+// Projection of mode m with the new factor: Y_{m+1} = Y_m x_m U_m^T (m = 0, 1,
+// working precision), or the core G = Y_2 x_3 U_3^T (m = 2, FP64 accumulation)
+template <typename Real>
+__global__ void __launch_bounds__(kTB) tucker_proj_kernel(TuckerStepParams P, TuckerSplitBufs B,
+                                                          int m) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int R = P.R;
+  const int N[3] = {P.N1, P.N2, P.N3};
+  const int64_t j = blockIdx.x, c = B.c0 + j;
+  int D[3];
+  split_dims(B, P.nxt, c, m, N, D);
+  const int n = D[m], r = P.nxt.rank[3 * c + m];
+  const double *U = P.nxt.fac[m] + c * (int64_t)n * R;
+  const Real *src = split_src<Real>(B, j, m, R, N);
+  if (m < 2) {
+    Smem<Real> sm{};
+    sm.Vr = reinterpret_cast<Real *>(smem_raw);
+    for (int idx = threadIdx.x; idx < n * r; idx += blockDim.x) {
+      const int i = idx / r, k = idx - i * r;
+      sm.Vr[idx] = (Real)U[(int64_t)i * R + k];
+    }
+    __syncthreads();
+    Real *dst = const_cast<Real *>(split_src<Real>(B, j, m + 1, R, N));
+    project<Real>(src, D, m, r, r, sm, dst);
+  } else {
+    double *Us = reinterpret_cast<double *>(smem_raw);
+    for (int idx = threadIdx.x; idx < n * r; idx += blockDim.x) {
+      const int i = idx / r, k = idx - i * r;
+      Us[idx] = U[(int64_t)i * R + k];
+    }
+    __syncthreads();
+    const int total = D[0] * D[1] * r;
+    double *G = P.nxt.core + c * (int64_t)R * R * R;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+      const int k3 = idx % r, k12 = idx / r;
+      const Real *y = src + (int64_t)k12 * n;
+      double s = 0.0;
+      for (int a = 0; a < n; ++a) s = fma(Us[a * r + k3], (double)y[a], s);
+      G[idx] = s;
+    }
   }
 }
 
@@ -1321,12 +1530,20 @@ int raise_smem_optin(K kernel, size_t smem, size_t &opted) {
 
 template <typename Real, int TS>
 struct OptIn {
-  static size_t step, expand;
+  static size_t step, expand, asm_, gram, eig, proj;
 };
 template <typename Real, int TS>
 size_t OptIn<Real, TS>::step = 0;
 template <typename Real, int TS>
 size_t OptIn<Real, TS>::expand = 0;
+template <typename Real, int TS>
+size_t OptIn<Real, TS>::asm_ = 0;
+template <typename Real, int TS>
+size_t OptIn<Real, TS>::gram = 0;
+template <typename Real, int TS>
+size_t OptIn<Real, TS>::eig = 0;
+template <typename Real, int TS>
+size_t OptIn<Real, TS>::proj = 0;
 
 template <typename Real, int TS>
 int launch_step_TS(const TuckerStepParams &p, int grid, cudaStream_t s) {
@@ -1343,6 +1560,51 @@ int launch_step_TS(const TuckerStepParams &p, int grid, cudaStream_t s) {
 template <typename Real>
 int launch_step_T(const TuckerStepParams &p, int grid, cudaStream_t s) {
   return p.Nmax <= 32 ? launch_step_TS<Real, 2>(p, grid, s) : launch_step_TS<Real, 4>(p, grid, s);
+}
+
+template <typename Real, int TS>
+struct SplitSmem {
+  size_t asm_, gram, eig, proj;
+  SplitSmem(int Nmax, int R) {
+    asm_ = smem_bytes<Real>(Nmax, R);
+    gram = sizeof(double) * (size_t)Nmax * Nmax + sizeof(Real) * (size_t)Nmax * kKP;
+    eig = smem_eig_bytes<Real>(Nmax, R);
+    proj = sizeof(double) * (size_t)Nmax * R;
+  }
+};
+
+template <typename Real, int TS>
+int prepare_split_TS(int Nmax, int R) {
+  const SplitSmem<Real, TS> z(Nmax, R);
+  using O = OptIn<Real, TS>;
+  if (raise_smem_optin(tucker_asm_kernel<Real>, z.asm_, O::asm_) != 0 ||
+      raise_smem_optin(tucker_gram_kernel<Real, TS>, z.gram, O::gram) != 0 ||
+      raise_smem_optin(tucker_eig_kernel<Real>, z.eig, O::eig) != 0 ||
+      raise_smem_optin(tucker_proj_kernel<Real>, z.proj, O::proj) != 0 ||
+      raise_smem_optin(tucker_step_kernel<Real, TS>, smem_bytes<Real>(Nmax, R), O::step) != 0)
+    return -1;
+  return 0;
+}
+
+template <typename Real, int TS>
+int launch_split_TS(const TuckerStepParams &p, TuckerSplitBufs b, int64_t chunk, int asm_grid,
+                    cudaStream_t s) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cap);
+  if (cap == cudaStreamCaptureStatusNone && prepare_split_TS<Real, TS>(p.Nmax, p.R) != 0) return -1;
+  const SplitSmem<Real, TS> z(p.Nmax, p.R);
+  for (int64_t c0 = 0; c0 < p.nc; c0 += chunk) {
+    b.c0 = c0;
+    b.cn = p.nc - c0 < chunk ? p.nc - c0 : chunk;
+    const int ga = (int)(b.cn < asm_grid ? b.cn : asm_grid);
+    tucker_asm_kernel<Real><<<ga, kTB, z.asm_, s>>>(p, b);
+    for (int m = 0; m < 3; ++m) {
+      tucker_gram_kernel<Real, TS><<<(unsigned)b.cn, kTB, z.gram, s>>>(p, b, m);
+      tucker_eig_kernel<Real><<<(unsigned)b.cn, 32, z.eig, s>>>(p, b, m);
+      tucker_proj_kernel<Real><<<(unsigned)b.cn, kTB, z.proj, s>>>(p, b, m);
+    }
+  }
+  return 0;
 }
 
 template <typename Real>
@@ -1392,6 +1654,27 @@ size_t tucker_smem_bytes(int Nmax, int R, bool fp64) {
 
 int launch_tucker_step(const TuckerStepParams &p, int grid, bool fp64, cudaStream_t s) {
   return fp64 ? launch_step_T<double>(p, grid, s) : launch_step_T<float>(p, grid, s);
+}
+
+int launch_tucker_split_step(const TuckerStepParams &p, TuckerSplitBufs b, int64_t chunk,
+                             int asm_grid, bool fp64, cudaStream_t s) {
+  if (fp64)
+    return p.Nmax <= 32 ? launch_split_TS<double, 2>(p, b, chunk, asm_grid, s)
+                        : launch_split_TS<double, 4>(p, b, chunk, asm_grid, s);
+  return p.Nmax <= 32 ? launch_split_TS<float, 2>(p, b, chunk, asm_grid, s)
+                      : launch_split_TS<float, 4>(p, b, chunk, asm_grid, s);
+}
+
+int tucker_prepare_launch(int Nmax, int R, bool fp64) {
+  if (fp64)
+    return Nmax <= 32 ? prepare_split_TS<double, 2>(Nmax, R) : prepare_split_TS<double, 4>(Nmax, R);
+  return Nmax <= 32 ? prepare_split_TS<float, 2>(Nmax, R) : prepare_split_TS<float, 4>(Nmax, R);
+}
+
+size_t tucker_split_bytes_per_cell(int N1, int N2, int N3, int R, int Nmax, bool fp64) {
+  const size_t es = fp64 ? sizeof(double) : sizeof(float);
+  return es * ((size_t)N1 * N2 * N3 + (size_t)R * N2 * N3 + (size_t)R * R * N3) +
+         sizeof(double) * ((size_t)Nmax * Nmax + 2);
 }
 
 int launch_tucker_expand(const TuckerDev &T, int64_t c0, int64_t ncell, int N1, int N2, int N3,

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstdlib>
 #include <string>
 #include <vector>
@@ -28,7 +29,11 @@ struct TuckerState {
   long long *phase = nullptr;  // [16] per-phase cycles (DVM_TUCKER_PHASES set)
   int max_grid = 0;             // CTAs the scratch is sized for
   bool tuned = false;           // grid picked by the autotuner
-  float tune_ms[5] = {0, 0, 0, 0, 0};  // step-kernel time per CTAs-per-SM candidate
+  float tune_ms[5] = {0, 0, 0, 0, 0};  // [0] phase-major step, [1..4] fused kernel per CTAs/SM
+  bool split = false;                  // phase-major variant chosen
+  TuckerSplitBufs sb{};                // its work buffers (one chunk of cells)
+  int64_t chunk = 0;                   // cells per chunk
+  void *split_mem = nullptr;
   cudaGraphExec_t graph = nullptr;     // two steps (returns to the same buffer parity)
   int graph_parity = -1;               // S->cur / S->scur when the graph was captured
   cudaStream_t gstream = nullptr;      // private stream the graph is captured on / replayed on
@@ -209,6 +214,10 @@ int tucker_alloc(dvm_ctx *C) {
   rc = ctx_malloc(C, reinterpret_cast<void **>(&S->err), sizeof(double) * nc);
   if (rc != DVM_OK) return rc;
   DVM_CUDA_TRY(cudaMemset(S->err, 0, sizeof(double) * nc));
+  if (tucker_prepare_launch(S->Nmax, R, S->fp64) != 0) {
+    set_error("Tucker kernels need more shared memory than the device allows");
+    return DVM_ERR_UNSUPPORTED;
+  }
   if (std::getenv("DVM_TUCKER_PHASES")) {
     rc = ctx_malloc(C, reinterpret_cast<void **>(&S->phase), sizeof(long long) * 16);
     if (rc != DVM_OK) return rc;
@@ -231,6 +240,7 @@ void tucker_free(dvm_ctx *C) {
   if (S->ev_in) cudaEventDestroy(S->ev_in);
   if (S->ev_out) cudaEventDestroy(S->ev_out);
   if (S->scratch) cudaFree(S->scratch);
+  if (S->split_mem) cudaFree(S->split_mem);
   if (S->ghostf) cudaFree(S->ghostf);
   if (S->err) cudaFree(S->err);
   if (S->phase) {
@@ -283,7 +293,9 @@ int enqueue_one_step(dvm_ctx *C, TuckerStepParams &p) {
   p.cur = S->buf[S->cur];
   p.nxt = S->buf[1 - S->cur];
   p.sums = C->d_sums[S->scur];
-  if (launch_tucker_step(p, S->grid, S->fp64, C->stream) != 0) {
+  const int lrc = S->split ? launch_tucker_split_step(p, S->sb, S->chunk, S->grid, S->fp64, C->stream)
+                           : launch_tucker_step(p, S->grid, S->fp64, C->stream);
+  if (lrc != 0) {
     set_error("Tucker kernel needs more shared memory than the device allows");
     return DVM_ERR_UNSUPPORTED;
   }
@@ -299,15 +311,67 @@ int enqueue_one_step(dvm_ctx *C, TuckerStepParams &p) {
   return DVM_OK;
 }
 
-// Autotuner: time the step kernel once for each resident-CTAs-per-SM choice the
-// scratch allows (writing into the spare buffer, so the state is untouched; a
-// cell's arithmetic does not depend on which CTA runs it) and keep the fastest.
+// Work buffers of the phase-major variant for a chunk of at most 1/8 of the
+// free device memory (at most all cells).
+int alloc_split(dvm_ctx *C) {
+  TuckerState *S = C->tucker;
+  size_t free_b = 0, total_b = 0;
+  DVM_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+  const size_t per =
+      tucker_split_bytes_per_cell(C->N[0], C->N[1], C->N[2], S->R, S->Nmax, S->fp64) + 64;
+  const int64_t chunk = std::min<int64_t>(C->nc, (int64_t)(free_b / 8 / per));
+  if (chunk < 1) {
+    set_error("no device memory for the phase-major Tucker step buffers");
+    return DVM_ERR_OOM;
+  }
+  void *mem = nullptr;
+  int rc = ctx_malloc(C, &mem, per * chunk);
+  if (rc != DVM_OK) return rc;
+  const size_t es = S->fp64 ? sizeof(double) : sizeof(float);
+  char *q = static_cast<char *>(mem);
+  TuckerSplitBufs b{};
+  b.X = q;
+  q += es * chunk * C->N[0] * C->N[1] * C->N[2];
+  b.Y1 = q;
+  q += es * chunk * S->R * C->N[1] * C->N[2];
+  b.Y2 = q;
+  q += es * chunk * S->R * S->R * C->N[2];
+  q = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(q) + 255) & ~uintptr_t(255));
+  b.C = reinterpret_cast<double *>(q);
+  q += sizeof(double) * chunk * S->Nmax * S->Nmax;
+  b.e = reinterpret_cast<double *>(q);
+  q += sizeof(double) * chunk;
+  b.disc = reinterpret_cast<double *>(q);
+  S->sb = b;
+  S->chunk = chunk;
+  S->split_mem = mem;
+  return DVM_OK;
+}
+
+void free_split(dvm_ctx *C) {
+  TuckerState *S = C->tucker;
+  if (!S->split_mem) return;
+  cudaFree(S->split_mem);
+  C->bytes -= std::min(C->bytes, (tucker_split_bytes_per_cell(C->N[0], C->N[1], C->N[2], S->R,
+                                                              S->Nmax, S->fp64) + 64) * S->chunk);
+  S->split_mem = nullptr;
+  S->chunk = 0;
+}
+
+// Autotuner, on the first step: time the fused step kernel once for each
+// resident-CTAs-per-SM choice the scratch allows and, unless the variant is
+// fixed, the phase-major step; keep the fastest.  Tuning launches write into the
+// spare buffer, so the state is untouched (a cell's arithmetic does not depend
+// on which CTA or variant runs it).  Meshes with no more cells than SMs keep the
+// fused kernel at one cell per CTA unless the phase-major variant is requested.
 int autotune(dvm_ctx *C) {
   TuckerState *S = C->tucker;
   S->tuned = true;
+  const int variant = C->opts.variant;
   int sms = 1;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, C->device);
-  if (std::getenv("DVM_NO_AUTOTUNE") || C->nc <= sms) return DVM_OK;
+  const bool small = C->nc <= sms || std::getenv("DVM_NO_AUTOTUNE");
+  if (small && variant != DVM_VARIANT_PHASED) return DVM_OK;
   TuckerStepParams p = step_params(C);
   p.mode = 0;
   p.cur = S->buf[S->cur];
@@ -317,27 +381,47 @@ int autotune(dvm_ctx *C) {
   cudaEvent_t e0, e1;
   DVM_CUDA_TRY(cudaEventCreate(&e0));
   DVM_CUDA_TRY(cudaEventCreate(&e1));
-  float best = 1e30f;
-  int best_grid = S->grid;
-  for (int per_sm = 1; per_sm <= 4; ++per_sm) {
-    const int grid = (int)std::min<int64_t>(C->nc, (int64_t)sms * per_sm);
-    if (grid > S->max_grid) break;
-    if (launch_tucker_step(p, grid, S->fp64, C->stream) != 0) break;  // warm-up
+  auto timed = [&](auto &&launch) -> float {
+    if (launch() != 0) return -1.f;  // warm-up
     cudaEventRecord(e0, C->stream);
-    launch_tucker_step(p, grid, S->fp64, C->stream);
+    launch();
     cudaEventRecord(e1, C->stream);
-    if (cudaEventSynchronize(e1) != cudaSuccess) break;
+    if (cudaEventSynchronize(e1) != cudaSuccess) return -1.f;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
+    return ms;
+  };
+  float best = 1e30f;
+  int best_grid = S->grid;
+  for (int per_sm = 1; per_sm <= 4 && !small; ++per_sm) {
+    const int grid = (int)std::min<int64_t>(C->nc, (int64_t)sms * per_sm);
+    if (grid > S->max_grid) break;
+    const float ms = timed([&] { return launch_tucker_step(p, grid, S->fp64, C->stream); });
+    if (ms < 0.f) break;
     S->tune_ms[per_sm] = ms;
     if (ms < best) {
       best = ms;
       best_grid = grid;
     }
   }
+  S->grid = best_grid;
+  int rc = DVM_OK;
+  if (variant != DVM_VARIANT_FUSED && !std::getenv("DVM_NO_SPLIT")) {
+    rc = alloc_split(C);
+    if (rc == DVM_OK) {
+      const float ms = timed([&] {
+        return launch_tucker_split_step(p, S->sb, S->chunk, S->grid, S->fp64, C->stream);
+      });
+      if (ms > 0.f) S->tune_ms[0] = ms;
+      S->split = variant == DVM_VARIANT_PHASED || (ms > 0.f && ms < best);
+      if (!S->split) free_split(C);
+    } else if (variant != DVM_VARIANT_PHASED) {
+      rc = DVM_OK;  // no memory for the buffers: keep the fused kernel
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  S->grid = best_grid;
+  if (rc != DVM_OK) return rc;
   DVM_CUDA_TRY(cudaGetLastError());
   return DVM_OK;
 }
@@ -408,7 +492,7 @@ int tucker_step(dvm_ctx *C, int32_t nsteps, double *residual_out) {
 
 int tucker_launch_info(dvm_ctx *C, int32_t *grid, float *tune_ms) {
   TuckerState *S = C->tucker;
-  if (grid) *grid = S->grid;
+  if (grid) *grid = S->split ? -S->grid : S->grid;
   if (tune_ms)
     for (int i = 0; i < 5; ++i) tune_ms[i] = S->tune_ms[i];
   return DVM_OK;
