@@ -42,6 +42,9 @@ struct TuckerSplitBufs {
   double *C;     // [cn][Nmax*Nmax] Gram matrix of the current mode
   double *e;     // [cn] ||X||^2
   double *disc;  // [cn] energy left out so far
+  void *t2;      // assembly staging, t2_stride elements per assembly CTA
+  size_t t2_stride;
+  int asm_grid;  // assembly CTAs (persistent over the chunk)
   int64_t c0, cn;
 };
 
@@ -65,12 +68,14 @@ size_t tucker_scratch_elems(int N1, int N2, int N3, int R);
 size_t tucker_smem_bytes(int Nmax, int R, bool fp64);
 int tucker_step_blocks_per_sm(int Nmax, int R, bool fp64);
 int launch_tucker_step(const TuckerStepParams &p, int grid, bool fp64, cudaStream_t s);
-// phase-major step over chunks of `chunk` cells (buffers sized for one chunk);
-// asm_grid persistent CTAs for the assembly
+// phase-major step over chunks of `chunk` cells (buffers sized for one chunk)
 int launch_tucker_split_step(const TuckerStepParams &p, TuckerSplitBufs b, int64_t chunk,
-                             int asm_grid, bool fp64, cudaStream_t s);
+                             bool fp64, cudaStream_t s);
 // bytes of TuckerSplitBufs per cell (working precision fp64 or float)
 size_t tucker_split_bytes_per_cell(int N1, int N2, int N3, int R, int Nmax, bool fp64);
+// assembly CTAs per SM of the phase-major variant and their staging elements
+int tucker_split_asm_per_sm();
+size_t tucker_split_t2_elems(int N1, int N2, int N3, int R);
 // raise the kernels' shared-memory opt-in for this size (outside stream captures)
 int tucker_prepare_launch(int Nmax, int R, bool fp64);
 int launch_tucker_expand(const TuckerDev &T, int64_t c0, int64_t ncell, int N1, int N2, int N3,

@@ -44,6 +44,10 @@ namespace {
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kTB = 256;   // threads per CTA for the step / rounding kernel
 constexpr int kKC = 32;    // column chunk of the Gram tiles
+// tile row of gram_w32: a warp reads rows 4 apart from 8 adjacent columns; a
+// stride of 2 mod 8 words puts those 4 rows on disjoint banks
+constexpr int kKP2 = kKC + 2;
+constexpr int kTileRow = kKP2 > kKC + 1 ? kKP2 : kKC + 1;  // row length of the tile buffers
 constexpr int kExtra = 4;  // oversampling columns of the subspace iteration
 constexpr int kPower = 3;     // orthogonal (power) iterations from a cold start
 constexpr int kWarmIter = 1;  // orthogonal iterations from the previous step's factor
@@ -83,13 +87,16 @@ template <typename Real>
 struct Smem {
   int nmax;       // Nmax the layout was carved for
   int kdim;       // K: columns of the eigen-solver blocks
+  int asm_space;  // doubles at sm.C usable as assembly staging space
   double *par;    // [32] cell scalars
   double *red;    // [32]
   double *C;      // [Nmax*Nmax] Gram matrix (FP64)
+  const double *Cg;  // the Gram matrix the eigen-solver reads (sm.C or a global copy)
+  Real *tile2;    // second Gram tile buffer (prefetch), or null
   double *Q;      // [Nmax*K] subspace basis
   double *W;      // [Nmax*K] C*Q, then the Ritz vectors
   double *B;      // [K*K] projected matrix
-  double *Z;      // [K*K] its eigenvectors
+  double *Z;      // [K] sorted Rayleigh quotients
   double *cs;     // [K+2] Jacobi cosines / sines
   Real *rt;       // [kTabs][Nmax] assembly tables
   Real *fac[3];   // [Nmax*R] factor rows of the expansion in progress
@@ -98,8 +105,8 @@ struct Smem {
   Real *tile;     // [Nmax*(kKC+1)] Gram tile
   Real *Vr;       // [Nmax*K] kept eigenvectors in the working precision
   float *C32;     // [Nmax*Nmax] FP32 copy of C (mixed path: power iterations)
-  float *Q32;     // [Nmax*K]
-  float *W32;     // [Nmax*K]
+  float *Q32;     // [Nmax*K] (inside sm.W)
+  float *W32;     // [Nmax*K] (inside sm.W)
   int *pairs;     // [K+2]
   int *perm;      // [K]
 };
@@ -108,12 +115,12 @@ template <typename Real>
 __host__ __device__ inline size_t smem_bytes(int Nmax, int R) {
   const int K = sub_k(Nmax, R);
   size_t b = sizeof(double) *
-             (64 + (size_t)Nmax * Nmax + 2 * (size_t)Nmax * K + 2 * (size_t)K * K + K + 2);
+             (64 + (size_t)Nmax * Nmax + 2 * (size_t)Nmax * K + (size_t)K * K + 2 * K + 2);
   b += sizeof(Real) * ((size_t)kTabs * padN(Nmax) + 3 * (size_t)Nmax * R +
                        (kTerms + 1) * (size_t)R * padN(Nmax) +
-                       (size_t)Nmax * (kKC + 1) +
+                       (size_t)(Nmax > 32 ? Nmax : 32) * kTileRow +
                        (size_t)Nmax * K);
-  b += sizeof(float) * ((size_t)Nmax * Nmax + 2 * (size_t)Nmax * K);
+  b += sizeof(float) * (size_t)Nmax * Nmax;
   b += sizeof(int) * (2 * (size_t)K + 2);
   return b + 64;
 }
@@ -124,6 +131,7 @@ __device__ Smem<Real> carve(unsigned char *base, int Nmax, int R) {
   Smem<Real> s;
   s.nmax = Nmax;
   s.kdim = K;
+  s.asm_space = Nmax * Nmax + 2 * Nmax * K;
   size_t off = 0;
   auto takeD = [&](size_t n) {
     double *p = reinterpret_cast<double *>(base + off);
@@ -133,10 +141,12 @@ __device__ Smem<Real> carve(unsigned char *base, int Nmax, int R) {
   s.par = takeD(32);
   s.red = takeD(32);
   s.C = takeD((size_t)Nmax * Nmax);
+  s.Cg = s.C;
+  s.tile2 = nullptr;
   s.Q = takeD((size_t)Nmax * K);
   s.W = takeD((size_t)Nmax * K);
   s.B = takeD((size_t)K * K);
-  s.Z = takeD((size_t)K * K);
+  s.Z = takeD((size_t)K);
   s.cs = takeD(K + 2);
   auto takeR = [&](size_t n) {
     Real *p = reinterpret_cast<Real *>(base + off);
@@ -146,25 +156,24 @@ __device__ Smem<Real> carve(unsigned char *base, int Nmax, int R) {
   s.rt = takeR((size_t)kTabs * padN(Nmax));
   for (int a = 0; a < 3; ++a) s.fac[a] = takeR((size_t)Nmax * R);
   s.u1 = takeR((size_t)(kTerms + 1) * R * padN(Nmax));
-  s.tile = takeR((size_t)Nmax * (kKC + 1));
+  s.tile = takeR((size_t)(Nmax > 32 ? Nmax : 32) * kTileRow);
   s.Vr = takeR((size_t)Nmax * K);
   off = (off + 3) & ~size_t(3);
   s.C32 = reinterpret_cast<float *>(base + off);
   off += sizeof(float) * (size_t)Nmax * Nmax;
-  s.Q32 = reinterpret_cast<float *>(base + off);
-  off += sizeof(float) * (size_t)Nmax * K;
-  s.W32 = reinterpret_cast<float *>(base + off);
-  off += sizeof(float) * (size_t)Nmax * K;
+  // the FP32 iteration blocks live in sm.W (consumed before sm.W is written)
+  s.Q32 = reinterpret_cast<float *>(s.W);
+  s.W32 = s.Q32 + (size_t)Nmax * K;
   s.pairs = reinterpret_cast<int *>(base + off);
   off += sizeof(int) * (K + 2);
   s.perm = reinterpret_cast<int *>(base + off);
   return s;
 }
 
-// doubles from sm.C to the end of sm.W (contiguous): work space of the assembly
+// doubles at sm.C usable by the assembly as staging space
 template <typename Real>
 __device__ __forceinline__ int asm_space_doubles(const Smem<Real> &sm) {
-  return sm.nmax * sm.nmax + 2 * sm.nmax * sm.kdim;
+  return sm.asm_space;
 }
 
 __device__ __forceinline__ double block_sum_d(double v, double *red) {
@@ -339,10 +348,190 @@ __device__ void gram_tiled(const Real *T, const int D[3], int m, Smem<Real> &sm)
   __syncthreads();
 }
 
-// TS = 2 covers n <= 32 and TS = 4 covers n <= 64 (16 x 16 thread grid)
+// Double-float (hi, lo) sum of two pairs (Knuth's two-sum of the high parts,
+// low parts added), renormalised.
+__device__ __forceinline__ void df_add(float &hi, float &lo, float h2, float l2) {
+  const float s = __fadd_rn(hi, h2);
+  const float bb = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(h2, bb));
+  const float t = __fadd_rn(__fadd_rn(lo, l2), err);
+  hi = __fadd_rn(s, t);
+  lo = __fsub_rn(t, __fsub_rn(hi, s));
+}
+
+// Gram matrix for n <= 32 with every thread of a 256-thread CTA busy: the upper
+// triangle of the 8 x 8 grid of 4 x 4 blocks is 28 off-diagonal blocks plus 8
+// diagonal ones, taken as 28 + 4 work items (a diagonal item is two diagonal
+// blocks, 2 x 10 distinct entries); each item is split 8 ways over the
+// columns of every tile (group g takes tile columns g, g + 8, ...).  The 8
+// partial sums of an entry sit in 8 adjacent lanes and are combined by a fixed
+// shuffle tree (double-float on the mixed path), so the result does not depend
+// on scheduling.  Same precision contract as gram_tiled.
+template <typename Real>
+__device__ __noinline__ void gram_w32(const Real *T, const int D[3], int m, Smem<Real> &sm) {
+  constexpr bool f32 = sizeof(Real) == 4;
+  const int n = D[m];
+  const int cols = (D[0] * D[1] * D[2]) / n;
+  const int item = threadIdx.x >> 3, g = threadIdx.x & 7;
+  const bool diag = item >= 28;
+  int ta, tb;
+  if (!diag) {  // item -> (ta < tb), row-major over the strict upper triangle
+    int t = item;
+    ta = 0;
+    while (t >= 7 - ta) {
+      t -= 7 - ta;
+      ++ta;
+    }
+    tb = ta + 1 + t;
+  } else {
+    ta = item - 28;  // diagonal blocks ta and ta + 4
+    tb = ta + 4;
+  }
+  Real hi[20], lo[20];
+#pragma unroll
+  for (int i = 0; i < 20; ++i) hi[i] = lo[i] = Real(0);
+  // tiles of kKC columns; each thread stages 32 * kKC / 256 elements of the next
+  // tile in registers while the current one is used (two buffers when
+  // sm.tile2 is set: one barrier per tile)
+  constexpr int kPer = 32 * kKC / 256;
+  Real pre[kPer];
+  auto fetch = [&](int j0) {
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int idx = threadIdx.x + 256 * q;
+      const int a = idx / kKC, jj = idx - a * kKC, j = j0 + jj;
+      Real v = 0;
+      if (a < n && j < cols) {
+        int64_t addr;
+        if (m == 0) {
+          addr = (int64_t)a * cols + j;
+        } else if (m == 1) {
+          const int kk = j / D[2], i = j - kk * D[2];
+          addr = ((int64_t)kk * D[1] + a) * D[2] + i;
+        } else {
+          addr = (int64_t)j * D[2] + a;
+        }
+        v = T[addr];
+      }
+      pre[q] = v;
+    }
+  };
+  auto stage = [&](Real *buf) {
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int idx = threadIdx.x + 256 * q;
+      const int a = idx / kKC, jj = idx - a * kKC;
+      buf[a * kKP2 + jj] = pre[q];
+    }
+  };
+  fetch(0);
+  stage(sm.tile);
+  __syncthreads();
+  for (int j0 = 0, t = 0; j0 < cols; j0 += kKC, ++t) {
+    const Real *cur = (sm.tile2 && (t & 1)) ? sm.tile2 : sm.tile;
+    const bool more = j0 + kKC < cols;
+    if (more) fetch(j0 + kKC);
+#pragma unroll
+    for (int q = 0; q < kKC / 8; ++q) {
+      const int kk = g + 8 * q;
+      Real xa[4], xb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        xa[i] = cur[(4 * ta + i) * kKP2 + kk];
+        xb[i] = cur[(4 * tb + i) * kKP2 + kk];
+      }
+      if (!diag) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if constexpr (f32) df_acc(xa[i], xb[j], hi[4 * i + j], lo[4 * i + j]);
+            else hi[4 * i + j] = fma(xa[i], xb[j], hi[4 * i + j]);
+          }
+      } else {
+        int e = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = i; j < 4; ++j, ++e) {
+            if constexpr (f32) {
+              df_acc(xa[i], xa[j], hi[e], lo[e]);
+              df_acc(xb[i], xb[j], hi[10 + e], lo[10 + e]);
+            } else {
+              hi[e] = fma(xa[i], xa[j], hi[e]);
+              hi[10 + e] = fma(xb[i], xb[j], hi[10 + e]);
+            }
+          }
+      }
+    }
+    if constexpr (f32) {
+#pragma unroll
+      for (int i = 0; i < 20; ++i) {  // renormalise (fast two-sum)
+        const float sum = __fadd_rn(hi[i], lo[i]);
+        lo[i] = __fsub_rn(lo[i], __fsub_rn(sum, hi[i]));
+        hi[i] = sum;
+      }
+    }
+    if (sm.tile2) {
+      if (more) stage((t & 1) ? sm.tile : sm.tile2);
+      __syncthreads();
+    } else {
+      __syncthreads();
+      if (more) {
+        stage(sm.tile);
+        __syncthreads();
+      }
+    }
+  }
+  // combine the 8 column groups (lanes 8*item' + g of this warp)
+#pragma unroll
+  for (int i = 0; i < 20; ++i) {
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      const Real h2 = __shfl_xor_sync(0xffffffffu, hi[i], o);
+      if constexpr (f32) {
+        const float l2 = __shfl_xor_sync(0xffffffffu, lo[i], o);
+        df_add(hi[i], lo[i], h2, l2);
+      } else {
+        hi[i] = hi[i] + h2;
+      }
+    }
+  }
+  if (g == 0) {
+    auto put = [&](int a, int b, double v) {
+      if (a < n && b < n) {
+        sm.C[a * n + b] = v;
+        sm.C[b * n + a] = v;
+      }
+    };
+    if (!diag) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          put(4 * ta + i, 4 * tb + j, (double)hi[4 * i + j] + (double)lo[4 * i + j]);
+    } else {
+      int e = 0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = i; j < 4; ++j, ++e) {
+          put(4 * ta + i, 4 * ta + j, (double)hi[e] + (double)lo[e]);
+          put(4 * tb + i, 4 * tb + j, (double)hi[10 + e] + (double)lo[10 + e]);
+        }
+    }
+  }
+  __syncthreads();
+}
+
+// n <= 32 with 256 threads: gram_w32; otherwise the 16 x 16 thread grid (TS = 2
+// covers n <= 32, TS = 4 covers n <= 64)
 template <typename Real, int TS>
 __device__ void gram(const Real *T, const int D[3], int m, Smem<Real> &sm) {
-  gram_tiled<Real, TS>(T, D, m, sm);
+  if (D[m] <= 32 && blockDim.x == 256)
+    gram_w32<Real>(T, D, m, sm);
+  else
+    gram_tiled<Real, TS>(T, D, m, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -350,7 +539,7 @@ __device__ void gram(const Real *T, const int D[3], int m, Smem<Real> &sm) {
 
 // W[n x k] = C[n x n] Q[n x k]
 template <typename T>
-__device__ void mat_cq(const T *C, const T *Q, T *W, int n, int k) {
+__device__ void mat_cq(const T *__restrict__ C, const T *Q, T *W, int n, int k) {
   for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) {
     const int i = idx / k, j = idx - i * k;
     T s = 0;
@@ -513,7 +702,7 @@ __device__ __noinline__ int orthonormalise(T *Q, int n, int k, A *Gs, A *dinv, i
   return nz;
 }
 
-// Leading eigenvectors of the n x n Gram matrix sm.C by orthogonal (block
+// Leading eigenvectors of the n x n Gram matrix sm.Cg by orthogonal (block
 // power) iteration with k basis columns: the start block is the warm basis
 // (r_warm columns, row stride ldw: the previous step's orthonormal factor, which
 // spans most of the new dominant subspace) completed by fixed start vectors.
@@ -536,7 +725,7 @@ __device__ __noinline__ int leading_eigs(Smem<Real> &sm, int n, int k, const WT 
     }
     __syncthreads();
     for (int it = 0; it < iters; ++it) {
-      mat_cq(sm.C, sm.Q, sm.W, n, k);
+      mat_cq(sm.Cg, sm.Q, sm.W, n, k);
       for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) sm.Q[idx] = sm.W[idx];
       __syncthreads();
       pc.mark(11);
@@ -547,7 +736,7 @@ __device__ __noinline__ int leading_eigs(Smem<Real> &sm, int n, int k, const WT 
       pc.mark(12);
     }
   } else {
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) sm.C32[idx] = (float)sm.C[idx];
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) sm.C32[idx] = (float)sm.Cg[idx];
     for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) {
       const int i = idx / k, j = idx - i * k;
       sm.Q32[idx] = (float)(j < r_warm ? (double)warm[(int64_t)i * ldw + j] : start_value(i, j));
@@ -564,7 +753,7 @@ __device__ __noinline__ int leading_eigs(Smem<Real> &sm, int n, int k, const WT 
     }
     for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) sm.Q[idx] = (double)sm.Q32[idx];
     __syncthreads();
-    mat_cq(sm.C, sm.Q, sm.W, n, k);
+    mat_cq(sm.Cg, sm.Q, sm.W, n, k);
     for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) sm.Q[idx] = sm.W[idx];
     __syncthreads();
     pc.mark(11);
@@ -575,7 +764,7 @@ __device__ __noinline__ int leading_eigs(Smem<Real> &sm, int n, int k, const WT 
   // Rayleigh quotients d_j = q_j^T C q_j of the orthonormal columns (FP64): any
   // leading set of columns captures exactly the sum of its d_j, so the columns
   // are ordered by d_j and the rank rule reads them (sorted, in sm.Z).
-  mat_cq(sm.C, sm.Q, sm.W, n, k);
+  mat_cq(sm.Cg, sm.Q, sm.W, n, k);
   if ((threadIdx.x >> 5) == 0) {
     const int lane = threadIdx.x & 31;
     for (int j = 0; j < k; ++j) {
@@ -618,7 +807,7 @@ template <typename Real>
 __device__ int choose_rank(Smem<Real> &sm, int n, int k, double thr, int cap, bool *met) {
   if (threadIdx.x == 0) {
     double tr = 0.0;
-    for (int i = 0; i < n; ++i) tr += sm.C[i * n + i];
+    for (int i = 0; i < n; ++i) tr += sm.Cg[i * n + i];
     double kept = 0.0;
     int r = k, found = 0;
     for (int j = 0; j < k && thr > 0.0; ++j) {
@@ -921,7 +1110,7 @@ __device__ __noinline__ double assemble(const TuckerStepParams &P, int64_t c, co
   const Real *V0 = tabp(sm, Nm, 9), *V1 = tabp(sm, Nm, 10), *V2 = tabp(sm, Nm, 11);
   const Real *G0 = tabp(sm, Nm, 12), *G1 = tabp(sm, Nm, 13), *G2 = tabp(sm, Nm, 14);
   const int nch = N1P / kRows;
-  double en = 0.0;
+  Real ens = 0, enc = 0;
   for (int item = tid; item < NP * nch; item += blockDim.x) {
     const int p = item % NP, ch = item / NP;
     const int i2 = p / N3, i3 = p - i2 * N3;
@@ -1035,11 +1224,16 @@ __device__ __noinline__ double assemble(const TuckerStepParams &P, int64_t c, co
       const int i1 = i10 + j;
       if (i1 < N1) {
         X[(int64_t)i1 * NP + p] = acc[j];
-        en += (double)acc[j] * (double)acc[j];
+        // ||X||^2 only scales the truncation threshold: a compensated (Kahan)
+        // sum in the working precision per thread is ample
+        const Real y = acc[j] * acc[j] - enc;
+        const Real t = ens + y;
+        enc = (t - ens) - y;
+        ens = t;
       }
     }
   }
-  return block_sum_d(en, sm.red);
+  return block_sum_d((double)ens - (double)enc, sm.red);
 }
 
 // Per-cell prologue of the assembly: slots, wall-density scales, the cell's
@@ -1159,16 +1353,49 @@ __global__ void __launch_bounds__(kTB, MinBlocks<Real>::value) tucker_step_kerne
 //   proj(m)  one CTA per cell: X x_1 U1^T -> Y1, Y1 x_2 U2^T -> Y2,
 //            Y2 x_3 U3^T -> core (FP64 accumulation)
 
+constexpr int kAsmTB = 128;  // threads per CTA of the phase-major assembly kernel
+
+// Shared memory of the assembly kernel: cell scalars, the core staging space
+// (one first-mode slab of G and of its mode-3 contraction), tables, factor rows.
 template <typename Real>
-__global__ void __launch_bounds__(kTB, MinBlocks<Real>::value)
+__host__ __device__ inline size_t smem_asm_bytes(int Nmax, int R) {
+  const size_t stage = ((size_t)R * (R + Nmax) * sizeof(Real) + 7) / 8;  // doubles
+  return sizeof(double) * (64 + stage) +
+         sizeof(Real) * ((size_t)kTabs * padN(Nmax) + 3 * (size_t)Nmax * R +
+                         (kTerms + 1) * (size_t)R * padN(Nmax)) +
+         64;
+}
+
+template <typename Real>
+__device__ Smem<Real> carve_asm(unsigned char *base, int Nmax, int R) {
+  Smem<Real> s{};
+  const int stage = (int)(((size_t)R * (R + Nmax) * sizeof(Real) + 7) / 8);
+  s.nmax = Nmax;
+  s.par = reinterpret_cast<double *>(base);
+  s.red = s.par + 32;
+  s.C = s.red + 32;
+  s.asm_space = stage;
+  Real *r = reinterpret_cast<Real *>(s.C + stage);
+  s.rt = r;
+  r += (size_t)kTabs * padN(Nmax);
+  for (int a = 0; a < 3; ++a) {
+    s.fac[a] = r;
+    r += (size_t)Nmax * R;
+  }
+  s.u1 = r;
+  return s;
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(kAsmTB, sizeof(Real) == 8 ? 4 : 6)
     tucker_asm_kernel(TuckerStepParams P, TuckerSplitBufs B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem<Real> sm = carve<Real>(smem_raw, P.Nmax, P.R);
+  Smem<Real> sm = carve_asm<Real>(smem_raw, P.Nmax, P.R);
   __shared__ SlotDev s_slot[6];
   __shared__ double s_scale[6];
   const int N[3] = {P.N1, P.N2, P.N3};
   const int64_t NN = (int64_t)P.N1 * P.N2 * P.N3;
-  Real *T2buf = reinterpret_cast<Real *>(P.scratch) + (size_t)blockIdx.x * P.scratch_stride;
+  Real *T2buf = reinterpret_cast<Real *>(B.t2) + (size_t)blockIdx.x * B.t2_stride;
   PhaseClock pc(nullptr);
   for (int64_t j = blockIdx.x; j < B.cn; j += gridDim.x) {
     const int64_t c = B.c0 + j;
@@ -1207,11 +1434,12 @@ __global__ void __launch_bounds__(kTB) tucker_gram_kernel(TuckerStepParams P, Tu
   Smem<Real> sm{};
   sm.C = reinterpret_cast<double *>(smem_raw);
   sm.tile = reinterpret_cast<Real *>(smem_raw + sizeof(double) * Nm * Nm);
+  sm.tile2 = sm.tile + (size_t)(Nm > 32 ? Nm : 32) * kTileRow;
   const int N[3] = {P.N1, P.N2, P.N3};
   const int64_t j = blockIdx.x, c = B.c0 + j;
   int D[3];
   split_dims(B, P.nxt, c, m, N, D);
-  gram_tiled<Real, TS>(split_src<Real>(B, j, m, P.R, N), D, m, sm);
+  gram<Real, TS>(split_src<Real>(B, j, m, P.R, N), D, m, sm);
   const int n = D[m];
   double *out = B.C + j * (int64_t)Nm * Nm;
   for (int i = threadIdx.x; i < n * n; i += blockDim.x) out[i] = sm.C[i];
@@ -1220,10 +1448,9 @@ __global__ void __launch_bounds__(kTB) tucker_gram_kernel(TuckerStepParams P, Tu
 template <typename Real>
 __host__ __device__ inline size_t smem_eig_bytes(int Nmax, int R) {
   const int K = sub_k(Nmax, R);
-  size_t b = sizeof(double) *
-             (64 + (size_t)Nmax * Nmax + 2 * (size_t)Nmax * K + 2 * (size_t)K * K + K + 2);
+  size_t b = sizeof(double) * (64 + 2 * (size_t)Nmax * K + (size_t)K * K + 2 * K + 2);
   b += sizeof(Real) * (size_t)Nmax * K;
-  b += sizeof(float) * ((size_t)Nmax * Nmax + 2 * (size_t)Nmax * K);
+  b += sizeof(float) * (size_t)Nmax * Nmax;
   b += sizeof(int) * (2 * (size_t)K + 2);
   return b + 64;
 }
@@ -1233,8 +1460,8 @@ __host__ __device__ inline size_t smem_eig_bytes(int Nmax, int R) {
 // energy left out accumulates in B.disc (the relative error is stored after
 // mode 3).
 template <typename Real>
-__global__ void __launch_bounds__(32) tucker_eig_kernel(TuckerStepParams P, TuckerSplitBufs B,
-                                                         int m) {
+__global__ void __launch_bounds__(32, 13) tucker_eig_kernel(TuckerStepParams P, TuckerSplitBufs B,
+                                                             int m) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int Nm = P.Nmax, R = P.R, K = sub_k(Nm, R);
   Smem<Real> sm{};
@@ -1249,21 +1476,18 @@ __global__ void __launch_bounds__(32) tucker_eig_kernel(TuckerStepParams P, Tuck
     };
     sm.par = takeD(32);
     sm.red = takeD(32);
-    sm.C = takeD((size_t)Nm * Nm);
     sm.Q = takeD((size_t)Nm * K);
     sm.W = takeD((size_t)Nm * K);
     sm.B = takeD((size_t)K * K);
-    sm.Z = takeD((size_t)K * K);
+    sm.Z = takeD(K);
     sm.cs = takeD(K + 2);
     sm.Vr = reinterpret_cast<Real *>(smem_raw + off);
     off += sizeof(Real) * (size_t)Nm * K;
     off = (off + 3) & ~size_t(3);
     sm.C32 = reinterpret_cast<float *>(smem_raw + off);
     off += sizeof(float) * (size_t)Nm * Nm;
-    sm.Q32 = reinterpret_cast<float *>(smem_raw + off);
-    off += sizeof(float) * (size_t)Nm * K;
-    sm.W32 = reinterpret_cast<float *>(smem_raw + off);
-    off += sizeof(float) * (size_t)Nm * K;
+    sm.Q32 = reinterpret_cast<float *>(sm.W);
+    sm.W32 = sm.Q32 + (size_t)Nm * K;
     sm.pairs = reinterpret_cast<int *>(smem_raw + off);
     off += sizeof(int) * (K + 2);
     sm.perm = reinterpret_cast<int *>(smem_raw + off);
@@ -1271,9 +1495,7 @@ __global__ void __launch_bounds__(32) tucker_eig_kernel(TuckerStepParams P, Tuck
   const int N[3] = {P.N1, P.N2, P.N3};
   const int64_t j = blockIdx.x, c = B.c0 + j;
   const int n = N[m];
-  const double *Cin = B.C + j * (int64_t)Nm * Nm;
-  for (int i = threadIdx.x; i < n * n; i += blockDim.x) sm.C[i] = Cin[i];
-  __syncthreads();
+  sm.Cg = B.C + j * (int64_t)Nm * Nm;  // read through L1
   const double thr = P.tol * P.tol / 3.0 * B.e[j];
   const double *wU = P.cur.fac[m] + c * (int64_t)n * R;
   const int wr = P.cur.rank[3 * c + m];
@@ -1566,8 +1788,9 @@ template <typename Real, int TS>
 struct SplitSmem {
   size_t asm_, gram, eig, proj;
   SplitSmem(int Nmax, int R) {
-    asm_ = smem_bytes<Real>(Nmax, R);
-    gram = sizeof(double) * (size_t)Nmax * Nmax + sizeof(Real) * (size_t)Nmax * kKP;
+    asm_ = smem_asm_bytes<Real>(Nmax, R);
+    gram = sizeof(double) * (size_t)Nmax * Nmax +
+           2 * sizeof(Real) * (size_t)(Nmax > 32 ? Nmax : 32) * kTileRow;
     eig = smem_eig_bytes<Real>(Nmax, R);
     proj = sizeof(double) * (size_t)Nmax * R;
   }
@@ -1587,8 +1810,8 @@ int prepare_split_TS(int Nmax, int R) {
 }
 
 template <typename Real, int TS>
-int launch_split_TS(const TuckerStepParams &p, TuckerSplitBufs b, int64_t chunk, int asm_grid,
-                    cudaStream_t s) {
+int launch_split_TS(const TuckerStepParams &p, TuckerSplitBufs b, int64_t chunk, cudaStream_t s) {
+  const int asm_grid = b.asm_grid;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(s, &cap);
   if (cap == cudaStreamCaptureStatusNone && prepare_split_TS<Real, TS>(p.Nmax, p.R) != 0) return -1;
@@ -1597,7 +1820,7 @@ int launch_split_TS(const TuckerStepParams &p, TuckerSplitBufs b, int64_t chunk,
     b.c0 = c0;
     b.cn = p.nc - c0 < chunk ? p.nc - c0 : chunk;
     const int ga = (int)(b.cn < asm_grid ? b.cn : asm_grid);
-    tucker_asm_kernel<Real><<<ga, kTB, z.asm_, s>>>(p, b);
+    tucker_asm_kernel<Real><<<ga, kAsmTB, z.asm_, s>>>(p, b);
     for (int m = 0; m < 3; ++m) {
       tucker_gram_kernel<Real, TS><<<(unsigned)b.cn, kTB, z.gram, s>>>(p, b, m);
       tucker_eig_kernel<Real><<<(unsigned)b.cn, 32, z.eig, s>>>(p, b, m);
@@ -1657,12 +1880,19 @@ int launch_tucker_step(const TuckerStepParams &p, int grid, bool fp64, cudaStrea
 }
 
 int launch_tucker_split_step(const TuckerStepParams &p, TuckerSplitBufs b, int64_t chunk,
-                             int asm_grid, bool fp64, cudaStream_t s) {
+                             bool fp64, cudaStream_t s) {
   if (fp64)
-    return p.Nmax <= 32 ? launch_split_TS<double, 2>(p, b, chunk, asm_grid, s)
-                        : launch_split_TS<double, 4>(p, b, chunk, asm_grid, s);
-  return p.Nmax <= 32 ? launch_split_TS<float, 2>(p, b, chunk, asm_grid, s)
-                      : launch_split_TS<float, 4>(p, b, chunk, asm_grid, s);
+    return p.Nmax <= 32 ? launch_split_TS<double, 2>(p, b, chunk, s)
+                        : launch_split_TS<double, 4>(p, b, chunk, s);
+  return p.Nmax <= 32 ? launch_split_TS<float, 2>(p, b, chunk, s)
+                      : launch_split_TS<float, 4>(p, b, chunk, s);
+}
+
+int tucker_split_asm_per_sm() { return 6; }
+
+size_t tucker_split_t2_elems(int N1, int N2, int N3, int R) {
+  (void)N1;
+  return (size_t)kTerms * R * N2 * N3 + 64;
 }
 
 int tucker_prepare_launch(int Nmax, int R, bool fp64) {

@@ -34,6 +34,7 @@ struct TuckerState {
   TuckerSplitBufs sb{};                // its work buffers (one chunk of cells)
   int64_t chunk = 0;                   // cells per chunk
   void *split_mem = nullptr;
+  size_t split_bytes = 0;
   cudaGraphExec_t graph = nullptr;     // two steps (returns to the same buffer parity)
   int graph_parity = -1;               // S->cur / S->scur when the graph was captured
   cudaStream_t gstream = nullptr;      // private stream the graph is captured on / replayed on
@@ -293,7 +294,7 @@ int enqueue_one_step(dvm_ctx *C, TuckerStepParams &p) {
   p.cur = S->buf[S->cur];
   p.nxt = S->buf[1 - S->cur];
   p.sums = C->d_sums[S->scur];
-  const int lrc = S->split ? launch_tucker_split_step(p, S->sb, S->chunk, S->grid, S->fp64, C->stream)
+  const int lrc = S->split ? launch_tucker_split_step(p, S->sb, S->chunk, S->fp64, C->stream)
                            : launch_tucker_step(p, S->grid, S->fp64, C->stream);
   if (lrc != 0) {
     set_error("Tucker kernel needs more shared memory than the device allows");
@@ -317,19 +318,28 @@ int alloc_split(dvm_ctx *C) {
   TuckerState *S = C->tucker;
   size_t free_b = 0, total_b = 0;
   DVM_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+  const size_t es = S->fp64 ? sizeof(double) : sizeof(float);
   const size_t per =
       tucker_split_bytes_per_cell(C->N[0], C->N[1], C->N[2], S->R, S->Nmax, S->fp64) + 64;
+  int sms = 1;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, C->device);
+  const size_t t2_stride = (tucker_split_t2_elems(C->N[0], C->N[1], C->N[2], S->R) + 63) & ~size_t(63);
   const int64_t chunk = std::min<int64_t>(C->nc, (int64_t)(free_b / 8 / per));
   if (chunk < 1) {
     set_error("no device memory for the phase-major Tucker step buffers");
     return DVM_ERR_OOM;
   }
+  const int asm_grid = (int)std::min<int64_t>(chunk, (int64_t)sms * tucker_split_asm_per_sm());
+  const size_t bytes = per * chunk + es * t2_stride * asm_grid + 256;
   void *mem = nullptr;
-  int rc = ctx_malloc(C, &mem, per * chunk);
+  int rc = ctx_malloc(C, &mem, bytes);
   if (rc != DVM_OK) return rc;
-  const size_t es = S->fp64 ? sizeof(double) : sizeof(float);
   char *q = static_cast<char *>(mem);
   TuckerSplitBufs b{};
+  b.t2 = q;
+  b.t2_stride = t2_stride;
+  b.asm_grid = asm_grid;
+  q += es * t2_stride * asm_grid;
   b.X = q;
   q += es * chunk * C->N[0] * C->N[1] * C->N[2];
   b.Y1 = q;
@@ -345,6 +355,7 @@ int alloc_split(dvm_ctx *C) {
   S->sb = b;
   S->chunk = chunk;
   S->split_mem = mem;
+  S->split_bytes = bytes;
   return DVM_OK;
 }
 
@@ -352,8 +363,7 @@ void free_split(dvm_ctx *C) {
   TuckerState *S = C->tucker;
   if (!S->split_mem) return;
   cudaFree(S->split_mem);
-  C->bytes -= std::min(C->bytes, (tucker_split_bytes_per_cell(C->N[0], C->N[1], C->N[2], S->R,
-                                                              S->Nmax, S->fp64) + 64) * S->chunk);
+  C->bytes -= std::min(C->bytes, S->split_bytes);
   S->split_mem = nullptr;
   S->chunk = 0;
 }
@@ -410,7 +420,7 @@ int autotune(dvm_ctx *C) {
     rc = alloc_split(C);
     if (rc == DVM_OK) {
       const float ms = timed([&] {
-        return launch_tucker_split_step(p, S->sb, S->chunk, S->grid, S->fp64, C->stream);
+        return launch_tucker_split_step(p, S->sb, S->chunk, S->fp64, C->stream);
       });
       if (ms > 0.f) S->tune_ms[0] = ms;
       S->split = variant == DVM_VARIANT_PHASED || (ms > 0.f && ms < best);
