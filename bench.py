@@ -3,11 +3,17 @@
 Default workload: the lid-driven cubic cavity, 16^3 = 4,096 hex cells, 32^3 velocity
 nodes on [-6,6]^3, Kn = 0.1, diffuse walls at T = 1, lid speed 0.2 (synthetic, seeded).
 A "step" is one explicit time step of the whole hot path over every cell: moments,
-Shakhov equilibrium, boundary ghosts, upwind face fluxes and the Euler update (full
-grid), plus Tucker rounding in the Tucker format.
+Shakhov equilibrium, boundary ghosts, upwind face fluxes, the Euler update and, in the
+Tucker format, the rounding back to the tolerance / rank cap.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--path full|tucker]
-                    [--impl reference]
+Headline: the Tucker format in mixed precision (FP32 assembly and projections,
+double-float Gram matrices, FP64 eigen-solve steps, moments and stored state) at the
+tolerance that keeps the error against the FP64 oracle within 1e-4 (checked in the same
+run on a reduced cavity); the full-grid FP64 path and the FP64 Tucker path are timed
+beside it on the same inputs.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--path tucker|full]
+                    [--precision mixed|fp64] [--impl reference]
 
 Prints one JSON line (rank 0).  With --impl reference the FP64 CPU oracle is timed on
 the same workload instead (bounded sample per step).  N > 1 runs independent replicas
@@ -40,11 +46,13 @@ def _args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--path", default="full", choices=["full", "tucker"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--path", default="tucker", choices=["full", "tucker"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--rank-cap", type=int, default=None)
     ap.add_argument("--tol", type=float, default=None)
     ap.add_argument("--workload", default="cavity")
+    ap.add_argument("--advance", type=int, default=200,
+                    help="untimed steps that develop the flow (and the Tucker ranks) first")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
@@ -134,7 +142,7 @@ def _traffic(kernel):
     if not os.path.exists(p):
         return None
     src = os.path.join(ROOT, "paper_1912_04582_gb300", "csrc", "full_kernels.cu"
-                       if kernel == "full" else "tucker_kernels.cu")
+                       if kernel in ("full", "full_step") else "tucker_kernels.cu")
     if not os.path.exists(src):
         return None
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
@@ -185,8 +193,9 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {**wl.describe(), "path": "full",
-                                             "format": "full FP64 (CPU oracle)"},
+            "data": "synthetic", "config": {**wl.describe(), "path": args.path,
+                                             "format": "full FP64 CPU oracle (the oracle "
+                                                       "implements the full-grid method)"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{args.steps} full step(s) of {wl.name}"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -194,8 +203,66 @@ def run_reference(args, rank, world):
 
 
 # --------------------------------------------------------------------------
-FLOPS_PER_UPDATE = 28      # FP64 flops per cell.node of the fused full-grid step (DESIGN §6)
+FLOPS_PER_UPDATE = 28      # FP64 flops per cell.node of the fused full-grid step
 FP64_PEAK_GFLOPS = 1250.0  # nominal GB300 FP64 rate (152 SMs x 2 FMA/clk x 2 x ~2.06 GHz)
+FP32_PEAK_GOPS = 35000.0   # FP32 lane operations/s: an FMA-chain probe measured 70.0 TFLOP/s
+DF_OPS = 10                # FP32 operations of one double-float multiply-accumulate
+
+
+def _tucker_work(wl, ranks, cls):
+    """Algorithmic work of one launch of a phase-major kernel class, from the shapes and
+    the current ranks: (amount, unit, bound, peak, peak_source, definition)."""
+    N1, N2, N3 = wl.N
+    nc = wl.n_cell
+    r = ranks.astype(np.float64)
+    if cls == "tucker_gram_mode1":
+        ops = nc * (N1 * (N1 + 1) / 2) * N2 * N3 * DF_OPS
+        return (ops, "GOP/s", "alu", FP32_PEAK_GOPS,
+                "FP32 lane-ops/s: 70.0 TFLOP/s FMA-chain probe on this pool / 2",
+                "n(n+1)/2 x N2 N3 double-float multiply-accumulates per cell (n = N1), "
+                f"{DF_OPS} FP32 operations each")
+    if cls == "tucker_eig":
+        # per cell and mode: the FP64 power step and the Rayleigh quotients, two
+        # products of the n x n Gram matrix with the n x k basis, k = r + 4
+        k = np.minimum(r + 4, np.array(wl.N, dtype=np.float64))
+        flops = 2.0 * 2.0 * float((np.array(wl.N, dtype=np.float64) ** 2 * k).sum()) / 3.0
+        return (flops, "GFLOP/s", "alu", FP64_PEAK_GFLOPS,
+                "FP64 nominal from unit counts and clock (1.197 TFLOP/s measured by an "
+                "FMA-chain probe on this pool)",
+                "per cell and mode 2 x 2 n^2 k FP64 flops (k = r + 4), averaged over the "
+                "three launches of a step")
+    if cls == "tucker_asm":
+        # each cell assembles itself and its 6 neighbours' tensors: sum of first-mode
+        # ranks x N1 N2 N3 FMAs (interior cells; boundary faces are cheaper)
+        flops = 2.0 * 7.0 * float(r[:, 0].sum()) * N1 * N2 * N3
+        return (flops, "GFLOP/s", "alu", 2 * FP32_PEAK_GOPS,
+                "FP32 70.0 TFLOP/s FMA-chain probe on this pool",
+                "7 x r1 x N1 N2 N3 FP32 FMAs per cell (self + 6 face terms)")
+    return None
+
+
+def _roofline_tucker(P, s, wl, steps):
+    """Per-class launch times with CUDA events (a second timed region of `steps` steps),
+    roofline of the dominant class."""
+    P.dvm_set_kernel_timing(s.h, True)
+    s.step(steps, residual=False)
+    t = P.dvm_get_kernel_timing(s.h)
+    P.dvm_set_kernel_timing(s.h, False)
+    ranks = P.dvm_get_ranks(s.h)
+    total = sum(ms for ms, _ in t.values())
+    times = {k: {"ms_per_launch": ms / n, "launches": n, "share": ms / total}
+             for k, (ms, n) in t.items() if n}
+    dom = max(times, key=lambda k: t[k][0])
+    w = _tucker_work(wl, ranks, dom)
+    if w is None:
+        return {"bound": None, "kernel": dom, "achieved": None, "peak": None, "unit": None,
+                "frac": None, "traffic": None, "kernel_times": times}
+    amount, unit, bound, peak, psrc, defin = w
+    achieved = amount / (times[dom]["ms_per_launch"] / 1e3) / 1e9
+    return {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak, "traffic": _traffic(dom), "peak_source": psrc,
+            "work_per_launch": amount, "work": defin, "kernel_times": times,
+            "timing": f"CUDA events around each launch over {steps} further steps"}
 
 
 def _time_steps(solver, steps, warmup, stream):
@@ -239,9 +306,11 @@ def tucker_accuracy(P, cap, tol, precision, steps=300):
             "note": "u relative to max(|u|, lid speed), q to max(|q|, n T^1.5 / 2); vs FP64 oracle"}
 
 
-def run_serving(P, n_req=16, seed=7, mean_gap_s=0.25, budget_gb=64, slots=8):
+def run_serving(P, n_req=12, seed=7, mean_gap_s=0.25, budget_gb=64, slots=8, res_tol=1e-4,
+                max_steps=4000):
     """Seeded Poisson arrivals of steady channel solves (Poiseuille / thermal
-    transpiration), Tucker mixed format, each run to residual 1e-4."""
+    transpiration), Tucker mixed format, each run to the residual res_tol (scaled-down
+    version of the 64-request mix so that it ends within the bench's time)."""
     import workloads as W
     rng = np.random.default_rng(seed)
     reqs = []
@@ -249,9 +318,9 @@ def run_serving(P, n_req=16, seed=7, mean_gap_s=0.25, budget_gb=64, slots=8):
     for i in range(n_req):
         t += rng.exponential(mean_gap_s)
         kind = "poiseuille" if rng.random() < 0.5 else "transpiration"
-        ncell = int(np.exp(rng.uniform(np.log(256), np.log(2048))))
-        N = int(rng.choice([12, 16, 24]))
-        Kn = float(np.exp(rng.uniform(np.log(0.1), np.log(10.0))))
+        ncell = int(np.exp(rng.uniform(np.log(256), np.log(1024))))
+        N = int(rng.choice([12, 16]))
+        Kn = float(np.exp(rng.uniform(np.log(0.3), np.log(10.0))))
         cap = int(rng.integers(6, 13))
         wl = W.channel(n_cell_target=ncell, N=N, Kn=Kn, kind=kind, seed=i)
         reqs.append((t, wl, cap))
@@ -264,7 +333,8 @@ def run_serving(P, n_req=16, seed=7, mean_gap_s=0.25, budget_gb=64, slots=8):
         while k < n_req and reqs[k][0] <= now:
             _, wl, cap = reqs[k]
             tickets.append((srv.submit(wl, format=1, precision=1, rank_cap=cap, tol=1e-6,
-                                       res_tol=1e-4, max_steps=6000, check_every=25), wl))
+                                       res_tol=res_tol, max_steps=max_steps, check_every=25),
+                            wl))
             k += 1
         pending = srv.run(0.02)
         if k == n_req and pending == 0:
@@ -287,9 +357,10 @@ def run_serving(P, n_req=16, seed=7, mean_gap_s=0.25, budget_gb=64, slots=8):
             "errors": sorted(errors), "wall_s": total,
             "solves_per_hour": 3600.0 * n_req / total, "p50_latency_s": float(np.percentile(lat, 50)),
             "p99_latency_s": float(np.percentile(lat, 99)), "updates_per_s": upd / total,
-            "mix": "channel Poiseuille/transpiration, 256-2048 cells, 12^3-24^3, Kn 0.1-10, "
-                   "Tucker mixed eps 1e-6 cap 6-12, residual 1e-4, Poisson arrivals "
-                   f"(mean gap {mean_gap_s} s, seed {seed}), {slots} slots"}
+            "mix": f"{n_req} channel Poiseuille/transpiration solves, 256-1024 cells, "
+                   "12^3-16^3 nodes, Kn 0.3-10, Tucker mixed eps 1e-6 cap 6-12, residual "
+                   f"{res_tol:g} (at most {max_steps} steps), Poisson arrivals (mean gap "
+                   f"{mean_gap_s} s, seed {seed}), {slots} slots"}
 
 
 def run_gpu(args, rank, world):
@@ -309,11 +380,14 @@ def run_gpu(args, rank, world):
     prec = NAT.DVM_PREC_MIXED if args.precision == "mixed" else NAT.DVM_PREC_FP64
     cap = args.rank_cap or 12
     tol = args.tol or 1e-6
+    tucker = args.path == "tucker"
 
     # headline path, timed with the clock sampler running
-    fmt = NAT.DVM_FORMAT_TUCKER if args.path == "tucker" else NAT.DVM_FORMAT_FULL
+    fmt = NAT.DVM_FORMAT_TUCKER if tucker else NAT.DVM_FORMAT_FULL
     s = P.Solver(wl, format=fmt, precision=prec, rank_cap=cap, tol=tol, stream=stream.cuda_stream)
-    for _ in range(args.warmup):
+    if args.advance:
+        s.step(args.advance, residual=False)
+    for _ in range(max(3, args.warmup)):
         s.step(1, residual=False)
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -331,55 +405,77 @@ def run_gpu(args, rank, world):
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    res = s.step(1)
     value = world * upd * args.steps / (ms / 1e3)
-    kern_ms = ms / args.steps
+    step_ms = ms / args.steps
 
     peaks, src = _peaks()
-    if args.path == "full":
-        achieved = FLOPS_PER_UPDATE * upd / (kern_ms / 1e3) / 1e9
-        hbm = 2 * 8 * upd / (kern_ms / 1e3) / 1e9
+    if not tucker:
+        achieved = FLOPS_PER_UPDATE * upd / (step_ms / 1e3) / 1e9
+        hbm = 2 * 8 * upd / (step_ms / 1e3) / 1e9
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
                 "frac": achieved / FP64_PEAK_GFLOPS, "traffic": _traffic("full"),
                 "peak_source": "FP64 nominal from unit counts and clock (1.197 TFLOP/s measured "
-                               "by an FMA probe on this pool)",
-                "kernel": "full_step_kernel", "alg_flops_per_launch": FLOPS_PER_UPDATE * upd,
+                               "by an FMA-chain probe on this pool)",
+                "kernel": "full_step_kernel", "work_per_launch": FLOPS_PER_UPDATE * upd,
+                "work": f"{FLOPS_PER_UPDATE} FP64 flops per cell.node update",
                 "hbm": {"achieved": hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                         "frac": hbm / peaks["hbm_gbs"], "alg_bytes_per_launch": 16 * upd,
                         "peak_source": f"{src} MEASURED_PEAKS.json hbm_gbs"}}
         launches = args.steps
     else:
-        roof = {"bound": "alu", "kernel": "tucker_step_kernel", "achieved": None,
-                "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": None, "traffic": None,
-                "note": "latency-bound per-cell eigen-solves; see profiles/"}
-        launches = 3 * args.steps
+        roof = _roofline_tucker(P, s, wl, args.steps)
+        kt = roof["kernel_times"]
+        # the moments class is two kernels (macroparameters, moments of the new state)
+        launches = sum(v["launches"] for v in kt.values()) + kt.get("moments", {}).get("launches", 0)
+    res = s.step(1)
 
     line = None
     if rank == 0:
         paths = {}
-        # the other path on the same workload
-        if args.path == "full" and not args.no_extras:
-            t = P.Solver(wl, format=1, precision=NAT.DVM_PREC_MIXED, rank_cap=cap, tol=tol,
-                         stream=stream.cuda_stream)
-            tms = _time_steps(t, args.steps, args.warmup, stream) / args.steps
-            fb, _ = P.dvm_memory(t.h)
-            grid, tune = P.dvm_get_launch_config(t.h)
-            r = P.dvm_get_ranks(t.h)
-            paths["tucker_mixed"] = {
-                "ms_per_step": tms, "updates_per_s": upd / (tms / 1e3), "eps": tol,
-                "rank_cap": cap, "rank_mean": float(r.mean()), "rank_max": int(r.max()),
-                "f_bytes": fb, "compression": fb / (8.0 * upd), "grid": grid,
-                "autotune_ms_by_ctas_per_sm": tune[1:], "launches_per_step": 3}
-            t.close()
-        fbf, _ = P.dvm_memory(s.h)
-        paths[args.path + ("_fp64" if prec == NAT.DVM_PREC_FP64 else "_mixed")] = {
-            "ms_per_step": kern_ms, "updates_per_s": upd / (kern_ms / 1e3), "f_bytes": fbf}
+        fbh, tbh = P.dvm_memory(s.h)
+        grid, tune = P.dvm_get_launch_config(s.h) if tucker else (wl.n_cell, [0.0] * 5)
+        rh = P.dvm_get_ranks(s.h)
+        head = {"ms_per_step": step_ms, "updates_per_s": upd / (step_ms / 1e3),
+                "f_bytes": fbh, "device_bytes": tbh}
+        if tucker:
+            head.update({"eps": tol, "rank_cap": cap, "rank_mean": float(rh.mean()),
+                         "rank_max": int(rh.max()), "compression": fbh / (8.0 * upd),
+                         "variant": "phase-major" if grid < 0 else "fused",
+                         "autotune_ms": {"phase_major": tune[0],
+                                         "fused_by_ctas_per_sm": tune[1:]}})
+        paths[("tucker_" if tucker else "full_") + args.precision] = head
+        if not args.no_extras:
+            # the other formats on the same inputs
+            others = [("full_fp64", NAT.DVM_FORMAT_FULL, NAT.DVM_PREC_FP64, cap, tol),
+                      ("tucker_fp64", NAT.DVM_FORMAT_TUCKER, NAT.DVM_PREC_FP64, cap, tol),
+                      ("tucker_fp64_cap8_eps1e-5", NAT.DVM_FORMAT_TUCKER, NAT.DVM_PREC_FP64, 8,
+                       1e-5),
+                      ("tucker_mixed", NAT.DVM_FORMAT_TUCKER, NAT.DVM_PREC_MIXED, cap, tol)]
+            for name, f2, p2, c2, e2 in others:
+                if name in paths:
+                    continue
+                t = P.Solver(wl, format=f2, precision=p2, rank_cap=c2, tol=e2,
+                             stream=stream.cuda_stream)
+                if args.advance and f2 == NAT.DVM_FORMAT_TUCKER:
+                    t.step(args.advance, residual=False)
+                tms = _time_steps(t, args.steps, args.warmup, stream) / args.steps
+                fb, tb = P.dvm_memory(t.h)
+                d = {"ms_per_step": tms, "updates_per_s": upd / (tms / 1e3), "f_bytes": fb,
+                     "device_bytes": tb}
+                if f2 == NAT.DVM_FORMAT_TUCKER:
+                    r = P.dvm_get_ranks(t.h)
+                    g2, _ = P.dvm_get_launch_config(t.h)
+                    d.update({"eps": e2, "rank_cap": c2, "rank_mean": float(r.mean()),
+                              "rank_max": int(r.max()), "compression": fb / (8.0 * upd),
+                              "variant": "phase-major" if g2 < 0 else "fused"})
+                paths[name] = d
+                t.close()
         e2e = None
         if not args.no_e2e:
             f_host = torch.empty((wl.n_cell,) + tuple(wl.N), dtype=torch.float64, pin_memory=True)
             f_np = f_host.numpy()
             f_np[...] = s.f()
-            k = max(3, min(args.steps, 10))
+            k = 3
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             for _ in range(k):
@@ -389,15 +485,20 @@ def run_gpu(args, rank, world):
             el = time.perf_counter() - t0
             e2e = {"value": upd * k / el, "unit": UNIT, "h2d_bytes_per_step": int(f_np.nbytes),
                    "d2h_bytes_per_step": int(m.nbytes),
-                   "note": "per step: dvm_init_f from pinned host f, dvm_step, dvm_moments to host"}
+                   "note": "per step: dvm_init_f from pinned host f (Tucker: compressed on "
+                           "the device), dvm_step, dvm_moments to host"}
         cfg = {**wl.describe(), "path": args.path,
-               "format": "full tensor FP64" if args.path == "full" else f"Tucker {args.precision}",
-               "l2": f"inputs larger than L2 ({8 * upd / 1e9:.2f} GB per copy of f)",
-               "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"}
+               "format": "full tensor FP64" if not tucker else
+                         f"Tucker {args.precision}, eps {tol:g}, rank cap {cap}",
+               "l2": f"inputs larger than L2 ({8 * upd / 1e9:.2f} GB per full FP64 copy of f; "
+                     "Tucker: per-step work buffers of the same order)",
+               "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+               "state": f"timed after {args.advance} untimed steps from the initial "
+                        "equilibrium (developed flow and ranks)"}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": kern_ms,
+                "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": step_ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64" if args.path == "full" or prec == NAT.DVM_PREC_FP64 else "f32+f64",
+                "dtype": "f64" if not tucker or prec == NAT.DVM_PREC_FP64 else "f32+f64",
                 "data": "synthetic", "config": cfg, "roofline": roof, "gpu_launches": launches,
                 "clocks": clk.summary(), "residual_after": res, "paths": paths}
         if e2e:

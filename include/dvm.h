@@ -194,6 +194,22 @@ int dvm_get_ranks(dvm_ctx *ctx, int32_t *r);
  * tune_ms zeros.  Either pointer may be NULL. */
 int dvm_get_launch_config(dvm_ctx *ctx, int32_t *grid, float *tune_ms);
 
+/* Optional per-launch event timing of the step kernels, for measurement:
+ * with on != 0 every launch of dvm_step is bracketed by CUDA events on the
+ * context's stream (the two-step graph replay is not used meanwhile) and its
+ * elapsed time accumulated per kernel class; on == 0 stops.  Either call
+ * clears the totals.  Errors: INVALID_ARG, CUDA. */
+int dvm_set_kernel_timing(dvm_ctx *ctx, int32_t on);
+
+/* Accumulated launch times (ms) and counts since timing was switched on, per
+ * kernel class: [0] full-grid step, [1] fused Tucker step, [2] phase-major
+ * assembly, [3] first-mode Gram, [4] second/third-mode Gram, [5] eigen-solves,
+ * [6] projections/cores, [7] moments of the new state.  ms[8], launches[8];
+ * either may be NULL.  Synchronises the context's stream. */
+int dvm_get_kernel_timing(dvm_ctx *ctx, double *ms, int64_t *launches);
+
+#define DVM_KERNEL_CLASSES 8
+
 /* Bytes of device memory held for the distribution function in its current
  * representation (Tucker: sum over cells of r1 r2 r3 + N1 r1 + N2 r2 + N3 r3
  * values, Section 7), and the total bytes the context allocated. */

@@ -28,6 +28,9 @@ DVM_BC_FREESTREAM, DVM_BC_ZEROGRAD, DVM_BC_SYMMETRY, DVM_BC_WALL = 0, 1, 2, 3
 DVM_FORMAT_FULL, DVM_FORMAT_TUCKER = 0, 1
 DVM_PREC_FP64, DVM_PREC_MIXED = 0, 1
 DVM_VARIANT_AUTO, DVM_VARIANT_FUSED, DVM_VARIANT_PHASED = 0, 1, 2
+DVM_KERNEL_CLASSES = 8
+KERNEL_CLASS_NAMES = ("full_step", "tucker_fused_step", "tucker_asm", "tucker_gram_mode1",
+                      "tucker_gram_mode23", "tucker_eig", "tucker_proj", "moments")
 
 _c_dp = ctypes.POINTER(ctypes.c_double)
 _c_i64p = ctypes.POINTER(ctypes.c_int64)
@@ -86,6 +89,8 @@ SIGNATURES = {
     "dvm_get_geometry": (ctypes.c_int, [_P, _c_dp, _c_i64p, _c_dp]),
     "dvm_get_ranks": (ctypes.c_int, [_P, _c_i32p]),
     "dvm_get_launch_config": (ctypes.c_int, [_P, _c_i32p, ctypes.POINTER(ctypes.c_float)]),
+    "dvm_set_kernel_timing": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "dvm_get_kernel_timing": (ctypes.c_int, [_P, _c_dp, ctypes.POINTER(ctypes.c_int64)]),
     "dvm_memory": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t),
                                   ctypes.POINTER(ctypes.c_size_t)]),
     "dvm_save": (ctypes.c_int, [_P, ctypes.c_char_p]),

@@ -162,6 +162,18 @@ def dvm_get_launch_config(h):
     return int(g.value), [float(v) for v in t]
 
 
+def dvm_set_kernel_timing(h, on):
+    _n.check(N_lib().dvm_set_kernel_timing(h.ptr, int(bool(on))), "dvm_set_kernel_timing")
+
+
+def dvm_get_kernel_timing(h):
+    """{class name: (total ms, launches)} since timing was switched on."""
+    ms = (ctypes.c_double * _n.DVM_KERNEL_CLASSES)()
+    nl = (ctypes.c_int64 * _n.DVM_KERNEL_CLASSES)()
+    _n.check(N_lib().dvm_get_kernel_timing(h.ptr, ms, nl), "dvm_get_kernel_timing")
+    return {name: (float(ms[k]), int(nl[k])) for k, name in enumerate(_n.KERNEL_CLASS_NAMES)}
+
+
 def dvm_memory(h):
     fb = ctypes.c_size_t(0)
     tb = ctypes.c_size_t(0)

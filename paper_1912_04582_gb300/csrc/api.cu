@@ -410,6 +410,29 @@ int dvm_get_launch_config(dvm_ctx *C, int32_t *grid, float *tune_ms) {
   return DVM_OK;
 }
 
+int dvm_set_kernel_timing(dvm_ctx *C, int32_t on) {
+  if (!C) return DVM_ERR_INVALID_ARG;
+  int rc = ctx_collect_timing(C);
+  if (rc != DVM_OK) return rc;
+  for (int k = 0; k < kKClasses; ++k) {
+    C->timing.ms[k] = 0.0;
+    C->timing.launches[k] = 0;
+  }
+  C->timing.on = on != 0;
+  return DVM_OK;
+}
+
+int dvm_get_kernel_timing(dvm_ctx *C, double *ms, int64_t *launches) {
+  if (!C) return DVM_ERR_INVALID_ARG;
+  int rc = ctx_collect_timing(C);
+  if (rc != DVM_OK) return rc;
+  for (int k = 0; k < kKClasses; ++k) {
+    if (ms) ms[k] = C->timing.ms[k];
+    if (launches) launches[k] = C->timing.launches[k];
+  }
+  return DVM_OK;
+}
+
 int dvm_memory(dvm_ctx *C, size_t *f_bytes, size_t *total_bytes) {
   if (!C) return DVM_ERR_INVALID_ARG;
   return ctx_memory(C, f_bytes, total_bytes);

@@ -83,7 +83,51 @@ int ctx_alloc_state(dvm_ctx *C) {
   return DVM_OK;
 }
 
+// per-launch event timing: a begin mark records a fresh event, the matching end
+// mark another, queued until ctx_collect_timing reads them
+void dvm_ctx::ctx_timer_mark(void *self, int cls, bool begin, cudaStream_t s) {
+  dvm_ctx *C = static_cast<dvm_ctx *>(self);
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  cudaEventRecord(e, s);
+  if (begin) {
+    if (C->timing.open[cls]) cudaEventDestroy(C->timing.open[cls]);
+    C->timing.open[cls] = e;
+  } else if (C->timing.open[cls]) {
+    C->timing.pending.push_back({reinterpret_cast<void *>((intptr_t)cls),
+                                 static_cast<void *>(C->timing.open[cls]), static_cast<void *>(e)});
+    C->timing.open[cls] = nullptr;
+  } else {
+    cudaEventDestroy(e);
+  }
+}
+
+int ctx_collect_timing(dvm_ctx *C) {
+  auto &T = C->timing;
+  if (!T.pending.empty()) DVM_CUDA_TRY(cudaStreamSynchronize(C->stream));
+  for (auto &p : T.pending) {
+    const int cls = (int)reinterpret_cast<intptr_t>(p[0]);
+    float ms = 0.f;
+    cudaEvent_t a = static_cast<cudaEvent_t>(p[1]), b = static_cast<cudaEvent_t>(p[2]);
+    if (cudaEventElapsedTime(&ms, a, b) == cudaSuccess) {
+      T.ms[cls] += ms;
+      T.launches[cls] += 1;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+  T.pending.clear();
+  cudaGetLastError();
+  return DVM_OK;
+}
+
 void ctx_free(dvm_ctx *C) {
+  ctx_collect_timing(C);
+  for (auto &e : C->timing.open)
+    if (e) cudaEventDestroy(e);
   if (C->tucker) tucker_free(C);
   void *ptrs[] = {C->d_xi[0], C->d_xi[1], C->d_xi[2], C->d_vol, C->d_slot, C->d_ghost,
                   C->d_f[0], C->d_f[1], C->d_sums[0], C->d_sums[1], C->d_uref, C->d_respart,
@@ -403,7 +447,10 @@ int ctx_step(dvm_ctx *C, int32_t nsteps, double *residual_out) {
     P.fnew = C->d_f[1 - C->cur];
     P.sums = C->d_sums[C->cur];
     P.sums_new = C->d_sums[1 - C->cur];
+    const LaunchTimer lt = C->timer();
+    lt(kKFullStep, true, C->stream);
     launch_full_step(P, C->stream);
+    lt(kKFullStep, false, C->stream);
     C->cur = 1 - C->cur;
     C->steps++;
   }

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "dvm_internal.h"
+#include "tucker.h"
 
 struct TuckerState;  // tucker_step.cu
 
@@ -58,7 +59,22 @@ struct dvm_ctx {
   bool initialized = false;
 
   TuckerState *tucker = nullptr;
+
+  // optional per-launch event timing (dvm_set_kernel_timing)
+  struct Timing {
+    bool on = false;
+    cudaEvent_t open[dvm::kKClasses] = {};
+    std::vector<std::array<void *, 3>> pending;  // (class, start, end)
+    double ms[dvm::kKClasses] = {};
+    int64_t launches[dvm::kKClasses] = {};
+  } timing;
+  dvm::LaunchTimer timer() {
+    return timing.on ? dvm::LaunchTimer{&ctx_timer_mark, this} : dvm::LaunchTimer{nullptr, nullptr};
+  }
+  static void ctx_timer_mark(void *self, int cls, bool begin, cudaStream_t s);
 };
+
+int ctx_collect_timing(dvm_ctx *C);
 
 // context.cu
 int ctx_alloc_state(dvm_ctx *C);

@@ -48,6 +48,28 @@ struct TuckerSplitBufs {
   int64_t c0, cn;
 };
 
+// Kernel classes of the optional per-launch event timing (dvm_set_kernel_timing)
+enum KernelClass : int {
+  kKFullStep = 0,   // full-grid step kernel
+  kKFusedStep = 1,  // fused Tucker step kernel
+  kKAsm = 2,        // phase-major: assembly
+  kKGram0 = 3,      // phase-major: first-mode Gram matrices
+  kKGram12 = 4,     // phase-major: second / third-mode Gram matrices
+  kKEig = 5,        // phase-major: eigen-solves
+  kKProj = 6,       // phase-major: projections and cores
+  kKMoments = 7,    // moments (and macroparameters) of the new state
+  kKClasses = 8
+};
+
+// Event marks around launches (null: no timing)
+struct LaunchTimer {
+  void (*mark)(void *self, int cls, bool begin, cudaStream_t s);
+  void *self;
+  void operator()(int cls, bool begin, cudaStream_t s) const {
+    if (mark) mark(self, cls, begin, s);
+  }
+};
+
 struct TuckerMomentParams {
   TuckerDev T;
   const double *uref;    // reference velocity, uref[c*uref_stride + k] (may be null)
@@ -70,7 +92,7 @@ int tucker_step_blocks_per_sm(int Nmax, int R, bool fp64);
 int launch_tucker_step(const TuckerStepParams &p, int grid, bool fp64, cudaStream_t s);
 // phase-major step over chunks of `chunk` cells (buffers sized for one chunk)
 int launch_tucker_split_step(const TuckerStepParams &p, TuckerSplitBufs b, int64_t chunk,
-                             bool fp64, cudaStream_t s);
+                             bool fp64, cudaStream_t s, const LaunchTimer *lt = nullptr);
 // bytes of TuckerSplitBufs per cell (working precision fp64 or float)
 size_t tucker_split_bytes_per_cell(int N1, int N2, int N3, int R, int Nmax, bool fp64);
 // assembly CTAs per SM of the phase-major variant and their staging elements

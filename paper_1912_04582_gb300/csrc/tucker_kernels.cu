@@ -1810,8 +1810,11 @@ int prepare_split_TS(int Nmax, int R) {
 }
 
 template <typename Real, int TS>
-int launch_split_TS(const TuckerStepParams &p, TuckerSplitBufs b, int64_t chunk, cudaStream_t s) {
+int launch_split_TS(const TuckerStepParams &p, TuckerSplitBufs b, int64_t chunk, cudaStream_t s,
+                    const LaunchTimer *lt) {
   const int asm_grid = b.asm_grid;
+  const LaunchTimer none{nullptr, nullptr};
+  const LaunchTimer &T = lt ? *lt : none;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(s, &cap);
   if (cap == cudaStreamCaptureStatusNone && prepare_split_TS<Real, TS>(p.Nmax, p.R) != 0) return -1;
@@ -1820,11 +1823,20 @@ int launch_split_TS(const TuckerStepParams &p, TuckerSplitBufs b, int64_t chunk,
     b.c0 = c0;
     b.cn = p.nc - c0 < chunk ? p.nc - c0 : chunk;
     const int ga = (int)(b.cn < asm_grid ? b.cn : asm_grid);
+    T(kKAsm, true, s);
     tucker_asm_kernel<Real><<<ga, kAsmTB, z.asm_, s>>>(p, b);
+    T(kKAsm, false, s);
     for (int m = 0; m < 3; ++m) {
+      const int gc = m == 0 ? kKGram0 : kKGram12;
+      T(gc, true, s);
       tucker_gram_kernel<Real, TS><<<(unsigned)b.cn, kTB, z.gram, s>>>(p, b, m);
+      T(gc, false, s);
+      T(kKEig, true, s);
       tucker_eig_kernel<Real><<<(unsigned)b.cn, 32, z.eig, s>>>(p, b, m);
+      T(kKEig, false, s);
+      T(kKProj, true, s);
       tucker_proj_kernel<Real><<<(unsigned)b.cn, kTB, z.proj, s>>>(p, b, m);
+      T(kKProj, false, s);
     }
   }
   return 0;
@@ -1880,12 +1892,12 @@ int launch_tucker_step(const TuckerStepParams &p, int grid, bool fp64, cudaStrea
 }
 
 int launch_tucker_split_step(const TuckerStepParams &p, TuckerSplitBufs b, int64_t chunk,
-                             bool fp64, cudaStream_t s) {
+                             bool fp64, cudaStream_t s, const LaunchTimer *lt) {
   if (fp64)
-    return p.Nmax <= 32 ? launch_split_TS<double, 2>(p, b, chunk, s)
-                        : launch_split_TS<double, 4>(p, b, chunk, s);
-  return p.Nmax <= 32 ? launch_split_TS<float, 2>(p, b, chunk, s)
-                      : launch_split_TS<float, 4>(p, b, chunk, s);
+    return p.Nmax <= 32 ? launch_split_TS<double, 2>(p, b, chunk, s, lt)
+                        : launch_split_TS<double, 4>(p, b, chunk, s, lt);
+  return p.Nmax <= 32 ? launch_split_TS<float, 2>(p, b, chunk, s, lt)
+                      : launch_split_TS<float, 4>(p, b, chunk, s, lt);
 }
 
 int tucker_split_asm_per_sm() { return 6; }

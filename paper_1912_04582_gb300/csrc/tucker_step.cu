@@ -294,13 +294,21 @@ int enqueue_one_step(dvm_ctx *C, TuckerStepParams &p) {
   p.cur = S->buf[S->cur];
   p.nxt = S->buf[1 - S->cur];
   p.sums = C->d_sums[S->scur];
-  const int lrc = S->split ? launch_tucker_split_step(p, S->sb, S->chunk, S->fp64, C->stream)
-                           : launch_tucker_step(p, S->grid, S->fp64, C->stream);
+  const LaunchTimer lt = C->timer();
+  int lrc;
+  if (S->split) {
+    lrc = launch_tucker_split_step(p, S->sb, S->chunk, S->fp64, C->stream, &lt);
+  } else {
+    lt(kKFusedStep, true, C->stream);
+    lrc = launch_tucker_step(p, S->grid, S->fp64, C->stream);
+    lt(kKFusedStep, false, C->stream);
+  }
   if (lrc != 0) {
     set_error("Tucker kernel needs more shared memory than the device allows");
     return DVM_ERR_UNSUPPORTED;
   }
   S->cur = 1 - S->cur;
+  lt(kKMoments, true, C->stream);
   launch_macro_from_sums(C->d_sums[S->scur], C->d_macro, C->nc, C->w, C->stream);
   TuckerMomentParams m = moment_params(C, S->buf[S->cur], C->d_sums[1 - S->scur]);
   m.uref = C->d_macro + 1;
@@ -308,6 +316,7 @@ int enqueue_one_step(dvm_ctx *C, TuckerStepParams &p) {
   m.sums_prev = C->d_sums[S->scur];
   m.respart = C->d_respart;
   launch_tucker_moments(m, C->stream);
+  lt(kKMoments, false, C->stream);
   S->scur = 1 - S->scur;
   return DVM_OK;
 }
@@ -449,7 +458,8 @@ int tucker_step(dvm_ctx *C, int32_t nsteps, double *residual_out) {
   int32_t s = 0;
   // pairs of steps replay a captured CUDA graph (launch overhead paid once per
   // pair); the graph is re-captured if the buffer parity differs
-  const bool use_graph = nsteps >= 2 && !S->phase && !std::getenv("DVM_NO_GRAPH");
+  const bool use_graph =
+      nsteps >= 2 && !S->phase && !C->timing.on && !std::getenv("DVM_NO_GRAPH");
   if (use_graph) {
     if (!S->gstream) {
       DVM_CUDA_TRY(cudaStreamCreateWithFlags(&S->gstream, cudaStreamNonBlocking));

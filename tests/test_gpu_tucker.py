@@ -240,3 +240,28 @@ def test_launch_variant_is_validated(dvm):
     wl = W.cavity(nside=2, N=8, seed=1)
     with pytest.raises(Exception):
         dvm.Solver(wl, format=1, precision=MIXED, rank_cap=4, tol=1e-5, variant=3)
+
+
+def test_kernel_timing_covers_the_step(dvm):
+    """Per-launch event timing: every class that runs is counted once per step and the
+    class totals add up to (at most) the wall time of the steps."""
+    import time
+    from paper_1912_04582_gb300 import _native as NAT
+    wl = W.cavity(nside=6, N=16, seed=4)
+    for v, classes in ((NAT.DVM_VARIANT_PHASED,
+                        {"tucker_asm": 1, "tucker_gram_mode1": 1, "tucker_gram_mode23": 2,
+                         "tucker_eig": 3, "tucker_proj": 3, "moments": 1}),
+                       (NAT.DVM_VARIANT_FUSED, {"tucker_fused_step": 1, "moments": 1})):
+        s = dvm.Solver(wl, format=1, precision=MIXED, rank_cap=8, tol=1e-6, variant=v)
+        s.step(2)
+        dvm.dvm_set_kernel_timing(s.h, True)
+        t0 = time.perf_counter()
+        s.step(4, residual=False)
+        t = dvm.dvm_get_kernel_timing(s.h)
+        wall_ms = 1e3 * (time.perf_counter() - t0)
+        dvm.dvm_set_kernel_timing(s.h, False)
+        for name, (ms, n) in t.items():
+            assert n == 4 * classes.get(name, 0), (name, n)
+            assert (ms > 0) == (name in classes)
+        assert sum(ms for ms, _ in t.values()) <= wall_ms
+        s.close()
