@@ -223,13 +223,13 @@ def _tucker_work(wl, ranks, cls):
                 f"{DF_OPS} FP32 operations each")
     if cls == "tucker_eig":
         # per cell and mode: the FP64 power step and the Rayleigh quotients, two
-        # products of the n x n Gram matrix with the n x k basis, k = r + 4
-        k = np.minimum(r + 4, np.array(wl.N, dtype=np.float64))
+        # products of the n x n Gram matrix with the n x k basis, k = r + 2
+        k = np.minimum(r + 2, np.array(wl.N, dtype=np.float64))
         flops = 2.0 * 2.0 * float((np.array(wl.N, dtype=np.float64) ** 2 * k).sum()) / 3.0
         return (flops, "GFLOP/s", "alu", FP64_PEAK_GFLOPS,
                 "FP64 nominal from unit counts and clock (1.197 TFLOP/s measured by an "
                 "FMA-chain probe on this pool)",
-                "per cell and mode 2 x 2 n^2 k FP64 flops (k = r + 4), averaged over the "
+                "per cell and mode 2 x 2 n^2 k FP64 flops (k = r + 2), averaged over the "
                 "three launches of a step")
     if cls == "tucker_asm":
         # each cell assembles itself and its 6 neighbours' tensors: sum of first-mode

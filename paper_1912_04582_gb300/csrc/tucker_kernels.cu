@@ -48,7 +48,7 @@ constexpr int kKC = 32;    // column chunk of the Gram tiles
 // stride of 2 mod 8 words puts those 4 rows on disjoint banks
 constexpr int kKP2 = kKC + 2;
 constexpr int kTileRow = kKP2 > kKC + 1 ? kKP2 : kKC + 1;  // row length of the tile buffers
-constexpr int kExtra = 4;  // oversampling columns of the subspace iteration
+constexpr int kExtra = 2;  // oversampling columns of the subspace iteration
 constexpr int kPower = 3;     // orthogonal (power) iterations from a cold start
 constexpr int kWarmIter = 1;  // orthogonal iterations from the previous step's factor
 constexpr int kF32Passes = 2; // Cholesky-QR passes per FP32 orthogonal iteration

@@ -211,7 +211,7 @@ def test_graph_replay_equals_single_steps(dvm):
     b.step(7, residual=False)
     assert np.array_equal(a.f(), b.f())
     grid, tune = dvm.dvm_get_launch_config(a.h)
-    assert grid >= 1 and len(tune) == 5
+    assert abs(grid) >= 1 and len(tune) == 5  # negative: the phase-major variant
 
 
 @pytest.mark.parametrize("precision", [FP64, MIXED])
