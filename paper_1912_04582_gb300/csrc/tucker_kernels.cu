@@ -266,6 +266,30 @@ __device__ __forceinline__ void df_acc(float x, float y, float &hi, float &lo) {
 
 constexpr int kKP = kKC + 1;  // padded tile row (no shared-memory bank conflicts)
 
+// Storage of one Gram entry: FP64 on the FP64 path; on the mixed path the
+// double-float accumulator itself, as a (hi, lo) pair of floats in the same 8 bytes
+// (the eigen-solver's FP64-accuracy products read it without FP64 arithmetic).
+template <typename Real>
+__device__ __forceinline__ void gram_store(double *C, int idx, Real hi, Real lo) {
+  if constexpr (sizeof(Real) == 8) {
+    C[idx] = hi;
+  } else {
+    const float s = __fadd_rn(hi, lo);  // renormalised pair
+    reinterpret_cast<float2 *>(C)[idx] = make_float2(s, __fsub_rn(lo, __fsub_rn(s, hi)));
+  }
+}
+
+// One Gram entry as a double
+template <typename Real>
+__device__ __forceinline__ double gram_load(const double *C, int idx) {
+  if constexpr (sizeof(Real) == 8) {
+    return C[idx];
+  } else {
+    const float2 v = reinterpret_cast<const float2 *>(C)[idx];
+    return (double)v.x + (double)v.y;
+  }
+}
+
 template <typename Real, int TS>
 __device__ void gram_tiled(const Real *T, const int D[3], int m, Smem<Real> &sm) {
   const int n = D[m];
@@ -339,9 +363,8 @@ __device__ void gram_tiled(const Real *T, const int D[3], int m, Smem<Real> &sm)
       for (int j = 0; j < TS; ++j) {
         const int a = ta * TS + i, b = tb * TS + j;
         if (a < n && b < n) {
-          const double v = (double)hi[i][j] + (double)lo[i][j];
-          sm.C[a * n + b] = v;
-          sm.C[b * n + a] = v;
+          gram_store<Real>(sm.C, a * n + b, hi[i][j], lo[i][j]);
+          gram_store<Real>(sm.C, b * n + a, hi[i][j], lo[i][j]);
         }
       }
   }
@@ -498,10 +521,10 @@ __device__ __noinline__ void gram_w32(const Real *T, const int D[3], int m, Smem
     }
   }
   if (g == 0) {
-    auto put = [&](int a, int b, double v) {
+    auto put = [&](int a, int b, Real h, Real l) {
       if (a < n && b < n) {
-        sm.C[a * n + b] = v;
-        sm.C[b * n + a] = v;
+        gram_store<Real>(sm.C, a * n + b, h, l);
+        gram_store<Real>(sm.C, b * n + a, h, l);
       }
     };
     if (!diag) {
@@ -509,15 +532,15 @@ __device__ __noinline__ void gram_w32(const Real *T, const int D[3], int m, Smem
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-          put(4 * ta + i, 4 * tb + j, (double)hi[4 * i + j] + (double)lo[4 * i + j]);
+          put(4 * ta + i, 4 * tb + j, hi[4 * i + j], lo[4 * i + j]);
     } else {
       int e = 0;
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = i; j < 4; ++j, ++e) {
-          put(4 * ta + i, 4 * ta + j, (double)hi[e] + (double)lo[e]);
-          put(4 * tb + i, 4 * tb + j, (double)hi[10 + e] + (double)lo[10 + e]);
+          put(4 * ta + i, 4 * ta + j, hi[e], lo[e]);
+          put(4 * tb + i, 4 * tb + j, hi[10 + e], lo[10 + e]);
         }
     }
   }
@@ -547,6 +570,26 @@ __device__ void mat_cq(const T *__restrict__ C, const T *Q, T *W, int n, int k) 
     W[idx] = s;
   }
   __syncthreads();
+}
+
+// Double-float inner product sum_t (c_t.hi + c_t.lo) (vh_t + vl_t) with exact
+// leading products (fma) and a two-sum accumulation: about 2^-48 relative.
+__device__ __forceinline__ double df_dot(const float2 *c, const float *vh, const float *vl,
+                                         int stride, int n) {
+  float hi = 0.f, lo = 0.f;
+  for (int t = 0; t < n; ++t) {
+    const float2 ct = c[t];
+    const float h = vh[t * stride];
+    const float l = vl ? vl[t * stride] : 0.f;
+    const float p = __fmul_rn(ct.x, h);
+    const float pe = __fmaf_rn(ct.x, h, -p);
+    const float s = __fadd_rn(hi, p);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(err, __fmaf_rn(ct.x, l, __fmaf_rn(ct.y, h, pe))));
+  }
+  return (double)hi + (double)lo;
 }
 
 constexpr int kOrthMax = 24;  // largest number of basis columns
@@ -736,7 +779,8 @@ __device__ __noinline__ int leading_eigs(Smem<Real> &sm, int n, int k, const WT 
       pc.mark(12);
     }
   } else {
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) sm.C32[idx] = (float)sm.Cg[idx];
+    const float2 *Cdf = reinterpret_cast<const float2 *>(sm.Cg);
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) sm.C32[idx] = Cdf[idx].x;
     for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) {
       const int i = idx / k, j = idx - i * k;
       sm.Q32[idx] = (float)(j < r_warm ? (double)warm[(int64_t)i * ldw + j] : start_value(i, j));
@@ -751,29 +795,55 @@ __device__ __noinline__ int leading_eigs(Smem<Real> &sm, int n, int k, const WT 
       orthonormalise<float, float>(sm.Q32, n, k, G32, d32, kF32Passes, 1e-5, false);
       pc.mark(10);
     }
-    for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) sm.Q[idx] = (double)sm.Q32[idx];
+    // one power step with the accurate Gram matrix: W = C Q32 in double-float
+    // (the FP32 basis moves out of sm.W's space first)
+    float *V = reinterpret_cast<float *>(sm.Vr);
+    for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) V[idx] = sm.Q32[idx];
     __syncthreads();
-    mat_cq(sm.Cg, sm.Q, sm.W, n, k);
-    for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) sm.Q[idx] = sm.W[idx];
+    for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) {
+      const int i = idx / k, j = idx - i * k;
+      sm.Q[idx] = df_dot(Cdf + i * n, V + j, nullptr, k, n);
+    }
     __syncthreads();
     pc.mark(11);
     const int nz = orthonormalise<double, double>(sm.Q, n, k, sm.B, sm.cs, 3, 1e-11, true);
     if (threadIdx.x == 0) sm.par[29] = (double)nz;
     pc.mark(12);
   }
-  // Rayleigh quotients d_j = q_j^T C q_j of the orthonormal columns (FP64): any
-  // leading set of columns captures exactly the sum of its d_j, so the columns
-  // are ordered by d_j and the rank rule reads them (sorted, in sm.Z).
-  mat_cq(sm.Cg, sm.Q, sm.W, n, k);
-  if ((threadIdx.x >> 5) == 0) {
-    const int lane = threadIdx.x & 31;
-    for (int j = 0; j < k; ++j) {
+  // Rayleigh quotients d_j = q_j^T C q_j of the orthonormal columns (FP64
+  // accuracy): any leading set of columns captures exactly the sum of its d_j, so
+  // the columns are ordered by d_j and the rank rule reads them (sorted, in sm.Z).
+  // One warp per column, a lane per row, a fixed shuffle tree.
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  if (sizeof(Real) == 8) {
+    mat_cq(sm.Cg, sm.Q, sm.W, n, k);
+    for (int j = warp; j < k; j += nwarp) {
       double d = 0.0;
       for (int i = lane; i < n; i += 32) d = fma(sm.Q[i * k + j], sm.W[i * k + j], d);
       for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
       if (lane == 0) sm.cs[j] = d;
     }
-    __syncwarp();
+  } else {
+    // (C q_j)_i in double-float with q split into float hi + lo parts (in sm.W)
+    const float2 *Cdf = reinterpret_cast<const float2 *>(sm.Cg);
+    float *qh = reinterpret_cast<float *>(sm.W), *ql = qh + n * k;
+    for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) {
+      const double q = sm.Q[idx];
+      const float h = (float)q;
+      qh[idx] = h;
+      ql[idx] = (float)(q - (double)h);
+    }
+    __syncthreads();
+    for (int j = warp; j < k; j += nwarp) {
+      double d = 0.0;
+      for (int i = lane; i < n; i += 32)
+        d = fma(sm.Q[i * k + j], df_dot(Cdf + i * n, qh + j, ql + j, k, n), d);
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+      if (lane == 0) sm.cs[j] = d;
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
     if (lane == 0) {  // order columns by quotient, descending
       for (int i = 0; i < k; ++i) sm.perm[i] = i;
       for (int i = 1; i < k; ++i) {
@@ -807,7 +877,7 @@ template <typename Real>
 __device__ int choose_rank(Smem<Real> &sm, int n, int k, double thr, int cap, bool *met) {
   if (threadIdx.x == 0) {
     double tr = 0.0;
-    for (int i = 0; i < n; ++i) tr += sm.Cg[i * n + i];
+    for (int i = 0; i < n; ++i) tr += gram_load<Real>(sm.Cg, i * n + i);
     double kept = 0.0;
     int r = k, found = 0;
     for (int j = 0; j < k && thr > 0.0; ++j) {
