@@ -51,6 +51,8 @@ def _args():
     ap.add_argument("--rank-cap", type=int, default=None)
     ap.add_argument("--tol", type=float, default=None)
     ap.add_argument("--workload", default="cavity")
+    ap.add_argument("--variant", default="auto", choices=["auto", "fused", "phased"],
+                    help="Tucker launch variant (auto: the autotuner times both)")
     ap.add_argument("--advance", type=int, default=200,
                     help="untimed steps that develop the flow (and the Tucker ranks) first")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -384,7 +386,10 @@ def run_gpu(args, rank, world):
 
     # headline path, timed with the clock sampler running
     fmt = NAT.DVM_FORMAT_TUCKER if tucker else NAT.DVM_FORMAT_FULL
-    s = P.Solver(wl, format=fmt, precision=prec, rank_cap=cap, tol=tol, stream=stream.cuda_stream)
+    variant = {"auto": NAT.DVM_VARIANT_AUTO, "fused": NAT.DVM_VARIANT_FUSED,
+               "phased": NAT.DVM_VARIANT_PHASED}[args.variant]
+    s = P.Solver(wl, format=fmt, precision=prec, rank_cap=cap, tol=tol, stream=stream.cuda_stream,
+                 variant=variant)
     if args.advance:
         s.step(args.advance, residual=False)
     for _ in range(max(3, args.warmup)):
