@@ -233,6 +233,12 @@ def _tucker_work(wl, ranks, cls):
                 "FMA-chain probe on this pool)",
                 "per cell and mode 2 x 2 n^2 k FP64 flops (k = r + 2), averaged over the "
                 "three launches of a step")
+    if cls == "tucker_contract":
+        # G x2 U2 x3 U3 once per cell: r1 r2 r3 N3 + r1 r2 N2 N3 FMAs
+        flops = 2.0 * float((r[:, 0] * r[:, 1] * r[:, 2] * N3 + r[:, 0] * r[:, 1] * N2 * N3).sum())
+        return (flops, "GFLOP/s", "alu", 2 * FP32_PEAK_GOPS,
+                "FP32 70.0 TFLOP/s FMA-chain probe on this pool",
+                "r1 r2 r3 N3 + r1 r2 N2 N3 FP32 FMAs per cell")
     if cls == "tucker_asm":
         # each cell assembles itself and its 6 neighbours' tensors: sum of first-mode
         # ranks x N1 N2 N3 FMAs (interior cells; boundary faces are cheaper)

@@ -204,11 +204,12 @@ int dvm_set_kernel_timing(dvm_ctx *ctx, int32_t on);
 /* Accumulated launch times (ms) and counts since timing was switched on, per
  * kernel class: [0] full-grid step, [1] fused Tucker step, [2] phase-major
  * assembly, [3] first-mode Gram, [4] second/third-mode Gram, [5] eigen-solves,
- * [6] projections/cores, [7] moments of the new state.  ms[8], launches[8];
- * either may be NULL.  Synchronises the context's stream. */
+ * [6] projections/cores, [7] moments of the new state, [8] phase-major
+ * mode-2/3 contractions of all cells.  ms[9], launches[9]; either may be NULL.
+ * Synchronises the context's stream. */
 int dvm_get_kernel_timing(dvm_ctx *ctx, double *ms, int64_t *launches);
 
-#define DVM_KERNEL_CLASSES 8
+#define DVM_KERNEL_CLASSES 9
 
 /* Bytes of device memory held for the distribution function in its current
  * representation (Tucker: sum over cells of r1 r2 r3 + N1 r1 + N2 r2 + N3 r3

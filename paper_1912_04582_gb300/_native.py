@@ -28,9 +28,10 @@ DVM_BC_FREESTREAM, DVM_BC_ZEROGRAD, DVM_BC_SYMMETRY, DVM_BC_WALL = 0, 1, 2, 3
 DVM_FORMAT_FULL, DVM_FORMAT_TUCKER = 0, 1
 DVM_PREC_FP64, DVM_PREC_MIXED = 0, 1
 DVM_VARIANT_AUTO, DVM_VARIANT_FUSED, DVM_VARIANT_PHASED = 0, 1, 2
-DVM_KERNEL_CLASSES = 8
+DVM_KERNEL_CLASSES = 9
 KERNEL_CLASS_NAMES = ("full_step", "tucker_fused_step", "tucker_asm", "tucker_gram_mode1",
-                      "tucker_gram_mode23", "tucker_eig", "tucker_proj", "moments")
+                      "tucker_gram_mode23", "tucker_eig", "tucker_proj", "moments",
+                      "tucker_contract")
 
 _c_dp = ctypes.POINTER(ctypes.c_double)
 _c_i64p = ctypes.POINTER(ctypes.c_int64)

@@ -85,8 +85,8 @@ size_t estimate(const dvm_request *q) {
     // work buffers of the phase-major step variant, if the autotuner keeps it
     b += (size_t)nc * (tucker_split_bytes_per_cell(q->vgrid.N[0], q->vgrid.N[1], q->vgrid.N[2],
                                                    (int)R, (int)Nmax, es == 8) + 64);
-    b += std::min<size_t>((size_t)nc, (size_t)sms * tucker_split_asm_per_sm()) * es *
-         (tucker_split_t2_elems(q->vgrid.N[0], q->vgrid.N[1], q->vgrid.N[2], (int)R) + 64);
+    b += (size_t)nc * tucker_split_t2all_bytes_per_cell(q->vgrid.N[0], q->vgrid.N[1],
+                                                        q->vgrid.N[2], (int)R, es == 8) + 512;
   }
   return b + b / 20 + (16u << 20);
 }

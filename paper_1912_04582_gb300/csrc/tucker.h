@@ -42,6 +42,8 @@ struct TuckerSplitBufs {
   double *C;     // [cn][Nmax*Nmax] Gram matrix of the current mode
   double *e;     // [cn] ||X||^2
   double *disc;  // [cn] energy left out so far
+  void *T2all;   // [nc][R][N2 N3] mode-2/3 contraction of every cell (working precision)
+  void *U1all;   // [nc][R][padN(N1)] first-mode factors, transposed, zero-padded
   void *t2;      // assembly staging, t2_stride elements per assembly CTA
   size_t t2_stride;
   int asm_grid;  // assembly CTAs (persistent over the chunk)
@@ -58,7 +60,8 @@ enum KernelClass : int {
   kKEig = 5,        // phase-major: eigen-solves
   kKProj = 6,       // phase-major: projections and cores
   kKMoments = 7,    // moments (and macroparameters) of the new state
-  kKClasses = 8
+  kKContract = 8,   // phase-major: mode-2/3 contraction of every cell
+  kKClasses = 9
 };
 
 // Event marks around launches (null: no timing)
@@ -98,6 +101,8 @@ size_t tucker_split_bytes_per_cell(int N1, int N2, int N3, int R, int Nmax, bool
 // assembly CTAs per SM of the phase-major variant and their staging elements
 int tucker_split_asm_per_sm();
 size_t tucker_split_t2_elems(int N1, int N2, int N3, int R);
+// bytes per cell of the all-cell contraction buffers (TuckerSplitBufs::T2all, U1all)
+size_t tucker_split_t2all_bytes_per_cell(int N1, int N2, int N3, int R, bool fp64);
 // raise the kernels' shared-memory opt-in for this size (outside stream captures)
 int tucker_prepare_launch(int Nmax, int R, bool fp64);
 int launch_tucker_expand(const TuckerDev &T, int64_t c0, int64_t ncell, int N1, int N2, int N3,

@@ -290,6 +290,22 @@ __device__ __forceinline__ double gram_load(const double *C, int idx) {
   }
 }
 
+// trace of the n x n Gram matrix at sm.Cg (thread 0 sums in order; all threads
+// return it)
+template <typename Real>
+__device__ double gram_trace(Smem<Real> &sm, int n) {
+  if (threadIdx.x == 0) {
+    double tr = 0.0;
+    for (int i = 0; i < n; ++i) tr += gram_load<Real>(sm.Cg, i * n + i);
+    sm.par[27] = tr;
+  }
+  __syncthreads();
+  const double tr = sm.par[27];
+  __syncthreads();
+  return tr;
+}
+
+
 template <typename Real, int TS>
 __device__ void gram_tiled(const Real *T, const int D[3], int m, Smem<Real> &sm) {
   const int n = D[m];
@@ -938,15 +954,9 @@ __device__ void project(const Real *T, const int D[3], int m, int r, int k, Smem
 template <typename Real, int TS>
 __device__ void round_hosvd(Real *X, Real *T1, Real *T2, const int N[3], int R, double eps,
                             TuckerDev &out, int64_t cell, Smem<Real> &sm, double *err_out,
-                            PhaseClock &pc, const TuckerDev *warm, double e = -1.0) {
+                            PhaseClock &pc, const TuckerDev *warm) {
   int D[3] = {N[0], N[1], N[2]};
-  const int NN = N[0] * N[1] * N[2];
-  if (e < 0.0) {  // ||X||^2 unless the caller has it
-    e = 0.0;
-    for (int i = threadIdx.x; i < NN; i += blockDim.x) e += (double)X[i] * (double)X[i];
-    e = block_sum_d(e, sm.red);
-  }
-  const double thr = eps * eps / 3.0 * e;
+  double e = 0.0, thr = 0.0;  // ||X||^2 = trace of the first Gram matrix
   double discarded = 0.0;
   int r[3];
   pc.mark(4);
@@ -955,6 +965,10 @@ __device__ void round_hosvd(Real *X, Real *T1, Real *T2, const int N[3], int R, 
   for (int m = 0; m < 3; ++m) {
     const int n = D[m];
     gram<Real, TS>(src, D, m, sm);
+    if (m == 0) {
+      e = gram_trace<Real>(sm, n);
+      thr = eps * eps / 3.0 * e;
+    }
     pc.mark(5);
     const double *wU = warm ? warm->fac[m] + cell * (int64_t)N[m] * R : nullptr;
     const int wr = warm ? warm->rank[3 * cell + m] : 0;
@@ -1046,7 +1060,7 @@ __device__ __forceinline__ Real *tabp(Smem<Real> &sm, int Nmax, int t) {
 // (rows of U1 reversed, or the mirrored (i2, i3) column).  X is written once and
 // its squared norm returned (FP64, block-reduced).
 struct AsmTerm {
-  int off;      // T2 offset in the scratch block (elements)
+  int64_t off;  // T2 offset from the T2 base (elements)
   int r1;       // first-mode rank
   int u1;       // U1 row block in sm.u1 (elements)
   int rev;      // 1: first-mode index mirrored
@@ -1114,32 +1128,46 @@ __device__ __noinline__ void term_contract(const TuckerDev &T, int64_t cell, con
   __syncthreads();
 }
 
-// The assembly pass proper (see above).  Returns ||X||^2 (FP64) on every thread.
+// The assembly pass proper (see above).  The mode-2/3 contractions come either
+// from T2all / U1all (computed once per cell by tucker_t2_kernel: [cell][R][N2 N3]
+// and [cell][R][padN(N1)]) or, when T2all is null, are formed here into T2buf.
 template <typename Real>
-__device__ __noinline__ double assemble(const TuckerStepParams &P, int64_t c, const int N[3],
-                                        Smem<Real> &sm, const SlotDev *s_slot,
-                                        const double *s_scale, Real *X, Real *T2buf,
-                                        PhaseClock &pc) {
+__device__ __noinline__ void assemble(const TuckerStepParams &P, int64_t c, const int N[3],
+                                      Smem<Real> &sm, const SlotDev *s_slot,
+                                      const double *s_scale, Real *X, Real *T2buf,
+                                      const Real *T2all, const Real *U1all, PhaseClock &pc) {
   __shared__ AsmTerm s_term[1 + 2 * 6];
   __shared__ int s_r1[kTerms];
   const int tid = threadIdx.x;
   const int N1 = N[0], N2 = N[1], N3 = N[2], NP = N2 * N3, Nm = P.Nmax, R = P.R;
   const int N1P = padN(N1), u1slot = R * padN(Nm);
-  // mode-2/3 contractions of the cell's own tensor and of each interior neighbour
-  int nsrc = 0, off = 0;
-  int src_off[kTerms], src_r1[kTerms];
+  int nsrc = 0;
+  int64_t off = 0;
+  int64_t src_off[kTerms];
+  int src_r1[kTerms];
   bool mirror1 = false;  // a symmetry face mirrors the first-mode index
   for (int l = -1; l < 6; ++l) {
     if (l >= 0 && s_slot[l].kind == kSymmetry && s_slot[l].flip == 0) mirror1 = true;
     if (l >= 0 && s_slot[l].kind != kInterior) continue;
     const int64_t cell = l < 0 ? c : (int64_t)s_slot[l].src;
-    term_contract<Real>(P.cur, cell, N, R, NP, sm, sm.u1 + nsrc * u1slot, T2buf + off,
-                        &s_r1[nsrc]);
-    src_off[nsrc] = off;
-    src_r1[nsrc] = s_r1[nsrc];
-    off += s_r1[nsrc] * NP;
+    if (T2all) {  // precomputed: first-mode rows to shared memory
+      const int r1 = P.cur.rank[3 * cell];
+      const Real *u = U1all + cell * (int64_t)R * N1P;
+      Real *d = sm.u1 + nsrc * u1slot;
+      for (int idx = tid; idx < r1 * N1P; idx += blockDim.x) d[idx] = u[idx];
+      src_off[nsrc] = cell * (int64_t)R * NP;
+      src_r1[nsrc] = r1;
+    } else {  // contraction of the cell's own tensor / each interior neighbour here
+      term_contract<Real>(P.cur, cell, N, R, NP, sm, sm.u1 + nsrc * u1slot, T2buf + off,
+                          &s_r1[nsrc]);
+      src_off[nsrc] = off;
+      src_r1[nsrc] = s_r1[nsrc];
+      off += (int64_t)s_r1[nsrc] * NP;
+    }
     ++nsrc;
   }
+  if (T2all) __syncthreads();
+  const Real *T2base = T2all ? T2all : T2buf;
   if (mirror1) {  // the cell's own first-mode factor with rows reversed, in the spare slot
     Real *dst = sm.u1 + kTerms * u1slot;
     for (int idx = tid; idx < src_r1[0] * N1P; idx += blockDim.x) {
@@ -1180,7 +1208,6 @@ __device__ __noinline__ double assemble(const TuckerStepParams &P, int64_t c, co
   const Real *V0 = tabp(sm, Nm, 9), *V1 = tabp(sm, Nm, 10), *V2 = tabp(sm, Nm, 11);
   const Real *G0 = tabp(sm, Nm, 12), *G1 = tabp(sm, Nm, 13), *G2 = tabp(sm, Nm, 14);
   const int nch = N1P / kRows;
-  Real ens = 0, enc = 0;
   for (int item = tid; item < NP * nch; item += blockDim.x) {
     const int p = item % NP, ch = item / NP;
     const int i2 = p / N3, i3 = p - i2 * N3;
@@ -1220,7 +1247,7 @@ __device__ __noinline__ double assemble(const TuckerStepParams &P, int64_t c, co
       int pp = p;
       if (tm.reflect == 1) pp = (N2 - 1 - i2) * N3 + i3;
       else if (tm.reflect == 2) pp = i2 * N3 + (N3 - 1 - i3);
-      const Real *t2 = T2buf + tm.off + pp;
+      const Real *t2 = T2base + tm.off + pp;
       const Real *u1 = sm.u1 + tm.u1 + i10;
 #pragma unroll
       for (int j = 0; j < kRows; ++j) sv[j] = 0;
@@ -1292,18 +1319,10 @@ __device__ __noinline__ double assemble(const TuckerStepParams &P, int64_t c, co
 #pragma unroll
     for (int j = 0; j < kRows; ++j) {
       const int i1 = i10 + j;
-      if (i1 < N1) {
-        X[(int64_t)i1 * NP + p] = acc[j];
-        // ||X||^2 only scales the truncation threshold: a compensated (Kahan)
-        // sum in the working precision per thread is ample
-        const Real y = acc[j] * acc[j] - enc;
-        const Real t = ens + y;
-        enc = (t - ens) - y;
-        ens = t;
-      }
+      if (i1 < N1) __stcs(X + (int64_t)i1 * NP + p, acc[j]);  // streamed past L2
     }
   }
-  return block_sum_d((double)ens - (double)enc, sm.red);
+  __syncthreads();
 }
 
 // Per-cell prologue of the assembly: slots, wall-density scales, the cell's
@@ -1348,7 +1367,13 @@ __device__ void cell_prologue(const TuckerStepParams &P, int64_t c, const int N[
         const double x = P.xi[a][i];
         const double v = x - sm.par[1 + a];
         tabp(sm, Nm, 0 + a)[i] = (Real)x;
-        tabp(sm, Nm, 3 + a)[i] = (Real)((a == 0 ? dtnu : 1.0) * amp * exp(-v * v / T));
+        if constexpr (sizeof(Real) == 8) {
+          tabp(sm, Nm, 3 + a)[i] = (a == 0 ? dtnu : 1.0) * amp * exp(-v * v / T);
+        } else {  // the table is FP32: evaluate it in FP32
+          const float vf = (float)v;
+          tabp(sm, Nm, 3 + a)[i] =
+              (float)(a == 0 ? dtnu * amp : amp) * expf(-vf * vf / (float)T);
+        }
         tabp(sm, Nm, 6 + a)[i] = (Real)(A * sm.par[5 + a] * v);
         tabp(sm, Nm, 9 + a)[i] = (Real)(v * v / T);
         double g = 0.0;
@@ -1405,10 +1430,10 @@ __global__ void __launch_bounds__(kTB, MinBlocks<Real>::value) tucker_step_kerne
     cell_prologue<Real>(P, c, N, sm, s_slot, s_scale);
     pc.mark(0);
     // ---- f^{n+1} before rounding, in one pass
-    const double eX = assemble<Real>(P, c, N, sm, s_slot, s_scale, X, T2buf, pc);
+    assemble<Real>(P, c, N, sm, s_slot, s_scale, X, T2buf, nullptr, nullptr, pc);
     pc.mark(3);
     // ---- rounding
-    round_hosvd<Real, TS>(X, T1, T2, N, P.R, P.tol, P.nxt, c, sm, P.err, pc, &P.cur, eX);
+    round_hosvd<Real, TS>(X, T1, T2, N, P.R, P.tol, P.nxt, c, sm, P.err, pc, &P.cur);
   }
 }
 
@@ -1471,11 +1496,26 @@ __global__ void __launch_bounds__(kAsmTB, sizeof(Real) == 8 ? 4 : 6)
     const int64_t c = B.c0 + j;
     cell_prologue<Real>(P, c, N, sm, s_slot, s_scale);
     Real *X = reinterpret_cast<Real *>(B.X) + j * NN;
-    const double e = assemble<Real>(P, c, N, sm, s_slot, s_scale, X, T2buf, pc);
-    if (threadIdx.x == 0) {
-      B.e[j] = e;
-      B.disc[j] = 0.0;
-    }
+    assemble<Real>(P, c, N, sm, s_slot, s_scale, X, T2buf, reinterpret_cast<const Real *>(B.T2all),
+                   reinterpret_cast<const Real *>(B.U1all), pc);
+    if (threadIdx.x == 0) B.disc[j] = 0.0;
+  }
+}
+
+// Mode-2/3 contraction T2 = G x2 U2 x3 U3 of every cell's current tensor and its
+// first-mode factor in the working precision (transposed, zero-padded), once per
+// step for all cells (each is used by the cell and its face neighbours).
+template <typename Real>
+__global__ void __launch_bounds__(kAsmTB) tucker_t2_kernel(TuckerStepParams P, TuckerSplitBufs B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem<Real> sm = carve_asm<Real>(smem_raw, P.Nmax, P.R);
+  const int N[3] = {P.N1, P.N2, P.N3};
+  const int NP = P.N2 * P.N3, R = P.R, N1P = padN(P.N1);
+  __shared__ int s_r1;
+  for (int64_t c = blockIdx.x; c < P.nc; c += gridDim.x) {
+    term_contract<Real>(P.cur, c, N, R, NP, sm,
+                        reinterpret_cast<Real *>(B.U1all) + c * (int64_t)R * N1P,
+                        reinterpret_cast<Real *>(B.T2all) + c * (int64_t)R * NP, &s_r1);
   }
 }
 
@@ -1566,6 +1606,11 @@ __global__ void __launch_bounds__(32, 13) tucker_eig_kernel(TuckerStepParams P, 
   const int64_t j = blockIdx.x, c = B.c0 + j;
   const int n = N[m];
   sm.Cg = B.C + j * (int64_t)Nm * Nm;  // read through L1
+  if (m == 0) {  // ||X||^2 = trace of the first Gram matrix
+    const double tr = gram_trace<Real>(sm, n);
+    if (threadIdx.x == 0) B.e[j] = tr;
+  }
+  __syncthreads();
   const double thr = P.tol * P.tol / 3.0 * B.e[j];
   const double *wU = P.cur.fac[m] + c * (int64_t)n * R;
   const int wr = P.cur.rank[3 * c + m];
@@ -1822,7 +1867,7 @@ int raise_smem_optin(K kernel, size_t smem, size_t &opted) {
 
 template <typename Real, int TS>
 struct OptIn {
-  static size_t step, expand, asm_, gram, eig, proj;
+  static size_t step, expand, asm_, gram, eig, proj, t2;
 };
 template <typename Real, int TS>
 size_t OptIn<Real, TS>::step = 0;
@@ -1836,6 +1881,8 @@ template <typename Real, int TS>
 size_t OptIn<Real, TS>::eig = 0;
 template <typename Real, int TS>
 size_t OptIn<Real, TS>::proj = 0;
+template <typename Real, int TS>
+size_t OptIn<Real, TS>::t2 = 0;
 
 template <typename Real, int TS>
 int launch_step_TS(const TuckerStepParams &p, int grid, cudaStream_t s) {
@@ -1871,6 +1918,7 @@ int prepare_split_TS(int Nmax, int R) {
   const SplitSmem<Real, TS> z(Nmax, R);
   using O = OptIn<Real, TS>;
   if (raise_smem_optin(tucker_asm_kernel<Real>, z.asm_, O::asm_) != 0 ||
+      raise_smem_optin(tucker_t2_kernel<Real>, z.asm_, O::t2) != 0 ||
       raise_smem_optin(tucker_gram_kernel<Real, TS>, z.gram, O::gram) != 0 ||
       raise_smem_optin(tucker_eig_kernel<Real>, z.eig, O::eig) != 0 ||
       raise_smem_optin(tucker_proj_kernel<Real>, z.proj, O::proj) != 0 ||
@@ -1889,6 +1937,9 @@ int launch_split_TS(const TuckerStepParams &p, TuckerSplitBufs b, int64_t chunk,
   cudaStreamIsCapturing(s, &cap);
   if (cap == cudaStreamCaptureStatusNone && prepare_split_TS<Real, TS>(p.Nmax, p.R) != 0) return -1;
   const SplitSmem<Real, TS> z(p.Nmax, p.R);
+  T(kKContract, true, s);
+  tucker_t2_kernel<Real><<<(unsigned)(p.nc < 65535 * 16 ? p.nc : 65535 * 16), kAsmTB, z.asm_, s>>>(p, b);
+  T(kKContract, false, s);
   for (int64_t c0 = 0; c0 < p.nc; c0 += chunk) {
     b.c0 = c0;
     b.cn = p.nc - c0 < chunk ? p.nc - c0 : chunk;
@@ -1987,6 +2038,11 @@ size_t tucker_split_bytes_per_cell(int N1, int N2, int N3, int R, int Nmax, bool
   const size_t es = fp64 ? sizeof(double) : sizeof(float);
   return es * ((size_t)N1 * N2 * N3 + (size_t)R * N2 * N3 + (size_t)R * R * N3) +
          sizeof(double) * ((size_t)Nmax * Nmax + 2);
+}
+
+size_t tucker_split_t2all_bytes_per_cell(int N1, int N2, int N3, int R, bool fp64) {
+  const size_t es = fp64 ? sizeof(double) : sizeof(float);
+  return es * (size_t)R * ((size_t)N2 * N3 + padN(N1));
 }
 
 int launch_tucker_expand(const TuckerDev &T, int64_t c0, int64_t ncell, int N1, int N2, int N3,

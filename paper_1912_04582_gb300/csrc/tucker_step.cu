@@ -338,17 +338,23 @@ int alloc_split(dvm_ctx *C) {
     set_error("no device memory for the phase-major Tucker step buffers");
     return DVM_ERR_OOM;
   }
+  (void)t2_stride;
   const int asm_grid = (int)std::min<int64_t>(chunk, (int64_t)sms * tucker_split_asm_per_sm());
-  const size_t bytes = per * chunk + es * t2_stride * asm_grid + 256;
+  const size_t t2all = tucker_split_t2all_bytes_per_cell(C->N[0], C->N[1], C->N[2], S->R, S->fp64);
+  const size_t bytes = per * chunk + t2all * C->nc + 512;
   void *mem = nullptr;
   int rc = ctx_malloc(C, &mem, bytes);
   if (rc != DVM_OK) return rc;
   char *q = static_cast<char *>(mem);
   TuckerSplitBufs b{};
-  b.t2 = q;
-  b.t2_stride = t2_stride;
+  b.t2 = nullptr;  // the assembly reads the all-cell contractions instead
+  b.t2_stride = 0;
   b.asm_grid = asm_grid;
-  q += es * t2_stride * asm_grid;
+  b.T2all = q;
+  q += es * (size_t)C->nc * S->R * C->N[1] * C->N[2];
+  b.U1all = q;
+  q += t2all * C->nc - es * (size_t)C->nc * S->R * C->N[1] * C->N[2];
+  q = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(q) + 255) & ~uintptr_t(255));
   b.X = q;
   q += es * chunk * C->N[0] * C->N[1] * C->N[2];
   b.Y1 = q;

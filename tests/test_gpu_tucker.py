@@ -249,8 +249,9 @@ def test_kernel_timing_covers_the_step(dvm):
     from paper_1912_04582_gb300 import _native as NAT
     wl = W.cavity(nside=6, N=16, seed=4)
     for v, classes in ((NAT.DVM_VARIANT_PHASED,
-                        {"tucker_asm": 1, "tucker_gram_mode1": 1, "tucker_gram_mode23": 2,
-                         "tucker_eig": 3, "tucker_proj": 3, "moments": 1}),
+                        {"tucker_contract": 1, "tucker_asm": 1, "tucker_gram_mode1": 1,
+                         "tucker_gram_mode23": 2, "tucker_eig": 3, "tucker_proj": 3,
+                         "moments": 1}),
                        (NAT.DVM_VARIANT_FUSED, {"tucker_fused_step": 1, "moments": 1})):
         s = dvm.Solver(wl, format=1, precision=MIXED, rank_cap=8, tol=1e-6, variant=v)
         s.step(2)
