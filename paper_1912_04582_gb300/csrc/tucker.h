@@ -47,7 +47,14 @@ struct TuckerSplitBufs {
   void *t2;      // assembly staging, t2_stride elements per assembly CTA
   size_t t2_stride;
   int asm_grid;  // assembly CTAs (persistent over the chunk)
-  int64_t c0, cn;
+  int64_t c0, cn;  // cells [c0, c0 + cn) of this launch
+  int64_t joff;    // their first buffer index (buffers hold one chunk)
+};
+
+// Second stream and fork / join events of the phase-major step (optional)
+struct SplitStreams {
+  cudaStream_t s2;
+  cudaEvent_t fork, join;
 };
 
 // Kernel classes of the optional per-launch event timing (dvm_set_kernel_timing)
@@ -95,7 +102,8 @@ int tucker_step_blocks_per_sm(int Nmax, int R, bool fp64);
 int launch_tucker_step(const TuckerStepParams &p, int grid, bool fp64, cudaStream_t s);
 // phase-major step over chunks of `chunk` cells (buffers sized for one chunk)
 int launch_tucker_split_step(const TuckerStepParams &p, TuckerSplitBufs b, int64_t chunk,
-                             bool fp64, cudaStream_t s, const LaunchTimer *lt = nullptr);
+                             bool fp64, cudaStream_t s, const LaunchTimer *lt = nullptr,
+                             const SplitStreams *ss = nullptr);
 // bytes of TuckerSplitBufs per cell (working precision fp64 or float)
 size_t tucker_split_bytes_per_cell(int N1, int N2, int N3, int R, int Nmax, bool fp64);
 // assembly CTAs per SM of the phase-major variant and their staging elements

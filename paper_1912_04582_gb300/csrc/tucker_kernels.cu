@@ -1493,12 +1493,12 @@ __global__ void __launch_bounds__(kAsmTB, sizeof(Real) == 8 ? 4 : 6)
   Real *T2buf = reinterpret_cast<Real *>(B.t2) + (size_t)blockIdx.x * B.t2_stride;
   PhaseClock pc(nullptr);
   for (int64_t j = blockIdx.x; j < B.cn; j += gridDim.x) {
-    const int64_t c = B.c0 + j;
+    const int64_t c = B.c0 + j, jb = B.joff + j;
     cell_prologue<Real>(P, c, N, sm, s_slot, s_scale);
-    Real *X = reinterpret_cast<Real *>(B.X) + j * NN;
+    Real *X = reinterpret_cast<Real *>(B.X) + jb * NN;
     assemble<Real>(P, c, N, sm, s_slot, s_scale, X, T2buf, reinterpret_cast<const Real *>(B.T2all),
                    reinterpret_cast<const Real *>(B.U1all), pc);
-    if (threadIdx.x == 0) B.disc[j] = 0.0;
+    if (threadIdx.x == 0) B.disc[jb] = 0.0;
   }
 }
 
@@ -1546,12 +1546,12 @@ __global__ void __launch_bounds__(kTB) tucker_gram_kernel(TuckerStepParams P, Tu
   sm.tile = reinterpret_cast<Real *>(smem_raw + sizeof(double) * Nm * Nm);
   sm.tile2 = sm.tile + (size_t)(Nm > 32 ? Nm : 32) * kTileRow;
   const int N[3] = {P.N1, P.N2, P.N3};
-  const int64_t j = blockIdx.x, c = B.c0 + j;
+  const int64_t j = blockIdx.x, c = B.c0 + j, jb = B.joff + j;
   int D[3];
   split_dims(B, P.nxt, c, m, N, D);
-  gram<Real, TS>(split_src<Real>(B, j, m, P.R, N), D, m, sm);
+  gram<Real, TS>(split_src<Real>(B, jb, m, P.R, N), D, m, sm);
   const int n = D[m];
-  double *out = B.C + j * (int64_t)Nm * Nm;
+  double *out = B.C + jb * (int64_t)Nm * Nm;
   for (int i = threadIdx.x; i < n * n; i += blockDim.x) out[i] = sm.C[i];
 }
 
@@ -1603,7 +1603,7 @@ __global__ void __launch_bounds__(32, 13) tucker_eig_kernel(TuckerStepParams P, 
     sm.perm = reinterpret_cast<int *>(smem_raw + off);
   }
   const int N[3] = {P.N1, P.N2, P.N3};
-  const int64_t j = blockIdx.x, c = B.c0 + j;
+  const int64_t c = B.c0 + blockIdx.x, j = B.joff + blockIdx.x;  // j: buffer index
   const int n = N[m];
   sm.Cg = B.C + j * (int64_t)Nm * Nm;  // read through L1
   if (m == 0) {  // ||X||^2 = trace of the first Gram matrix
@@ -1648,7 +1648,7 @@ __global__ void __launch_bounds__(kTB) tucker_proj_kernel(TuckerStepParams P, Tu
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int R = P.R;
   const int N[3] = {P.N1, P.N2, P.N3};
-  const int64_t j = blockIdx.x, c = B.c0 + j;
+  const int64_t c = B.c0 + blockIdx.x, j = B.joff + blockIdx.x;  // j: buffer index
   int D[3];
   split_dims(B, P.nxt, c, m, N, D);
   const int n = D[m], r = P.nxt.rank[3 * c + m];
@@ -1927,10 +1927,32 @@ int prepare_split_TS(int Nmax, int R) {
   return 0;
 }
 
+// The chain of one range of cells: assembly, then per mode Gram / eigen-solve /
+// projection.
+template <typename Real, int TS>
+void split_chain(const TuckerStepParams &p, const TuckerSplitBufs &b, const SplitSmem<Real, TS> &z,
+                 cudaStream_t s, const LaunchTimer &T) {
+  const int ga = (int)(b.cn < b.asm_grid ? b.cn : b.asm_grid);
+  T(kKAsm, true, s);
+  tucker_asm_kernel<Real><<<ga, kAsmTB, z.asm_, s>>>(p, b);
+  T(kKAsm, false, s);
+  for (int m = 0; m < 3; ++m) {
+    const int gc = m == 0 ? kKGram0 : kKGram12;
+    T(gc, true, s);
+    tucker_gram_kernel<Real, TS><<<(unsigned)b.cn, kTB, z.gram, s>>>(p, b, m);
+    T(gc, false, s);
+    T(kKEig, true, s);
+    tucker_eig_kernel<Real><<<(unsigned)b.cn, 32, z.eig, s>>>(p, b, m);
+    T(kKEig, false, s);
+    T(kKProj, true, s);
+    tucker_proj_kernel<Real><<<(unsigned)b.cn, kTB, z.proj, s>>>(p, b, m);
+    T(kKProj, false, s);
+  }
+}
+
 template <typename Real, int TS>
 int launch_split_TS(const TuckerStepParams &p, TuckerSplitBufs b, int64_t chunk, cudaStream_t s,
-                    const LaunchTimer *lt) {
-  const int asm_grid = b.asm_grid;
+                    const LaunchTimer *lt, const SplitStreams *ss) {
   const LaunchTimer none{nullptr, nullptr};
   const LaunchTimer &T = lt ? *lt : none;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -1940,25 +1962,44 @@ int launch_split_TS(const TuckerStepParams &p, TuckerSplitBufs b, int64_t chunk,
   T(kKContract, true, s);
   tucker_t2_kernel<Real><<<(unsigned)(p.nc < 65535 * 16 ? p.nc : 65535 * 16), kAsmTB, z.asm_, s>>>(p, b);
   T(kKContract, false, s);
+  // with a second stream (and no per-launch timing), each chunk's two halves run
+  // their chains concurrently: one half's FP64-bound eigen-solves overlap the
+  // other half's FP32-bound Gram / assembly kernels
+  const bool dual = ss && ss->s2 && !(lt && lt->mark);
+  if (dual) {
+    if (cudaEventRecord(ss->fork, s) != cudaSuccess) return -1;
+    if (cudaStreamWaitEvent(ss->s2, ss->fork, 0) != cudaSuccess) return -1;
+  }
   for (int64_t c0 = 0; c0 < p.nc; c0 += chunk) {
-    b.c0 = c0;
-    b.cn = p.nc - c0 < chunk ? p.nc - c0 : chunk;
-    const int ga = (int)(b.cn < asm_grid ? b.cn : asm_grid);
-    T(kKAsm, true, s);
-    tucker_asm_kernel<Real><<<ga, kAsmTB, z.asm_, s>>>(p, b);
-    T(kKAsm, false, s);
-    for (int m = 0; m < 3; ++m) {
-      const int gc = m == 0 ? kKGram0 : kKGram12;
-      T(gc, true, s);
-      tucker_gram_kernel<Real, TS><<<(unsigned)b.cn, kTB, z.gram, s>>>(p, b, m);
-      T(gc, false, s);
-      T(kKEig, true, s);
-      tucker_eig_kernel<Real><<<(unsigned)b.cn, 32, z.eig, s>>>(p, b, m);
-      T(kKEig, false, s);
-      T(kKProj, true, s);
-      tucker_proj_kernel<Real><<<(unsigned)b.cn, kTB, z.proj, s>>>(p, b, m);
-      T(kKProj, false, s);
+    const int64_t cn = p.nc - c0 < chunk ? p.nc - c0 : chunk;
+    if (dual && cn >= 2) {
+      const int64_t h = cn / 2;
+      TuckerSplitBufs b0 = b, b1 = b;
+      b0.c0 = c0;
+      b0.cn = h;
+      b0.joff = 0;
+      b1.c0 = c0 + h;
+      b1.cn = cn - h;
+      b1.joff = h;
+      split_chain<Real, TS>(p, b0, z, s, T);
+      split_chain<Real, TS>(p, b1, z, ss->s2, T);
+      // the next chunk reuses the buffers: both halves must be done
+      if (c0 + chunk < p.nc) {
+        if (cudaEventRecord(ss->join, ss->s2) != cudaSuccess) return -1;
+        if (cudaStreamWaitEvent(s, ss->join, 0) != cudaSuccess) return -1;
+        if (cudaEventRecord(ss->fork, s) != cudaSuccess) return -1;
+        if (cudaStreamWaitEvent(ss->s2, ss->fork, 0) != cudaSuccess) return -1;
+      }
+    } else {
+      b.c0 = c0;
+      b.cn = cn;
+      b.joff = 0;
+      split_chain<Real, TS>(p, b, z, s, T);
     }
+  }
+  if (dual) {
+    if (cudaEventRecord(ss->join, ss->s2) != cudaSuccess) return -1;
+    if (cudaStreamWaitEvent(s, ss->join, 0) != cudaSuccess) return -1;
   }
   return 0;
 }
@@ -2013,12 +2054,13 @@ int launch_tucker_step(const TuckerStepParams &p, int grid, bool fp64, cudaStrea
 }
 
 int launch_tucker_split_step(const TuckerStepParams &p, TuckerSplitBufs b, int64_t chunk,
-                             bool fp64, cudaStream_t s, const LaunchTimer *lt) {
+                             bool fp64, cudaStream_t s, const LaunchTimer *lt,
+                             const SplitStreams *ss) {
   if (fp64)
-    return p.Nmax <= 32 ? launch_split_TS<double, 2>(p, b, chunk, s, lt)
-                        : launch_split_TS<double, 4>(p, b, chunk, s, lt);
-  return p.Nmax <= 32 ? launch_split_TS<float, 2>(p, b, chunk, s, lt)
-                      : launch_split_TS<float, 4>(p, b, chunk, s, lt);
+    return p.Nmax <= 32 ? launch_split_TS<double, 2>(p, b, chunk, s, lt, ss)
+                        : launch_split_TS<double, 4>(p, b, chunk, s, lt, ss);
+  return p.Nmax <= 32 ? launch_split_TS<float, 2>(p, b, chunk, s, lt, ss)
+                      : launch_split_TS<float, 4>(p, b, chunk, s, lt, ss);
 }
 
 int tucker_split_asm_per_sm() { return 6; }

@@ -35,6 +35,7 @@ struct TuckerState {
   int64_t chunk = 0;                   // cells per chunk
   void *split_mem = nullptr;
   size_t split_bytes = 0;
+  SplitStreams ss{};                   // second stream of the phase-major step
   cudaGraphExec_t graph = nullptr;     // two steps (returns to the same buffer parity)
   int graph_parity = -1;               // S->cur / S->scur when the graph was captured
   cudaStream_t gstream = nullptr;      // private stream the graph is captured on / replayed on
@@ -242,6 +243,9 @@ void tucker_free(dvm_ctx *C) {
   if (S->ev_out) cudaEventDestroy(S->ev_out);
   if (S->scratch) cudaFree(S->scratch);
   if (S->split_mem) cudaFree(S->split_mem);
+  if (S->ss.s2) cudaStreamDestroy(S->ss.s2);
+  if (S->ss.fork) cudaEventDestroy(S->ss.fork);
+  if (S->ss.join) cudaEventDestroy(S->ss.join);
   if (S->ghostf) cudaFree(S->ghostf);
   if (S->err) cudaFree(S->err);
   if (S->phase) {
@@ -297,7 +301,7 @@ int enqueue_one_step(dvm_ctx *C, TuckerStepParams &p) {
   const LaunchTimer lt = C->timer();
   int lrc;
   if (S->split) {
-    lrc = launch_tucker_split_step(p, S->sb, S->chunk, S->fp64, C->stream, &lt);
+    lrc = launch_tucker_split_step(p, S->sb, S->chunk, S->fp64, C->stream, &lt, &S->ss);
   } else {
     lt(kKFusedStep, true, C->stream);
     lrc = launch_tucker_step(p, S->grid, S->fp64, C->stream);
@@ -371,6 +375,11 @@ int alloc_split(dvm_ctx *C) {
   S->chunk = chunk;
   S->split_mem = mem;
   S->split_bytes = bytes;
+  if (!S->ss.s2) {
+    DVM_CUDA_TRY(cudaStreamCreateWithFlags(&S->ss.s2, cudaStreamNonBlocking));
+    DVM_CUDA_TRY(cudaEventCreateWithFlags(&S->ss.fork, cudaEventDisableTiming));
+    DVM_CUDA_TRY(cudaEventCreateWithFlags(&S->ss.join, cudaEventDisableTiming));
+  }
   return DVM_OK;
 }
 
@@ -435,7 +444,7 @@ int autotune(dvm_ctx *C) {
     rc = alloc_split(C);
     if (rc == DVM_OK) {
       const float ms = timed([&] {
-        return launch_tucker_split_step(p, S->sb, S->chunk, S->fp64, C->stream);
+        return launch_tucker_split_step(p, S->sb, S->chunk, S->fp64, C->stream, nullptr, &S->ss);
       });
       if (ms > 0.f) S->tune_ms[0] = ms;
       S->split = variant == DVM_VARIANT_PHASED || (ms > 0.f && ms < best);
