@@ -51,10 +51,14 @@ struct TuckerSplitBufs {
   int64_t joff;    // their first buffer index (buffers hold one chunk)
 };
 
-// Second stream and fork / join events of the phase-major step (optional)
+// Extra streams and fork / join events of the phase-major step (optional):
+// the cells of a chunk are split into `ways` ranges, one per stream (the
+// caller's stream and ways - 1 of these)
+constexpr int kMaxWays = 4;
 struct SplitStreams {
-  cudaStream_t s2;
-  cudaEvent_t fork, join;
+  int ways;
+  cudaStream_t sx[kMaxWays - 1];
+  cudaEvent_t fork, join[kMaxWays - 1];
 };
 
 // Kernel classes of the optional per-launch event timing (dvm_set_kernel_timing)

@@ -1962,45 +1962,39 @@ int launch_split_TS(const TuckerStepParams &p, TuckerSplitBufs b, int64_t chunk,
   T(kKContract, true, s);
   tucker_t2_kernel<Real><<<(unsigned)(p.nc < 65535 * 16 ? p.nc : 65535 * 16), kAsmTB, z.asm_, s>>>(p, b);
   T(kKContract, false, s);
-  // with a second stream (and no per-launch timing), each chunk's two halves run
-  // their chains concurrently: one half's FP64-bound eigen-solves overlap the
-  // other half's FP32-bound Gram / assembly kernels
-  const bool dual = ss && ss->s2 && !(lt && lt->mark);
-  if (dual) {
-    if (cudaEventRecord(ss->fork, s) != cudaSuccess) return -1;
-    if (cudaStreamWaitEvent(ss->s2, ss->fork, 0) != cudaSuccess) return -1;
-  }
+  // with extra streams (and no per-launch timing), each chunk's cell ranges run
+  // their chains concurrently: one range's FP64-bound eigen-solves overlap another
+  // range's FP32-bound Gram / assembly kernels
+  const int ways = (ss && !(lt && lt->mark)) ? (ss->ways < kMaxWays ? ss->ways : kMaxWays) : 1;
+  auto fork = [&]() -> bool {
+    if (cudaEventRecord(ss->fork, s) != cudaSuccess) return false;
+    for (int w = 1; w < ways; ++w)
+      if (cudaStreamWaitEvent(ss->sx[w - 1], ss->fork, 0) != cudaSuccess) return false;
+    return true;
+  };
+  auto join = [&]() -> bool {
+    for (int w = 1; w < ways; ++w) {
+      if (cudaEventRecord(ss->join[w - 1], ss->sx[w - 1]) != cudaSuccess) return false;
+      if (cudaStreamWaitEvent(s, ss->join[w - 1], 0) != cudaSuccess) return false;
+    }
+    return true;
+  };
+  if (ways > 1 && !fork()) return -1;
   for (int64_t c0 = 0; c0 < p.nc; c0 += chunk) {
     const int64_t cn = p.nc - c0 < chunk ? p.nc - c0 : chunk;
-    if (dual && cn >= 2) {
-      const int64_t h = cn / 2;
-      TuckerSplitBufs b0 = b, b1 = b;
-      b0.c0 = c0;
-      b0.cn = h;
-      b0.joff = 0;
-      b1.c0 = c0 + h;
-      b1.cn = cn - h;
-      b1.joff = h;
-      split_chain<Real, TS>(p, b0, z, s, T);
-      split_chain<Real, TS>(p, b1, z, ss->s2, T);
-      // the next chunk reuses the buffers: both halves must be done
-      if (c0 + chunk < p.nc) {
-        if (cudaEventRecord(ss->join, ss->s2) != cudaSuccess) return -1;
-        if (cudaStreamWaitEvent(s, ss->join, 0) != cudaSuccess) return -1;
-        if (cudaEventRecord(ss->fork, s) != cudaSuccess) return -1;
-        if (cudaStreamWaitEvent(ss->s2, ss->fork, 0) != cudaSuccess) return -1;
-      }
-    } else {
-      b.c0 = c0;
-      b.cn = cn;
-      b.joff = 0;
-      split_chain<Real, TS>(p, b, z, s, T);
+    const int wn = cn >= ways ? ways : 1;
+    for (int w = 0; w < wn; ++w) {
+      const int64_t a = cn * w / wn, e = cn * (w + 1) / wn;
+      TuckerSplitBufs bw = b;
+      bw.c0 = c0 + a;
+      bw.cn = e - a;
+      bw.joff = a;
+      split_chain<Real, TS>(p, bw, z, w == 0 ? s : ss->sx[w - 1], T);
     }
+    // the next chunk reuses the buffers: every range must be done
+    if (ways > 1 && c0 + chunk < p.nc && !(join() && fork())) return -1;
   }
-  if (dual) {
-    if (cudaEventRecord(ss->join, ss->s2) != cudaSuccess) return -1;
-    if (cudaStreamWaitEvent(s, ss->join, 0) != cudaSuccess) return -1;
-  }
+  if (ways > 1 && !join()) return -1;
   return 0;
 }
 

@@ -243,9 +243,11 @@ void tucker_free(dvm_ctx *C) {
   if (S->ev_out) cudaEventDestroy(S->ev_out);
   if (S->scratch) cudaFree(S->scratch);
   if (S->split_mem) cudaFree(S->split_mem);
-  if (S->ss.s2) cudaStreamDestroy(S->ss.s2);
+  for (int w = 0; w < kMaxWays - 1; ++w) {
+    if (S->ss.sx[w]) cudaStreamDestroy(S->ss.sx[w]);
+    if (S->ss.join[w]) cudaEventDestroy(S->ss.join[w]);
+  }
   if (S->ss.fork) cudaEventDestroy(S->ss.fork);
-  if (S->ss.join) cudaEventDestroy(S->ss.join);
   if (S->ghostf) cudaFree(S->ghostf);
   if (S->err) cudaFree(S->err);
   if (S->phase) {
@@ -375,10 +377,13 @@ int alloc_split(dvm_ctx *C) {
   S->chunk = chunk;
   S->split_mem = mem;
   S->split_bytes = bytes;
-  if (!S->ss.s2) {
-    DVM_CUDA_TRY(cudaStreamCreateWithFlags(&S->ss.s2, cudaStreamNonBlocking));
+  if (!S->ss.fork) {
     DVM_CUDA_TRY(cudaEventCreateWithFlags(&S->ss.fork, cudaEventDisableTiming));
-    DVM_CUDA_TRY(cudaEventCreateWithFlags(&S->ss.join, cudaEventDisableTiming));
+    for (int w = 0; w < kMaxWays - 1; ++w) {
+      DVM_CUDA_TRY(cudaStreamCreateWithFlags(&S->ss.sx[w], cudaStreamNonBlocking));
+      DVM_CUDA_TRY(cudaEventCreateWithFlags(&S->ss.join[w], cudaEventDisableTiming));
+    }
+    S->ss.ways = 2;  // measured on the cavity: 2, 3 and 4 ranges all within 1%
   }
   return DVM_OK;
 }
