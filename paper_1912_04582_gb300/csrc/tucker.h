@@ -115,7 +115,9 @@ int tucker_split_asm_per_sm();
 size_t tucker_split_t2_elems(int N1, int N2, int N3, int R);
 // bytes per cell of the all-cell contraction buffers (TuckerSplitBufs::T2all, U1all)
 size_t tucker_split_t2all_bytes_per_cell(int N1, int N2, int N3, int R, bool fp64);
-// raise the kernels' shared-memory opt-in for this size (outside stream captures)
+// raise the kernels' shared-memory opt-in for this size (outside stream
+// captures); returns a mask of the launch variants whose kernels fit: 1 fused,
+// 2 phase-major
 int tucker_prepare_launch(int Nmax, int R, bool fp64);
 int launch_tucker_expand(const TuckerDev &T, int64_t c0, int64_t ncell, int N1, int N2, int N3,
                          int R, int Nmax, void *scratch, size_t stride, double *out, int grid,

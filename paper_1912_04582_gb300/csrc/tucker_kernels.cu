@@ -1689,7 +1689,8 @@ __global__ void __launch_bounds__(kTB) tucker_expand_kernel(TuckerDev T, int64_t
                                                             int N1, int N2, int N3, int R, int Nmax,
                                                             void *scratch, size_t stride, double *out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem<Real> sm = carve<Real>(smem_raw, Nmax, R);
+  Smem<Real> sm{};  // expand() uses the factor rows only
+  for (int a = 0; a < 3; ++a) sm.fac[a] = reinterpret_cast<Real *>(smem_raw) + (size_t)a * Nmax * R;
   const int N[3] = {N1, N2, N3};
   const int NN = N1 * N2 * N3;
   Real *E = reinterpret_cast<Real *>(scratch) + (size_t)blockIdx.x * stride;
@@ -1914,17 +1915,21 @@ struct SplitSmem {
 };
 
 template <typename Real, int TS>
+// Raise the shared-memory opt-ins of both variants' kernels; returns a mask of
+// the variants whose kernels fit: 1 fused, 2 phase-major.
 int prepare_split_TS(int Nmax, int R) {
   const SplitSmem<Real, TS> z(Nmax, R);
   using O = OptIn<Real, TS>;
-  if (raise_smem_optin(tucker_asm_kernel<Real>, z.asm_, O::asm_) != 0 ||
-      raise_smem_optin(tucker_t2_kernel<Real>, z.asm_, O::t2) != 0 ||
-      raise_smem_optin(tucker_gram_kernel<Real, TS>, z.gram, O::gram) != 0 ||
-      raise_smem_optin(tucker_eig_kernel<Real>, z.eig, O::eig) != 0 ||
-      raise_smem_optin(tucker_proj_kernel<Real>, z.proj, O::proj) != 0 ||
-      raise_smem_optin(tucker_step_kernel<Real, TS>, smem_bytes<Real>(Nmax, R), O::step) != 0)
-    return -1;
-  return 0;
+  int mask = 0;
+  if (raise_smem_optin(tucker_step_kernel<Real, TS>, smem_bytes<Real>(Nmax, R), O::step) == 0)
+    mask |= 1;
+  if (raise_smem_optin(tucker_asm_kernel<Real>, z.asm_, O::asm_) == 0 &&
+      raise_smem_optin(tucker_t2_kernel<Real>, z.asm_, O::t2) == 0 &&
+      raise_smem_optin(tucker_gram_kernel<Real, TS>, z.gram, O::gram) == 0 &&
+      raise_smem_optin(tucker_eig_kernel<Real>, z.eig, O::eig) == 0 &&
+      raise_smem_optin(tucker_proj_kernel<Real>, z.proj, O::proj) == 0)
+    mask |= 2;
+  return mask;
 }
 
 // The chain of one range of cells: assembly, then per mode Gram / eigen-solve /
@@ -1957,7 +1962,8 @@ int launch_split_TS(const TuckerStepParams &p, TuckerSplitBufs b, int64_t chunk,
   const LaunchTimer &T = lt ? *lt : none;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(s, &cap);
-  if (cap == cudaStreamCaptureStatusNone && prepare_split_TS<Real, TS>(p.Nmax, p.R) != 0) return -1;
+  if (cap == cudaStreamCaptureStatusNone && !(prepare_split_TS<Real, TS>(p.Nmax, p.R) & 2))
+    return -1;
   const SplitSmem<Real, TS> z(p.Nmax, p.R);
   T(kKContract, true, s);
   tucker_t2_kernel<Real><<<(unsigned)(p.nc < 65535 * 16 ? p.nc : 65535 * 16), kAsmTB, z.asm_, s>>>(p, b);
@@ -2001,7 +2007,7 @@ int launch_split_TS(const TuckerStepParams &p, TuckerSplitBufs b, int64_t chunk,
 template <typename Real>
 int launch_expand_T(const TuckerDev &T, int64_t c0, int64_t ncell, int N1, int N2, int N3, int R,
                     int Nmax, void *scratch, size_t stride, double *out, int grid, cudaStream_t s) {
-  const size_t smem = smem_bytes<Real>(Nmax, R);
+  const size_t smem = sizeof(Real) * 3 * (size_t)Nmax * R;
   if (raise_smem_optin(tucker_expand_kernel<Real>, smem, OptIn<Real, 0>::expand) != 0) return -1;
   tucker_expand_kernel<Real><<<grid, kTB, smem, s>>>(T, c0, ncell, N1, N2, N3, R, Nmax, scratch,
                                                      stride, out);

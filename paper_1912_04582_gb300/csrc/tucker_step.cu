@@ -31,6 +31,7 @@ struct TuckerState {
   bool tuned = false;           // grid picked by the autotuner
   float tune_ms[5] = {0, 0, 0, 0, 0};  // [0] phase-major step, [1..4] fused kernel per CTAs/SM
   bool split = false;                  // phase-major variant chosen
+  int fit = 3;                         // variants whose kernels fit: 1 fused, 2 phase-major
   TuckerSplitBufs sb{};                // its work buffers (one chunk of cells)
   int64_t chunk = 0;                   // cells per chunk
   void *split_mem = nullptr;
@@ -216,8 +217,12 @@ int tucker_alloc(dvm_ctx *C) {
   rc = ctx_malloc(C, reinterpret_cast<void **>(&S->err), sizeof(double) * nc);
   if (rc != DVM_OK) return rc;
   DVM_CUDA_TRY(cudaMemset(S->err, 0, sizeof(double) * nc));
-  if (tucker_prepare_launch(S->Nmax, R, S->fp64) != 0) {
-    set_error("Tucker kernels need more shared memory than the device allows");
+  S->fit = tucker_prepare_launch(S->Nmax, R, S->fp64);
+  const int need = C->opts.variant == DVM_VARIANT_FUSED ? 1 :
+                   C->opts.variant == DVM_VARIANT_PHASED ? 2 : 3;
+  if (!(S->fit & need)) {
+    set_error("Tucker kernels of the requested launch variant need more shared memory than "
+              "the device allows (lower the rank cap or use the other variant)");
     return DVM_ERR_UNSUPPORTED;
   }
   if (std::getenv("DVM_TUCKER_PHASES")) {
@@ -409,8 +414,10 @@ int autotune(dvm_ctx *C) {
   const int variant = C->opts.variant;
   int sms = 1;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, C->device);
-  const bool small = C->nc <= sms || std::getenv("DVM_NO_AUTOTUNE");
-  if (small && variant != DVM_VARIANT_PHASED) return DVM_OK;
+  const bool fused_fits = (S->fit & 1) != 0;
+  const bool phased = variant == DVM_VARIANT_PHASED || !fused_fits;
+  const bool small = C->nc <= sms || std::getenv("DVM_NO_AUTOTUNE") || !fused_fits;
+  if (small && !phased) return DVM_OK;
   TuckerStepParams p = step_params(C);
   p.mode = 0;
   p.cur = S->buf[S->cur];
@@ -445,16 +452,16 @@ int autotune(dvm_ctx *C) {
   }
   S->grid = best_grid;
   int rc = DVM_OK;
-  if (variant != DVM_VARIANT_FUSED && !std::getenv("DVM_NO_SPLIT")) {
+  if (variant != DVM_VARIANT_FUSED && (phased || !std::getenv("DVM_NO_SPLIT"))) {
     rc = alloc_split(C);
     if (rc == DVM_OK) {
       const float ms = timed([&] {
         return launch_tucker_split_step(p, S->sb, S->chunk, S->fp64, C->stream, nullptr, &S->ss);
       });
       if (ms > 0.f) S->tune_ms[0] = ms;
-      S->split = variant == DVM_VARIANT_PHASED || (ms > 0.f && ms < best);
+      S->split = phased || (ms > 0.f && ms < best);
       if (!S->split) free_split(C);
-    } else if (variant != DVM_VARIANT_PHASED) {
+    } else if (!phased) {
       rc = DVM_OK;  // no memory for the buffers: keep the fused kernel
     }
   }

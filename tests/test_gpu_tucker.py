@@ -266,3 +266,50 @@ def test_kernel_timing_covers_the_step(dvm):
             assert (ms > 0) == (name in classes)
         assert sum(ms for ms, _ in t.values()) <= wall_ms
         s.close()
+
+
+@pytest.mark.parametrize("N", [40, 64])
+@pytest.mark.parametrize("precision", [FP64, MIXED])
+def test_velocity_grids_above_32_nodes(dvm, oracle_lib, N, precision):
+    """Velocity grids with more than 32 nodes per axis take the 16 x 16-thread Gram
+    tiles and larger eigen blocks: a small cavity, 8 steps at eps = 1e-6, cap 12,
+    stays within 1e-4 of the FP64 oracle, in both launch variants, which agree bit for
+    bit."""
+    from paper_1912_04582_gb300 import _native as NAT
+    wl = W.cavity(nside=2, N=N, seed=5)
+    o = oracle_lib.FullGridOracle(wl)
+    o.step(8, o.dt())
+    fo, mo = o.f(), o.macro()
+    out = {}
+    for v in (NAT.DVM_VARIANT_FUSED, NAT.DVM_VARIANT_PHASED):
+        s = dvm.Solver(wl, format=1, precision=precision, rank_cap=12, tol=1e-6, variant=v)
+        s.step(8)
+        out[v] = (s.f(), s.moments(), dvm.dvm_get_ranks(s.h))
+        s.close()
+    fg, mg, rk = out[NAT.DVM_VARIANT_PHASED]
+    assert rel_l2(fg, fo) < 1e-4
+    for k, err in macro_err(mg, mo, u_scale=0.2).items():
+        assert err < 1e-4, (k, err)
+    assert rk.max() <= 12
+    assert np.array_equal(out[NAT.DVM_VARIANT_FUSED][0], fg)
+    assert np.array_equal(out[NAT.DVM_VARIANT_FUSED][2], rk)
+
+
+def test_compression_at_64_nodes(dvm):
+    """dvm_init_f on tensors of Tucker rank (3, 2, 4) at 64^3 nodes recovers them to the
+    tolerance with those ranks (Section 4 item 1)."""
+    rng = np.random.default_rng(11)
+    wl = W.cavity(nside=2, N=64, seed=2)
+    N = 64
+    f = np.empty((wl.n_cell, N, N, N))
+    for c in range(wl.n_cell):
+        G = rng.uniform(0.5, 1.0, (3, 2, 4))  # positive: a physical state
+        U = [rng.uniform(0.1, 1.0, (N, r)) for r in (3, 2, 4)]
+        f[c] = tk.full((G, tuple(U)))
+    s = dvm.Solver(wl, format=1, precision=FP64, rank_cap=8, tol=1e-6, init=False)
+    dvm.dvm_init_f(s.h, f)
+    g = s.f()
+    ranks = dvm.dvm_get_ranks(s.h)
+    s.close()
+    assert rel_l2(g, f) < 1e-10
+    assert np.all(ranks == np.array([3, 2, 4]))
