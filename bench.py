@@ -371,6 +371,49 @@ def run_serving(P, n_req=12, seed=7, mean_gap_s=0.25, budget_gb=64, slots=8, res
                    f"{mean_gap_s} s, seed {seed}), {slots} slots"}
 
 
+def run_configs(P, NAT, stream):
+    """The larger configurations on the same code path, a few steps each: C3 (cavity,
+    32^3 cells x 48^3, mixed Tucker cap 12, eps 1e-5, beside the full grid FP64) and C4
+    (Mach-3 flow past a cube, 101,888 jittered cells x 64^3, mixed Tucker cap 20,
+    eps 1e-5; its full-grid FP64 state would need two copies of 213.7 GB)."""
+    import torch
+    import workloads as W
+    out = {}
+
+    def timed(wl, fmt, prec, cap, tol, advance, steps):
+        s = P.Solver(wl, format=fmt, precision=prec, rank_cap=cap, tol=tol,
+                     stream=stream.cuda_stream)
+        if advance:
+            s.step(advance, residual=False)
+        ms = _time_steps(s, steps, 2, stream) / steps
+        fb, tb = P.dvm_memory(s.h)
+        d = {"ms_per_step": ms, "updates_per_s": wl.n_cell * wl.nodes_per_cell / (ms / 1e3),
+             "f_bytes": fb, "device_bytes": tb, "steps_timed": steps,
+             "untimed_steps_before": advance + 2}
+        if fmt == NAT.DVM_FORMAT_TUCKER:
+            r = P.dvm_get_ranks(s.h)
+            g, _ = P.dvm_get_launch_config(s.h)
+            d.update({"eps": tol, "rank_cap": cap, "rank_mean": float(r.mean()),
+                      "rank_max": int(r.max()), "variant": "phase-major" if g < 0 else "fused"})
+        s.close()
+        torch.cuda.synchronize()
+        return d
+
+    c3 = W.cavity(nside=32, N=48)
+    out["C3_cavity_32^3x48^3"] = {
+        "tucker_mixed": timed(c3, NAT.DVM_FORMAT_TUCKER, NAT.DVM_PREC_MIXED, 12, 1e-5, 20, 5),
+        "full_fp64": timed(c3, NAT.DVM_FORMAT_FULL, NAT.DVM_PREC_FP64, 12, 1e-5, 0, 3)}
+    del c3
+    c4 = W.obstacle()
+    total = torch.cuda.get_device_properties(torch.cuda.current_device()).total_memory
+    need = P.dvm_estimate_memory(c4, format=NAT.DVM_FORMAT_FULL)
+    out[f"C4_obstacle_{c4.n_cell}x64^3"] = {
+        "tucker_mixed": timed(c4, NAT.DVM_FORMAT_TUCKER, NAT.DVM_PREC_MIXED, 20, 1e-5, 10, 3),
+        "full_fp64": {"device_bytes_needed": need, "device_bytes_total": int(total),
+                      "fits": bool(need <= total)}}
+    return out
+
+
 def run_gpu(args, rank, world):
     import torch
     import paper_1912_04582_gb300 as P
@@ -517,6 +560,7 @@ def run_gpu(args, rank, world):
         if not args.no_extras:
             line["tucker_accuracy"] = tucker_accuracy(P, cap, tol, NAT.DVM_PREC_MIXED)
             line["serving"] = run_serving(P)
+            line["configs"] = run_configs(P, NAT, stream)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(wl)
         print(json.dumps(line), flush=True)
