@@ -273,6 +273,23 @@ def _roofline_tucker(P, s, wl, steps):
             "timing": f"CUDA events around each launch over {steps} further steps"}
 
 
+def max_over_ranks(ms, dist=None, device="cpu"):
+    """The timed region's duration as the job sees it: the maximum over the ranks of an
+    initialised process group (the local value without one)."""
+    if dist is None:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, updates_per_step, steps, ms):
+    """Whole-job throughput: every rank advances its own replica by `steps` steps of
+    `updates_per_step` updates; the job takes the slowest rank's time."""
+    return world * updates_per_step * steps / (ms / 1e3)
+
+
 def _time_steps(solver, steps, warmup, stream):
     import torch
     for _ in range(warmup):
@@ -454,12 +471,8 @@ def run_gpu(args, rank, world):
         s.step(args.steps, residual=False)
         ev1.record(stream)
         torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * upd * args.steps / (ms / 1e3)
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
+    value = job_value(world, upd, args.steps, ms)
     step_ms = ms / args.steps
 
     peaks, src = _peaks()
