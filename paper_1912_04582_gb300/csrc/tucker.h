@@ -21,6 +21,7 @@ struct TuckerStepParams {
   const double *sums;    // [nc][kSums] moment sums of cur
   const SlotDev *slot;   // [nc][6]
   const double *ghostf;  // [nghost][3][Nmax] rank-1 ghost Maxwellian factors
+  const float *ghostf32; // the same in FP32
   const double *xi[3];
   const double *finit;   // mode 1: [nc][N^3] tensors to compress
   double *err;           // [nc] relative truncation error of the last rounding (may be null)

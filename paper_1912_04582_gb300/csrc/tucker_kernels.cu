@@ -1201,6 +1201,16 @@ __device__ __noinline__ void assemble(const TuckerStepParams &P, int64_t c, cons
   }
   __syncthreads();
   pc.mark(13);
+  // face coefficients in the working precision: e0, e1, e2, c, wall-density scale
+  __shared__ Real s_fr[6 * 5];
+  if (tid < 30) {
+    const int l = tid / 5, q = tid - l * 5;
+    const SlotDev &sl = s_slot[l];
+    s_fr[tid] = (Real)(q < 3 ? sl.e[q] : (q == 3 ? sl.c : s_scale[l]));
+  }
+  __syncthreads();
+  const Real *ghostR = sizeof(Real) == 8 ? reinterpret_cast<const Real *>(P.ghostf)
+                                         : reinterpret_cast<const Real *>(P.ghostf32);
   const Real w0 = (Real)(1.0 - sm.par[8]);
   const Real *x0 = tabp(sm, Nm, 0), *x1 = tabp(sm, Nm, 1), *x2 = tabp(sm, Nm, 2);
   const Real *F0 = tabp(sm, Nm, 3), *F1 = tabp(sm, Nm, 4), *F2 = tabp(sm, Nm, 5);
@@ -1225,11 +1235,12 @@ __device__ __noinline__ void assemble(const TuckerStepParams &P, int64_t c, cons
     for (int l = 0; l < 6; ++l) {
       const SlotDev &sl = s_slot[l];
       if (sl.kind != kFreeStream && sl.kind != kWall) continue;
-      const double *gf = P.ghostf + (int64_t)sl.src * 3 * Nm;
-      const Real g23 = (Real)(gf[Nm + i2] * gf[2 * Nm + i3]);
+      const Real *gf = ghostR + (int64_t)sl.src * 3 * Nm;
+      const Real g23 = gf[Nm + i2] * gf[2 * Nm + i3];
       const Real *tab = tabp(sm, Nm, 15 + l);
-      const Real e0 = (Real)sl.e[0], cl = (Real)sl.c, sc = (Real)s_scale[l];
-      const Real xn23 = (Real)sl.e[1] * x1[i2] + (Real)sl.e[2] * x2[i3];
+      const Real *fr = s_fr + 5 * l;
+      const Real e0 = fr[0], cl = fr[3], sc = fr[4];
+      const Real xn23 = fr[1] * x1[i2] + fr[2] * x2[i3];
       const Real m23 = sl.axis == 1 ? tab[i2] : (sl.axis == 2 ? tab[i3] : Real(0));
 #pragma unroll
       for (int j = 0; j < kRows; ++j) {
@@ -1238,7 +1249,7 @@ __device__ __noinline__ void assemble(const TuckerStepParams &P, int64_t c, cons
         if (sl.axis == 0) m = tab[i1];
         else if (sl.axis > 0) m = m23;
         else m = -cl * fmin(e0 * x0[i1] + xn23, Real(0)) * sc;
-        acc[j] = fma(m, (Real)gf[min(i1, N1 - 1)] * g23, acc[j]);
+        acc[j] = fma(m, gf[min(i1, N1 - 1)] * g23, acc[j]);
       }
     }
     // Tucker terms: f = U1 T2 in registers, then the weight
@@ -1275,9 +1286,10 @@ __device__ __noinline__ void assemble(const TuckerStepParams &P, int64_t c, cons
           const SlotDev &sl = s_slot[l];
           const bool nonaxis = sl.axis < 0, zg = sl.kind == kZeroGrad;
           if (!nonaxis && !zg) continue;
-          const Real e0 = (Real)sl.e[0], cl = (Real)sl.c, sc = (Real)s_scale[l];
+          const Real *fr = s_fr + 5 * l;
+          const Real e0 = fr[0], cl = fr[3], sc = fr[4];
           const Real *tab = tabp(sm, Nm, 15 + l);
-          const Real xn23 = (Real)sl.e[1] * x1[i2] + (Real)sl.e[2] * x2[i3];
+          const Real xn23 = fr[1] * x1[i2] + fr[2] * x2[i3];
           const Real m23 = sl.axis == 1 ? tab[i2] : (sl.axis == 2 ? tab[i3] : Real(0));
 #pragma unroll
           for (int j = 0; j < kRows; ++j) {
@@ -1305,8 +1317,9 @@ __device__ __noinline__ void assemble(const TuckerStepParams &P, int64_t c, cons
 #pragma unroll
           for (int j = 0; j < kRows; ++j) acc[j] = fma(m, sv[j], acc[j]);
         } else {
-          const Real e0 = (Real)sl.e[0], cl = (Real)sl.c, sc = (Real)s_scale[tm.face];
-          const Real xn23 = (Real)sl.e[1] * x1[i2] + (Real)sl.e[2] * x2[i3];
+          const Real *fr = s_fr + 5 * tm.face;
+          const Real e0 = fr[0], cl = fr[3], sc = fr[4];
+          const Real xn23 = fr[1] * x1[i2] + fr[2] * x2[i3];
           const Real *xr = x0 + i10;
 #pragma unroll
           for (int j = 0; j < kRows; ++j) {
@@ -1364,24 +1377,34 @@ __device__ void cell_prologue(const TuckerStepParams &P, int64_t c, const int N[
           for (int t = a; t < 15; t += 3) tabp(sm, Nm, t)[i] = Real(0);
           continue;
         }
-        const double x = P.xi[a][i];
-        const double v = x - sm.par[1 + a];
-        tabp(sm, Nm, 0 + a)[i] = (Real)x;
         if constexpr (sizeof(Real) == 8) {
+          const double x = P.xi[a][i];
+          const double v = x - sm.par[1 + a];
+          tabp(sm, Nm, 0 + a)[i] = x;
           tabp(sm, Nm, 3 + a)[i] = (a == 0 ? dtnu : 1.0) * amp * exp(-v * v / T);
-        } else {  // the table is FP32: evaluate it in FP32
-          const float vf = (float)v;
-          tabp(sm, Nm, 3 + a)[i] =
-              (float)(a == 0 ? dtnu * amp : amp) * expf(-vf * vf / (float)T);
+          tabp(sm, Nm, 6 + a)[i] = A * sm.par[5 + a] * v;
+          tabp(sm, Nm, 9 + a)[i] = v * v / T;
+          double g = 0.0;
+          for (int l = 0; l < 6; ++l) {
+            const SlotDev &sl = s_slot[l];
+            if (sl.axis == a) g -= sl.c * fmax(sl.sgn * x, 0.0);
+          }
+          tabp(sm, Nm, 12 + a)[i] = g;
+        } else {  // the tables are FP32: evaluate them in FP32
+          const float x = (float)P.xi[a][i];
+          const float v = x - (float)sm.par[1 + a];
+          const float iT = 1.0f / (float)T;
+          tabp(sm, Nm, 0 + a)[i] = x;
+          tabp(sm, Nm, 3 + a)[i] = (float)(a == 0 ? dtnu * amp : amp) * expf(-v * v * iT);
+          tabp(sm, Nm, 6 + a)[i] = (float)(A * sm.par[5 + a]) * v;
+          tabp(sm, Nm, 9 + a)[i] = v * v * iT;
+          float g = 0.0f;
+          for (int l = 0; l < 6; ++l) {
+            const SlotDev &sl = s_slot[l];
+            if (sl.axis == a) g -= (float)sl.c * fmaxf((float)sl.sgn * x, 0.0f);
+          }
+          tabp(sm, Nm, 12 + a)[i] = g;
         }
-        tabp(sm, Nm, 6 + a)[i] = (Real)(A * sm.par[5 + a] * v);
-        tabp(sm, Nm, 9 + a)[i] = (Real)(v * v / T);
-        double g = 0.0;
-        for (int l = 0; l < 6; ++l) {
-          const SlotDev &sl = s_slot[l];
-          if (sl.axis == a) g -= sl.c * fmax(sl.sgn * x, 0.0);
-        }
-        tabp(sm, Nm, 12 + a)[i] = (Real)g;
       }
     for (int l = 0; l < 6; ++l) {
       const SlotDev &sl = s_slot[l];

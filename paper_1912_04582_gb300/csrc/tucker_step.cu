@@ -25,6 +25,7 @@ struct TuckerState {
   size_t stride = 0;   // scratch elements per CTA
   int grid = 0;
   double *ghostf = nullptr;  // [nghost][3][Nmax]
+  float *ghostf32 = nullptr; // the same in FP32 (mixed-precision assembly)
   double *err = nullptr;     // [nc]
   long long *phase = nullptr;  // [16] per-phase cycles (DVM_TUCKER_PHASES set)
   int max_grid = 0;             // CTAs the scratch is sized for
@@ -58,6 +59,7 @@ TuckerStepParams step_params(dvm_ctx *C) {
   TuckerStepParams p{};
   p.slot = C->d_slot;
   p.ghostf = S->ghostf;
+  p.ghostf32 = S->ghostf32;
   for (int a = 0; a < 3; ++a) p.xi[a] = C->d_xi[a];
   p.err = S->err;
   p.phase = S->phase;
@@ -141,6 +143,15 @@ int build_ghost_factors(dvm_ctx *C) {
   int rc = ctx_malloc(C, reinterpret_cast<void **>(&S->ghostf), sizeof(double) * h.size());
   if (rc != DVM_OK) return rc;
   DVM_CUDA_TRY(cudaMemcpyAsync(S->ghostf, h.data(), sizeof(double) * h.size(),
+                               cudaMemcpyHostToDevice, C->stream));
+  if (S->ghostf32) {
+    cudaFree(S->ghostf32);
+    S->ghostf32 = nullptr;
+  }
+  std::vector<float> h32(h.begin(), h.end());
+  rc = ctx_malloc(C, reinterpret_cast<void **>(&S->ghostf32), sizeof(float) * h32.size());
+  if (rc != DVM_OK) return rc;
+  DVM_CUDA_TRY(cudaMemcpyAsync(S->ghostf32, h32.data(), sizeof(float) * h32.size(),
                                cudaMemcpyHostToDevice, C->stream));
   return sync_check(C);
 }
@@ -254,6 +265,7 @@ void tucker_free(dvm_ctx *C) {
   }
   if (S->ss.fork) cudaEventDestroy(S->ss.fork);
   if (S->ghostf) cudaFree(S->ghostf);
+  if (S->ghostf32) cudaFree(S->ghostf32);
   if (S->err) cudaFree(S->err);
   if (S->phase) {
     long long h[16] = {0};
