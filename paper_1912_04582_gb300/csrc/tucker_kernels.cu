@@ -294,10 +294,11 @@ __device__ __forceinline__ double gram_load(const double *C, int idx) {
 // return it)
 template <typename Real>
 __device__ double gram_trace(Smem<Real> &sm, int n) {
-  if (threadIdx.x == 0) {
-    double tr = 0.0;
-    for (int i = 0; i < n; ++i) tr += gram_load<Real>(sm.Cg, i * n + i);
-    sm.par[27] = tr;
+  if (threadIdx.x < 32) {  // warp 0: a lane per diagonal entry, fixed shuffle tree
+    double t = 0.0;
+    for (int i = threadIdx.x; i < n; i += 32) t += gram_load<Real>(sm.Cg, i * n + i);
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) sm.par[27] = t;
   }
   __syncthreads();
   const double tr = sm.par[27];
@@ -650,16 +651,11 @@ __device__ __noinline__ int chol_warp(A *Gs, A *dinv, int k, A shift, A rel) {
   const int lane = threadIdx.x & 31;
   const A tiny = (A)(sizeof(A) == 8 ? 1e-300 : 1e-30);
   A g[KM];
-  A diag0 = 0;
+  const A diag0 = lane < k ? Gs[lane * k + lane] : A(0);
+  if (lane < k) Gs[lane * k + lane] = diag0 + shift;
+  __syncwarp();
 #pragma unroll
-  for (int c = 0; c < KM; ++c) {
-    A v = (lane < k && c < k) ? Gs[lane * k + c] : A(0);
-    if (c == lane) {
-      diag0 = v;
-      v += shift;
-    }
-    g[c] = v;
-  }
+  for (int c = 0; c < KM; ++c) g[c] = (lane < k && c < k) ? Gs[lane * k + c] : A(0);
   int ndep = 0;
 #pragma unroll
   for (int j = 0; j < KM; ++j) {
@@ -884,16 +880,16 @@ __device__ __noinline__ int leading_eigs(Smem<Real> &sm, int n, int k, const WT 
   return k;
 }
 
-// Truncation rank from the energy the first r basis vectors capture: the
-// smallest r with trace(C) - sum_{j<r} d_j <= thr (thr > 0), else all k; then
+// Truncation rank from the energy the first r basis vectors capture (tr =
+// trace(C)): the smallest r with tr - sum_{j<r} d_j <= thr (thr > 0), else all k; then
 // r <- min(r, cap, non-zero columns), r >= 1.  Returns r; *met tells whether
 // the threshold was reached within the k columns, sm.par[31] holds the energy
 // the r columns leave out.
 template <typename Real>
-__device__ int choose_rank(Smem<Real> &sm, int n, int k, double thr, int cap, bool *met) {
+__device__ int choose_rank(Smem<Real> &sm, int n, int k, double thr, int cap, bool *met,
+                           double tr) {
+  (void)n;
   if (threadIdx.x == 0) {
-    double tr = 0.0;
-    for (int i = 0; i < n; ++i) tr += gram_load<Real>(sm.Cg, i * n + i);
     double kept = 0.0;
     int r = k, found = 0;
     for (int j = 0; j < k && thr > 0.0; ++j) {
@@ -965,8 +961,9 @@ __device__ void round_hosvd(Real *X, Real *T1, Real *T2, const int N[3], int R, 
   for (int m = 0; m < 3; ++m) {
     const int n = D[m];
     gram<Real, TS>(src, D, m, sm);
+    const double tr = gram_trace<Real>(sm, n);
     if (m == 0) {
-      e = gram_trace<Real>(sm, n);
+      e = tr;
       thr = eps * eps / 3.0 * e;
     }
     pc.mark(5);
@@ -982,7 +979,7 @@ __device__ void round_hosvd(Real *X, Real *T1, Real *T2, const int N[3], int R, 
     k = leading_eigs<Real, double>(sm, n, k, wU, R, wr, pc);
     pc.mark(6);
     bool met;
-    r[m] = choose_rank<Real>(sm, n, k, thr, R, &met);
+    r[m] = choose_rank<Real>(sm, n, k, thr, R, &met, tr);
     if (!met && k < kmax) {
       // the k columns found start the full solve (kept in sm.Vr, which the
       // iteration does not touch)
@@ -990,7 +987,7 @@ __device__ void round_hosvd(Real *X, Real *T1, Real *T2, const int N[3], int R, 
       __syncthreads();
       k = leading_eigs<Real, Real>(sm, n, kmax, sm.Vr, k, k, pc);
       pc.mark(6);
-      r[m] = choose_rank<Real>(sm, n, k, thr, R, &met);
+      r[m] = choose_rank<Real>(sm, n, k, thr, R, &met, tr);
     }
     discarded += sm.par[31];
     double *U = out.fac[m] + cell * (int64_t)N[m] * R;
@@ -1629,10 +1626,8 @@ __global__ void __launch_bounds__(32, 13) tucker_eig_kernel(TuckerStepParams P, 
   const int64_t c = B.c0 + blockIdx.x, j = B.joff + blockIdx.x;  // j: buffer index
   const int n = N[m];
   sm.Cg = B.C + j * (int64_t)Nm * Nm;  // read through L1
-  if (m == 0) {  // ||X||^2 = trace of the first Gram matrix
-    const double tr = gram_trace<Real>(sm, n);
-    if (threadIdx.x == 0) B.e[j] = tr;
-  }
+  const double tr = gram_trace<Real>(sm, n);
+  if (m == 0 && threadIdx.x == 0) B.e[j] = tr;  // ||X||^2 = trace of the first Gram matrix
   __syncthreads();
   const double thr = P.tol * P.tol / 3.0 * B.e[j];
   const double *wU = P.cur.fac[m] + c * (int64_t)n * R;
@@ -1643,12 +1638,12 @@ __global__ void __launch_bounds__(32, 13) tucker_eig_kernel(TuckerStepParams P, 
   int k = (wr > 0 && thr > 0.0 && wr + kExtra < kmax) ? wr + kExtra : kmax;
   k = leading_eigs<Real, double>(sm, n, k, wU, R, wr, pc);
   bool met;
-  int r = choose_rank<Real>(sm, n, k, thr, R, &met);
+  int r = choose_rank<Real>(sm, n, k, thr, R, &met, tr);
   if (!met && k < kmax) {
     for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) sm.Vr[idx] = (Real)sm.W[idx];
     __syncthreads();
     k = leading_eigs<Real, Real>(sm, n, kmax, sm.Vr, k, k, pc);
-    r = choose_rank<Real>(sm, n, k, thr, R, &met);
+    r = choose_rank<Real>(sm, n, k, thr, R, &met, tr);
   }
   double *U = P.nxt.fac[m] + c * (int64_t)n * R;
   for (int idx = threadIdx.x; idx < n * r; idx += blockDim.x) {
