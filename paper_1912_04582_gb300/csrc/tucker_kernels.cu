@@ -505,11 +505,13 @@ __device__ __noinline__ void gram_w32(const Real *T, const int D[3], int m, Smem
       }
     }
     if constexpr (f32) {
-#pragma unroll
-      for (int i = 0; i < 20; ++i) {  // renormalise (fast two-sum)
-        const float sum = __fadd_rn(hi[i], lo[i]);
-        lo[i] = __fsub_rn(lo[i], __fsub_rn(sum, hi[i]));
-        hi[i] = sum;
+      if ((t & 3) == 3 || !more) {  // renormalise (fast two-sum) every 4 tiles: the low
+#pragma unroll                      // word takes at most 16 additions in between
+        for (int i = 0; i < 20; ++i) {
+          const float sum = __fadd_rn(hi[i], lo[i]);
+          lo[i] = __fsub_rn(lo[i], __fsub_rn(sum, hi[i]));
+          hi[i] = sum;
+        }
       }
     }
     if (sm.tile2) {
