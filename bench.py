@@ -492,8 +492,14 @@ def run_gpu(args, rank, world):
     else:
         roof = _roofline_tucker(P, s, wl, args.steps)
         kt = roof["kernel_times"]
-        # the moments class is two kernels (macroparameters, moments of the new state)
-        launches = sum(v["launches"] for v in kt.values()) + kt.get("moments", {}).get("launches", 0)
+        # the timing pass runs one stream (one event pair per kernel launch); the
+        # headline region runs the phase-major chain per cell range on two streams:
+        # the contraction and macroparameter kernels once, the rest once per range
+        per_step = sum(v["launches"] for v in kt.values()) / args.steps
+        if "tucker_contract" in kt:
+            once = 2
+            per_step = once + 2 * (per_step - once)
+        launches = int(round(per_step * args.steps))
     res = s.step(1)
 
     line = None

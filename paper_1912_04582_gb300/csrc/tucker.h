@@ -96,7 +96,8 @@ struct TuckerMomentParams {
   double *respart;       // [nc][2] or null
   const double *vol;
   int *flag;
-  int64_t nc;
+  int64_t nc;            // cells [c0, nc) are processed
+  int64_t c0;
   int N1, N2, N3, R;
   double w;
 };
@@ -106,9 +107,12 @@ size_t tucker_smem_bytes(int Nmax, int R, bool fp64);
 int tucker_step_blocks_per_sm(int Nmax, int R, bool fp64);
 int launch_tucker_step(const TuckerStepParams &p, int grid, bool fp64, cudaStream_t s);
 // phase-major step over chunks of `chunk` cells (buffers sized for one chunk)
+// mp (optional): moments of the new state, launched per cell range at the end of
+// its chain (cells [c0, nc) of mp are ignored; each range sets its own)
 int launch_tucker_split_step(const TuckerStepParams &p, TuckerSplitBufs b, int64_t chunk,
                              bool fp64, cudaStream_t s, const LaunchTimer *lt = nullptr,
-                             const SplitStreams *ss = nullptr);
+                             const SplitStreams *ss = nullptr,
+                             const TuckerMomentParams *mp = nullptr);
 // bytes of TuckerSplitBufs per cell (working precision fp64 or float)
 size_t tucker_split_bytes_per_cell(int N1, int N2, int N3, int R, int Nmax, bool fp64);
 // assembly CTAs per SM of the phase-major variant and their staging elements

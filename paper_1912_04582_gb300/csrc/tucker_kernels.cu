@@ -1731,7 +1731,7 @@ __global__ void __launch_bounds__(128) tucker_moments_kernel(TuckerMomentParams 
   extern __shared__ double msm[];  // [3][5][R] projections, [6][R] wall projections
   __shared__ double s_out[32];
   __shared__ SlotDev s_slot[6];
-  const int64_t c = blockIdx.x;
+  const int64_t c = P.c0 + blockIdx.x;
   const int tid = threadIdx.x;
   const int R = P.R;
   const int N[3] = {P.N1, P.N2, P.N3};
@@ -1956,7 +1956,7 @@ int prepare_split_TS(int Nmax, int R) {
 // projection.
 template <typename Real, int TS>
 void split_chain(const TuckerStepParams &p, const TuckerSplitBufs &b, const SplitSmem<Real, TS> &z,
-                 cudaStream_t s, const LaunchTimer &T) {
+                 cudaStream_t s, const LaunchTimer &T, const TuckerMomentParams *mp) {
   const int ga = (int)(b.cn < b.asm_grid ? b.cn : b.asm_grid);
   T(kKAsm, true, s);
   tucker_asm_kernel<Real><<<ga, kAsmTB, z.asm_, s>>>(p, b);
@@ -1973,11 +1973,19 @@ void split_chain(const TuckerStepParams &p, const TuckerSplitBufs &b, const Spli
     tucker_proj_kernel<Real><<<(unsigned)b.cn, kTB, z.proj, s>>>(p, b, m);
     T(kKProj, false, s);
   }
+  if (mp) {  // moments of the new state of these cells
+    TuckerMomentParams q = *mp;
+    q.c0 = b.c0;
+    q.nc = b.c0 + b.cn;
+    T(kKMoments, true, s);
+    launch_tucker_moments(q, s);
+    T(kKMoments, false, s);
+  }
 }
 
 template <typename Real, int TS>
 int launch_split_TS(const TuckerStepParams &p, TuckerSplitBufs b, int64_t chunk, cudaStream_t s,
-                    const LaunchTimer *lt, const SplitStreams *ss) {
+                    const LaunchTimer *lt, const SplitStreams *ss, const TuckerMomentParams *mp) {
   const LaunchTimer none{nullptr, nullptr};
   const LaunchTimer &T = lt ? *lt : none;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -2015,7 +2023,7 @@ int launch_split_TS(const TuckerStepParams &p, TuckerSplitBufs b, int64_t chunk,
       bw.c0 = c0 + a;
       bw.cn = e - a;
       bw.joff = a;
-      split_chain<Real, TS>(p, bw, z, w == 0 ? s : ss->sx[w - 1], T);
+      split_chain<Real, TS>(p, bw, z, w == 0 ? s : ss->sx[w - 1], T, mp);
     }
     // the next chunk reuses the buffers: every range must be done
     if (ways > 1 && c0 + chunk < p.nc && !(join() && fork())) return -1;
@@ -2075,12 +2083,12 @@ int launch_tucker_step(const TuckerStepParams &p, int grid, bool fp64, cudaStrea
 
 int launch_tucker_split_step(const TuckerStepParams &p, TuckerSplitBufs b, int64_t chunk,
                              bool fp64, cudaStream_t s, const LaunchTimer *lt,
-                             const SplitStreams *ss) {
+                             const SplitStreams *ss, const TuckerMomentParams *mp) {
   if (fp64)
-    return p.Nmax <= 32 ? launch_split_TS<double, 2>(p, b, chunk, s, lt, ss)
-                        : launch_split_TS<double, 4>(p, b, chunk, s, lt, ss);
-  return p.Nmax <= 32 ? launch_split_TS<float, 2>(p, b, chunk, s, lt, ss)
-                      : launch_split_TS<float, 4>(p, b, chunk, s, lt, ss);
+    return p.Nmax <= 32 ? launch_split_TS<double, 2>(p, b, chunk, s, lt, ss, mp)
+                        : launch_split_TS<double, 4>(p, b, chunk, s, lt, ss, mp);
+  return p.Nmax <= 32 ? launch_split_TS<float, 2>(p, b, chunk, s, lt, ss, mp)
+                      : launch_split_TS<float, 4>(p, b, chunk, s, lt, ss, mp);
 }
 
 int tucker_split_asm_per_sm() { return 6; }
@@ -2124,7 +2132,7 @@ void launch_tucker_maxwellians(TuckerDev T, const double *n, const double *u, co
 
 void launch_tucker_moments(const TuckerMomentParams &p, cudaStream_t s) {
   const size_t smem = sizeof(double) * 18 * (size_t)p.R;
-  tucker_moments_kernel<<<(unsigned)p.nc, 128, smem, s>>>(p);
+  tucker_moments_kernel<<<(unsigned)(p.nc - p.c0), 128, smem, s>>>(p);
 }
 
 }  // namespace dvm

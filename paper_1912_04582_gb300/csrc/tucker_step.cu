@@ -318,28 +318,37 @@ int enqueue_one_step(dvm_ctx *C, TuckerStepParams &p) {
   p.nxt = S->buf[1 - S->cur];
   p.sums = C->d_sums[S->scur];
   const LaunchTimer lt = C->timer();
+  // the moments of the new state are taken about the current state's velocity
+  // (from the current sums, untouched by the step)
+  TuckerMomentParams m = moment_params(C, p.nxt, C->d_sums[1 - S->scur]);
+  m.uref = C->d_macro + 1;
+  m.uref_stride = 8;
+  m.sums_prev = C->d_sums[S->scur];
+  m.respart = C->d_respart;
   int lrc;
   if (S->split) {
-    lrc = launch_tucker_split_step(p, S->sb, S->chunk, S->fp64, C->stream, &lt, &S->ss);
+    lt(kKMoments, true, C->stream);
+    launch_macro_from_sums(C->d_sums[S->scur], C->d_macro, C->nc, C->w, C->stream);
+    lt(kKMoments, false, C->stream);
+    lrc = launch_tucker_split_step(p, S->sb, S->chunk, S->fp64, C->stream, &lt, &S->ss, &m);
   } else {
     lt(kKFusedStep, true, C->stream);
     lrc = launch_tucker_step(p, S->grid, S->fp64, C->stream);
     lt(kKFusedStep, false, C->stream);
+    if (lrc == 0) {
+      lt(kKMoments, true, C->stream);
+      launch_macro_from_sums(C->d_sums[S->scur], C->d_macro, C->nc, C->w, C->stream);
+      lt(kKMoments, false, C->stream);
+      lt(kKMoments, true, C->stream);
+      launch_tucker_moments(m, C->stream);
+      lt(kKMoments, false, C->stream);
+    }
   }
   if (lrc != 0) {
     set_error("Tucker kernel needs more shared memory than the device allows");
     return DVM_ERR_UNSUPPORTED;
   }
   S->cur = 1 - S->cur;
-  lt(kKMoments, true, C->stream);
-  launch_macro_from_sums(C->d_sums[S->scur], C->d_macro, C->nc, C->w, C->stream);
-  TuckerMomentParams m = moment_params(C, S->buf[S->cur], C->d_sums[1 - S->scur]);
-  m.uref = C->d_macro + 1;
-  m.uref_stride = 8;
-  m.sums_prev = C->d_sums[S->scur];
-  m.respart = C->d_respart;
-  launch_tucker_moments(m, C->stream);
-  lt(kKMoments, false, C->stream);
   S->scur = 1 - S->scur;
   return DVM_OK;
 }
