@@ -93,6 +93,8 @@ struct Smem {
   double *C;      // [Nmax*Nmax] Gram matrix (FP64)
   const double *Cg;  // the Gram matrix the eigen-solver reads (sm.C or a global copy)
   Real *tile2;    // second Gram tile buffer (prefetch), or null
+  int *cidx;      // first-mode Gram: indices of the columns kept (cidx_cap entries)
+  int cidx_cap;
   double *Q;      // [Nmax*K] subspace basis
   double *W;      // [Nmax*K] C*Q, then the Ritz vectors
   double *B;      // [K*K] projected matrix
@@ -156,6 +158,8 @@ __device__ Smem<Real> carve(unsigned char *base, int Nmax, int R) {
   s.rt = takeR((size_t)kTabs * padN(Nmax));
   for (int a = 0; a < 3; ++a) s.fac[a] = takeR((size_t)Nmax * R);
   s.u1 = takeR((size_t)(kTerms + 1) * R * padN(Nmax));
+  s.cidx = reinterpret_cast<int *>(s.u1);  // the assembly's rows are dead during rounding
+  s.cidx_cap = (int)((size_t)(kTerms + 1) * R * padN(Nmax) * sizeof(Real) / sizeof(int));
   s.tile = takeR((size_t)(Nmax > 32 ? Nmax : 32) * kTileRow);
   s.Vr = takeR((size_t)Nmax * K);
   off = (off + 3) & ~size_t(3);
@@ -186,6 +190,28 @@ __device__ __forceinline__ double block_sum_d(double v, double *red) {
   for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
   __syncthreads();
   return t;
+}
+
+// Exclusive prefix sum of v over the block (thread order) and the total; uses
+// red[0..32) as scratch (ints); ends with a barrier.
+__device__ __forceinline__ int block_scan_excl(int v, int *red, int *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  __syncthreads();
+  if (lane == 31) red[warp] = x;
+  __syncthreads();
+  int base = 0, tot = 0;
+  for (int q = 0; q < nw; ++q) {
+    if (q < warp) base += red[q];
+    tot += red[q];
+  }
+  __syncthreads();
+  *total = tot;
+  return base + x - v;
 }
 
 // ---------------------------------------------------------------------------
@@ -408,10 +434,59 @@ __device__ __forceinline__ void df_add(float &hi, float &lo, float h2, float l2)
 // shuffle tree (double-float on the mixed path), so the result does not depend
 // on scheduling.  Same precision contract as gram_tiled.
 template <typename Real>
-__device__ __noinline__ void gram_w32(const Real *T, const int D[3], int m, Smem<Real> &sm) {
+__device__ __noinline__ void gram_w32(const Real *T, const int D[3], int m, Smem<Real> &sm,
+                                      double skip_rel) {
   constexpr bool f32 = sizeof(Real) == 4;
   const int n = D[m];
-  const int cols = (D[0] * D[1] * D[2]) / n;
+  const int cols_all = (D[0] * D[1] * D[2]) / n;
+  // First mode: columns whose energy is at most skip_rel of the tensor's are left
+  // out (their total, the "dropped" energy, is returned in sm.par[26] for the
+  // caller's error budget); the kept columns are listed in order in sm.cidx.
+  const bool select = m == 0 && skip_rel > 0.0 && sm.cidx && cols_all <= sm.cidx_cap &&
+                      cols_all <= 4 * (int)blockDim.x;
+  int cols = cols_all;
+  if (select) {
+    float e[4];
+    double part = 0.0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = 4 * threadIdx.x + q;
+      float s = 0.f;
+      if (j < cols_all)
+        for (int a = 0; a < n; ++a) {
+          const float v = (float)T[(int64_t)a * cols_all + j];
+          s = fmaf(v, v, s);
+        }
+      e[q] = s;
+      part += (double)s;
+    }
+    const double total = block_sum_d(part, sm.red);
+    const float cut = (float)(skip_rel * total);
+    int keep = 0;
+    double drop = 0.0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = 4 * threadIdx.x + q;
+      if (j >= cols_all) continue;
+      if (e[q] > cut) ++keep;
+      else drop += (double)e[q];
+    }
+    int kept_total;
+    int off = block_scan_excl(keep, reinterpret_cast<int *>(sm.red), &kept_total);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = 4 * threadIdx.x + q;
+      if (j < cols_all && e[q] > cut) sm.cidx[off++] = j;
+    }
+    // FP32 column energies: the dropped total is raised by a relative 1e-5 so that
+    // it bounds the exact one
+    drop = block_sum_d(drop, sm.red) * (1.0 + 1e-5);
+    if (threadIdx.x == 0) sm.par[26] = drop;
+    cols = kept_total;
+    __syncthreads();
+  } else if (m == 0 && threadIdx.x == 0) {
+    sm.par[26] = 0.0;
+  }
   const int item = threadIdx.x >> 3, g = threadIdx.x & 7;
   const bool diag = item >= 28;
   int ta, tb;
@@ -444,7 +519,7 @@ __device__ __noinline__ void gram_w32(const Real *T, const int D[3], int m, Smem
       if (a < n && j < cols) {
         int64_t addr;
         if (m == 0) {
-          addr = (int64_t)a * cols + j;
+          addr = (int64_t)a * cols_all + (select ? sm.cidx[j] : j);
         } else if (m == 1) {
           const int kk = j / D[2], i = j - kk * D[2];
           addr = ((int64_t)kk * D[1] + a) * D[2] + i;
@@ -569,11 +644,21 @@ __device__ __noinline__ void gram_w32(const Real *T, const int D[3], int m, Smem
 // n <= 32 with 256 threads: gram_w32; otherwise the 16 x 16 thread grid (TS = 2
 // covers n <= 32, TS = 4 covers n <= 64)
 template <typename Real, int TS>
-__device__ void gram(const Real *T, const int D[3], int m, Smem<Real> &sm) {
-  if (D[m] <= 32 && blockDim.x == 256)
-    gram_w32<Real>(T, D, m, sm);
-  else
+__device__ void gram(const Real *T, const int D[3], int m, Smem<Real> &sm, double skip_rel = 0.0) {
+  if (D[m] <= 32 && blockDim.x == 256) {
+    gram_w32<Real>(T, D, m, sm, skip_rel);
+  } else {
     gram_tiled<Real, TS>(T, D, m, sm);
+    if (m == 0 && threadIdx.x == 0) sm.par[26] = 0.0;
+    __syncthreads();
+  }
+}
+
+// relative energy below which a first-mode Gram column is left out: all such
+// columns together hold at most 1e-3 of the first mode's truncation budget
+// (eps^2/3 of the energy)
+__host__ __device__ inline double gram_skip_rel(double eps, int cols) {
+  return eps > 0.0 ? 1e-3 * (eps * eps / 3.0) / (double)cols : 0.0;
 }
 
 // ---------------------------------------------------------------------------
@@ -962,10 +1047,12 @@ __device__ void round_hosvd(Real *X, Real *T1, Real *T2, const int N[3], int R, 
   Real *dst[2] = {T2, T1};
   for (int m = 0; m < 3; ++m) {
     const int n = D[m];
-    gram<Real, TS>(src, D, m, sm);
+    gram<Real, TS>(src, D, m, sm, m == 0 ? gram_skip_rel(eps, D[1] * D[2]) : 0.0);
     const double tr = gram_trace<Real>(sm, n);
+    double dropped = 0.0;  // energy of the columns the first Gram matrix left out
     if (m == 0) {
-      e = tr;
+      dropped = sm.par[26];
+      e = tr + dropped;
       thr = eps * eps / 3.0 * e;
     }
     pc.mark(5);
@@ -981,7 +1068,7 @@ __device__ void round_hosvd(Real *X, Real *T1, Real *T2, const int N[3], int R, 
     k = leading_eigs<Real, double>(sm, n, k, wU, R, wr, pc);
     pc.mark(6);
     bool met;
-    r[m] = choose_rank<Real>(sm, n, k, thr, R, &met, tr);
+    r[m] = choose_rank<Real>(sm, n, k, thr - dropped, R, &met, tr);
     if (!met && k < kmax) {
       // the k columns found start the full solve (kept in sm.Vr, which the
       // iteration does not touch)
@@ -989,9 +1076,9 @@ __device__ void round_hosvd(Real *X, Real *T1, Real *T2, const int N[3], int R, 
       __syncthreads();
       k = leading_eigs<Real, Real>(sm, n, kmax, sm.Vr, k, k, pc);
       pc.mark(6);
-      r[m] = choose_rank<Real>(sm, n, k, thr, R, &met, tr);
+      r[m] = choose_rank<Real>(sm, n, k, thr - dropped, R, &met, tr);
     }
-    discarded += sm.par[31];
+    discarded += sm.par[31] + dropped;
     double *U = out.fac[m] + cell * (int64_t)N[m] * R;
     for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) {
       const int i = idx / k, j = idx - i * k;
@@ -1564,14 +1651,20 @@ __global__ void __launch_bounds__(kTB) tucker_gram_kernel(TuckerStepParams P, Tu
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int Nm = P.Nmax;
   Smem<Real> sm{};
-  sm.C = reinterpret_cast<double *>(smem_raw);
-  sm.tile = reinterpret_cast<Real *>(smem_raw + sizeof(double) * Nm * Nm);
+  sm.par = reinterpret_cast<double *>(smem_raw);
+  sm.red = sm.par + 32;
+  sm.C = sm.red + 32;
+  sm.tile = reinterpret_cast<Real *>(sm.C + (size_t)Nm * Nm);
   sm.tile2 = sm.tile + (size_t)(Nm > 32 ? Nm : 32) * kTileRow;
+  sm.cidx = reinterpret_cast<int *>(sm.tile2 + (size_t)(Nm > 32 ? Nm : 32) * kTileRow);
+  sm.cidx_cap = 4 * kTB;
   const int N[3] = {P.N1, P.N2, P.N3};
   const int64_t j = blockIdx.x, c = B.c0 + j, jb = B.joff + j;
   int D[3];
   split_dims(B, P.nxt, c, m, N, D);
-  gram<Real, TS>(split_src<Real>(B, jb, m, P.R, N), D, m, sm);
+  gram<Real, TS>(split_src<Real>(B, jb, m, P.R, N), D, m, sm,
+                 m == 0 ? gram_skip_rel(P.tol, D[1] * D[2]) : 0.0);
+  if (m == 0 && threadIdx.x == 0) B.disc[jb] = sm.par[26];  // columns left out
   const int n = D[m];
   double *out = B.C + jb * (int64_t)Nm * Nm;
   for (int i = threadIdx.x; i < n * n; i += blockDim.x) out[i] = sm.C[i];
@@ -1629,9 +1722,11 @@ __global__ void __launch_bounds__(32, 13) tucker_eig_kernel(TuckerStepParams P, 
   const int n = N[m];
   sm.Cg = B.C + j * (int64_t)Nm * Nm;  // read through L1
   const double tr = gram_trace<Real>(sm, n);
-  if (m == 0 && threadIdx.x == 0) B.e[j] = tr;  // ||X||^2 = trace of the first Gram matrix
+  // ||X||^2 = trace of the first Gram matrix + the columns it left out (B.disc)
+  if (m == 0 && threadIdx.x == 0) B.e[j] = tr + B.disc[j];
   __syncthreads();
-  const double thr = P.tol * P.tol / 3.0 * B.e[j];
+  const double dropped = m == 0 ? B.disc[j] : 0.0;
+  const double thr = P.tol * P.tol / 3.0 * B.e[j] - dropped;
   const double *wU = P.cur.fac[m] + c * (int64_t)n * R;
   const int wr = P.cur.rank[3 * c + m];
   int kmax = n < R + kExtra ? n : R + kExtra;
@@ -1927,8 +2022,9 @@ struct SplitSmem {
   size_t asm_, gram, eig, proj;
   SplitSmem(int Nmax, int R) {
     asm_ = smem_asm_bytes<Real>(Nmax, R);
-    gram = sizeof(double) * (size_t)Nmax * Nmax +
-           2 * sizeof(Real) * (size_t)(Nmax > 32 ? Nmax : 32) * kTileRow;
+    gram = sizeof(double) * (64 + (size_t)Nmax * Nmax) +
+           2 * sizeof(Real) * (size_t)(Nmax > 32 ? Nmax : 32) * kTileRow +
+           sizeof(int) * 4 * kTB + 64;
     eig = smem_eig_bytes<Real>(Nmax, R);
     proj = sizeof(double) * (size_t)Nmax * R;
   }
