@@ -713,15 +713,32 @@ __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
 
 // G = Q^T Q for the k columns of Q (n x k), accumulated in A, both triangles.
+// With at most 16 entries (k <= 5) each entry's sum is split over two adjacent
+// lanes (rows of one parity each) and combined by one shuffle, so a single warp
+// is fully used; the split depends on k only (the same sums in any block size).
 template <typename T, typename A>
 __device__ void gram_cols(const T *Q, int n, int k, A *Gs) {
-  for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
-    const int a = idx / k, b = idx - a * k;
-    if (a > b) continue;
+  const int ne = k * (k + 1) / 2;
+  const int parts = ne <= 16 ? 2 : 1;
+  for (int base = 0; base < ne * parts; base += blockDim.x) {
+    const int idx = base + threadIdx.x;
+    const int e = idx / parts, h = idx - e * parts;
+    int a = 0, b = 0;
     A s = 0;
-    for (int r = 0; r < n; ++r) s = fma((A)Q[r * k + a], (A)Q[r * k + b], s);
-    Gs[a * k + b] = s;
-    Gs[b * k + a] = s;
+    if (e < ne) {
+      int t = e;  // e -> (a <= b), row-major over the upper triangle
+      while (t >= k - a) {
+        t -= k - a;
+        ++a;
+      }
+      b = a + t;
+      for (int r = h; r < n; r += parts) s = fma((A)Q[r * k + a], (A)Q[r * k + b], s);
+    }
+    if (parts == 2) s += __shfl_xor_sync(0xffffffffu, s, 1);
+    if (e < ne && h == 0) {
+      Gs[a * k + b] = s;
+      Gs[b * k + a] = s;
+    }
   }
 }
 
@@ -748,8 +765,8 @@ __device__ __noinline__ int chol_warp(A *Gs, A *dinv, int k, A shift, A rel) {
   for (int j = 0; j < KM; ++j) {
     if (j < k) {
       const A d = __shfl_sync(0xffffffffu, g[j], j);
-      const A d0 = __shfl_sync(0xffffffffu, diag0, j);
-      const bool dep = !(d > tiny) || !(d > rel * d0);
+      bool dep = !(d > tiny);
+      if (rel > A(0)) dep = dep || !(d > rel * __shfl_sync(0xffffffffu, diag0, j));
       const A inv = dep ? A(0) : rsqrt_t(d);
       ndep += dep;
       const A lij = lane > j ? g[j] * inv : A(0);
