@@ -545,21 +545,37 @@ def run_gpu(args, rank, world):
                 t.close()
         e2e = None
         if not args.no_e2e:
-            f_host = torch.empty((wl.n_cell,) + tuple(wl.N), dtype=torch.float64, pin_memory=True)
-            f_np = f_host.numpy()
-            f_np[...] = s.f()
-            k = 3
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            for _ in range(k):
-                P.dvm_init_f(s.h, f_np)
-                s.step(1, residual=False)
-                m = s.moments()
-            el = time.perf_counter() - t0
-            e2e = {"value": upd * k / el, "unit": UNIT, "h2d_bytes_per_step": int(f_np.nbytes),
-                   "d2h_bytes_per_step": int(m.nbytes),
-                   "note": "per step: dvm_init_f from pinned host f (Tucker: compressed on "
-                           "the device), dvm_step, dvm_moments to host"}
+            k = 5
+            if tucker:
+                # the state in the solver's own format, from pinned host memory
+                ranks, core, fac = P.dvm_get_tucker(s.h, cap)
+                pin = [torch.from_numpy(x).pin_memory().numpy() for x in [ranks, core] + fac]
+                h2d = sum(int(x.nbytes) for x in pin)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for _ in range(k):
+                    P.dvm_init_tucker(s.h, pin[0], pin[1], pin[2:])
+                    s.step(1, residual=False)
+                    m = s.moments()
+                el = time.perf_counter() - t0
+                note = ("per step: dvm_init_tucker from pinned host arrays (ranks, cores, "
+                        "factors), dvm_step, dvm_moments to host")
+            else:
+                f_host = torch.empty((wl.n_cell,) + tuple(wl.N), dtype=torch.float64,
+                                     pin_memory=True)
+                f_np = f_host.numpy()
+                f_np[...] = s.f()
+                h2d = int(f_np.nbytes)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for _ in range(k):
+                    P.dvm_init_f(s.h, f_np)
+                    s.step(1, residual=False)
+                    m = s.moments()
+                el = time.perf_counter() - t0
+                note = "per step: dvm_init_f from pinned host f, dvm_step, dvm_moments to host"
+            e2e = {"value": upd * k / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                   "d2h_bytes_per_step": int(m.nbytes), "note": note}
         cfg = {**wl.describe(), "path": args.path,
                "format": "full tensor FP64" if not tucker else
                          f"Tucker {args.precision}, eps {tol:g}, rank cap {cap}",

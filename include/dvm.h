@@ -150,6 +150,23 @@ int dvm_init_maxwellian(dvm_ctx *ctx, const double *n, const double *u, const do
  * then kept. */
 int dvm_init_f(dvm_ctx *ctx, const double *f, int32_t on_device);
 
+/* Tucker format only: the state given directly, in the layout the solver keeps
+ * (Section 4: f = G x1 U1 x2 U2 x3 U3 per cell).  ranks[n_cell][3] with
+ * 1 <= r_a <= min(N_a, rank cap R); core[n_cell][R^3], the r1 x r2 x r3 core
+ * at the front of each cell's block (k3 fastest); u_a[n_cell][N_a][R], row i of
+ * a cell's factor at i*R, its first r_a columns used (orthonormal columns are
+ * not required).  Copied (host or device pointers, on_device as for
+ * dvm_init_f); as for the other initialisations the macroparameters are
+ * recomputed and the time step is kept once set.  Errors: INVALID_ARG (not a
+ * Tucker context, ranks out of range), NONPHYSICAL, CUDA. */
+int dvm_init_tucker(dvm_ctx *ctx, const int32_t *ranks, const double *core, const double *u1,
+                    const double *u2, const double *u3, int32_t on_device);
+
+/* Tucker format only: the current state into host arrays in the layout of
+ * dvm_init_tucker (any pointer may be NULL).  Errors: INVALID_ARG, STATE. */
+int dvm_get_tucker(dvm_ctx *ctx, int32_t *ranks, double *core, double *u1, double *u2,
+                   double *u3);
+
 /* Advance nsteps explicit Euler steps (Section 3, Algorithm 1 with
  * Algorithm 2 inside; Tucker: Section 5 with one rounding per cell and step).
  * If residual_out is not NULL the call synchronises and stores the residual

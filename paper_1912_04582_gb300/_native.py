@@ -90,6 +90,8 @@ SIGNATURES = {
     "dvm_get_geometry": (ctypes.c_int, [_P, _c_dp, _c_i64p, _c_dp]),
     "dvm_get_ranks": (ctypes.c_int, [_P, _c_i32p]),
     "dvm_get_launch_config": (ctypes.c_int, [_P, _c_i32p, ctypes.POINTER(ctypes.c_float)]),
+    "dvm_init_tucker": (ctypes.c_int, [_P, _c_i32p, _c_dp, _c_dp, _c_dp, _c_dp, ctypes.c_int32]),
+    "dvm_get_tucker": (ctypes.c_int, [_P, _c_i32p, _c_dp, _c_dp, _c_dp, _c_dp]),
     "dvm_set_kernel_timing": (ctypes.c_int, [_P, ctypes.c_int32]),
     "dvm_get_kernel_timing": (ctypes.c_int, [_P, _c_dp, ctypes.POINTER(ctypes.c_int64)]),
     "dvm_memory": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t),

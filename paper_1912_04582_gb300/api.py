@@ -162,6 +162,27 @@ def dvm_get_launch_config(h):
     return int(g.value), [float(v) for v in t]
 
 
+def dvm_get_tucker(h, R):
+    """Current Tucker state (ranks [nc,3], core [nc,R^3], factors [nc,N_a,R]), host arrays in
+    the solver's layout."""
+    nc = h.n_cell
+    ranks = np.empty((nc, 3), dtype=np.int32)
+    core = np.empty((nc, R * R * R))
+    fac = [np.empty((nc, h.N[a], R)) for a in range(3)]
+    _n.check(N_lib().dvm_get_tucker(h.ptr, _i32p(ranks), _dp(core), _dp(fac[0]), _dp(fac[1]),
+                                    _dp(fac[2])), "dvm_get_tucker")
+    return ranks, core, fac
+
+
+def dvm_init_tucker(h, ranks, core, fac):
+    """Set the Tucker state from host arrays in the layout of ``dvm_get_tucker``."""
+    ranks = np.ascontiguousarray(ranks, dtype=np.int32)
+    core = np.ascontiguousarray(core, dtype=np.float64)
+    fac = [np.ascontiguousarray(u, dtype=np.float64) for u in fac]
+    return _n.check(N_lib().dvm_init_tucker(h.ptr, _i32p(ranks), _dp(core), _dp(fac[0]),
+                                            _dp(fac[1]), _dp(fac[2]), 0), "dvm_init_tucker")
+
+
 def dvm_set_kernel_timing(h, on):
     _n.check(N_lib().dvm_set_kernel_timing(h.ptr, int(bool(on))), "dvm_set_kernel_timing")
 

@@ -293,6 +293,38 @@ int dvm_init_f(dvm_ctx *C, const double *f, int32_t on_device) {
   return ctx_init_from_full(C, f, on_device != 0);
 }
 
+int dvm_init_tucker(dvm_ctx *C, const int32_t *ranks, const double *core, const double *u1,
+                    const double *u2, const double *u3, int32_t on_device) {
+  if (!C || !ranks || !core || !u1 || !u2 || !u3) {
+    set_error("dvm_init_tucker: null argument");
+    return DVM_ERR_INVALID_ARG;
+  }
+  if (C->opts.format != DVM_FORMAT_TUCKER || !C->tucker) {
+    set_error("dvm_init_tucker: the context is not in Tucker format");
+    return DVM_ERR_INVALID_ARG;
+  }
+  int rc = ctx_prepare_boundaries(C);
+  if (rc != DVM_OK) return rc;
+  const double *fac[3] = {u1, u2, u3};
+  rc = tucker_set_state(C, ranks, core, fac, on_device != 0);
+  if (rc == DVM_OK) C->initialized = true;
+  return rc;
+}
+
+int dvm_get_tucker(dvm_ctx *C, int32_t *ranks, double *core, double *u1, double *u2, double *u3) {
+  if (!C) return DVM_ERR_INVALID_ARG;
+  if (C->opts.format != DVM_FORMAT_TUCKER || !C->tucker) {
+    set_error("dvm_get_tucker: the context is not in Tucker format");
+    return DVM_ERR_INVALID_ARG;
+  }
+  if (!C->initialized) {
+    set_error("dvm_get_tucker: context not initialised");
+    return DVM_ERR_STATE;
+  }
+  double *fac[3] = {u1, u2, u3};
+  return tucker_get_state(C, ranks, core, fac);
+}
+
 int dvm_step(dvm_ctx *C, int32_t nsteps, double *residual_out) {
   if (!C || nsteps < 0) {
     set_error("dvm_step: bad argument");

@@ -100,6 +100,9 @@ int build_topology(dvm_ctx *C, const dvm_mesh *m);
 int tucker_alloc(dvm_ctx *C);
 void tucker_free(dvm_ctx *C);
 int tucker_init_from_full(dvm_ctx *C, const double *d_f_full);
+int tucker_set_state(dvm_ctx *C, const int32_t *ranks, const double *core,
+                     const double *const fac[3], bool on_device);
+int tucker_get_state(dvm_ctx *C, int32_t *ranks, double *core, double *const fac[3]);
 int tucker_init_maxwellians(dvm_ctx *C, const double *d_n, const double *d_u, const double *d_T);
 int tucker_step(dvm_ctx *C, int32_t nsteps, double *residual_out);
 int tucker_moments(dvm_ctx *C, double *d_macro);

@@ -292,6 +292,58 @@ int tucker_init_maxwellians(dvm_ctx *C, const double *d_n, const double *d_u, co
   return finish_init(C);
 }
 
+// The Tucker state given directly (host or device arrays in the arena layout:
+// ranks [nc][3], core [nc][R^3] with the r1 x r2 x r3 core at the front, factor
+// a [nc][N_a][R] with the first r_a columns used).
+int tucker_set_state(dvm_ctx *C, const int32_t *ranks, const double *core,
+                     const double *const fac[3], bool on_device) {
+  TuckerState *S = C->tucker;
+  const int64_t nc = C->nc;
+  const int R = S->R;
+  std::vector<int32_t> r(3 * nc);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (on_device) {
+    DVM_CUDA_TRY(cudaMemcpyAsync(r.data(), ranks, sizeof(int32_t) * 3 * nc,
+                                 cudaMemcpyDeviceToHost, C->stream));
+    int rc = sync_check(C);
+    if (rc != DVM_OK) return rc;
+  } else {
+    std::copy(ranks, ranks + 3 * nc, r.begin());
+  }
+  for (int64_t i = 0; i < 3 * nc; ++i)
+    if (r[i] < 1 || r[i] > R || r[i] > C->N[i % 3]) {
+      set_error("dvm_init_tucker: ranks must lie in 1 .. min(N_a, rank cap)");
+      return DVM_ERR_INVALID_ARG;
+    }
+  TuckerDev &T = S->buf[S->cur];
+  DVM_CUDA_TRY(cudaMemcpyAsync(T.rank, ranks, sizeof(int32_t) * 3 * nc, kind, C->stream));
+  DVM_CUDA_TRY(cudaMemcpyAsync(T.core, core, sizeof(double) * nc * R * R * R, kind, C->stream));
+  for (int a = 0; a < 3; ++a)
+    DVM_CUDA_TRY(cudaMemcpyAsync(T.fac[a], fac[a], sizeof(double) * nc * (int64_t)C->N[a] * R,
+                                 kind, C->stream));
+  int rc = sync_check(C);
+  if (rc != DVM_OK) return rc;
+  return finish_init(C);
+}
+
+int tucker_get_state(dvm_ctx *C, int32_t *ranks, double *core, double *const fac[3]) {
+  TuckerState *S = C->tucker;
+  const int64_t nc = C->nc;
+  const int R = S->R;
+  const TuckerDev &T = S->buf[S->cur];
+  if (ranks)
+    DVM_CUDA_TRY(cudaMemcpyAsync(ranks, T.rank, sizeof(int32_t) * 3 * nc, cudaMemcpyDeviceToHost,
+                                 C->stream));
+  if (core)
+    DVM_CUDA_TRY(cudaMemcpyAsync(core, T.core, sizeof(double) * nc * R * R * R,
+                                 cudaMemcpyDeviceToHost, C->stream));
+  for (int a = 0; a < 3; ++a)
+    if (fac[a])
+      DVM_CUDA_TRY(cudaMemcpyAsync(fac[a], T.fac[a], sizeof(double) * nc * (int64_t)C->N[a] * R,
+                                   cudaMemcpyDeviceToHost, C->stream));
+  return sync_check(C);
+}
+
 int tucker_init_from_full(dvm_ctx *C, const double *d_f_full) {
   TuckerState *S = C->tucker;
   TuckerStepParams p = step_params(C);

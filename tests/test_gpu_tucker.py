@@ -314,3 +314,28 @@ def test_compression_at_64_nodes(dvm):
     s.close()
     assert rel_l2(g, f) < 1e-10
     assert np.all(ranks == np.array([3, 2, 4]))
+
+
+def test_tucker_state_round_trip(dvm):
+    """dvm_get_tucker / dvm_init_tucker: a state read from one context and given to a
+    fresh one (same time step) reproduces it exactly, and both continue alike (the
+    moments are re-taken about each cell's own velocity, so to round-off); ranks out of
+    range are rejected."""
+    wl = W.cavity(nside=4, N=16, seed=4)
+    a = tucker_solver(dvm, wl, 8, 1e-6, precision=MIXED)
+    a.step(6)
+    ranks, core, fac = dvm.dvm_get_tucker(a.h, 8)
+    b = dvm.Solver(wl, format=1, precision=MIXED, rank_cap=8, tol=1e-6,
+                   dt=dvm.dvm_get_dt(a.h), init=False)
+    dvm.dvm_init_tucker(b.h, ranks, core, fac)
+    assert np.array_equal(a.f(), b.f())
+    assert np.max(np.abs(a.moments() - b.moments())) < 1e-12
+    a.step(3)
+    b.step(3)
+    assert rel_l2(b.f(), a.f()) < 1e-10
+    bad = ranks.copy()
+    bad[0, 1] = 9
+    with pytest.raises(Exception):
+        dvm.dvm_init_tucker(b.h, bad, core, fac)
+    a.close()
+    b.close()
