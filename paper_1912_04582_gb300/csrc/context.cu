@@ -416,6 +416,10 @@ static int read_residual(dvm_ctx *C, double *residual_out) {
     set_error("non-physical state: n <= 0 or T <= 0 in some cell");
     return DVM_ERR_NONPHYSICAL;
   }
+  if (flag & 2) {  // the step's result is still complete (direct reads were used)
+    set_error("a bulk shared-memory copy did not complete within its wait limit");
+    return DVM_ERR_TIMEOUT;
+  }
   return DVM_OK;
 }
 

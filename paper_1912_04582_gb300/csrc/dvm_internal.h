@@ -60,7 +60,7 @@ struct FullParams {
   const double *ghost;   // [nghost][nn] free-stream / unit wall Maxwellians
   const double *vol;     // [nc]
   const double *xi[3];   // nodes per axis
-  int *flag;             // bit 0: non-physical n or T seen
+  int *flag;             // bit 0: non-physical n or T seen; bit 1: a bulk copy wait ran out
   int64_t nc;
   int N1, N2, N3;
   int all_axis;          // 1 if every face normal is a signed coordinate axis

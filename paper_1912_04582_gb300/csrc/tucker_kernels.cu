@@ -75,6 +75,11 @@ struct PhaseClock {
       t = now;
     }
   }
+  // event counts in slots 1 and 2 (re-seeding rounds, eigen-solver retries)
+  __device__ void count(int i, int v) {
+    if (acc && threadIdx.x == 0 && v > 0)
+      atomicAdd(reinterpret_cast<unsigned long long *>(acc + i), (unsigned long long)v);
+  }
 };
 
 __host__ __device__ inline int sub_k(int Nmax, int R) {
@@ -106,7 +111,6 @@ struct Smem {
                   // transposed (column k contiguous), zero-padded
   Real *tile;     // [Nmax*(kKC+1)] Gram tile
   Real *Vr;       // [Nmax*K] kept eigenvectors in the working precision
-  float *C32;     // [Nmax*Nmax] FP32 copy of C (mixed path: power iterations)
   float *Q32;     // [Nmax*K] (inside sm.W)
   float *W32;     // [Nmax*K] (inside sm.W)
   int *pairs;     // [K+2]
@@ -122,7 +126,6 @@ __host__ __device__ inline size_t smem_bytes(int Nmax, int R) {
                        (kTerms + 1) * (size_t)R * padN(Nmax) +
                        (size_t)(Nmax > 32 ? Nmax : 32) * kTileRow +
                        (size_t)Nmax * K);
-  b += sizeof(float) * (size_t)Nmax * Nmax;
   b += sizeof(int) * (2 * (size_t)K + 2);
   return b + 64;
 }
@@ -163,8 +166,6 @@ __device__ Smem<Real> carve(unsigned char *base, int Nmax, int R) {
   s.tile = takeR((size_t)(Nmax > 32 ? Nmax : 32) * kTileRow);
   s.Vr = takeR((size_t)Nmax * K);
   off = (off + 3) & ~size_t(3);
-  s.C32 = reinterpret_cast<float *>(base + off);
-  off += sizeof(float) * (size_t)Nmax * Nmax;
   // the FP32 iteration blocks live in sm.W (consumed before sm.W is written)
   s.Q32 = reinterpret_cast<float *>(s.W);
   s.W32 = s.Q32 + (size_t)Nmax * K;
@@ -670,19 +671,35 @@ __device__ void mat_cq(const T *__restrict__ C, const T *Q, T *W, int n, int k) 
   for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) {
     const int i = idx / k, j = idx - i * k;
     T s = 0;
-    for (int t = 0; t < n; ++t) s = fma(C[i * n + t], Q[t * k + j], s);
+    // C is stored exactly symmetric: C[i][t] is read as C[t][i], so the lanes of
+    // a warp (consecutive i) touch consecutive words
+    for (int t = 0; t < n; ++t) s = fma(C[t * n + i], Q[t * k + j], s);
+    W[idx] = s;
+  }
+  __syncthreads();
+}
+
+// W = C_hi Q in FP32 (the mixed path's orthogonal iterations), C_hi the leading
+// float of every double-float Gram entry, read by columns like mat_cq
+__device__ void mat_cq_hi(const float2 *__restrict__ C, const float *Q, float *W, int n, int k) {
+  for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) {
+    const int i = idx / k, j = idx - i * k;
+    float s = 0.f;
+    for (int t = 0; t < n; ++t) s = fmaf(C[t * n + i].x, Q[t * k + j], s);
     W[idx] = s;
   }
   __syncthreads();
 }
 
 // Double-float inner product sum_t (c_t.hi + c_t.lo) (vh_t + vl_t) with exact
-// leading products (fma) and a two-sum accumulation: about 2^-48 relative.
-__device__ __forceinline__ double df_dot(const float2 *c, const float *vh, const float *vl,
-                                         int stride, int n) {
+// leading products (fma) and a two-sum accumulation: about 2^-48 relative.  c_t
+// is read at c[t * cstride] (a column of the symmetric Gram matrix, so that the
+// lanes of a warp, one row each, read consecutive entries).
+__device__ __forceinline__ double df_dot(const float2 *c, int cstride, const float *vh,
+                                         const float *vl, int stride, int n) {
   float hi = 0.f, lo = 0.f;
   for (int t = 0; t < n; ++t) {
-    const float2 ct = c[t];
+    const float2 ct = c[t * cstride];
     const float h = vh[t * stride];
     const float l = vl ? vl[t * stride] : 0.f;
     const float p = __fmul_rn(ct.x, h);
@@ -824,9 +841,10 @@ __device__ __noinline__ void solve_rows(T *Q, int n, int k, const A *L, const A 
 // barrier.
 template <typename T, typename A>
 __device__ __noinline__ int orthonormalise(T *Q, int n, int k, A *Gs, A *dinv, int passes,
-                                           double shift_rel, bool reseed) {
+                                           double shift_rel, bool reseed, int *reseeds = nullptr) {
   __shared__ int s_dep;
-  for (int round = 0; round < 3; ++round) {
+  int round = 0;
+  for (; round < 3; ++round) {
     for (int pass = 0; pass < passes; ++pass) {
       const bool shifted = round == 0 && pass == 0;
       gram_cols<T, A>(Q, n, k, Gs);
@@ -837,12 +855,16 @@ __device__ __noinline__ int orthonormalise(T *Q, int n, int k, A *Gs, A *dinv, i
         for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
         const A shift = shifted ? (A)shift_rel * tr : A(0);
         const A rel = (reseed && !shifted) ? A(1e-10) : A(0);
-        const int ndep = k <= 16 ? chol_warp<A, 16>(Gs, dinv, k, shift, rel)
-                                 : chol_warp<A, kOrthMax>(Gs, dinv, k, shift, rel);
+        // register arrays sized for k (the arithmetic does not depend on the size)
+        const int ndep = k <= 8    ? chol_warp<A, 8>(Gs, dinv, k, shift, rel)
+                         : k <= 16 ? chol_warp<A, 16>(Gs, dinv, k, shift, rel)
+                                   : chol_warp<A, kOrthMax>(Gs, dinv, k, shift, rel);
         if (lane == 0) s_dep = ndep;
       }
       __syncthreads();
-      if (k <= 16)
+      if (k <= 8)
+        solve_rows<T, A, 8>(Q, n, k, Gs, dinv);
+      else if (k <= 16)
         solve_rows<T, A, 16>(Q, n, k, Gs, dinv);
       else
         solve_rows<T, A, kOrthMax>(Q, n, k, Gs, dinv);
@@ -857,6 +879,7 @@ __device__ __noinline__ int orthonormalise(T *Q, int n, int k, A *Gs, A *dinv, i
     passes = 2;
   }
   const int nz = k - s_dep;
+  if (reseeds) *reseeds = round < 3 ? round : 2;
   __syncthreads();
   return nz;
 }
@@ -896,7 +919,6 @@ __device__ __noinline__ int leading_eigs(Smem<Real> &sm, int n, int k, const WT 
     }
   } else {
     const float2 *Cdf = reinterpret_cast<const float2 *>(sm.Cg);
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) sm.C32[idx] = Cdf[idx].x;
     for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) {
       const int i = idx / k, j = idx - i * k;
       sm.Q32[idx] = (float)(j < r_warm ? (double)warm[(int64_t)i * ldw + j] : start_value(i, j));
@@ -904,7 +926,7 @@ __device__ __noinline__ int leading_eigs(Smem<Real> &sm, int n, int k, const WT 
     __syncthreads();
     pc.mark(6);
     for (int it = 0; it < iters; ++it) {
-      mat_cq(sm.C32, sm.Q32, sm.W32, n, k);
+      mat_cq_hi(Cdf, sm.Q32, sm.W32, n, k);
       for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) sm.Q32[idx] = sm.W32[idx];
       __syncthreads();
       pc.mark(9);
@@ -918,13 +940,15 @@ __device__ __noinline__ int leading_eigs(Smem<Real> &sm, int n, int k, const WT 
     __syncthreads();
     for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) {
       const int i = idx / k, j = idx - i * k;
-      sm.Q[idx] = df_dot(Cdf + i * n, V + j, nullptr, k, n);
+      sm.Q[idx] = df_dot(Cdf + i, n, V + j, nullptr, k, n);
     }
     __syncthreads();
     pc.mark(11);
-    const int nz = orthonormalise<double, double>(sm.Q, n, k, sm.B, sm.cs, 3, 1e-11, true);
+    int rounds = 0;
+    const int nz = orthonormalise<double, double>(sm.Q, n, k, sm.B, sm.cs, 3, 1e-11, true, &rounds);
     if (threadIdx.x == 0) sm.par[29] = (double)nz;
     pc.mark(12);
+    pc.count(1, rounds);
   }
   // Rayleigh quotients d_j = q_j^T C q_j of the orthonormal columns (FP64
   // accuracy): any leading set of columns captures exactly the sum of its d_j, so
@@ -953,12 +977,13 @@ __device__ __noinline__ int leading_eigs(Smem<Real> &sm, int n, int k, const WT 
     for (int j = warp; j < k; j += nwarp) {
       double d = 0.0;
       for (int i = lane; i < n; i += 32)
-        d = fma(sm.Q[i * k + j], df_dot(Cdf + i * n, qh + j, ql + j, k, n), d);
+        d = fma(sm.Q[i * k + j], df_dot(Cdf + i, n, qh + j, ql + j, k, n), d);
       for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
       if (lane == 0) sm.cs[j] = d;
     }
   }
   __syncthreads();
+  pc.mark(14);
   if (warp == 0) {
     if (lane == 0) {  // order columns by quotient, descending
       for (int i = 0; i < k; ++i) sm.perm[i] = i;
@@ -981,6 +1006,7 @@ __device__ __noinline__ int leading_eigs(Smem<Real> &sm, int n, int k, const WT 
     sm.W[idx] = sm.Q[i * k + sm.perm[j]];
   }
   __syncthreads();
+  pc.mark(15);
   return k;
 }
 
@@ -1691,10 +1717,63 @@ template <typename Real>
 __host__ __device__ inline size_t smem_eig_bytes(int Nmax, int R) {
   const int K = sub_k(Nmax, R);
   size_t b = sizeof(double) * (64 + 2 * (size_t)Nmax * K + (size_t)K * K + 2 * K + 2);
-  b += sizeof(Real) * (size_t)Nmax * K;
-  b += sizeof(float) * (size_t)Nmax * Nmax;
+  b += sizeof(Real) * (size_t)Nmax * K + 16;
+  b += sizeof(double) * (size_t)Nmax * Nmax;  // the staged Gram matrix
   b += sizeof(int) * (2 * (size_t)K + 2);
   return b + 64;
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+constexpr int kBulkWaitIters = 1 << 22;  // bound on the polls of a bulk copy's barrier
+
+// Copy `count` 8-byte Gram entries from global to shared memory with one bulk
+// asynchronous copy (cp.async.bulk, completion counted in bytes on an mbarrier)
+// and return the shared copy.  A plain copy is used when an address or the size
+// is not a multiple of 16 bytes.  The barrier is polled at most kBulkWaitIters
+// times; if the copy has not landed by then the block reads the global matrix
+// instead (same values) and sets bit 1 of *flag.  Called by every thread.
+__device__ __noinline__ const double *stage_gram(double *dst, const double *src, int count,
+                                                 int *flag) {
+  __shared__ __align__(8) unsigned long long s_bar;
+  const unsigned bytes = 8u * (unsigned)count;
+  const bool bulk =
+      ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0 &&
+      (bytes & 15u) == 0 && bytes > 0;
+  if (!bulk) {
+    for (int i = threadIdx.x; i < count; i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+    return dst;
+  }
+  const unsigned bar = smem_u32(&s_bar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+  }
+  unsigned done = 0;
+  for (int it = 0; it < kBulkWaitIters && !done; ++it)
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar)
+        : "memory");
+  if (__syncthreads_and(done)) return dst;
+  if (threadIdx.x == 0) atomicOr(flag, 2);
+  return src;
 }
 
 // Eigen-solve and rank rule of mode m for cell j: one warp per cell.  On exit
@@ -1709,6 +1788,7 @@ __global__ void __launch_bounds__(32, 13) tucker_eig_kernel(TuckerStepParams P, 
   Smem<Real> sm{};
   sm.nmax = Nm;
   sm.kdim = K;
+  double *Cs;  // the Gram matrix staged in shared memory
   {
     size_t off = 0;
     auto takeD = [&](size_t n) {
@@ -1725,19 +1805,20 @@ __global__ void __launch_bounds__(32, 13) tucker_eig_kernel(TuckerStepParams P, 
     sm.cs = takeD(K + 2);
     sm.Vr = reinterpret_cast<Real *>(smem_raw + off);
     off += sizeof(Real) * (size_t)Nm * K;
-    off = (off + 3) & ~size_t(3);
-    sm.C32 = reinterpret_cast<float *>(smem_raw + off);
-    off += sizeof(float) * (size_t)Nm * Nm;
+    off = (off + 15) & ~size_t(15);
+    Cs = reinterpret_cast<double *>(smem_raw + off);
+    off += sizeof(double) * (size_t)Nm * Nm;
     sm.Q32 = reinterpret_cast<float *>(sm.W);
     sm.W32 = sm.Q32 + (size_t)Nm * K;
     sm.pairs = reinterpret_cast<int *>(smem_raw + off);
     off += sizeof(int) * (K + 2);
     sm.perm = reinterpret_cast<int *>(smem_raw + off);
   }
+  PhaseClock pc(P.phase);
   const int N[3] = {P.N1, P.N2, P.N3};
   const int64_t c = B.c0 + blockIdx.x, j = B.joff + blockIdx.x;  // j: buffer index
   const int n = N[m];
-  sm.Cg = B.C + j * (int64_t)Nm * Nm;  // read through L1
+  sm.Cg = stage_gram(Cs, B.C + j * (int64_t)Nm * Nm, n * n, P.flag);
   const double tr = gram_trace<Real>(sm, n);
   // ||X||^2 = trace of the first Gram matrix + the columns it left out (B.disc)
   if (m == 0 && threadIdx.x == 0) B.e[j] = tr + B.disc[j];
@@ -1748,16 +1829,19 @@ __global__ void __launch_bounds__(32, 13) tucker_eig_kernel(TuckerStepParams P, 
   const int wr = P.cur.rank[3 * c + m];
   int kmax = n < R + kExtra ? n : R + kExtra;
   if (kmax > kOrthMax) kmax = kOrthMax;
-  PhaseClock pc(nullptr);
   int k = (wr > 0 && thr > 0.0 && wr + kExtra < kmax) ? wr + kExtra : kmax;
+  pc.mark(4);
   k = leading_eigs<Real, double>(sm, n, k, wU, R, wr, pc);
   bool met;
   int r = choose_rank<Real>(sm, n, k, thr, R, &met, tr);
+  pc.mark(7);
   if (!met && k < kmax) {
     for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) sm.Vr[idx] = (Real)sm.W[idx];
     __syncthreads();
     k = leading_eigs<Real, Real>(sm, n, kmax, sm.Vr, k, k, pc);
     r = choose_rank<Real>(sm, n, k, thr, R, &met, tr);
+    pc.mark(8);
+    pc.count(2, 1);
   }
   double *U = P.nxt.fac[m] + c * (int64_t)n * R;
   for (int idx = threadIdx.x; idx < n * r; idx += blockDim.x) {
@@ -1770,6 +1854,7 @@ __global__ void __launch_bounds__(32, 13) tucker_eig_kernel(TuckerStepParams P, 
     B.disc[j] = d;
     if (m == 2 && P.err) P.err[c] = B.e[j] > 0.0 ? sqrt(d / B.e[j]) : 0.0;
   }
+  pc.mark(13);
 }
 
 // Projection of mode m with the new factor: Y_{m+1} = Y_m x_m U_m^T (m = 0, 1,

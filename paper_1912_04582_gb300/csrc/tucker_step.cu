@@ -270,11 +270,13 @@ void tucker_free(dvm_ctx *C) {
   if (S->phase) {
     long long h[16] = {0};
     if (cudaMemcpy(h, S->phase, sizeof h, cudaMemcpyDeviceToHost) == cudaSuccess) {
-      static const char *names[14] = {"prologue", "-", "-", "assemble", "energy",
-                                      "gram",     "eig",        "rank",      "project",   "eig_cq32",
-                                      "eig_orth32", "eig_cq64", "eig_orth64", "contract"};
-      std::fprintf(stderr, "tucker phases (SM cycles, summed over CTAs):");
-      for (int i = 0; i < 14; ++i) std::fprintf(stderr, " %s=%lld", names[i], h[i]);
+      // fused kernel / eigen-solve kernel
+      static const char *names[16] = {"prologue",    "reseeds",    "retries",    "assemble",
+                                      "energy|setup", "gram",      "eig_init",   "rank",
+                                      "project|retry", "eig_cq32", "eig_orth32", "eig_cq64",
+                                      "eig_orth64",  "contract|store", "rayleigh", "sort"};
+      std::fprintf(stderr, "tucker phases (SM cycles summed over CTAs; reseeds, retries: counts):");
+      for (int i = 0; i < 16; ++i) std::fprintf(stderr, " %s=%lld", names[i], h[i]);
       std::fprintf(stderr, "\n");
     }
     cudaFree(S->phase);
