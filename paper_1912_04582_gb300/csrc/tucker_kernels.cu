@@ -826,22 +826,30 @@ __device__ __noinline__ void solve_rows(T *Q, int n, int k, const A *L, const A 
   }
 }
 
+// Treatment of numerically dependent columns by orthonormalise()
+constexpr int kDepNone = 0;    // no relative test (only breakdown zeroes a column)
+constexpr int kDepZero = 1;    // relative test; dependent columns are zeroed
+constexpr int kDepReseed = 2;  // relative test; dependent columns are re-seeded
+
 // Orthonormalise the k <= n columns of Q (n x k, row-major) in place by
 // Cholesky-QR repeated `passes` times: G = Q^T Q, its Cholesky factor L, then
 // Q <- Q L^{-T}; arithmetic in A.  The first pass factors G + shift_rel *
 // trace(G) I instead (shifted Cholesky-QR, Fukaya et al. 2020): the shift keeps
 // the factorisation from breaking down on nearly dependent columns while leaving
 // span(Q) unchanged, and the following unshifted passes restore orthonormality
-// to the working precision.  With reseed (the last step of an eigen-solve, where
-// the basis must keep full rank), the unshifted passes also flag columns that
-// are numerically dependent (pivot <= 1e-10 G_jj); flagged columns are replaced
-// by fresh start vectors and two more passes run (at most two such rounds).
-// Without reseed a dependent column is zeroed.  Returns the number of non-zero
-// columns.  Gs (k x k) and dinv (k) are scratch in shared memory; ends with a
-// barrier.
+// to the working precision.  With dep != kDepNone (the last step of an
+// eigen-solve) the unshifted passes also flag columns that are numerically
+// dependent (pivot <= 1e-10 G_jj: the part outside the span of the previous
+// columns has no accurate digits left) and zero them, so the non-zero columns
+// are orthonormal to round-off.  With kDepReseed (where the basis must keep full
+// rank) flagged columns are then replaced by fresh start vectors and two more
+// passes run (at most two such rounds).  Returns the number of non-zero columns;
+// *reseeds (if given) receives the number of re-seeding rounds.  Gs (k x k) and
+// dinv (k) are scratch in shared memory; ends with a barrier.
 template <typename T, typename A>
 __device__ __noinline__ int orthonormalise(T *Q, int n, int k, A *Gs, A *dinv, int passes,
-                                           double shift_rel, bool reseed, int *reseeds = nullptr) {
+                                           double shift_rel, int dep, int *reseeds = nullptr) {
+  const bool reseed = dep == kDepReseed;
   __shared__ int s_dep;
   int round = 0;
   for (; round < 3; ++round) {
@@ -854,7 +862,7 @@ __device__ __noinline__ int orthonormalise(T *Q, int n, int k, A *Gs, A *dinv, i
         A tr = lane < k ? Gs[lane * k + lane] : A(0);
         for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
         const A shift = shifted ? (A)shift_rel * tr : A(0);
-        const A rel = (reseed && !shifted) ? A(1e-10) : A(0);
+        const A rel = (dep != kDepNone && !shifted) ? A(1e-10) : A(0);
         // register arrays sized for k (the arithmetic does not depend on the size)
         const int ndep = k <= 8    ? chol_warp<A, 8>(Gs, dinv, k, shift, rel)
                          : k <= 16 ? chol_warp<A, 16>(Gs, dinv, k, shift, rel)
@@ -890,12 +898,14 @@ __device__ __noinline__ int orthonormalise(T *Q, int n, int k, A *Gs, A *dinv, i
 // spans most of the new dominant subspace) completed by fixed start vectors.
 // FP64 path: FP64 iterations.  Mixed path: FP32 iterations on the rounded Gram
 // matrix, then one FP64 step on the accurate one.  Every path ends with an FP64
-// shifted Cholesky-QR3, so the basis is orthonormal to FP64 round-off.  On exit
+// shifted Cholesky-QR3, so the basis is orthonormal to FP64 round-off; columns it
+// finds dependent are handled as dep_final says (zeroed on a first solve: the
+// rank rule never keeps a zero column; re-seeded on a retry).  On exit
 // sm.W holds the k columns ordered by their Rayleigh quotients (descending), sm.Z
 // the sorted quotients, sm.par[29] the number of non-zero columns.  Returns k.
 template <typename Real, typename WT>
 __device__ __noinline__ int leading_eigs(Smem<Real> &sm, int n, int k, const WT *warm, int ldw, int r_warm,
-                            PhaseClock &pc) {
+                            PhaseClock &pc, int dep_final) {
   if (!warm) r_warm = 0;
   if (r_warm > k) r_warm = k;
   const int iters = r_warm > 0 ? kWarmIter : kPower;
@@ -913,7 +923,7 @@ __device__ __noinline__ int leading_eigs(Smem<Real> &sm, int n, int k, const WT 
       pc.mark(11);
       const bool last = it == iters - 1;
       const int nz = orthonormalise<double, double>(sm.Q, n, k, sm.B, sm.cs, last ? 3 : 2,
-                                                    last ? 1e-11 : 1e-12, last);
+                                                    last ? 1e-11 : 1e-12, last ? dep_final : kDepNone);
       if (threadIdx.x == 0) sm.par[29] = (double)nz;
       pc.mark(12);
     }
@@ -930,7 +940,7 @@ __device__ __noinline__ int leading_eigs(Smem<Real> &sm, int n, int k, const WT 
       for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) sm.Q32[idx] = sm.W32[idx];
       __syncthreads();
       pc.mark(9);
-      orthonormalise<float, float>(sm.Q32, n, k, G32, d32, kF32Passes, 1e-5, false);
+      orthonormalise<float, float>(sm.Q32, n, k, G32, d32, kF32Passes, 1e-5, kDepNone);
       pc.mark(10);
     }
     // one power step with the accurate Gram matrix: W = C Q32 in double-float
@@ -945,7 +955,7 @@ __device__ __noinline__ int leading_eigs(Smem<Real> &sm, int n, int k, const WT 
     __syncthreads();
     pc.mark(11);
     int rounds = 0;
-    const int nz = orthonormalise<double, double>(sm.Q, n, k, sm.B, sm.cs, 3, 1e-11, true, &rounds);
+    const int nz = orthonormalise<double, double>(sm.Q, n, k, sm.B, sm.cs, 3, 1e-11, dep_final, &rounds);
     if (threadIdx.x == 0) sm.par[29] = (double)nz;
     pc.mark(12);
     pc.count(1, rounds);
@@ -953,7 +963,9 @@ __device__ __noinline__ int leading_eigs(Smem<Real> &sm, int n, int k, const WT 
   // Rayleigh quotients d_j = q_j^T C q_j of the orthonormal columns (FP64
   // accuracy): any leading set of columns captures exactly the sum of its d_j, so
   // the columns are ordered by d_j and the rank rule reads them (sorted, in sm.Z).
-  // One warp per column, a lane per row, a fixed shuffle tree.
+  // One warp per column, a lane per row, a fixed shuffle tree.  A column the last
+  // Cholesky-QR pass zeroed (sm.cs[j] = 1 / L_jj = 0) gets -1, so it sorts after
+  // every non-zero column (its captured energy, 0, is what the rank rule adds).
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   if (sizeof(Real) == 8) {
     mat_cq(sm.Cg, sm.Q, sm.W, n, k);
@@ -961,7 +973,7 @@ __device__ __noinline__ int leading_eigs(Smem<Real> &sm, int n, int k, const WT 
       double d = 0.0;
       for (int i = lane; i < n; i += 32) d = fma(sm.Q[i * k + j], sm.W[i * k + j], d);
       for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-      if (lane == 0) sm.cs[j] = d;
+      if (lane == 0) sm.cs[j] = sm.cs[j] == 0.0 ? -1.0 : d;  // zeroed columns sort last
     }
   } else {
     // (C q_j)_i in double-float with q split into float hi + lo parts (in sm.W)
@@ -979,7 +991,7 @@ __device__ __noinline__ int leading_eigs(Smem<Real> &sm, int n, int k, const WT 
       for (int i = lane; i < n; i += 32)
         d = fma(sm.Q[i * k + j], df_dot(Cdf + i, n, qh + j, ql + j, k, n), d);
       for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-      if (lane == 0) sm.cs[j] = d;
+      if (lane == 0) sm.cs[j] = sm.cs[j] == 0.0 ? -1.0 : d;  // zeroed columns sort last
     }
   }
   __syncthreads();
@@ -1108,7 +1120,10 @@ __device__ void round_hosvd(Real *X, Real *T1, Real *T2, const int N[3], int R, 
     int kmax = n < R + kExtra ? n : R + kExtra;
     if (kmax > kOrthMax) kmax = kOrthMax;
     int k = (wU && wr > 0 && thr > 0.0 && wr + kExtra < kmax) ? wr + kExtra : kmax;
-    k = leading_eigs<Real, double>(sm, n, k, wU, R, wr, pc);
+    // truncating: dependent columns are zeroed (a zero column is never kept, and the
+    // full solve below follows if the rest miss the threshold); exact (no threshold):
+    // re-seeded, so the basis spans the whole space
+    k = leading_eigs<Real, double>(sm, n, k, wU, R, wr, pc, thr - dropped > 0.0 ? kDepZero : kDepReseed);
     pc.mark(6);
     bool met;
     r[m] = choose_rank<Real>(sm, n, k, thr - dropped, R, &met, tr);
@@ -1117,7 +1132,7 @@ __device__ void round_hosvd(Real *X, Real *T1, Real *T2, const int N[3], int R, 
       // iteration does not touch)
       for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) sm.Vr[idx] = (Real)sm.W[idx];
       __syncthreads();
-      k = leading_eigs<Real, Real>(sm, n, kmax, sm.Vr, k, k, pc);
+      k = leading_eigs<Real, Real>(sm, n, kmax, sm.Vr, k, k, pc, kDepReseed);
       pc.mark(6);
       r[m] = choose_rank<Real>(sm, n, k, thr - dropped, R, &met, tr);
     }
@@ -1831,14 +1846,15 @@ __global__ void __launch_bounds__(32, 13) tucker_eig_kernel(TuckerStepParams P, 
   if (kmax > kOrthMax) kmax = kOrthMax;
   int k = (wr > 0 && thr > 0.0 && wr + kExtra < kmax) ? wr + kExtra : kmax;
   pc.mark(4);
-  k = leading_eigs<Real, double>(sm, n, k, wU, R, wr, pc);
+  // truncating: dependent columns zeroed; exact: re-seeded (as in round_hosvd)
+  k = leading_eigs<Real, double>(sm, n, k, wU, R, wr, pc, thr > 0.0 ? kDepZero : kDepReseed);
   bool met;
   int r = choose_rank<Real>(sm, n, k, thr, R, &met, tr);
   pc.mark(7);
   if (!met && k < kmax) {
     for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) sm.Vr[idx] = (Real)sm.W[idx];
     __syncthreads();
-    k = leading_eigs<Real, Real>(sm, n, kmax, sm.Vr, k, k, pc);
+    k = leading_eigs<Real, Real>(sm, n, kmax, sm.Vr, k, k, pc, kDepReseed);
     r = choose_rank<Real>(sm, n, k, thr, R, &met, tr);
     pc.mark(8);
     pc.count(2, 1);
