@@ -100,6 +100,7 @@ struct TuckerMomentParams {
   int64_t c0;
   int N1, N2, N3, R;
   double w;
+  int stage;             // set by launch_tucker_moments: factors (1) / core (2) to shared memory
 };
 
 size_t tucker_scratch_elems(int N1, int N2, int N3, int R);

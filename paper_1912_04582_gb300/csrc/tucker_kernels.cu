@@ -59,6 +59,12 @@ constexpr int kRows = 16;  // first-mode rows one thread assembles per pass
 // table / first-mode row length padded to a multiple of kRows (zero-filled)
 __host__ __device__ inline int padN(int n) { return (n + kRows - 1) / kRows * kRows; }
 
+// p rounded up to a 16-byte boundary
+template <typename T>
+__device__ __forceinline__ T *align16(T *p) {
+  return reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
+}
+
 // Optional per-phase cycle counters (thread 0 of every CTA adds clock64 deltas
 // to P.phase[i] when P.phase is not null); no effect on the computation.
 struct PhaseClock {
@@ -158,8 +164,10 @@ __device__ Smem<Real> carve(unsigned char *base, int Nmax, int R) {
     off += sizeof(Real) * n;
     return p;
   };
-  s.rt = takeR((size_t)kTabs * padN(Nmax));
+  off = (off + 15) & ~size_t(15);  // the tables and the first-mode rows are read
+  s.rt = takeR((size_t)kTabs * padN(Nmax));  // by 16-byte loads
   for (int a = 0; a < 3; ++a) s.fac[a] = takeR((size_t)Nmax * R);
+  off = (off + 15) & ~size_t(15);
   s.u1 = takeR((size_t)(kTerms + 1) * R * padN(Nmax));
   s.cidx = reinterpret_cast<int *>(s.u1);  // the assembly's rows are dead during rounding
   s.cidx_cap = (int)((size_t)(kTerms + 1) * R * padN(Nmax) * sizeof(Real) / sizeof(int));
@@ -1186,6 +1194,31 @@ __device__ __forceinline__ Real *tabp(Smem<Real> &sm, int Nmax, int t) {
   return sm.rt + t * padN(Nmax);
 }
 
+// kRows consecutive values from 16-byte aligned shared memory by 16-byte loads
+// (the tables, the first-mode factor rows and row offsets are multiples of 16 bytes)
+template <typename Real>
+__device__ __forceinline__ void ld_rows(const Real *src, Real (&v)[kRows]) {
+  if constexpr (sizeof(Real) == 4) {
+    const float4 *s4 = reinterpret_cast<const float4 *>(src);
+#pragma unroll
+    for (int q = 0; q < kRows / 4; ++q) {
+      const float4 t = s4[q];
+      v[4 * q] = t.x;
+      v[4 * q + 1] = t.y;
+      v[4 * q + 2] = t.z;
+      v[4 * q + 3] = t.w;
+    }
+  } else {
+    const double2 *s2 = reinterpret_cast<const double2 *>(src);
+#pragma unroll
+    for (int q = 0; q < kRows / 2; ++q) {
+      const double2 t = s2[q];
+      v[2 * q] = t.x;
+      v[2 * q + 1] = t.y;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Fused assembly of f^{n+1} for one cell (Section 5, Lemma 1) into X, one pass.
 //
@@ -1371,7 +1404,10 @@ __device__ __noinline__ void assemble(const TuckerStepParams &P, int64_t c, cons
     // cubic Shakhov polynomial)
     {
       const Real fM12 = F1[i2] * F2[i3], Qp = Q1[i2] + Q2[i3], Vp = V1[i2] + V2[i3] - Real(2.5);
-      const Real *f0 = F0 + i10, *q0 = Q0 + i10, *v0 = V0 + i10;
+      Real f0[kRows], q0[kRows], v0[kRows];
+      ld_rows(F0 + i10, f0);
+      ld_rows(Q0 + i10, q0);
+      ld_rows(V0 + i10, v0);
 #pragma unroll
       for (int j = 0; j < kRows; ++j) acc[j] = f0[j] * fM12 * (Real(1) + (q0[j] + Qp) * (v0[j] + Vp));
     }
@@ -1396,6 +1432,7 @@ __device__ __noinline__ void assemble(const TuckerStepParams &P, int64_t c, cons
         acc[j] = fma(m, gf[min(i1, N1 - 1)] * g23, acc[j]);
       }
     }
+    pc.mark(5);
     // Tucker terms: f = U1 T2 in registers, then the weight
     for (int t = 0; t < nterm; ++t) {
       const AsmTerm tm = s_term[t];
@@ -1413,7 +1450,8 @@ __device__ __noinline__ void assemble(const TuckerStepParams &P, int64_t c, cons
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           if (k1 + q < tm.r1) {
-            const Real *ur = u1 + (k1 + q) * N1P;
+            Real ur[kRows];
+            ld_rows(u1 + (k1 + q) * N1P, ur);
 #pragma unroll
             for (int j = 0; j < kRows; ++j) sv[j] = fma(ur[j], tv[q], sv[j]);
           }
@@ -1421,7 +1459,8 @@ __device__ __noinline__ void assemble(const TuckerStepParams &P, int64_t c, cons
       }
       if (tm.face < 0) {  // Lemma-1 self weight
         const Real c0p = w0 + G1[i2] + G2[i3];
-        const Real *g0 = G0 + i10;
+        Real g0[kRows];
+        ld_rows(G0 + i10, g0);
 #pragma unroll
         for (int j = 0; j < kRows; ++j) acc[j] = fma(c0p + g0[j], sv[j], acc[j]);
         // outflow of faces whose normal is not a coordinate axis, inflow of
@@ -1453,7 +1492,8 @@ __device__ __noinline__ void assemble(const TuckerStepParams &P, int64_t c, cons
         const SlotDev &sl = s_slot[tm.face];
         const Real *tab = tabp(sm, Nm, 15 + tm.face);
         if (sl.axis == 0) {
-          const Real *tr = tab + i10;
+          Real tr[kRows];
+          ld_rows(tab + i10, tr);
 #pragma unroll
           for (int j = 0; j < kRows; ++j) acc[j] = fma(tr[j], sv[j], acc[j]);
         } else if (sl.axis > 0) {
@@ -1478,6 +1518,7 @@ __device__ __noinline__ void assemble(const TuckerStepParams &P, int64_t c, cons
       const int i1 = i10 + j;
       if (i1 < N1) __stcs(X + (int64_t)i1 * NP + p, acc[j]);  // streamed past L2
     }
+    pc.mark(3);
   }
   __syncthreads();
 }
@@ -1621,7 +1662,7 @@ constexpr int kAsmTB = 128;  // threads per CTA of the phase-major assembly kern
 // (one first-mode slab of G and of its mode-3 contraction), tables, factor rows.
 template <typename Real>
 __host__ __device__ inline size_t smem_asm_bytes(int Nmax, int R) {
-  const size_t stage = ((size_t)R * (R + Nmax) * sizeof(Real) + 7) / 8;  // doubles
+  const size_t stage = ((size_t)R * (R + Nmax) * sizeof(Real) + 15) / 16 * 2;  // doubles
   return sizeof(double) * (64 + stage) +
          sizeof(Real) * ((size_t)kTabs * padN(Nmax) + 3 * (size_t)Nmax * R +
                          (kTerms + 1) * (size_t)R * padN(Nmax)) +
@@ -1631,7 +1672,8 @@ __host__ __device__ inline size_t smem_asm_bytes(int Nmax, int R) {
 template <typename Real>
 __device__ Smem<Real> carve_asm(unsigned char *base, int Nmax, int R) {
   Smem<Real> s{};
-  const int stage = (int)(((size_t)R * (R + Nmax) * sizeof(Real) + 7) / 8);
+  // doubles; even, so that the tables start on a 16-byte boundary
+  const int stage = (int)(((size_t)R * (R + Nmax) * sizeof(Real) + 15) / 16) * 2;
   s.nmax = Nmax;
   s.par = reinterpret_cast<double *>(base);
   s.red = s.par + 32;
@@ -1644,7 +1686,7 @@ __device__ Smem<Real> carve_asm(unsigned char *base, int Nmax, int R) {
     s.fac[a] = r;
     r += (size_t)Nmax * R;
   }
-  s.u1 = r;
+  s.u1 = align16(r);
   return s;
 }
 
@@ -1658,13 +1700,15 @@ __global__ void __launch_bounds__(kAsmTB, sizeof(Real) == 8 ? 4 : 6)
   const int N[3] = {P.N1, P.N2, P.N3};
   const int64_t NN = (int64_t)P.N1 * P.N2 * P.N3;
   Real *T2buf = reinterpret_cast<Real *>(B.t2) + (size_t)blockIdx.x * B.t2_stride;
-  PhaseClock pc(nullptr);
+  PhaseClock pc(P.phase);
   for (int64_t j = blockIdx.x; j < B.cn; j += gridDim.x) {
     const int64_t c = B.c0 + j, jb = B.joff + j;
     cell_prologue<Real>(P, c, N, sm, s_slot, s_scale);
+    pc.mark(0);
     Real *X = reinterpret_cast<Real *>(B.X) + jb * NN;
     assemble<Real>(P, c, N, sm, s_slot, s_scale, X, T2buf, reinterpret_cast<const Real *>(B.T2all),
                    reinterpret_cast<const Real *>(B.U1all), pc);
+    pc.mark(3);
     if (threadIdx.x == 0) B.disc[jb] = 0.0;
   }
 }
@@ -1744,51 +1788,75 @@ __device__ __forceinline__ unsigned smem_u32(const void *p) {
 
 constexpr int kBulkWaitIters = 1 << 22;  // bound on the polls of a bulk copy's barrier
 
-// Copy `count` 8-byte Gram entries from global to shared memory with one bulk
-// asynchronous copy (cp.async.bulk, completion counted in bytes on an mbarrier)
-// and return the shared copy.  A plain copy is used when an address or the size
-// is not a multiple of 16 bytes.  The barrier is polled at most kBulkWaitIters
-// times; if the copy has not landed by then the block reads the global matrix
-// instead (same values) and sets bit 1 of *flag.  Called by every thread.
-__device__ __noinline__ const double *stage_gram(double *dst, const double *src, int count,
-                                                 int *flag) {
+// One global -> shared copy of `bytes` bytes (a multiple of 8) for stage_to_shared
+struct StagePiece {
+  void *dst;
+  const void *src;
+  unsigned bytes;
+};
+
+__device__ __forceinline__ bool bulk_ok(const StagePiece &q) {
+  return q.bytes > 0 && (q.bytes & 15u) == 0 &&
+         ((reinterpret_cast<uintptr_t>(q.src) | reinterpret_cast<uintptr_t>(q.dst)) & 15) == 0;
+}
+
+__device__ __forceinline__ void plain_copy(const StagePiece &q) {
+  double *d = static_cast<double *>(q.dst);
+  const double *v = static_cast<const double *>(q.src);
+  for (int i = threadIdx.x; i < (int)(q.bytes >> 3); i += blockDim.x) d[i] = v[i];
+}
+
+// Copy np pieces from global to shared memory.  Pieces whose addresses and size
+// are multiples of 16 bytes go by bulk asynchronous copies (cp.async.bulk; thread 0
+// issues them, completion is counted in bytes on one mbarrier, which every thread
+// polls at most kBulkWaitIters times); the others, meanwhile, by plain loads of
+// the block.  If the barrier has not completed within the limit, the bulk pieces
+// are copied again by plain loads (the same bytes, so a late bulk write changes
+// nothing) and bit 1 of *flag is set.  Called by every thread; ends with a barrier.
+template <int NP>
+__device__ __noinline__ void stage_to_shared(const StagePiece (&pc)[NP], int np, int *flag) {
   __shared__ __align__(8) unsigned long long s_bar;
-  const unsigned bytes = 8u * (unsigned)count;
-  const bool bulk =
-      ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0 &&
-      (bytes & 15u) == 0 && bytes > 0;
-  if (!bulk) {
-    for (int i = threadIdx.x; i < count; i += blockDim.x) dst[i] = src[i];
-    __syncthreads();
-    return dst;
-  }
+  unsigned tx = 0;
+  for (int q = 0; q < np; ++q)
+    if (bulk_ok(pc[q])) tx += pc[q].bytes;
   const unsigned bar = smem_u32(&s_bar);
-  if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  if (tx > 0) {
+    if (threadIdx.x == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tx)
+                   : "memory");
+      for (int q = 0; q < np; ++q)
+        if (bulk_ok(pc[q]))
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+              "[%3];" ::"r"(smem_u32(pc[q].dst)),
+              "l"(pc[q].src), "r"(pc[q].bytes), "r"(bar)
+              : "memory");
+    }
+  }
+  for (int q = 0; q < np; ++q)
+    if (!bulk_ok(pc[q])) plain_copy(pc[q]);
+  if (tx > 0) {
+    unsigned done = 0;
+    for (int it = 0; it < kBulkWaitIters && !done; ++it)
+      asm volatile(
+          "{\n\t.reg .pred p;\n\t"
+          "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+          "selp.u32 %0, 1, 0, p;\n\t}"
+          : "=r"(done)
+          : "r"(bar)
+          : "memory");
+    if (!__syncthreads_and(done)) {
+      if (threadIdx.x == 0) atomicOr(flag, 2);
+      for (int q = 0; q < np; ++q)
+        if (bulk_ok(pc[q])) plain_copy(pc[q]);
+    }
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(bar)
-        : "memory");
-  }
-  unsigned done = 0;
-  for (int it = 0; it < kBulkWaitIters && !done; ++it)
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(bar)
-        : "memory");
-  if (__syncthreads_and(done)) return dst;
-  if (threadIdx.x == 0) atomicOr(flag, 2);
-  return src;
 }
 
 // Eigen-solve and rank rule of mode m for cell j: one warp per cell.  On exit
@@ -1833,14 +1901,24 @@ __global__ void __launch_bounds__(32, 13) tucker_eig_kernel(TuckerStepParams P, 
   const int N[3] = {P.N1, P.N2, P.N3};
   const int64_t c = B.c0 + blockIdx.x, j = B.joff + blockIdx.x;  // j: buffer index
   const int n = N[m];
-  sm.Cg = stage_gram(Cs, B.C + j * (int64_t)Nm * Nm, n * n, P.flag);
+  // the Gram matrix and the previous factor (the warm start) to shared memory; the
+  // factor goes to a block the eigen-solver fills only after reading it (sm.Q on the
+  // mixed path, where the FP32 basis lives in sm.W; sm.W on the FP64 path)
+  double *Ws = sizeof(Real) == 4 ? sm.Q : sm.W;
+  {
+    const StagePiece pcs[2] = {
+        {Cs, B.C + j * (int64_t)Nm * Nm, 8u * (unsigned)(n * n)},
+        {Ws, P.cur.fac[m] + c * (int64_t)n * R, 8u * (unsigned)(n * R)}};
+    stage_to_shared(pcs, 2, P.flag);
+  }
+  sm.Cg = Cs;
   const double tr = gram_trace<Real>(sm, n);
   // ||X||^2 = trace of the first Gram matrix + the columns it left out (B.disc)
   if (m == 0 && threadIdx.x == 0) B.e[j] = tr + B.disc[j];
   __syncthreads();
   const double dropped = m == 0 ? B.disc[j] : 0.0;
   const double thr = P.tol * P.tol / 3.0 * B.e[j] - dropped;
-  const double *wU = P.cur.fac[m] + c * (int64_t)n * R;
+  const double *wU = Ws;
   const int wr = P.cur.rank[3 * c + m];
   int kmax = n < R + kExtra ? n : R + kExtra;
   if (kmax > kOrthMax) kmax = kOrthMax;
@@ -1870,7 +1948,7 @@ __global__ void __launch_bounds__(32, 13) tucker_eig_kernel(TuckerStepParams P, 
     B.disc[j] = d;
     if (m == 2 && P.err) P.err[c] = B.e[j] > 0.0 ? sqrt(d / B.e[j]) : 0.0;
   }
-  pc.mark(13);
+  pc.mark(7);
 }
 
 // Projection of mode m with the new factor: Y_{m+1} = Y_m x_m U_m^T (m = 0, 1,
@@ -1941,7 +2019,9 @@ __global__ void __launch_bounds__(kTB) tucker_expand_kernel(TuckerDev T, int64_t
 // velocity r: the same 19 raw sums as the full-grid path plus the outflow sums
 // of axis-aligned wall faces; FP64.
 __global__ void __launch_bounds__(128) tucker_moments_kernel(TuckerMomentParams P) {
-  extern __shared__ double msm[];  // [3][5][R] projections, [6][R] wall projections
+  // [3][4][R] projections, [6][R] wall projections, [3][4][Nx] powers of the
+  // velocities, then (P.stage) the cell's factors and core staged from global memory
+  extern __shared__ __align__(16) double msm[];
   __shared__ double s_out[32];
   __shared__ SlotDev s_slot[6];
   const int64_t c = P.c0 + blockIdx.x;
@@ -1954,20 +2034,48 @@ __global__ void __launch_bounds__(128) tucker_moments_kernel(TuckerMomentParams 
                          P.uref ? P.uref[us * c + 2] : 0.0};
   double *Sp = msm;            // [a][p][k], p = 0..3
   double *Sw = msm + 12 * R;   // [l][k] wall outflow projection for slot l
+  const double *Uc[3], *G = P.T.core + c * (int64_t)R * R * R;
+  for (int a = 0; a < 3; ++a) Uc[a] = P.T.fac[a] + c * (int64_t)N[a] * R;
+  const int Nx = max(N[0], max(N[1], N[2]));
+  // (xi_a,i - r_a)^p for p = 0..3, formed once per cell (not once per column k)
+  double *Pw = msm + ((18 * (size_t)R + 1) & ~size_t(1));  // [a][p][Nx]
+  for (int idx = tid; idx < 12 * Nx; idx += blockDim.x) {
+    const int i = idx % Nx, ap = idx / Nx, p = ap % 4, a = ap / 4;
+    double w = 1.0;
+    if (i < N[a]) {
+      const double v = P.xi[a][i] - ref[a];
+      for (int e = 0; e < p; ++e) w *= v;
+    }
+    Pw[idx] = w;
+  }
   if (tid < 6) s_slot[tid] = P.slot[c * 6 + tid];
-  __syncthreads();
+  if (P.stage) {  // bit 0: factors, bit 1: core (the leading r1 r2 r3 entries)
+    StagePiece pcs[4];
+    int np = 0;
+    size_t off = ((18 * (size_t)R + 1) & ~size_t(1)) + 12 * (size_t)Nx;
+    if (P.stage & 1)
+      for (int a = 0; a < 3; ++a) {
+        pcs[np++] = {msm + off, Uc[a], 8u * (unsigned)(N[a] * R)};
+        Uc[a] = msm + off;
+        off += ((size_t)N[a] * R + 1) & ~size_t(1);
+      }
+    if (P.stage & 2) {
+      const int g = r[0] * r[1] * r[2];
+      const int ge = (g & 1) && g < R * R * R ? g + 1 : g;  // 16-byte multiple when possible
+      pcs[np++] = {msm + off, G, 8u * (unsigned)ge};
+      G = msm + off;
+    }
+    stage_to_shared(pcs, np, P.flag);
+  } else {
+    __syncthreads();
+  }
   // S_a^(p)[k] = sum_i U_a[i][k] (xi_a,i - r_a)^p
   for (int idx = tid; idx < 12 * R; idx += blockDim.x) {
     const int k = idx % R, ap = idx / R, p = ap % 4, a = ap / 4;
     double s = 0.0;
     if (k < r[a]) {
-      const double *U = P.T.fac[a] + c * (int64_t)N[a] * R;
-      for (int i = 0; i < N[a]; ++i) {
-        const double v = P.xi[a][i] - ref[a];
-        double w = 1.0;
-        for (int e = 0; e < p; ++e) w *= v;
-        s = fma(U[(int64_t)i * R + k], w, s);
-      }
+      const double *U = Uc[a], *w = Pw + ap * Nx;
+      for (int i = 0; i < N[a]; ++i) s = fma(U[(int64_t)i * R + k], w[i], s);
     }
     Sp[idx] = s;
   }
@@ -1977,7 +2085,7 @@ __global__ void __launch_bounds__(128) tucker_moments_kernel(TuckerMomentParams 
     double s = 0.0;
     if (sl.kind == kWall && sl.axis >= 0 && k < r[sl.axis]) {
       const int a = sl.axis;
-      const double *U = P.T.fac[a] + c * (int64_t)N[a] * R;
+      const double *U = Uc[a];
       for (int i = 0; i < N[a]; ++i) s = fma(U[(int64_t)i * R + k], fmax(sl.sgn * P.xi[a][i], 0.0), s);
     }
     Sw[idx] = s;
@@ -1985,7 +2093,6 @@ __global__ void __launch_bounds__(128) tucker_moments_kernel(TuckerMomentParams 
   __syncthreads();
   // monomials (a1, a2, a3) of the 19 sums; thread j < 19 computes sum j,
   // threads 19..24 the wall outflows
-  const double *G = P.T.core + c * (int64_t)R * R * R;
   if (tid < 25) {
     const double *w0, *w1, *w2;
     const int mono[19][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0}, {0, 2, 0},
@@ -2344,9 +2451,21 @@ void launch_tucker_maxwellians(TuckerDev T, const double *n, const double *u, co
   tucker_maxwellian_kernel<<<(unsigned)nc, 32, 0, s>>>(T, n, u, Tc, xi0, xi1, xi2, N1, N2, N3, R);
 }
 
+// The cell's factors (and core) are staged in shared memory when they fit in the
+// default 48 KB with the projections.
 void launch_tucker_moments(const TuckerMomentParams &p, cudaStream_t s) {
-  const size_t smem = sizeof(double) * 18 * (size_t)p.R;
-  tucker_moments_kernel<<<(unsigned)(p.nc - p.c0), 128, smem, s>>>(p);
+  const int N[3] = {p.N1, p.N2, p.N3};
+  const int Nx = std::max(N[0], std::max(N[1], N[2]));
+  const size_t base = ((18 * (size_t)p.R + 1) & ~size_t(1)) + 12 * (size_t)Nx;
+  size_t fac = 0;
+  for (int a = 0; a < 3; ++a) fac += ((size_t)N[a] * p.R + 1) & ~size_t(1);
+  const size_t core = (size_t)p.R * p.R * p.R + 1;
+  constexpr size_t kLimit = 48 * 1024 / sizeof(double);
+  TuckerMomentParams q = p;
+  q.stage = base + fac + core <= kLimit ? 3 : (base + fac <= kLimit ? 1 : 0);
+  const size_t smem =
+      sizeof(double) * (q.stage == 3 ? base + fac + core : (q.stage == 1 ? base + fac : base));
+  tucker_moments_kernel<<<(unsigned)(p.nc - p.c0), 128, smem, s>>>(q);
 }
 
 }  // namespace dvm

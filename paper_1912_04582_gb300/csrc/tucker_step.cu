@@ -271,10 +271,10 @@ void tucker_free(dvm_ctx *C) {
     long long h[16] = {0};
     if (cudaMemcpy(h, S->phase, sizeof h, cudaMemcpyDeviceToHost) == cudaSuccess) {
       // fused kernel / eigen-solve kernel
-      static const char *names[16] = {"prologue",    "reseeds",    "retries",    "assemble",
-                                      "energy|setup", "gram",      "eig_init",   "rank",
+      static const char *names[16] = {"prologue",    "reseeds",    "retries",    "assemble|asm_terms",
+                                      "energy|setup", "gram|asm_eq",      "eig_init",   "rank",
                                       "project|retry", "eig_cq32", "eig_orth32", "eig_cq64",
-                                      "eig_orth64",  "contract|store", "rayleigh", "sort"};
+                                      "eig_orth64",  "contract",   "rayleigh",   "sort"};
       std::fprintf(stderr, "tucker phases (SM cycles summed over CTAs; reseeds, retries: counts):");
       for (int i = 0; i < 16; ++i) std::fprintf(stderr, " %s=%lld", names[i], h[i]);
       std::fprintf(stderr, "\n");
