@@ -1951,6 +1951,46 @@ __global__ void __launch_bounds__(32, 13) tucker_eig_kernel(TuckerStepParams P, 
   pc.mark(7);
 }
 
+// out = T x_m V^T for m = 0, 1 (V: n x r, row-major): a thread takes one position of
+// the other two indices and forms all r outputs there, so each input fibre is read
+// once; each output is the same fma chain as project()'s (a = 0 .. n-1).
+template <typename Real, int KM>
+__device__ void project_fibres(const Real *T, const int D[3], int m, int r, const Real *V,
+                               Real *out) {
+  const int n = D[m];
+  const int npos = m == 0 ? D[1] * D[2] : D[0] * D[2];
+  const int64_t plane = (int64_t)D[1] * D[2];
+  for (int pos = threadIdx.x; pos < npos; pos += blockDim.x) {
+    int64_t base, stride, obase, ostride;
+    if (m == 0) {
+      base = pos;
+      stride = plane;
+      obase = pos;
+      ostride = plane;
+    } else {
+      const int i0 = pos / D[2], i2 = pos - i0 * D[2];
+      base = (int64_t)i0 * plane + i2;
+      stride = D[2];
+      obase = (int64_t)i0 * r * D[2] + i2;
+      ostride = D[2];
+    }
+    Real s[KM];
+#pragma unroll
+    for (int k = 0; k < KM; ++k) s[k] = 0;
+    for (int a = 0; a < n; ++a) {
+      const Real x = T[base + a * stride];
+      const Real *v = V + a * r;
+#pragma unroll
+      for (int k = 0; k < KM; ++k)
+        if (k < r) s[k] = fma(v[k], x, s[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < KM; ++k)
+      if (k < r) out[obase + k * ostride] = s[k];
+  }
+  __syncthreads();
+}
+
 // Projection of mode m with the new factor: Y_{m+1} = Y_m x_m U_m^T (m = 0, 1,
 // working precision), or the core G = Y_2 x_3 U_3^T (m = 2, FP64 accumulation)
 template <typename Real>
@@ -1966,15 +2006,17 @@ __global__ void __launch_bounds__(kTB) tucker_proj_kernel(TuckerStepParams P, Tu
   const double *U = P.nxt.fac[m] + c * (int64_t)n * R;
   const Real *src = split_src<Real>(B, j, m, R, N);
   if (m < 2) {
-    Smem<Real> sm{};
-    sm.Vr = reinterpret_cast<Real *>(smem_raw);
+    Real *V = reinterpret_cast<Real *>(smem_raw);
     for (int idx = threadIdx.x; idx < n * r; idx += blockDim.x) {
       const int i = idx / r, k = idx - i * r;
-      sm.Vr[idx] = (Real)U[(int64_t)i * R + k];
+      V[idx] = (Real)U[(int64_t)i * R + k];
     }
     __syncthreads();
     Real *dst = const_cast<Real *>(split_src<Real>(B, j, m + 1, R, N));
-    project<Real>(src, D, m, r, r, sm, dst);
+    if (r <= 8)
+      project_fibres<Real, 8>(src, D, m, r, V, dst);
+    else
+      project_fibres<Real, kOrthMax>(src, D, m, r, V, dst);
   } else {
     double *Us = reinterpret_cast<double *>(smem_raw);
     for (int idx = threadIdx.x; idx < n * r; idx += blockDim.x) {
