@@ -15,6 +15,10 @@ struct TuckerDev {
   int *rank;      // [nc][3]
 };
 
+// per-cell parameters of the assembly: n, u (3), T, q (3), dt nu, the Shakhov
+// coefficient, the Maxwellian amplitude
+constexpr int kCellPar = 12;
+
 struct TuckerStepParams {
   TuckerDev cur;         // state at t^n (read)
   TuckerDev nxt;         // state at t^{n+1} (written)
@@ -26,6 +30,8 @@ struct TuckerStepParams {
   const double *finit;   // mode 1: [nc][N^3] tensors to compress
   double *err;           // [nc] relative truncation error of the last rounding (may be null)
   long long *phase;      // [16] optional per-phase cycle counters (null: off)
+  const double *cellpar; // [nc][kCellPar] per-cell parameters of the assembly (null: the
+                         // assembly forms them from the sums)
   int *flag;
   void *scratch;         // per-CTA work space
   size_t scratch_stride; // elements (of the kernel's scalar type) per CTA
@@ -50,6 +56,8 @@ struct TuckerSplitBufs {
   int asm_grid;  // assembly CTAs (persistent over the chunk)
   int64_t c0, cn;  // cells [c0, c0 + cn) of this launch
   int64_t joff;    // their first buffer index (buffers hold one chunk)
+  double *cellpar; // [nc][kCellPar] per-cell parameters, formed at the start of the step
+  double *macro;   // [nc][8] macroparameters of the current state (may be null)
 };
 
 // Extra streams and fork / join events of the phase-major step (optional):

@@ -1523,6 +1523,41 @@ __device__ __noinline__ void assemble(const TuckerStepParams &P, int64_t c, cons
   __syncthreads();
 }
 
+// The cell's parameters from its moment sums (Section 4 item 5): n, u, T, q
+// (out[0..7]), dt nu with nu = delta n T^(1 - omega) (out[8]), the Shakhov
+// coefficient (8/5)(1 - Pr)/(n T^2) (out[9]) and the Maxwellian amplitude
+// n^(1/3) / sqrt(pi T) of each per-axis factor (out[10]).  Sets bit 0 of *P.flag
+// for a non-physical state.
+template <typename Params>
+__device__ void cell_params(const double *S, const Params &P, double *out) {
+  CellMacro m;
+  macro_from_sums(S, P.w, m);
+  if (m.bad) atomicOr(P.flag, 1);
+  const double nu = P.delta * m.n * pow(m.T, 1.0 - P.omega);
+  out[0] = m.n;
+  for (int a = 0; a < 3; ++a) {
+    out[1 + a] = m.u[a];
+    out[5 + a] = m.q[a];
+  }
+  out[4] = m.T;
+  out[8] = P.dt * nu;
+  out[9] = 1.6 * (1.0 - P.Pr) / (m.n * m.T * m.T);
+  out[10] = cbrt(m.n) / sqrt(kPi * m.T);
+}
+
+// Per-cell parameters of every cell, one thread per cell, and (macro != null) the
+// macroparameters [nc][8] (n, u, T, q) of the current state
+__global__ void tucker_cellpar_kernel(TuckerStepParams P, double *cellpar, double *macro) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= P.nc) return;
+  double par[kCellPar];
+  cell_params(P.sums + c * kSums, P, par);
+  par[11] = 0.0;
+  for (int k = 0; k < kCellPar; ++k) cellpar[c * kCellPar + k] = par[k];
+  if (macro)
+    for (int k = 0; k < 8; ++k) macro[c * 8 + k] = par[k];
+}
+
 // Per-cell prologue of the assembly: slots, wall-density scales, the cell's
 // macroparameters (moments of f^n, Section 4 item 5) and the per-axis tables of
 // the Maxwellian, Shakhov and face weights (zero-padded to padN(Nmax)).
@@ -1537,20 +1572,10 @@ __device__ void cell_prologue(const TuckerStepParams &P, int64_t c, const int N[
     s_slot[tid] = P.slot[c * 6 + tid];
     s_scale[tid] = (s_slot[tid].kind == kWall) ? -S[16 + tid] / s_slot[tid].wall_den : 1.0;
   }
-  if (tid == 0) {
-    CellMacro m;
-    macro_from_sums(S, P.w, m);
-    if (m.bad) atomicOr(P.flag, 1);
-    const double nu = P.delta * m.n * pow(m.T, 1.0 - P.omega);
-    sm.par[0] = m.n;
-    for (int a = 0; a < 3; ++a) {
-      sm.par[1 + a] = m.u[a];
-      sm.par[5 + a] = m.q[a];
-    }
-    sm.par[4] = m.T;
-    sm.par[8] = P.dt * nu;
-    sm.par[9] = 1.6 * (1.0 - P.Pr) / (m.n * m.T * m.T);
-    sm.par[10] = cbrt(m.n) / sqrt(kPi * m.T);
+  if (P.cellpar) {  // formed for all cells at the start of the step
+    if (tid < 11) sm.par[tid] = P.cellpar[c * kCellPar + tid];
+  } else if (tid == 0) {
+    cell_params(S, P, sm.par);
   }
   __syncthreads();
   {
@@ -2356,8 +2381,15 @@ int launch_split_TS(const TuckerStepParams &p, TuckerSplitBufs b, int64_t chunk,
   if (cap == cudaStreamCaptureStatusNone && !(prepare_split_TS<Real, TS>(p.Nmax, p.R) & 2))
     return -1;
   const SplitSmem<Real, TS> z(p.Nmax, p.R);
+  // per-cell parameters (and the macroparameters) of every cell, one thread each,
+  // so that no assembly block forms them serially
+  T(kKMoments, true, s);
+  tucker_cellpar_kernel<<<(unsigned)((p.nc + 127) / 128), 128, 0, s>>>(p, b.cellpar, b.macro);
+  T(kKMoments, false, s);
+  TuckerStepParams q = p;
+  q.cellpar = b.cellpar;
   T(kKContract, true, s);
-  tucker_t2_kernel<Real><<<(unsigned)(p.nc < 65535 * 16 ? p.nc : 65535 * 16), kAsmTB, z.asm_, s>>>(p, b);
+  tucker_t2_kernel<Real><<<(unsigned)(p.nc < 65535 * 16 ? p.nc : 65535 * 16), kAsmTB, z.asm_, s>>>(q, b);
   T(kKContract, false, s);
   // with extra streams (and no per-launch timing), each chunk's cell ranges run
   // their chains concurrently: one range's FP64-bound eigen-solves overlap another
@@ -2386,7 +2418,7 @@ int launch_split_TS(const TuckerStepParams &p, TuckerSplitBufs b, int64_t chunk,
       bw.c0 = c0 + a;
       bw.cn = e - a;
       bw.joff = a;
-      split_chain<Real, TS>(p, bw, z, w == 0 ? s : ss->sx[w - 1], T, mp);
+      split_chain<Real, TS>(q, bw, z, w == 0 ? s : ss->sx[w - 1], T, mp);
     }
     // the next chunk reuses the buffers: every range must be done
     if (ways > 1 && c0 + chunk < p.nc && !(join() && fork())) return -1;
@@ -2475,7 +2507,7 @@ size_t tucker_split_bytes_per_cell(int N1, int N2, int N3, int R, int Nmax, bool
 
 size_t tucker_split_t2all_bytes_per_cell(int N1, int N2, int N3, int R, bool fp64) {
   const size_t es = fp64 ? sizeof(double) : sizeof(float);
-  return es * (size_t)R * ((size_t)N2 * N3 + padN(N1));
+  return es * (size_t)R * ((size_t)N2 * N3 + padN(N1)) + sizeof(double) * kCellPar;
 }
 
 int launch_tucker_expand(const TuckerDev &T, int64_t c0, int64_t ncell, int N1, int N2, int N3,

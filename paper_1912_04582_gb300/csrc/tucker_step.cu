@@ -380,10 +380,7 @@ int enqueue_one_step(dvm_ctx *C, TuckerStepParams &p) {
   m.sums_prev = C->d_sums[S->scur];
   m.respart = C->d_respart;
   int lrc;
-  if (S->split) {
-    lt(kKMoments, true, C->stream);
-    launch_macro_from_sums(C->d_sums[S->scur], C->d_macro, C->nc, C->w, C->stream);
-    lt(kKMoments, false, C->stream);
+  if (S->split) {  // the split step forms the macroparameters (S->sb.macro) first
     lrc = launch_tucker_split_step(p, S->sb, S->chunk, S->fp64, C->stream, &lt, &S->ss, &m);
   } else {
     lt(kKFusedStep, true, C->stream);
@@ -436,10 +433,14 @@ int alloc_split(dvm_ctx *C) {
   b.t2 = nullptr;  // the assembly reads the all-cell contractions instead
   b.t2_stride = 0;
   b.asm_grid = asm_grid;
+  b.cellpar = reinterpret_cast<double *>(q);  // first: 8-byte aligned
+  q += sizeof(double) * kCellPar * (size_t)C->nc;
+  b.macro = C->d_macro;
   b.T2all = q;
   q += es * (size_t)C->nc * S->R * C->N[1] * C->N[2];
   b.U1all = q;
-  q += t2all * C->nc - es * (size_t)C->nc * S->R * C->N[1] * C->N[2];
+  q += t2all * C->nc - es * (size_t)C->nc * S->R * C->N[1] * C->N[2] -
+       sizeof(double) * kCellPar * (size_t)C->nc;
   q = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(q) + 255) & ~uintptr_t(255));
   b.X = q;
   q += es * chunk * C->N[0] * C->N[1] * C->N[2];
