@@ -1978,10 +1978,13 @@ __global__ void __launch_bounds__(32, 13) tucker_eig_kernel(TuckerStepParams P, 
 
 // out = T x_m V^T for m = 0, 1 (V: n x r, row-major): a thread takes one position of
 // the other two indices and forms all r outputs there, so each input fibre is read
-// once; each output is the same fma chain as project()'s (a = 0 .. n-1).
-template <typename Real, int KM>
+// once; each output is the same fma chain as project()'s (a = 0 .. n-1).  KM >= r
+// bounds the accumulators; Exact (r == KM) drops the per-output guards, so that no
+// predicated-off FP64 instruction takes a slot of the FP64 pipe.
+template <typename Real, int KM, bool Exact>
 __device__ void project_fibres(const Real *T, const int D[3], int m, int r, const Real *V,
                                Real *out) {
+  if (Exact) r = KM;
   const int n = D[m];
   const int npos = m == 0 ? D[1] * D[2] : D[0] * D[2];
   const int64_t plane = (int64_t)D[1] * D[2];
@@ -2007,13 +2010,30 @@ __device__ void project_fibres(const Real *T, const int D[3], int m, int r, cons
       const Real *v = V + a * r;
 #pragma unroll
       for (int k = 0; k < KM; ++k)
-        if (k < r) s[k] = fma(v[k], x, s[k]);
+        if (Exact || k < r) s[k] = fma(v[k], x, s[k]);
     }
 #pragma unroll
     for (int k = 0; k < KM; ++k)
-      if (k < r) out[obase + k * ostride] = s[k];
+      if (Exact || k < r) out[obase + k * ostride] = s[k];
   }
   __syncthreads();
+}
+
+// project_fibres with the accumulator count fixed to r for r <= 8
+template <typename Real>
+__device__ void project_fibres_r(const Real *T, const int D[3], int m, int r, const Real *V,
+                                 Real *out) {
+  switch (r) {
+    case 1: project_fibres<Real, 1, true>(T, D, m, r, V, out); break;
+    case 2: project_fibres<Real, 2, true>(T, D, m, r, V, out); break;
+    case 3: project_fibres<Real, 3, true>(T, D, m, r, V, out); break;
+    case 4: project_fibres<Real, 4, true>(T, D, m, r, V, out); break;
+    case 5: project_fibres<Real, 5, true>(T, D, m, r, V, out); break;
+    case 6: project_fibres<Real, 6, true>(T, D, m, r, V, out); break;
+    case 7: project_fibres<Real, 7, true>(T, D, m, r, V, out); break;
+    case 8: project_fibres<Real, 8, true>(T, D, m, r, V, out); break;
+    default: project_fibres<Real, kOrthMax, false>(T, D, m, r, V, out); break;
+  }
 }
 
 // Projection of mode m with the new factor: Y_{m+1} = Y_m x_m U_m^T (m = 0, 1,
@@ -2038,10 +2058,7 @@ __global__ void __launch_bounds__(kTB) tucker_proj_kernel(TuckerStepParams P, Tu
     }
     __syncthreads();
     Real *dst = const_cast<Real *>(split_src<Real>(B, j, m + 1, R, N));
-    if (r <= 8)
-      project_fibres<Real, 8>(src, D, m, r, V, dst);
-    else
-      project_fibres<Real, kOrthMax>(src, D, m, r, V, dst);
+    project_fibres_r<Real>(src, D, m, r, V, dst);
   } else {
     double *Us = reinterpret_cast<double *>(smem_raw);
     for (int idx = threadIdx.x; idx < n * r; idx += blockDim.x) {

@@ -30,6 +30,8 @@ struct TuckerState {
   long long *phase = nullptr;  // [16] per-phase cycles (DVM_TUCKER_PHASES set)
   int max_grid = 0;             // CTAs the scratch is sized for
   bool tuned = false;           // grid picked by the autotuner
+  bool retuned = false;         // picked again once the state has developed
+  int64_t tuned_step = 0;       // step counter at the first tuning
   float tune_ms[5] = {0, 0, 0, 0, 0};  // [0] phase-major step, [1..4] fused kernel per CTAs/SM
   bool split = false;                  // phase-major variant chosen
   int fit = 3;                         // variants whose kernels fit: 1 fused, 2 phase-major
@@ -478,6 +480,8 @@ void free_split(dvm_ctx *C) {
   S->chunk = 0;
 }
 
+constexpr int64_t kRetuneSteps = 16;
+
 // Autotuner, on the first step: time the fused step kernel once for each
 // resident-CTAs-per-SM choice the scratch allows and, unless the variant is
 // fixed, the phase-major step; keep the fastest.  Tuning launches write into the
@@ -487,6 +491,7 @@ void free_split(dvm_ctx *C) {
 int autotune(dvm_ctx *C) {
   TuckerState *S = C->tucker;
   S->tuned = true;
+  S->tuned_step = C->steps;
   const int variant = C->opts.variant;
   int sms = 1;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, C->device);
@@ -529,7 +534,7 @@ int autotune(dvm_ctx *C) {
   S->grid = best_grid;
   int rc = DVM_OK;
   if (variant != DVM_VARIANT_FUSED && (phased || !std::getenv("DVM_NO_SPLIT"))) {
-    rc = alloc_split(C);
+    rc = S->split_mem ? DVM_OK : alloc_split(C);
     if (rc == DVM_OK) {
       const float ms = timed([&] {
         return launch_tucker_split_step(p, S->sb, S->chunk, S->fp64, C->stream, nullptr, &S->ss);
@@ -553,7 +558,17 @@ int autotune(dvm_ctx *C) {
 int tucker_step(dvm_ctx *C, int32_t nsteps, double *residual_out) {
   (void)residual_out;
   TuckerState *S = C->tucker;
-  if (!S->tuned) {
+  // the variant is picked on the first step and once more after kRetuneSteps
+  // steps, when the ranks (and with them the cost of each variant) have developed
+  if (!S->tuned || (!S->retuned && C->steps >= S->tuned_step + kRetuneSteps)) {
+    if (S->tuned) {
+      S->retuned = true;
+      if (S->graph) {  // re-captured with the variant chosen now
+        DVM_CUDA_TRY(cudaStreamSynchronize(S->gstream));
+        cudaGraphExecDestroy(S->graph);
+        S->graph = nullptr;
+      }
+    }
     int rc = autotune(C);
     if (rc != DVM_OK) return rc;
   }
