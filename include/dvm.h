@@ -172,7 +172,10 @@ int dvm_get_tucker(dvm_ctx *ctx, int32_t *ranks, double *core, double *u1, doubl
  * If residual_out is not NULL the call synchronises and stores the residual
  * of the last step, ||U^{n+1}-U^n||_{2,V} / (dt ||U^n||_{2,V}) with
  * U = (n, n u, sum w |xi|^2 f) per cell; with NULL the call only enqueues.
- * Errors: NONPHYSICAL (n <= 0 or T <= 0 seen in a cell), CUDA. */
+ * Errors: NONPHYSICAL (n <= 0 or T <= 0 seen in a cell), TIMEOUT (Tucker: a
+ * bulk shared-memory copy did not complete within its bounded wait; the block
+ * re-read the data with plain loads, so the state is still the correct step),
+ * CUDA.  Both device flags are reported only by calls with residual_out. */
 int dvm_step(dvm_ctx *ctx, int32_t nsteps, double *residual_out);
 
 /* Macroparameters of every cell (Section 2): host arrays out[n_cell][8] =
