@@ -650,11 +650,90 @@ __device__ __noinline__ void gram_w32(const Real *T, const int D[3], int m, Smem
   __syncthreads();
 }
 
-// n <= 32 with 256 threads: gram_w32; otherwise the 16 x 16 thread grid (TS = 2
-// covers n <= 32, TS = 4 covers n <= 64)
+// Gram matrix of a second- or third-mode unfolding with n <= 32 rows by 256 threads:
+// one thread per entry of the upper triangle (at most three each), each a sequential
+// sum over the columns in order — double-float with exact products, renormalised
+// every 16 products, on the mixed path; FP64 FMAs on the FP64 path — with the columns
+// staged 32 at a time in sm.tile.  The result does not depend on the block size.  These
+// unfoldings are small (r1 N3 or r1 r2 columns), and gram_w32's 40 register
+// accumulators per thread would hold the kernel to two blocks per SM.
+template <typename Real>
+__device__ __noinline__ void gram_seq(const Real *T, const int D[3], int m, Smem<Real> &sm) {
+  constexpr bool f32 = sizeof(Real) == 4;
+  const int n = D[m];
+  const int cols = (D[0] * D[1] * D[2]) / n;
+  const int ne = n * (n + 1) / 2;
+  int ea[3], eb[3];
+  Real hi[3], lo[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const int e = threadIdx.x + 256 * q;
+    ea[q] = -1;
+    eb[q] = -1;
+    hi[q] = lo[q] = Real(0);
+    if (e < ne) {
+      int a = 0, t = e;  // e -> (a <= b), row-major over the upper triangle
+      while (t >= n - a) {
+        t -= n - a;
+        ++a;
+      }
+      ea[q] = a;
+      eb[q] = a + t;
+    }
+  }
+  for (int j0 = 0; j0 < cols; j0 += kKC) {
+    for (int idx = threadIdx.x; idx < n * kKC; idx += blockDim.x) {
+      const int a = idx / kKC, jj = idx - a * kKC, j = j0 + jj;
+      Real v = 0;
+      if (j < cols) {
+        int64_t addr;
+        if (m == 1) {
+          const int kk = j / D[2], i = j - kk * D[2];
+          addr = ((int64_t)kk * D[1] + a) * D[2] + i;
+        } else {
+          addr = (int64_t)j * D[2] + a;
+        }
+        v = T[addr];
+      }
+      sm.tile[a * kKP2 + jj] = v;
+    }
+    __syncthreads();
+    const int cn = cols - j0 < kKC ? cols - j0 : kKC;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      if (ea[q] < 0) continue;
+      const Real *xa = sm.tile + ea[q] * kKP2, *xb = sm.tile + eb[q] * kKP2;
+      for (int jj = 0; jj < cn; ++jj) {
+        if constexpr (f32) {
+          df_acc(xa[jj], xb[jj], hi[q], lo[q]);
+          if ((jj & 15) == 15 || jj == cn - 1) {  // fast two-sum renormalisation
+            const float sum = __fadd_rn(hi[q], lo[q]);
+            lo[q] = __fsub_rn(lo[q], __fsub_rn(sum, hi[q]));
+            hi[q] = sum;
+          }
+        } else {
+          hi[q] = fma(xa[jj], xb[jj], hi[q]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    if (ea[q] < 0) continue;
+    gram_store<Real>(sm.C, ea[q] * n + eb[q], hi[q], lo[q]);
+    gram_store<Real>(sm.C, eb[q] * n + ea[q], hi[q], lo[q]);
+  }
+  __syncthreads();
+}
+
+// n <= 32 with 256 threads: gram_w32 (first mode) or gram_seq (second and third
+// modes); otherwise the 16 x 16 thread grid (TS = 2 covers n <= 32, TS = 4 covers n <= 64)
 template <typename Real, int TS>
 __device__ void gram(const Real *T, const int D[3], int m, Smem<Real> &sm, double skip_rel = 0.0) {
-  if (D[m] <= 32 && blockDim.x == 256) {
+  if (m >= 1 && D[m] <= 32 && blockDim.x == 256) {
+    gram_seq<Real>(T, D, m, sm);
+  } else if (D[m] <= 32 && blockDim.x == 256) {
     gram_w32<Real>(T, D, m, sm, skip_rel);
   } else {
     gram_tiled<Real, TS>(T, D, m, sm);
@@ -1797,6 +1876,28 @@ __global__ void __launch_bounds__(kTB) tucker_gram_kernel(TuckerStepParams P, Tu
   for (int i = threadIdx.x; i < n * n; i += blockDim.x) out[i] = sm.C[i];
 }
 
+// Gram matrix of mode m >= 1 (second / third) of cell j's tensor when N_m <= 32, into
+// B.C[j] (gram_seq: few registers, so many blocks per SM)
+template <typename Real>
+__global__ void __launch_bounds__(kTB, 4) tucker_gram_small_kernel(TuckerStepParams P,
+                                                                    TuckerSplitBufs B, int m) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int Nm = P.Nmax;
+  Smem<Real> sm{};
+  sm.par = reinterpret_cast<double *>(smem_raw);
+  sm.red = sm.par + 32;
+  sm.C = sm.red + 32;
+  sm.tile = reinterpret_cast<Real *>(sm.C + (size_t)Nm * Nm);
+  const int N[3] = {P.N1, P.N2, P.N3};
+  const int64_t j = blockIdx.x, c = B.c0 + j, jb = B.joff + j;
+  int D[3];
+  split_dims(B, P.nxt, c, m, N, D);
+  gram_seq<Real>(split_src<Real>(B, jb, m, P.R, N), D, m, sm);
+  const int n = D[m];
+  double *out = B.C + jb * (int64_t)Nm * Nm;
+  for (int i = threadIdx.x; i < n * n; i += blockDim.x) out[i] = sm.C[i];
+}
+
 template <typename Real>
 __host__ __device__ inline size_t smem_eig_bytes(int Nmax, int R) {
   const int K = sub_k(Nmax, R);
@@ -2292,7 +2393,7 @@ int raise_smem_optin(K kernel, size_t smem, size_t &opted) {
 
 template <typename Real, int TS>
 struct OptIn {
-  static size_t step, expand, asm_, gram, eig, proj, t2;
+  static size_t step, expand, asm_, gram, gram_small, eig, proj, t2;
 };
 template <typename Real, int TS>
 size_t OptIn<Real, TS>::step = 0;
@@ -2302,6 +2403,8 @@ template <typename Real, int TS>
 size_t OptIn<Real, TS>::asm_ = 0;
 template <typename Real, int TS>
 size_t OptIn<Real, TS>::gram = 0;
+template <typename Real, int TS>
+size_t OptIn<Real, TS>::gram_small = 0;
 template <typename Real, int TS>
 size_t OptIn<Real, TS>::eig = 0;
 template <typename Real, int TS>
@@ -2328,8 +2431,9 @@ int launch_step_T(const TuckerStepParams &p, int grid, cudaStream_t s) {
 
 template <typename Real, int TS>
 struct SplitSmem {
-  size_t asm_, gram, eig, proj;
+  size_t asm_, gram, gram_small, eig, proj;
   SplitSmem(int Nmax, int R) {
+    gram_small = sizeof(double) * (64 + (size_t)Nmax * Nmax) + sizeof(Real) * 32 * kTileRow + 64;
     asm_ = smem_asm_bytes<Real>(Nmax, R);
     gram = sizeof(double) * (64 + (size_t)Nmax * Nmax) +
            2 * sizeof(Real) * (size_t)(Nmax > 32 ? Nmax : 32) * kTileRow +
@@ -2351,6 +2455,7 @@ int prepare_split_TS(int Nmax, int R) {
   if (raise_smem_optin(tucker_asm_kernel<Real>, z.asm_, O::asm_) == 0 &&
       raise_smem_optin(tucker_t2_kernel<Real>, z.asm_, O::t2) == 0 &&
       raise_smem_optin(tucker_gram_kernel<Real, TS>, z.gram, O::gram) == 0 &&
+      raise_smem_optin(tucker_gram_small_kernel<Real>, z.gram_small, O::gram_small) == 0 &&
       raise_smem_optin(tucker_eig_kernel<Real>, z.eig, O::eig) == 0 &&
       raise_smem_optin(tucker_proj_kernel<Real>, z.proj, O::proj) == 0)
     mask |= 2;
@@ -2369,7 +2474,10 @@ void split_chain(const TuckerStepParams &p, const TuckerSplitBufs &b, const Spli
   for (int m = 0; m < 3; ++m) {
     const int gc = m == 0 ? kKGram0 : kKGram12;
     T(gc, true, s);
-    tucker_gram_kernel<Real, TS><<<(unsigned)b.cn, kTB, z.gram, s>>>(p, b, m);
+    if (m >= 1 && p.Nmax <= 32)  // every cell's N_m <= 32: gram_seq in a light kernel
+      tucker_gram_small_kernel<Real><<<(unsigned)b.cn, kTB, z.gram_small, s>>>(p, b, m);
+    else
+      tucker_gram_kernel<Real, TS><<<(unsigned)b.cn, kTB, z.gram, s>>>(p, b, m);
     T(gc, false, s);
     T(kKEig, true, s);
     tucker_eig_kernel<Real><<<(unsigned)b.cn, 32, z.eig, s>>>(p, b, m);
