@@ -1,6 +1,6 @@
 """Full-grid FP64 CUDA path vs the FP64 CPU oracle, element by element, through the C ABI.
 
-Tolerance (north-star): relative L2 over all (cell, node) <= 1e-12 on f, and the same on
+Tolerance (the FP64 path's bar): relative L2 over all (cell, node) <= 1e-12 on f, and the same on
 each macroparameter (n, u, T, q; u and q normalised by max(|u|, 1e-3), max(|q|, 1e-6)
 where they are ~0).
 """
