@@ -7,6 +7,7 @@ the textbook upwind scheme in the free-molecular limit, steadiness of a uniform 
 stream, conservation in closed boxes, and invariance under renumbering.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -186,6 +187,41 @@ def test_collision_frequency_law(oracle_lib):
         p = 0.5 * n * T
         mu = 0.37 / math.sqrt(math.pi) * T ** 0.81
         assert abs(o.nu(n, T) - p / mu) < 1e-13 * (p / mu)
+
+
+def _figures():
+    path = os.path.join(os.path.dirname(__file__), "golden", "paper_figures.txt")
+    out = {}
+    for ln in open(path):
+        t = ln.split()
+        if t and not t[0].startswith("#") and len(t) == 2:
+            out[t[0]] = float(t[1])
+    return out
+
+
+def test_units_reproduce_the_section7_free_stream(oracle_lib):
+    """Section 7 prints the cylinder test's free stream (v0, n0, T0, cylinder radius r,
+    mu0 at T0) together with Kn ~ 0.56 and Mach 10.  In the oracle's units (R_g = 1/2:
+    speeds in units of sqrt(2 R T0), lengths in units of r, p = n T / 2) the dimensional
+    collision frequency p0 / mu0 of that stream fixes the Knudsen number at which the
+    oracle's nu(n, T) equals it: within 2% of the printed 0.56 (two printed digits; a
+    hard-sphere mean free path would give 1.9% more), whereas a dropped factor 2, sqrt(2)
+    or sqrt(pi) in nu or in the velocity scale moves it by 29% or more.  The printed Mach
+    number fixes the gas constant: that of argon (molar mass 39.948 g/mol; the paper
+    names no gas) gives 9.99."""
+    f = _figures()
+    k_b = 1.380649e-23                      # J/K (exact in SI)
+    m = 39.948 * 1.66053906660e-27          # kg
+    R = k_b / m
+    v0, n0, T0 = f["free_stream_v0"], f["free_stream_n0"], f["free_stream_T0"]
+    r, mu0 = f["cylinder_radius"], f["viscosity_mu0"]
+    mach = v0 / math.sqrt(5.0 / 3.0 * R * T0)
+    assert abs(mach - f["free_stream_mach"]) < 0.01 * f["free_stream_mach"], mach
+    c = math.sqrt(2.0 * R * T0)             # speed unit of R_g = 1/2
+    nu_stream = n0 * k_b * T0 / mu0 * (r / c)   # p0 / mu0 in units of c / r
+    o = oracle_lib.FullGridOracle(_one_cell(N=4, vmax=4.0, Kn=1.0))
+    kn = o.nu(1.0, 1.0) / nu_stream         # nu is proportional to 1 / Kn
+    assert abs(kn - f["free_stream_kn"]) < 0.02 * f["free_stream_kn"], kn
 
 
 def test_free_molecular_row_is_textbook_upwind(oracle_lib):
