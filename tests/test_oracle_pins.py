@@ -334,3 +334,135 @@ def test_time_step_rule(oracle_lib):
     xi_max = math.sqrt(3) * 5.0
     rates = [o.nu(m[c, 0], m[c, 4]) + 3.0 * xi_max / h for c in range(wl.n_cell)]
     assert abs(o.dt(0.5) - 0.5 / max(rates)) < 1e-15
+
+
+def _one_cell_zero_gradient(N, vmax, Pr, Kn=0.3):
+    """One cube cell whose six faces are zero-gradient boundaries: every face carries
+    (xi.e) f of the cell itself, so the fluxes cancel by closure (sum_l A_l e_l = 0) and
+    only the relaxation term acts."""
+    wl = W.specular_box(shape=(1, 1, 1), N=N, vmax=vmax, Kn=Kn)
+    wl.bcs = [(0, W.BC_ZEROGRAD, np.zeros(8))]
+    wl.Pr = Pr
+    return wl
+
+
+@pytest.mark.parametrize("Pr", [2.0 / 3.0, 1.0, 0.4])
+def test_relaxation_term_rate_and_sign(oracle_lib, Pr):
+    """The update's collision term nu (f^S - f) (Algorithm 1; Section 2,
+    shakhov_integral): with the fluxes cancelling, one explicit step of a state with
+    heat flux keeps n, u and T (f^S carries the same n, u, T) and relaxes the heat flux
+    as q1 = q0 + dt nu ((1 - Pr) q0 - q0) = (1 - dt nu Pr) q0, with nu = sqrt(pi)/(2 Kn)
+    n T^(1-omega).  A wrong sign, a wrong rate or a dropped factor in the relaxation term
+    moves q1 by at least dt nu Pr |q0|, here 1e-2 |q0|."""
+    wl = _one_cell_zero_gradient(N=48, vmax=9.0, Pr=Pr)
+    o = oracle_lib.FullGridOracle(wl, init=False)
+    comps = [(0.8, (0.9, -0.3, 0.1), 0.9), (0.5, (-0.6, 0.5, -0.4), 1.6)]
+    f0 = sum(o.maxwellian(n, u, T) for n, u, T in comps)
+    o.init_f(f0[None])
+    n, u, T, q = _mixture_closed_form(comps)
+    nu = math.sqrt(math.pi) / (2.0 * wl.Kn) * n * T ** (1.0 - wl.omega)
+    dt = 0.02 / nu                                   # dt nu = 0.02
+    o.step(1, dt)
+    a = o.macro()[0]
+    assert abs(a[0] - n) < 1e-12 * n
+    assert np.max(np.abs(a[1:4] - u)) < 1e-12
+    assert abs(a[4] - T) < 1e-12 * T
+    q1 = (1.0 - dt * nu * Pr) * q
+    assert np.max(np.abs(a[5:8] - q1)) < 1e-11 * np.max(np.abs(q))
+    assert np.max(np.abs(q1 - q)) > 5e-3 * np.max(np.abs(q))   # the step did act
+
+
+def _wall(Tw, uw):
+    """Boundary parameter block of a diffuse wall: [unused, u_w (3), T_w, 0, 0, 0]."""
+    p = np.zeros(8)
+    p[1:4] = uw
+    p[4] = Tw
+    return p
+
+
+def test_moving_wall_keeps_comoving_equilibrium(oracle_lib):
+    """Diffuse walls moving tangentially (Section 2, wall-bc-f, read with the wall's
+    velocity u_w in the reflected Maxwellian): gas in equilibrium at the wall's velocity
+    and temperature between two such walls reflects into exactly itself (n_w = n from
+    impermeability on a grid symmetric in the normal velocity), so every face carries
+    (xi.e) f and the state is steady to round-off.  A sign error in u_w, or u_w left
+    out, makes the reflected Maxwellian move at -u_w or 0 and changes f at O(|u_w|)."""
+    uw = (0.3, 0.0, -0.2)
+
+    def classify(ijk, axis, sign, outer):
+        return 1 if axis == 1 else 0
+
+    xyz, hex8, bface, bgroup, ijk = W.lattice_hex_mesh(
+        (1, 4, 1), (0.0, 0.0, 0.0), (0.25, 0.25, 0.25), perm_seed=2, rotate_seed=3,
+        classify=classify)
+    nc = hex8.shape[0]
+    wl = W.Workload(
+        name="moving_walls", xyz=xyz, hex8=hex8, bface=bface, bgroup=bgroup, N=(28, 28, 28),
+        lo=(-5.5,) * 3, hi=(5.5,) * 3, Pr=2.0 / 3.0, omega=0.81, Kn=0.1,
+        bcs=[(0, W.BC_ZEROGRAD, np.zeros(8)), (1, W.BC_WALL, _wall(1.0, uw))],
+        n0=np.full(nc, 0.8), u0=np.tile(np.asarray(uw), (nc, 1)), T0=np.ones(nc),
+        cell_ijk=ijk, steps=5, h=(0.25,) * 3)
+    o = oracle_lib.FullGridOracle(wl)
+    f0 = o.f()
+    o.step(5, 2e-3)
+    assert np.max(np.abs(o.f() - f0)) < 1e-13 * np.max(f0)
+    nw = o.wall_density()
+    _, fcell, _ = o.geometry()
+    walls = [j for j in range(fcell.shape[0]) if fcell[j, 1] < 0 and fcell[j, 2] == 1]
+    assert len(walls) == 2 and np.max(np.abs(nw[walls] - 0.8)) < 1e-14
+    # the same gas between walls at rest is not steady: the test can see u_w
+    wl.bcs = [(0, W.BC_ZEROGRAD, np.zeros(8)), (1, W.BC_WALL, _wall(1.0, (0.0, 0.0, 0.0)))]
+    o2 = oracle_lib.FullGridOracle(wl)
+    o2.step(5, 2e-3)
+    assert np.max(np.abs(o2.f() - f0)) > 1e-4 * np.max(f0)
+
+
+def _half_range_sums(N, vmax, T):
+    """1D node sums of g = (pi T)^(-1/2) exp(-xi^2/T) on N uniform nodes of [-vmax, vmax]
+    (weight dxi): full-range m0, m2 and half-range (xi > 0) h1, h2, h3."""
+    x = -vmax + np.arange(N) * (2.0 * vmax / (N - 1))
+    dx = 2.0 * vmax / (N - 1)
+    g = np.exp(-x * x / T) / math.sqrt(math.pi * T)
+    p = x > 0
+    return (dx * g.sum(), dx * (x * x * g).sum(), dx * (x[p] * g[p]).sum(),
+            dx * (x[p] ** 2 * g[p]).sum(), dx * (x[p] ** 3 * g[p]).sum())
+
+
+def test_residual_of_one_sod_step_closed_form(oracle_lib):
+    """The residual ||U^{n+1} - U^n||_{2,V} / (dt ||U^n||_{2,V}) (U = n, n u, sum w|xi|^2 f
+    per cell) after one step of the two-state row, from half-range sums of the two
+    Maxwellians alone: only the two cells beside the discontinuity change, by
+    -dt/h (F_face - F_same) with the upwind face flux F_face = F+(left) + F-(right) of
+    mass, x-momentum and energy; collisions change no conserved moment (to the
+    quadrature defect, ~1e-20 on this grid).  This pins the residual's numerator,
+    denominator, volume weighting and the 1/dt."""
+    N, vmax, h = 28, 5.5, 1.0 / 16
+    wl = W.sod_row(N=N, vmax=vmax, Kn=0.1, seed=6)
+    o = oracle_lib.FullGridOracle(wl)
+    states = {"L": (1.0, 1.0), "R": (0.5, 0.8)}
+    s = {k: _half_range_sums(N, vmax, T) for k, (_, T) in states.items()}
+
+    def U(k):
+        n = states[k][0]
+        m0, m2 = s[k][0], s[k][1]
+        return np.array([n * m0 ** 3, 0.0, 0.0, 0.0, 3.0 * n * m2 * m0 ** 2])
+
+    def plus(k):     # fluxes of the part moving in +x (xi1 > 0) of state k
+        n = states[k][0]
+        m0, m2, h1, h2, h3 = s[k]
+        return np.array([n * h1 * m0 ** 2, n * h2 * m0 ** 2, 0.0, 0.0,
+                         n * (h3 * m0 ** 2 + 2.0 * h1 * m2 * m0)])
+
+    refl = np.array([-1.0, 1.0, 1.0, 1.0, -1.0])  # the xi1 < 0 half: odd moments flip sign
+    F_face = plus("L") + refl * plus("R")
+    F_LL = plus("L") + refl * plus("L")
+    F_RR = plus("R") + refl * plus("R")
+    dt = 1.5e-3
+    dU_k = -dt / h * (F_face - F_LL)
+    dU_k1 = -dt / h * (F_RR - F_face)
+    V = h ** 3
+    num = math.sqrt(V * (dU_k @ dU_k + dU_k1 @ dU_k1))
+    den = math.sqrt(V * 8 * (U("L") @ U("L") + U("R") @ U("R")))
+    expect = num / (dt * den)
+    res = o.step(1, dt)
+    assert abs(res - expect) < 1e-10 * expect, (res, expect)
