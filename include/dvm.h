@@ -113,6 +113,11 @@ typedef struct {
                        * mode Gram / eigen-solve (one warp per cell) /
                        * projection kernels over chunks of cells).  Both
                        * compute the same values cell by cell.              */
+  int64_t max_chunk;  /* Tucker phase-major variant: at most this many cells
+                       * per chunk of its per-step work buffers (0: chunks
+                       * sized to 1/8 of the free device memory, at most all
+                       * cells); bounds the context's memory.  Results do not
+                       * depend on it.                                      */
 } dvm_opts;
 
 #define DVM_VARIANT_AUTO 0
@@ -173,9 +178,11 @@ int dvm_get_tucker(dvm_ctx *ctx, int32_t *ranks, double *core, double *u1, doubl
  * of the last step, ||U^{n+1}-U^n||_{2,V} / (dt ||U^n||_{2,V}) with
  * U = (n, n u, sum w |xi|^2 f) per cell; with NULL the call only enqueues.
  * Errors: NONPHYSICAL (n <= 0 or T <= 0 seen in a cell), TIMEOUT (Tucker: a
- * bulk shared-memory copy did not complete within its bounded wait; the block
- * re-read the data with plain loads, so the state is still the correct step),
- * CUDA.  Both device flags are reported only by calls with residual_out. */
+ * bulk shared-memory copy did not complete within its bounded wait; the blocks
+ * that saw it returned without writing their results, so the step failed and
+ * the state is undefined until the next dvm_init_* or dvm_load), CUDA.  Both
+ * device flags are reported only by calls with residual_out, and stay set (every
+ * later such call reports them) until the state is initialised again. */
 int dvm_step(dvm_ctx *ctx, int32_t nsteps, double *residual_out);
 
 /* Macroparameters of every cell (Section 2): host arrays out[n_cell][8] =
@@ -279,6 +286,7 @@ typedef struct {
 #define DVM_REQ_CONVERGED 2
 #define DVM_REQ_NOT_CONVERGED 3
 #define DVM_REQ_FAILED 4
+#define DVM_REQ_CANCELLED 5
 
 /* Device-memory estimate of one request's context (bytes). */
 int dvm_estimate_memory(const dvm_request *req, size_t *bytes);
@@ -306,6 +314,13 @@ int dvm_server_poll(dvm_server *srv, int64_t ticket, int32_t *state, int64_t *st
  * memory was released). */
 int dvm_server_result(dvm_server *srv, int64_t ticket, double *macro);
 
+/* Cancel a request.  A queued request is retired at once (state CANCELLED); a
+ * running one keeps its slot until the chunk of steps it has in flight ends, and
+ * the next dvm_server_run retires it there (state CANCELLED, its device memory
+ * released, dvm_server_result giving the macroparameters reached).  Errors:
+ * INVALID_ARG (unknown ticket), STATE (already finished). */
+int dvm_server_cancel(dvm_server *srv, int64_t ticket);
+
 /* Message of a failed request ("" otherwise); valid until the server is
  * destroyed. */
 const char *dvm_server_error(dvm_server *srv, int64_t ticket);
@@ -325,14 +340,36 @@ void dvm_server_destroy(dvm_server *srv);
  * The per-cell intermediate sums live in a fixed array inside the library
  * with room for 16384 cells (1 MiB, held by every GPU that loads the library
  * until the process exits); a larger n_cell is rejected with
- * DVM_ERR_INVALID_ARG.  The first call on each device looks up that array's
- * device address with cudaGetSymbolAddress, so make the first call on a device
- * before any stream capture.  Every call uses the same array: calls whose GPU
- * work overlaps (other streams or host threads on the same device) race on it
- * and must be serialised by the caller.  Results equal those of dvm_moments on
- * a context initialised with the same tensors, up to summation order. */
+ * DVM_ERR_INVALID_ARG.  The first call on each device (and the first after that
+ * device's context has been replaced, e.g. by cudaDeviceReset) looks up that
+ * array's device address with cudaGetSymbolAddress, so make the first call on a
+ * device before any stream capture.  Every call uses the same array: calls whose
+ * GPU work overlaps (other streams or host threads on the same device) race on
+ * it and must be serialised by the caller.  A cell whose density sum is zero
+ * gets NaN macroparameters (there is no per-cell status).  Results equal those
+ * of dvm_moments on a context initialised with the same tensors, up to
+ * summation order. */
 int dvm_full_macro_noalloc(const double *f, int64_t n_cell, const dvm_vgrid *vgrid,
                            double *macro, void *cuda_stream);
+
+/* Host-side fault injection, for testing the error paths (the paper has no
+ * counterpart).  Process-wide; each kind fires once and then disarms:
+ *   DVM_FAULT_ALLOC    the device allocation made after `count` more succeed
+ *                      fails as out of memory (DVM_ERR_OOM from the call that
+ *                      made it, e.g. dvm_create, or a failed serving request);
+ *   DVM_FAULT_TIMEOUT  the dvm_step call made after `count` more finds the
+ *                      context's device flag set as a timed-out bulk-copy wait
+ *                      leaves it (DVM_ERR_TIMEOUT from the next call with
+ *                      residual_out, or a failed serving request);
+ *   DVM_FAULT_ADMIT    the next `count` admission checks of every server see
+ *                      the memory budget as full (requests stay queued);
+ *   DVM_FAULT_NONE     disarms all.
+ * A negative count disarms that kind.  No device fault is ever raised. */
+#define DVM_FAULT_NONE 0
+#define DVM_FAULT_ALLOC 1
+#define DVM_FAULT_TIMEOUT 2
+#define DVM_FAULT_ADMIT 3
+int dvm_fault_inject(int32_t kind, int64_t count);
 
 void dvm_destroy(dvm_ctx *ctx);
 

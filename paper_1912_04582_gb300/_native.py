@@ -57,7 +57,8 @@ class dvm_opts(ctypes.Structure):
     _fields_ = [("format", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("rank_cap", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("cfl", ctypes.c_double), ("dt", ctypes.c_double),
-                ("cuda_stream", ctypes.c_void_p), ("variant", ctypes.c_int32)]
+                ("cuda_stream", ctypes.c_void_p), ("variant", ctypes.c_int32),
+                ("max_chunk", ctypes.c_int64)]
 
 
 class dvm_request(ctypes.Structure):
@@ -68,7 +69,9 @@ class dvm_request(ctypes.Structure):
                 ("check_every", ctypes.c_int32)]
 
 
-DVM_REQ_QUEUED, DVM_REQ_RUNNING, DVM_REQ_CONVERGED, DVM_REQ_NOT_CONVERGED, DVM_REQ_FAILED = range(5)
+(DVM_REQ_QUEUED, DVM_REQ_RUNNING, DVM_REQ_CONVERGED, DVM_REQ_NOT_CONVERGED, DVM_REQ_FAILED,
+ DVM_REQ_CANCELLED) = range(6)
+DVM_FAULT_NONE, DVM_FAULT_ALLOC, DVM_FAULT_TIMEOUT, DVM_FAULT_ADMIT = range(4)
 
 _P = ctypes.c_void_p
 _PP = ctypes.POINTER(ctypes.c_void_p)
@@ -109,6 +112,8 @@ SIGNATURES = {
     "dvm_server_poll": (ctypes.c_int, [_P, ctypes.c_int64, _c_i32p, _c_i64p, _c_dp, _c_dp]),
     "dvm_server_result": (ctypes.c_int, [_P, ctypes.c_int64, _c_dp]),
     "dvm_server_error": (ctypes.c_char_p, [_P, ctypes.c_int64]),
+    "dvm_server_cancel": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "dvm_fault_inject": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64]),
     "dvm_server_destroy": (None, [_P]),
     "dvm_destroy": (None, [_P]),
     "dvm_last_error": (ctypes.c_char_p, []),

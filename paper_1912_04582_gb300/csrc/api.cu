@@ -187,6 +187,10 @@ int dvm_create(dvm_ctx **out, const dvm_mesh *mesh, const dvm_vgrid *vg, const d
     set_error("dvm_create: unknown format");
     return DVM_ERR_INVALID_ARG;
   }
+  if (opts->max_chunk < 0) {
+    set_error("dvm_create: max_chunk must be >= 0");
+    return DVM_ERR_INVALID_ARG;
+  }
   if (opts->variant < DVM_VARIANT_AUTO || opts->variant > DVM_VARIANT_PHASED) {
     set_error("dvm_create: variant must be DVM_VARIANT_AUTO, _FUSED or _PHASED");
     return DVM_ERR_INVALID_ARG;
@@ -279,6 +283,7 @@ int dvm_init_maxwellian(dvm_ctx *C, const double *n, const double *u, const doub
       return DVM_ERR_INVALID_ARG;
     }
   int rc = ctx_prepare_boundaries(C);
+  if (rc == DVM_OK) rc = ctx_clear_flag(C);
   if (rc != DVM_OK) return rc;
   return ctx_init_from_maxwellians(C, n, u, T);
 }
@@ -289,6 +294,7 @@ int dvm_init_f(dvm_ctx *C, const double *f, int32_t on_device) {
     return DVM_ERR_INVALID_ARG;
   }
   int rc = ctx_prepare_boundaries(C);
+  if (rc == DVM_OK) rc = ctx_clear_flag(C);
   if (rc != DVM_OK) return rc;
   return ctx_init_from_full(C, f, on_device != 0);
 }
@@ -304,6 +310,7 @@ int dvm_init_tucker(dvm_ctx *C, const int32_t *ranks, const double *core, const 
     return DVM_ERR_INVALID_ARG;
   }
   int rc = ctx_prepare_boundaries(C);
+  if (rc == DVM_OK) rc = ctx_clear_flag(C);
   if (rc != DVM_OK) return rc;
   const double *fac[3] = {u1, u2, u3};
   rc = tucker_set_state(C, ranks, core, fac, on_device != 0);
@@ -482,6 +489,7 @@ int dvm_save(dvm_ctx *C, const char *path) {
 int dvm_load(dvm_ctx *C, const char *path) {
   if (!C || !path) return DVM_ERR_INVALID_ARG;
   int rc = ctx_prepare_boundaries(C);
+  if (rc == DVM_OK) rc = ctx_clear_flag(C);
   if (rc != DVM_OK) return rc;
   return ctx_load(C, path);
 }

@@ -38,6 +38,12 @@ int sync_and_check(dvm_ctx *C) {
 }  // namespace
 
 int ctx_malloc(dvm_ctx *C, void **p, size_t bytes) {
+  if (fault_alloc()) {
+    *p = nullptr;
+    set_error("device allocation of " + std::to_string(bytes) +
+              " bytes failed: out of memory (injected by dvm_fault_inject)");
+    return DVM_ERR_OOM;
+  }
   cudaError_t e = cudaMalloc(p, bytes == 0 ? 16 : bytes);
   if (e != cudaSuccess) {
     *p = nullptr;
@@ -416,14 +422,26 @@ static int read_residual(dvm_ctx *C, double *residual_out) {
     set_error("non-physical state: n <= 0 or T <= 0 in some cell");
     return DVM_ERR_NONPHYSICAL;
   }
-  if (flag & 2) {  // the step's result is still complete (direct reads were used)
-    set_error("a bulk shared-memory copy did not complete within its wait limit");
+  if (flag & 2) {  // blocks returned without writing their results
+    set_error("a bulk shared-memory copy did not complete within its wait limit: the step "
+              "failed and the solver state is undefined (initialise again or load a checkpoint)");
     return DVM_ERR_TIMEOUT;
   }
   return DVM_OK;
 }
 
+// A new state starts with no device error recorded (the flag is sticky until then).
+int ctx_clear_flag(dvm_ctx *C) {
+  DVM_CUDA_TRY(cudaMemsetAsync(C->d_flag, 0, sizeof(int) * 4, C->stream));
+  return DVM_OK;
+}
+
 int ctx_step(dvm_ctx *C, int32_t nsteps, double *residual_out) {
+  if (fault_timeout()) {  // the device flag as a timed-out bulk-copy wait leaves it
+    static const int kTimedOut = 2;
+    DVM_CUDA_TRY(cudaMemcpyAsync(C->d_flag, &kTimedOut, sizeof(int), cudaMemcpyHostToDevice,
+                                 C->stream));
+  }
   if (C->opts.format == DVM_FORMAT_TUCKER) {
     int rc = tucker_step(C, nsteps, residual_out);
     if (rc != DVM_OK) return rc;

@@ -82,6 +82,7 @@ void ctx_free(dvm_ctx *C);
 int ctx_prepare_boundaries(dvm_ctx *C);
 int ctx_init_from_maxwellians(dvm_ctx *C, const double *n, const double *u, const double *T);
 int ctx_init_from_full(dvm_ctx *C, const double *f, bool on_device);
+int ctx_clear_flag(dvm_ctx *C);
 int ctx_step(dvm_ctx *C, int32_t nsteps, double *residual_out);
 int ctx_moments(dvm_ctx *C, double *out);
 int ctx_get_f(dvm_ctx *C, int64_t cell0, int64_t ncell, double *out);

@@ -99,6 +99,12 @@ void launch_cell_maxwellians(double *f, const double *n, const double *u, const 
 // error plumbing
 void set_error(const std::string &msg);
 
+// host-side fault injection (faults.cu): true when the armed failure of that kind
+// fires at this call
+bool fault_alloc();
+bool fault_timeout();
+bool fault_admit();
+
 }  // namespace dvm
 
 #define DVM_CUDA_TRY(expr)                                                       \

@@ -17,6 +17,8 @@
 // serialised by the caller.  Nothing in it needs to start at zero: the first
 // pass writes every entry that the second pass reads, and a later call simply
 // overwrites what the previous one left there.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "dvm_internal.h"
@@ -31,6 +33,38 @@ static __device__ __align__(256) double g_noalloc_scratch[kNoallocMaxCells * kNo
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double *g_scratch_ptr[kMaxDevices] = {};
+unsigned long long g_ctx_id[kMaxDevices] = {};  // context the address was looked up in
+
+// Unique id of the calling thread's current CUDA context (0 if there is none or it
+// cannot be queried), through the driver's entry points so that the library needs
+// no link against the driver library.  A looked-up symbol address belongs to one
+// context: after a device reset the next call finds a new id and looks it up again.
+// Called with g_mu held.
+unsigned long long current_ctx_id() {
+  using GetCurrent = CUresult (*)(CUcontext *);
+  using GetId = CUresult (*)(CUcontext, unsigned long long *);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    looked_up = true;
+    cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", reinterpret_cast<void **>(&get_current),
+                                         12000, cudaEnableDefault, &q1) != cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", reinterpret_cast<void **>(&get_id), 12000,
+                                         cudaEnableDefault, &q2) != cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      get_current = nullptr;
+      get_id = nullptr;
+    }
+  }
+  if (!get_current || !get_id) return 0;
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
 
 // velocity node i of one axis: ((N-1-i) lo + i hi) / (N-1), without contraction
 __device__ __forceinline__ double node(int i, int N, double lo, double hi) {
@@ -186,20 +220,24 @@ extern "C" int dvm_full_macro_noalloc(const double *f, int64_t n_cell, const dvm
   }
   double *scratch = nullptr;
   {
-    // one-time set-up per device, with that device current: host code must not
-    // use g_noalloc_scratch itself (on the host it names a stand-in, not device
+    // set-up once per device (again if its context has changed, e.g. after a
+    // device reset), with that device current: host code must not use
+    // g_noalloc_scratch itself (on the host it names a stand-in, not device
     // memory), so look up its device address.
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_ptr[dev]) {
+    const unsigned long long id = current_ctx_id();
+    if (!g_scratch_ptr[dev] || id == 0 || id != g_ctx_id[dev]) {
       void *p = nullptr;
       cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
       if (e != cudaSuccess || !p) {
         cudaGetLastError();
+        g_scratch_ptr[dev] = nullptr;
         dvm::set_error(std::string("dvm_full_macro_noalloc: cudaGetSymbolAddress failed: ") +
                        cudaGetErrorString(e));
         return DVM_ERR_CUDA;
       }
       g_scratch_ptr[dev] = static_cast<double *>(p);
+      g_ctx_id[dev] = current_ctx_id();  // the look-up has made the context current
     }
     scratch = g_scratch_ptr[dev];
   }

@@ -51,6 +51,7 @@ struct Request {
   cudaEvent_t ev = nullptr;
   double *h_out = nullptr;  // pinned: residual, flag
   bool in_flight = false;
+  bool cancel = false;  // retire at the end of the chunk in flight
   int64_t steps = 0;
   double res = INFINITY;
   double t_submit = 0.0, t_done = 0.0;
@@ -243,7 +244,7 @@ int dvm_server_run(dvm_server *S, double max_seconds, int64_t *pending) {
     // admission: FIFO while a slot is free and the estimate fits
     while (!S->queue.empty() && (int32_t)S->running.size() < S->max_slots) {
       Request &r = S->reqs[S->queue.front()];
-      if (S->used + r.est > S->budget) break;
+      if (S->used + r.est > S->budget || fault_admit()) break;
       S->queue.pop_front();
       S->used += r.est;
       int rc = start(r);
@@ -276,11 +277,14 @@ int dvm_server_run(dvm_server *S, double max_seconds, int64_t *pending) {
         int flag = 0;
         std::memcpy(&flag, r.h_out + 1, sizeof flag);
         if (flag != 0 || !std::isfinite(r.res)) {
-          r.error = flag != 0 ? "non-physical state: n <= 0 or T <= 0 in some cell"
-                              : "residual is not finite";
+          r.error = (flag & 2) ? "a bulk shared-memory copy did not complete within its wait "
+                                 "limit: the solve's state is undefined"
+                    : (flag & 1) ? "non-physical state: n <= 0 or T <= 0 in some cell"
+                                 : "residual is not finite";
           done = DVM_REQ_FAILED;
         }
         else if (r.res <= r.tol) done = DVM_REQ_CONVERGED;
+        else if (r.cancel) done = DVM_REQ_CANCELLED;
         else if (r.steps >= r.max_steps) done = DVM_REQ_NOT_CONVERGED;
         else if (launch_chunk(r) != DVM_OK) done = DVM_REQ_FAILED;
       }
@@ -323,6 +327,32 @@ int dvm_server_result(dvm_server *S, int64_t ticket, double *macro) {
   }
   std::memcpy(macro, it->second.macro.data(), sizeof(double) * it->second.macro.size());
   return DVM_OK;
+}
+
+int dvm_server_cancel(dvm_server *S, int64_t ticket) {
+  if (!S) return DVM_ERR_INVALID_ARG;
+  auto it = S->reqs.find(ticket);
+  if (it == S->reqs.end()) {
+    set_error("dvm_server_cancel: unknown ticket");
+    return DVM_ERR_INVALID_ARG;
+  }
+  Request &r = it->second;
+  if (r.state == DVM_REQ_QUEUED) {  // never admitted: nothing on the device
+    for (auto q = S->queue.begin(); q != S->queue.end(); ++q)
+      if (*q == ticket) {
+        S->queue.erase(q);
+        break;
+      }
+    r.state = DVM_REQ_CANCELLED;
+    r.t_done = now_s();
+    return DVM_OK;
+  }
+  if (r.state == DVM_REQ_RUNNING) {  // retired by dvm_server_run after its current chunk
+    r.cancel = true;
+    return DVM_OK;
+  }
+  set_error("dvm_server_cancel: the request has already finished");
+  return DVM_ERR_STATE;
 }
 
 const char *dvm_server_error(dvm_server *S, int64_t ticket) {

@@ -1936,11 +1936,27 @@ __device__ __forceinline__ void plain_copy(const StagePiece &q) {
 // are multiples of 16 bytes go by bulk asynchronous copies (cp.async.bulk; thread 0
 // issues them, completion is counted in bytes on one mbarrier, which every thread
 // polls at most kBulkWaitIters times); the others, meanwhile, by plain loads of
-// the block.  If the barrier has not completed within the limit, the bulk pieces
-// are copied again by plain loads (the same bytes, so a late bulk write changes
-// nothing) and bit 1 of *flag is set.  Called by every thread; ends with a barrier.
+// the block.  Returns true (in every thread) when all pieces are in place.  If the
+// barrier has not completed within the limit, bit 1 of *flag is set, the block
+// polls once more (again bounded) so that it does not give up shared memory with a
+// copy still landing in it, and false is returned: the caller then returns at
+// once, writes nothing, and the host reports the step as failed (DVM_ERR_TIMEOUT,
+// the state undefined).  Called by every thread; ends with a barrier.
+__device__ __forceinline__ unsigned poll_bulk(unsigned bar) {
+  unsigned done = 0;
+  for (int it = 0; it < kBulkWaitIters && !done; ++it)
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar)
+        : "memory");
+  return done;
+}
+
 template <int NP>
-__device__ __noinline__ void stage_to_shared(const StagePiece (&pc)[NP], int np, int *flag) {
+__device__ __noinline__ bool stage_to_shared(const StagePiece (&pc)[NP], int np, int *flag) {
   __shared__ __align__(8) unsigned long long s_bar;
   unsigned tx = 0;
   for (int q = 0; q < np; ++q)
@@ -1966,23 +1982,14 @@ __device__ __noinline__ void stage_to_shared(const StagePiece (&pc)[NP], int np,
   }
   for (int q = 0; q < np; ++q)
     if (!bulk_ok(pc[q])) plain_copy(pc[q]);
-  if (tx > 0) {
-    unsigned done = 0;
-    for (int it = 0; it < kBulkWaitIters && !done; ++it)
-      asm volatile(
-          "{\n\t.reg .pred p;\n\t"
-          "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
-          "selp.u32 %0, 1, 0, p;\n\t}"
-          : "=r"(done)
-          : "r"(bar)
-          : "memory");
-    if (!__syncthreads_and(done)) {
-      if (threadIdx.x == 0) atomicOr(flag, 2);
-      for (int q = 0; q < np; ++q)
-        if (bulk_ok(pc[q])) plain_copy(pc[q]);
-    }
+  if (tx > 0 && !__syncthreads_and(poll_bulk(bar))) {
+    if (threadIdx.x == 0) atomicOr(flag, 2);
+    poll_bulk(bar);  // drain (bounded) before the block leaves
+    __syncthreads();
+    return false;
   }
   __syncthreads();
+  return true;
 }
 
 // Eigen-solve and rank rule of mode m for cell j: one warp per cell.  On exit
@@ -2035,7 +2042,7 @@ __global__ void __launch_bounds__(32, 13) tucker_eig_kernel(TuckerStepParams P, 
     const StagePiece pcs[2] = {
         {Cs, B.C + j * (int64_t)Nm * Nm, 8u * (unsigned)(n * n)},
         {Ws, P.cur.fac[m] + c * (int64_t)n * R, 8u * (unsigned)(n * R)}};
-    stage_to_shared(pcs, 2, P.flag);
+    if (!stage_to_shared(pcs, 2, P.flag)) return;  // timed out: step reported failed
   }
   sm.Cg = Cs;
   const double tr = gram_trace<Real>(sm, n);
@@ -2250,7 +2257,7 @@ __global__ void __launch_bounds__(128) tucker_moments_kernel(TuckerMomentParams 
       pcs[np++] = {msm + off, G, 8u * (unsigned)ge};
       G = msm + off;
     }
-    stage_to_shared(pcs, np, P.flag);
+    if (!stage_to_shared(pcs, np, P.flag)) return;  // timed out: step reported failed
   } else {
     __syncthreads();
   }

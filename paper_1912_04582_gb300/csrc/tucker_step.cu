@@ -418,7 +418,8 @@ int alloc_split(dvm_ctx *C) {
   int sms = 1;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, C->device);
   const size_t t2_stride = (tucker_split_t2_elems(C->N[0], C->N[1], C->N[2], S->R) + 63) & ~size_t(63);
-  const int64_t chunk = std::min<int64_t>(C->nc, (int64_t)(free_b / 8 / per));
+  int64_t chunk = std::min<int64_t>(C->nc, (int64_t)(free_b / 8 / per));
+  if (C->opts.max_chunk > 0) chunk = std::min<int64_t>(chunk, C->opts.max_chunk);
   if (chunk < 1) {
     set_error("no device memory for the phase-major Tucker step buffers");
     return DVM_ERR_OOM;

@@ -192,3 +192,12 @@ def test_cavity_full_size_three_steps(dvm, oracle_lib):
     configuration the benchmark times): every cell and node after 3 steps."""
     wl = W.cavity()
     check_pair(*run_pair(dvm, oracle_lib, wl, 3))
+
+
+@pytest.mark.slow
+def test_c3_velocity_grid_against_oracle(dvm, oracle_lib):
+    """The full-grid FP64 path is the same-run reference of the benchmark's Tucker error
+    on the 32^3-cell x 48^3 cavity; here it is checked against the oracle with that
+    velocity grid on 16^3 cells (every cell and node after 3 steps)."""
+    wl = W.cavity(nside=16, N=48)
+    check_pair(*run_pair(dvm, oracle_lib, wl, 3))

@@ -339,3 +339,63 @@ def test_tucker_state_round_trip(dvm):
         dvm.dvm_init_tucker(b.h, bad, core, fac)
     a.close()
     b.close()
+
+
+def test_cavity_at_the_benchmark_size_against_oracle(dvm, oracle_lib):
+    """The C2 cavity at full size (16^3 cells x 32^3 nodes) in the mixed-precision
+    Tucker path at eps = 1e-6, cap 12, over 20 steps in the launch configuration the
+    benchmark times (autotuned variant, graph replay), element by element against the
+    FP64 oracle: within 1e-4 on f and on every macroparameter."""
+    wl = W.cavity()
+    o = oracle_lib.FullGridOracle(wl)
+    o.step(20, o.dt())
+    s = tucker_solver(dvm, wl, 12, 1e-6, precision=MIXED)
+    s.step(20, residual=False)
+    assert rel_l2(s.f(), o.f()) < 1e-4
+    for k, err in macro_err(s.moments(), o.macro(), u_scale=0.2).items():
+        assert err < 1e-4, (k, err)
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [FP64, MIXED])
+def test_non_cubic_velocity_grid(dvm, oracle_lib, precision):
+    """A 40 x 24 x 20 velocity grid (first mode above 32 nodes, the others below; every
+    mode a different size) in both launch variants: within 1e-4 of the oracle after 8
+    steps, and the variants agree bit for bit."""
+    from paper_1912_04582_gb300 import _native as NAT
+    wl = W.cavity(nside=3, N=40, seed=6)
+    wl.N = (40, 24, 20)
+    wl.lo, wl.hi = (-6.0, -5.5, -5.0), (6.0, 5.5, 5.0)
+    o = oracle_lib.FullGridOracle(wl)
+    o.step(8, o.dt())
+    fo, mo = o.f(), o.macro()
+    out = {}
+    for v in (NAT.DVM_VARIANT_FUSED, NAT.DVM_VARIANT_PHASED):
+        s = dvm.Solver(wl, format=1, precision=precision, rank_cap=12, tol=1e-6, variant=v)
+        s.step(8)
+        out[v] = (s.f(), s.moments(), dvm.dvm_get_ranks(s.h))
+        s.close()
+    fg, mg, rk = out[NAT.DVM_VARIANT_PHASED]
+    assert rel_l2(fg, fo) < 1e-4
+    for k, err in macro_err(mg, mo, u_scale=0.2).items():
+        assert err < 1e-4, (k, err)
+    assert np.array_equal(out[NAT.DVM_VARIANT_FUSED][0], fg)
+    assert np.array_equal(out[NAT.DVM_VARIANT_FUSED][2], rk)
+
+
+def test_chunked_step_equals_single_chunk(dvm):
+    """The phase-major step over several chunks of cells (the last one ragged, every
+    chunk split over two streams) gives bit for bit the single-chunk result."""
+    from paper_1912_04582_gb300 import _native as NAT
+    wl = W.cavity(nside=6, N=16, seed=8)
+    out = []
+    for chunk in (0, 50, 7):
+        s = dvm.Solver(wl, format=1, precision=MIXED, rank_cap=8, tol=1e-6,
+                       variant=NAT.DVM_VARIANT_PHASED, max_chunk=chunk)
+        s.step(6)
+        out.append((s.f(), s.moments(), dvm.dvm_get_ranks(s.h)))
+        s.close()
+    for f, m, r in out[1:]:
+        assert np.array_equal(r, out[0][2])
+        assert np.array_equal(f, out[0][0])
+        assert np.array_equal(m, out[0][1])

@@ -3,8 +3,8 @@
 This entry point serves callers that cannot allocate device memory where they need the
 moments (their memory is owned by their own pool allocator, or a cudaMalloc's implicit
 synchronisation would stall work they have queued).  It must give the same
-macroparameters as the allocating route — dvm_init_f + dvm_moments on a context — on
-two calls in a row, since every call reuses the same fixed scratch array inside the
+macroparameters as the allocating route — dvm_init_f + dvm_moments on a context — and
+as the FP64 oracle on two calls in a row, since every call reuses the same fixed scratch array inside the
 library.  The file sorts last so that a stop-at-first-failure run has done all other
 tests first; it builds everything it needs, so it also passes alone.
 """
@@ -26,6 +26,13 @@ def _macro_err(mg, mo):
     qn = max(np.linalg.norm(mo[:, 5:8]), 1e-6 * np.sqrt(mo.shape[0]))
     err["q"] = np.linalg.norm(mg[:, 5:8] - mo[:, 5:8]) / qn
     return err
+
+
+def _oracle_moments(wl, f):
+    import oracle
+    o = oracle.FullGridOracle(wl, init=False)
+    o.init_f(f)
+    return o.macro()
 
 
 def _reference_moments(P, wl, f):
@@ -60,6 +67,8 @@ def test_noalloc_macro_matches_allocating_route_twice():
         assert np.all(np.isfinite(got))
         for k, v in _macro_err(got, ref).items():
             assert v <= TOL, (k, v)
+        for k, v in _macro_err(got, _oracle_moments(wl, f)).items():   # and the FP64 oracle's
+            assert v <= TOL, ("oracle", k, v)
 
 
 def test_noalloc_macro_rejects_oversized_batch():
