@@ -1,19 +1,23 @@
 """Benchmark: S-model DVM cell x velocity-node updates per second on one GB300.
 
-Default workload: the lid-driven cubic cavity, 16^3 = 4,096 hex cells, 32^3 velocity
-nodes on [-6,6]^3, Kn = 0.1, diffuse walls at T = 1, lid speed 0.2 (synthetic, seeded).
-A "step" is one explicit time step of the whole hot path over every cell: moments,
-Shakhov equilibrium, boundary ghosts, upwind face fluxes, the Euler update and, in the
-Tucker format, the rounding back to the tolerance / rank cap.
+Headline workload (C3): the lid-driven cubic cavity on 32^3 = 32,768 hex cells, 48^3
+velocity nodes on [-6,6]^3, Kn = 0.1, diffuse walls at T = 1, lid speed 0.2 (synthetic,
+seeded), in the Tucker format in mixed precision (FP32 assembly and projections,
+tensor-core or double-float Gram matrices, FP64 eigen-solve steps, moments and stored
+state) with rank cap 12 at eps = 1e-6: the tolerance that keeps the error within 1e-4
+on this workload (eps = 1e-5, the configuration's nominal tolerance, does not; both are
+reported).  A "step" is one explicit time step of the whole hot path over every cell:
+moments, Shakhov equilibrium, boundary ghosts, upwind face fluxes, the Euler update and
+the rounding back to the tolerance / rank cap.
 
-Headline: the Tucker format in mixed precision (FP32 assembly and projections,
-double-float Gram matrices, FP64 eigen-solve steps, moments and stored state) at the
-tolerance that keeps the error against the FP64 oracle within 1e-4 (checked in the same
-run on a reduced cavity); the full-grid FP64 path and the FP64 Tucker path are timed
-beside it on the same inputs.
+In the same run, on the same workload and at the same step count, the full-grid FP64
+path (itself checked against the FP64 oracle at this size by the GPU tests) is timed
+and is the reference of the Tucker path's per-macroparameter error.  The C2 cavity
+(16^3 cells x 32^3) paths, C4 (Mach-3 flow past a cube, 101,888 jittered cells x 64^3)
+and a serving mix are reported beside it.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--path tucker|full]
-                    [--precision mixed|fp64] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c3|c2]
+                    [--path tucker|full] [--precision mixed|fp64] [--impl reference]
 
 Prints one JSON line (rank 0).  With --impl reference the FP64 CPU oracle is timed on
 the same workload instead (bounded sample per step).  N > 1 runs independent replicas
@@ -50,7 +54,7 @@ def _args():
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--rank-cap", type=int, default=None)
     ap.add_argument("--tol", type=float, default=None)
-    ap.add_argument("--workload", default="cavity")
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "cavity_small", "sod"])
     ap.add_argument("--variant", default="auto", choices=["auto", "fused", "phased"],
                     help="Tucker launch variant (auto: the autotuner times both)")
     ap.add_argument("--advance", type=int, default=200,
@@ -58,13 +62,17 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the other path, the accuracy check and the serving run")
+                    help="skip the reference run, the other configurations and the serving mix")
+    ap.add_argument("--no-reference", action="store_true",
+                    help="skip the same-run full-grid reference (accuracy and full-grid timing)")
     return ap.parse_args()
 
 
 def make_workload(name):
     import workloads as W
-    if name == "cavity":
+    if name == "c3":
+        return W.cavity(nside=32, N=48)
+    if name in ("c2", "cavity"):
         return W.cavity()
     if name == "cavity_small":
         return W.cavity(nside=8, N=24)
@@ -156,11 +164,22 @@ def _traffic(kernel):
 
 
 # --------------------------------------------------------------------------
+def oracle_sample(wl):
+    """The bounded sample of a workload the FP64 oracle is timed on: the same velocity
+    grid, gas and boundary conditions on a cavity of at most 12^3 cells (the full C3
+    mesh would need two 29 GB copies of f and about 9 s per step on the host)."""
+    import workloads as W
+    if wl.n_cell <= 4096 or not wl.name.startswith("cavity"):
+        return wl
+    return W.cavity(nside=12, N=int(wl.N[0]), vmax=float(wl.hi[0]), Kn=wl.Kn)
+
+
 def cpu_baseline(wl, budget_s=20.0):
-    """The FP64 oracle (as it stands) on the host cores: full-workload steps until the
-    budget is used (at least one)."""
+    """The FP64 oracle (as it stands) on the host cores: steps of the bounded sample until
+    the budget is used (at least one)."""
     import oracle
-    o = oracle.FullGridOracle(wl)
+    sw = oracle_sample(wl)
+    o = oracle.FullGridOracle(sw)
     dt = o.dt()
     n = 0
     t0 = time.perf_counter()
@@ -171,9 +190,10 @@ def cpu_baseline(wl, budget_s=20.0):
             break
     el = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count()))
-    return {"value": wl.n_cell * wl.nodes_per_cell * n / el, "unit": UNIT, "cores": cores,
+    return {"value": sw.n_cell * sw.nodes_per_cell * n / el, "unit": UNIT, "cores": cores,
             "kind": "oracle",
-            "sample": f"{n} full step(s) of {wl.name} in {el:.1f} s (FP64 C oracle, OpenMP)"}
+            "sample": f"{n} full step(s) of {sw.name} in {el:.1f} s (FP64 C oracle, OpenMP; "
+                      f"the velocity grid, gas and walls of {wl.name})"}
 
 
 def run_reference(args, rank, world):
@@ -181,7 +201,8 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     import oracle
-    o = oracle.FullGridOracle(wl)
+    sw = oracle_sample(wl)
+    o = oracle.FullGridOracle(sw)
     dt = o.dt()
     for _ in range(args.warmup):
         o.step(1, dt)
@@ -189,9 +210,11 @@ def run_reference(args, rank, world):
     for _ in range(args.steps):
         o.step(1, dt)
     el = time.perf_counter() - t0
-    upd = wl.n_cell * wl.nodes_per_cell
+    upd = sw.n_cell * sw.nodes_per_cell
     v = upd * args.steps / el
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count()))
+    sample = (f"{args.steps} full step(s) of {sw.name}" +
+              ("" if sw is wl else f" (the velocity grid, gas and walls of {wl.name})"))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -199,7 +222,7 @@ def run_reference(args, rank, world):
                                              "format": "full FP64 CPU oracle (the oracle "
                                                        "implements the full-grid method)"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{args.steps} full step(s) of {wl.name}"},
+                             "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -249,7 +272,7 @@ def _tucker_work(wl, ranks, cls):
     return None
 
 
-def _roofline_tucker(P, s, wl, steps):
+def _roofline_tucker(P, s, wl, steps, peaks=None, peak_src=None):
     """Per-class launch times with CUDA events (a second timed region of `steps` steps),
     roofline of the dominant class."""
     P.dvm_set_kernel_timing(s.h, True)
@@ -308,34 +331,73 @@ def _rel(a, b):
     return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
 
 
-def tucker_accuracy(P, cap, tol, precision, steps=300):
-    """Tucker path vs the FP64 full-grid oracle on a reduced cavity (8^3 cells x 24^3)."""
-    import oracle
-    import workloads as W
-    wl = W.cavity(nside=8, N=24)
-    o = oracle.FullGridOracle(wl)
-    o.step(steps, o.dt())
-    fo, mo = o.f(), o.macro()
-    s = P.Solver(wl, format=1, precision=precision, rank_cap=cap, tol=tol)
-    s.step(steps, residual=False)
-    fg, mg = s.f(), s.moments()
-    ranks = P.dvm_get_ranks(s.h)
-    s.close()
-    un = max(np.linalg.norm(mo[:, 1:4]), 0.2 * np.sqrt(wl.n_cell))
+def sample_cells(wl):
+    """Cells whose full tensors enter the f error (every 257th: 128 of the C3 cavity)."""
+    return np.arange(0, wl.n_cell, max(1, wl.n_cell // 128 + 1))
+
+
+def snapshot(P, s, wl):
+    """Macroparameters and the full tensors of the sampled cells of a solve."""
+    cells = sample_cells(wl)
+    f = np.concatenate([s.f(int(c), 1) for c in cells])
+    return {"macro": s.moments(), "f": f, "steps": P.dvm_get_step_count(s.h)}
+
+
+def macro_errors(snap, ref, wl):
+    """Relative L2 errors of a snapshot against the reference snapshot: f over the sampled
+    cells, n and T per cell; u relative to max(|u|, lid speed sqrt(N_C)) and q relative to
+    max(|q|, |n T^1.5 / 2|), since both vanish at rest in most cells."""
+    assert snap["steps"] == ref["steps"], (snap["steps"], ref["steps"])
+    mg, mo = snap["macro"], ref["macro"]
+    lid = max(abs(float(p[1])) for _, _, p in wl.bcs) or 0.2
+    un = max(np.linalg.norm(mo[:, 1:4]), lid * np.sqrt(wl.n_cell))
     qn = max(np.linalg.norm(mo[:, 5:8]), np.linalg.norm(0.5 * mo[:, 0] * mo[:, 4] ** 1.5))
-    return {"workload": f"cavity_8^3x24^3, {steps} steps", "eps": tol, "rank_cap": cap,
-            "f": _rel(fg, fo), "n": _rel(mg[:, 0], mo[:, 0]), "T": _rel(mg[:, 4], mo[:, 4]),
+    return {"f": _rel(snap["f"], ref["f"]), "n": _rel(mg[:, 0], mo[:, 0]),
+            "T": _rel(mg[:, 4], mo[:, 4]),
             "u": float(np.linalg.norm(mg[:, 1:4] - mo[:, 1:4]) / un),
             "q": float(np.linalg.norm(mg[:, 5:8] - mo[:, 5:8]) / qn),
-            "rank_mean": float(ranks.mean()), "rank_max": int(ranks.max()),
-            "note": "u relative to max(|u|, lid speed), q to max(|q|, n T^1.5 / 2); vs FP64 oracle"}
+            "at_step": snap["steps"]}
+
+
+def rank_histogram(r):
+    h = np.bincount(np.asarray(r).ravel(), minlength=1)
+    return {int(k): int(v) for k, v in enumerate(h) if v}
+
+
+def run_path(P, NAT, wl, fmt, prec, cap, tol, advance, warmup, steps, stream, snap=True):
+    """One solve on one path: `advance` untimed steps, `warmup` more, `steps` timed; its
+    step time, memory, ranks and (snap) a snapshot after exactly advance + warmup + steps
+    steps."""
+    import torch
+    s = P.Solver(wl, format=fmt, precision=prec, rank_cap=cap, tol=tol,
+                 stream=stream.cuda_stream)
+    if advance:
+        s.step(advance, residual=False)
+    ms = _time_steps(s, steps, warmup, stream) / steps
+    fb, tb = P.dvm_memory(s.h)
+    d = {"ms_per_step": ms, "updates_per_s": wl.n_cell * wl.nodes_per_cell / (ms / 1e3),
+         "f_bytes": fb, "device_bytes": tb, "steps_timed": steps,
+         "untimed_steps_before": advance + warmup}
+    if fmt == NAT.DVM_FORMAT_TUCKER:
+        r = P.dvm_get_ranks(s.h)
+        g, _ = P.dvm_get_launch_config(s.h)
+        d.update({"eps": tol, "rank_cap": cap, "rank_mean": float(r.mean()),
+                  "rank_max": int(r.max()), "rank_histogram": rank_histogram(r),
+                  "compression": fb / (8.0 * wl.n_cell * wl.nodes_per_cell),
+                  "variant": "phase-major" if g < 0 else "fused"})
+    sn = snapshot(P, s, wl) if snap else None
+    s.close()
+    torch.cuda.synchronize()
+    return d, sn
 
 
 def run_serving(P, n_req=12, seed=7, mean_gap_s=0.25, budget_gb=64, slots=8, res_tol=1e-4,
                 max_steps=4000):
     """Seeded Poisson arrivals of steady channel solves (Poiseuille / thermal
     transpiration), Tucker mixed format, each run to the residual res_tol (scaled-down
-    version of the 64-request mix so that it ends within the bench's time)."""
+    version of the 64-request mix so that it ends within the bench's time).  Latency
+    percentiles and solves/hour count the converged solves only; the others are
+    reported by state."""
     import workloads as W
     rng = np.random.default_rng(seed)
     reqs = []
@@ -368,67 +430,66 @@ def run_serving(P, n_req=12, seed=7, mean_gap_s=0.25, budget_gb=64, slots=8, res
     lat, conv, upd, states, errors = [], 0, 0, {}, set()
     for tk, wl in tickets:
         st = srv.poll(tk)
-        lat.append(st["latency_s"])
-        conv += st["state"] == 2
+        if st["state"] == 2:
+            lat.append(st["latency_s"])
+            conv += 1
         states[st["state"]] = states.get(st["state"], 0) + 1
         if st["state"] == 4:
             errors.add(srv.error(tk))
         upd += st["steps"] * wl.n_cell * wl.nodes_per_cell
     srv.close()
     lat = np.array(lat)
-    return {"requests": n_req, "converged": int(conv),
-            "states": {["queued", "running", "converged", "not_converged", "failed"][k]: v
-                       for k, v in sorted(states.items())},
+    names = ["queued", "running", "converged", "not_converged", "failed", "cancelled"]
+    return {"requests": n_req, "converged": int(conv), "not_converged": n_req - int(conv),
+            "states": {names[k]: v for k, v in sorted(states.items())},
             "errors": sorted(errors), "wall_s": total,
-            "solves_per_hour": 3600.0 * n_req / total, "p50_latency_s": float(np.percentile(lat, 50)),
-            "p99_latency_s": float(np.percentile(lat, 99)), "updates_per_s": upd / total,
+            "converged_solves_per_hour": 3600.0 * conv / total,
+            "p50_latency_s": float(np.percentile(lat, 50)) if conv else None,
+            "p99_latency_s": float(np.percentile(lat, 99)) if conv else None,
+            "latency_over": "converged solves only (submission to converged residual)",
+            "updates_per_s": upd / total,
             "mix": f"{n_req} channel Poiseuille/transpiration solves, 256-1024 cells, "
                    "12^3-16^3 nodes, Kn 0.3-10, Tucker mixed eps 1e-6 cap 6-12, residual "
                    f"{res_tol:g} (at most {max_steps} steps), Poisson arrivals (mean gap "
                    f"{mean_gap_s} s, seed {seed}), {slots} slots"}
 
 
-def run_configs(P, NAT, stream):
-    """The larger configurations on the same code path, a few steps each: C3 (cavity,
-    32^3 cells x 48^3, mixed Tucker cap 12, eps 1e-5, beside the full grid FP64) and C4
-    (Mach-3 flow past a cube, 101,888 jittered cells x 64^3, mixed Tucker cap 20,
-    eps 1e-5; its full-grid FP64 state would need two copies of 213.7 GB)."""
+def run_c2(P, NAT, stream, advance=200, warmup=3, steps=10):
+    """C2, the cavity on 16^3 cells x 32^3: full grid FP64 (the reference at the same step
+    count), Tucker FP64 at the configuration's literal setting (cap 8, eps 1e-5), and
+    Tucker FP64 / mixed at cap 12, eps 1e-6."""
+    import workloads as W
+    wl = W.cavity()
+    out = {}
+    full, ref = run_path(P, NAT, wl, NAT.DVM_FORMAT_FULL, NAT.DVM_PREC_FP64, 8, 0.0, advance,
+                         warmup, steps, stream)
+    out["full_fp64"] = full
+    for name, prec, cap, tol in [("tucker_fp64_cap8_eps1e-5", NAT.DVM_PREC_FP64, 8, 1e-5),
+                                 ("tucker_fp64_cap12_eps1e-6", NAT.DVM_PREC_FP64, 12, 1e-6),
+                                 ("tucker_mixed_cap12_eps1e-6", NAT.DVM_PREC_MIXED, 12, 1e-6)]:
+        d, sn = run_path(P, NAT, wl, NAT.DVM_FORMAT_TUCKER, prec, cap, tol, advance, warmup,
+                         steps, stream)
+        d["error_vs_full_fp64"] = macro_errors(sn, ref, wl)
+        d["speedup_vs_full"] = full["ms_per_step"] / d["ms_per_step"]
+        out[name] = d
+    return out
+
+
+def run_c4(P, NAT, stream, advance=10, steps=3):
+    """C4, Mach-3 flow past a cube on 101,888 jittered cells x 64^3, Tucker mixed cap 20,
+    eps 1e-5, a few steps from the initial free stream (its full-grid FP64 state would need
+    two copies of 213.7 GB)."""
     import torch
     import workloads as W
-    out = {}
-
-    def timed(wl, fmt, prec, cap, tol, advance, steps):
-        s = P.Solver(wl, format=fmt, precision=prec, rank_cap=cap, tol=tol,
-                     stream=stream.cuda_stream)
-        if advance:
-            s.step(advance, residual=False)
-        ms = _time_steps(s, steps, 2, stream) / steps
-        fb, tb = P.dvm_memory(s.h)
-        d = {"ms_per_step": ms, "updates_per_s": wl.n_cell * wl.nodes_per_cell / (ms / 1e3),
-             "f_bytes": fb, "device_bytes": tb, "steps_timed": steps,
-             "untimed_steps_before": advance + 2}
-        if fmt == NAT.DVM_FORMAT_TUCKER:
-            r = P.dvm_get_ranks(s.h)
-            g, _ = P.dvm_get_launch_config(s.h)
-            d.update({"eps": tol, "rank_cap": cap, "rank_mean": float(r.mean()),
-                      "rank_max": int(r.max()), "variant": "phase-major" if g < 0 else "fused"})
-        s.close()
-        torch.cuda.synchronize()
-        return d
-
-    c3 = W.cavity(nside=32, N=48)
-    out["C3_cavity_32^3x48^3"] = {
-        "tucker_mixed": timed(c3, NAT.DVM_FORMAT_TUCKER, NAT.DVM_PREC_MIXED, 12, 1e-5, 20, 5),
-        "full_fp64": timed(c3, NAT.DVM_FORMAT_FULL, NAT.DVM_PREC_FP64, 12, 1e-5, 0, 3)}
-    del c3
     c4 = W.obstacle()
     total = torch.cuda.get_device_properties(torch.cuda.current_device()).total_memory
     need = P.dvm_estimate_memory(c4, format=NAT.DVM_FORMAT_FULL)
-    out[f"C4_obstacle_{c4.n_cell}x64^3"] = {
-        "tucker_mixed": timed(c4, NAT.DVM_FORMAT_TUCKER, NAT.DVM_PREC_MIXED, 20, 1e-5, 10, 3),
+    d, _ = run_path(P, NAT, c4, NAT.DVM_FORMAT_TUCKER, NAT.DVM_PREC_MIXED, 20, 1e-5, advance,
+                    2, steps, stream, snap=False)
+    return {f"C4_obstacle_{c4.n_cell}x64^3": {
+        "tucker_mixed": d,
         "full_fp64": {"device_bytes_needed": need, "device_bytes_total": int(total),
-                      "fits": bool(need <= total)}}
-    return out
+                      "fits": bool(need <= total)}}}
 
 
 def run_gpu(args, rank, world):
@@ -449,6 +510,7 @@ def run_gpu(args, rank, world):
     cap = args.rank_cap or 12
     tol = args.tol or 1e-6
     tucker = args.path == "tucker"
+    W_ = max(3, args.warmup)
 
     # headline path, timed with the clock sampler running
     fmt = NAT.DVM_FORMAT_TUCKER if tucker else NAT.DVM_FORMAT_FULL
@@ -458,7 +520,7 @@ def run_gpu(args, rank, world):
                  variant=variant)
     if args.advance:
         s.step(args.advance, residual=False)
-    for _ in range(max(3, args.warmup)):
+    for _ in range(W_):
         s.step(1, residual=False)
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -490,7 +552,7 @@ def run_gpu(args, rank, world):
                         "peak_source": f"{src} MEASURED_PEAKS.json hbm_gbs"}}
         launches = args.steps
     else:
-        roof = _roofline_tucker(P, s, wl, args.steps)
+        roof = _roofline_tucker(P, s, wl, args.steps, peaks, src)
         kt = roof["kernel_times"]
         # the timing pass runs one stream (one event pair per kernel launch); the
         # headline region runs the phase-major chain per cell range on two streams:
@@ -512,37 +574,13 @@ def run_gpu(args, rank, world):
                 "f_bytes": fbh, "device_bytes": tbh}
         if tucker:
             head.update({"eps": tol, "rank_cap": cap, "rank_mean": float(rh.mean()),
-                         "rank_max": int(rh.max()), "compression": fbh / (8.0 * upd),
+                         "rank_max": int(rh.max()), "rank_histogram": rank_histogram(rh),
+                         "compression": fbh / (8.0 * upd),
                          "variant": "phase-major" if grid < 0 else "fused",
                          "autotune_ms": {"phase_major": tune[0],
                                          "fused_by_ctas_per_sm": tune[1:]}})
+        head_snap = snapshot(P, s, wl) if tucker and not args.no_reference else None
         paths[("tucker_" if tucker else "full_") + args.precision] = head
-        if not args.no_extras:
-            # the other formats on the same inputs
-            others = [("full_fp64", NAT.DVM_FORMAT_FULL, NAT.DVM_PREC_FP64, cap, tol),
-                      ("tucker_fp64", NAT.DVM_FORMAT_TUCKER, NAT.DVM_PREC_FP64, cap, tol),
-                      ("tucker_fp64_cap8_eps1e-5", NAT.DVM_FORMAT_TUCKER, NAT.DVM_PREC_FP64, 8,
-                       1e-5),
-                      ("tucker_mixed", NAT.DVM_FORMAT_TUCKER, NAT.DVM_PREC_MIXED, cap, tol)]
-            for name, f2, p2, c2, e2 in others:
-                if name in paths:
-                    continue
-                t = P.Solver(wl, format=f2, precision=p2, rank_cap=c2, tol=e2,
-                             stream=stream.cuda_stream)
-                if args.advance and f2 == NAT.DVM_FORMAT_TUCKER:
-                    t.step(args.advance, residual=False)
-                tms = _time_steps(t, args.steps, args.warmup, stream) / args.steps
-                fb, tb = P.dvm_memory(t.h)
-                d = {"ms_per_step": tms, "updates_per_s": upd / (tms / 1e3), "f_bytes": fb,
-                     "device_bytes": tb}
-                if f2 == NAT.DVM_FORMAT_TUCKER:
-                    r = P.dvm_get_ranks(t.h)
-                    g2, _ = P.dvm_get_launch_config(t.h)
-                    d.update({"eps": e2, "rank_cap": c2, "rank_mean": float(r.mean()),
-                              "rank_max": int(r.max()), "compression": fb / (8.0 * upd),
-                              "variant": "phase-major" if g2 < 0 else "fused"})
-                paths[name] = d
-                t.close()
         e2e = None
         if not args.no_e2e:
             k = 5
@@ -559,7 +597,7 @@ def run_gpu(args, rank, world):
                     m = s.moments()
                 el = time.perf_counter() - t0
                 note = ("per step: dvm_init_tucker from pinned host arrays (ranks, cores, "
-                        "factors), dvm_step, dvm_moments to host")
+                        "factors in the rank-cap arena layout), dvm_step, dvm_moments to host")
             else:
                 f_host = torch.empty((wl.n_cell,) + tuple(wl.N), dtype=torch.float64,
                                      pin_memory=True)
@@ -576,30 +614,52 @@ def run_gpu(args, rank, world):
                 note = "per step: dvm_init_f from pinned host f, dvm_step, dvm_moments to host"
             e2e = {"value": upd * k / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": int(m.nbytes), "note": note}
+    s.close()
+    torch.cuda.synchronize()
+    if rank == 0:
+        accuracy = None
+        if tucker and not args.no_reference:
+            # the full-grid FP64 path on the same workload, to the same step count: its step
+            # time beside the Tucker path's, and the reference of the Tucker path's error
+            n_ref = head_snap["steps"]
+            full, ref = run_path(P, NAT, wl, NAT.DVM_FORMAT_FULL, NAT.DVM_PREC_FP64, cap, tol,
+                                 n_ref - args.steps - W_, W_, args.steps, stream)
+            paths["full_fp64"] = full
+            head["speedup_vs_full"] = full["ms_per_step"] / step_ms
+            head["memory_ratio_vs_full"] = full["f_bytes"] / fbh
+            accuracy = {**macro_errors(head_snap, ref, wl), "eps": tol, "rank_cap": cap,
+                        "reference": "full-grid FP64 GPU path, same workload and step count "
+                                     "(checked against the FP64 oracle at this size by the "
+                                     "GPU tests)",
+                        "meets_1e-4": None}
+            accuracy["meets_1e-4"] = bool(max(accuracy[k] for k in "fnTuq") <= 1e-4)
         cfg = {**wl.describe(), "path": args.path,
                "format": "full tensor FP64" if not tucker else
                          f"Tucker {args.precision}, eps {tol:g}, rank cap {cap}",
                "l2": f"inputs larger than L2 ({8 * upd / 1e9:.2f} GB per full FP64 copy of f; "
                      "Tucker: per-step work buffers of the same order)",
                "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
-               "state": f"timed after {args.advance} untimed steps from the initial "
+               "state": f"timed after {args.advance + W_} untimed steps from the initial "
                         "equilibrium (developed flow and ranks)"}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-                "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": step_ms,
+                "steps": args.steps, "warmup": W_, "ms_per_step": step_ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64" if not tucker or prec == NAT.DVM_PREC_FP64 else "f32+f64",
                 "data": "synthetic", "config": cfg, "roofline": roof, "gpu_launches": launches,
                 "clocks": clk.summary(), "residual_after": res, "paths": paths}
+        if accuracy:
+            line["tucker_accuracy"] = accuracy
         if e2e:
             line["e2e"] = e2e
         if not args.no_extras:
-            line["tucker_accuracy"] = tucker_accuracy(P, cap, tol, NAT.DVM_PREC_MIXED)
+            line["configs"] = {}
+            if args.workload != "c2":
+                line["configs"]["C2_cavity_16^3x32^3"] = run_c2(P, NAT, stream)
+            line["configs"].update(run_c4(P, NAT, stream))
             line["serving"] = run_serving(P)
-            line["configs"] = run_configs(P, NAT, stream)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(wl)
         print(json.dumps(line), flush=True)
-    s.close()
     if dist:
         dist.barrier()
         dist.destroy_process_group()
