@@ -118,7 +118,19 @@ typedef struct {
                        * sized to 1/8 of the free device memory, at most all
                        * cells); bounds the context's memory.  Results do not
                        * depend on it.                                      */
+  int32_t gram_engine; /* mixed-precision Tucker, phase-major variant: how the
+                       * first-mode Gram matrices are formed.  DVM_GRAM_AUTO
+                       * (0): on the tensor cores (exact integer split, see
+                       * dvm_gram_tc) when N1 <= 64 and N2 N3 is a multiple
+                       * of 8 up to 4096, else on the CUDA cores;
+                       * DVM_GRAM_CUDA_CORES (1): exact FP32 products summed
+                       * in double-FP32 on the CUDA cores, as the fused
+                       * variant does (the two variants then agree bit for
+                       * bit).  Both are accurate far below FP32 rounding.  */
 } dvm_opts;
+
+#define DVM_GRAM_AUTO 0
+#define DVM_GRAM_CUDA_CORES 1
 
 #define DVM_VARIANT_AUTO 0
 #define DVM_VARIANT_FUSED 1
@@ -351,6 +363,23 @@ void dvm_server_destroy(dvm_server *srv);
  * summation order. */
 int dvm_full_macro_noalloc(const double *f, int64_t n_cell, const dvm_vgrid *vgrid,
                            double *macro, void *cuda_stream);
+
+/* Gram matrices C_j = X_j X_j^T of ncell row-major n x K FP32 matrices on the
+ * tensor cores (tcgen05, bf16 MMAs with FP32 accumulators), exact up to FP64
+ * rounding for the tensor whose elements are rounded to 35 bits below their
+ * row's largest magnitude (an Ozaki-type split into five 7-bit integer slices).
+ * This is the Gram step of the mixed-precision Tucker rounding (Section 4 item 4,
+ * the truncated SVD of each unfolding), exported as a building block; the paper
+ * has no such call.
+ *   X       device pointer, [ncell][n][K] floats, 16-byte aligned
+ *   n, K    1 <= n <= 64, 8 <= K <= 4096, K a multiple of 8 (else INVALID_ARG)
+ *   C       device pointer, [ncell][n][n] doubles, written on cuda_stream (the
+ *           call only enqueues; synchronise before reading)
+ *   status  device pointer to an int the kernel ORs 2 into if one of its
+ *           bounded waits runs out (C is then incomplete); the caller zeroes it
+ * Errors: INVALID_ARG, UNSUPPORTED (no such launch on this device), CUDA. */
+int dvm_gram_tc(const float *X, int64_t ncell, int32_t n, int32_t K, double *C,
+                int32_t *status, void *cuda_stream);
 
 /* Host-side fault injection, for testing the error paths (the paper has no
  * counterpart).  Process-wide; each kind fires once and then disarms:

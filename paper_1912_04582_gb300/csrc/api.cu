@@ -187,6 +187,10 @@ int dvm_create(dvm_ctx **out, const dvm_mesh *mesh, const dvm_vgrid *vg, const d
     set_error("dvm_create: unknown format");
     return DVM_ERR_INVALID_ARG;
   }
+  if (opts->gram_engine != DVM_GRAM_AUTO && opts->gram_engine != DVM_GRAM_CUDA_CORES) {
+    set_error("dvm_create: gram_engine must be DVM_GRAM_AUTO or DVM_GRAM_CUDA_CORES");
+    return DVM_ERR_INVALID_ARG;
+  }
   if (opts->max_chunk < 0) {
     set_error("dvm_create: max_chunk must be >= 0");
     return DVM_ERR_INVALID_ARG;

@@ -38,6 +38,7 @@ struct TuckerStepParams {
   int64_t nc;
   int N1, N2, N3, R, Nmax;
   int mode;              // 0 = time step, 1 = compress finit
+  int tc_gram;           // phase-major mixed path: first-mode Gram on the tensor cores
   double w, dt, Pr, omega, delta, tol;
 };
 
@@ -110,6 +111,29 @@ struct TuckerMomentParams {
   double w;
   int stage;             // set by launch_tucker_moments: factors (1) / core (2) to shared memory
 };
+
+// Tensor-core Gram matrices (gram_tc.cu): plan of the MMA groups for n rows
+constexpr int kTcSlices = 5;     // integer slices per FP32 value
+constexpr int kTcMaxGroups = 4;  // MMA groups per K-chunk
+struct GramTcPlan {
+  int n, sp;                     // rows, rows per slice in shared memory
+  int ngroups;                   // 0: no plan
+  int a0[kTcMaxGroups];          // first slice of the A operand (128 rows)
+  int b0[kTcMaxGroups];          // first slice of the B operand
+  int nb[kTcMaxGroups];          // slices in the B operand
+  int N[kTcMaxGroups];           // MMA N (B rows, a multiple of 16)
+  int col[kTcMaxGroups];         // first tensor-memory column of the group's accumulator
+  int ncols;                     // tensor-memory columns allocated
+  int buf_rows;                  // rows of one shared-memory stage
+  signed char own[kTcSlices * kTcSlices];  // group + 1 that owns product (k, l), else 0
+};
+GramTcPlan gram_tc_plan(int n);
+bool gram_tc_supported(int n, int K);
+// raise the kernel's shared-memory opt-in for n rows (outside stream captures); 0 ok
+int gram_tc_prepare(int n);
+// C (double-float pairs) or Cd (doubles), cstride elements per cell; disc[cell] = 0
+int launch_gram_tc(const float *X, int64_t xstride, int64_t ncell, int n, int K, float2 *C,
+                   double *Cd, int64_t cstride, double *disc, int *flag, cudaStream_t s);
 
 size_t tucker_scratch_elems(int N1, int N2, int N3, int R);
 size_t tucker_smem_bytes(int Nmax, int R, bool fp64);

@@ -33,6 +33,8 @@
 // matrices, eigen-solves, energy sums and the stored state are FP64.
 #include <cfloat>
 #include <cmath>
+#include <map>
+#include <mutex>
 
 #include "dvm_device.cuh"
 #include "dvm_internal.h"
@@ -2385,9 +2387,15 @@ __global__ void tucker_maxwellian_kernel(TuckerDev Tk, const double *n, const do
 // The kernels' dynamic shared-memory opt-in is a per-function setting shared by
 // every context in the process: only ever raise it (to the largest size any
 // context needs), and do so outside stream captures (tucker_prepare_launch is
-// called when a context is created).
+// called when a context is created).  The sizes set so far are kept per kernel
+// function (one kernel serves contexts of every size).
+std::mutex g_optin_mu;
+std::map<const void *, size_t> g_optin;
+
 template <typename K>
-int raise_smem_optin(K kernel, size_t smem, size_t &opted) {
+int raise_smem_optin(K kernel, size_t smem) {
+  std::lock_guard<std::mutex> lk(g_optin_mu);
+  size_t &opted = g_optin[reinterpret_cast<const void *>(kernel)];
   if (smem <= opted) return 0;
   if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess) {
@@ -2399,33 +2407,12 @@ int raise_smem_optin(K kernel, size_t smem, size_t &opted) {
 }
 
 template <typename Real, int TS>
-struct OptIn {
-  static size_t step, expand, asm_, gram, gram_small, eig, proj, t2;
-};
-template <typename Real, int TS>
-size_t OptIn<Real, TS>::step = 0;
-template <typename Real, int TS>
-size_t OptIn<Real, TS>::expand = 0;
-template <typename Real, int TS>
-size_t OptIn<Real, TS>::asm_ = 0;
-template <typename Real, int TS>
-size_t OptIn<Real, TS>::gram = 0;
-template <typename Real, int TS>
-size_t OptIn<Real, TS>::gram_small = 0;
-template <typename Real, int TS>
-size_t OptIn<Real, TS>::eig = 0;
-template <typename Real, int TS>
-size_t OptIn<Real, TS>::proj = 0;
-template <typename Real, int TS>
-size_t OptIn<Real, TS>::t2 = 0;
-
-template <typename Real, int TS>
 int launch_step_TS(const TuckerStepParams &p, int grid, cudaStream_t s) {
   const size_t smem = smem_bytes<Real>(p.Nmax, p.R);
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(s, &cap);
   if (cap == cudaStreamCaptureStatusNone &&
-      raise_smem_optin(tucker_step_kernel<Real, TS>, smem, OptIn<Real, TS>::step) != 0)
+      raise_smem_optin(tucker_step_kernel<Real, TS>, smem) != 0)
     return -1;
   tucker_step_kernel<Real, TS><<<grid, kTB, smem, s>>>(p);
   return 0;
@@ -2455,16 +2442,14 @@ template <typename Real, int TS>
 // the variants whose kernels fit: 1 fused, 2 phase-major.
 int prepare_split_TS(int Nmax, int R) {
   const SplitSmem<Real, TS> z(Nmax, R);
-  using O = OptIn<Real, TS>;
   int mask = 0;
-  if (raise_smem_optin(tucker_step_kernel<Real, TS>, smem_bytes<Real>(Nmax, R), O::step) == 0)
-    mask |= 1;
-  if (raise_smem_optin(tucker_asm_kernel<Real>, z.asm_, O::asm_) == 0 &&
-      raise_smem_optin(tucker_t2_kernel<Real>, z.asm_, O::t2) == 0 &&
-      raise_smem_optin(tucker_gram_kernel<Real, TS>, z.gram, O::gram) == 0 &&
-      raise_smem_optin(tucker_gram_small_kernel<Real>, z.gram_small, O::gram_small) == 0 &&
-      raise_smem_optin(tucker_eig_kernel<Real>, z.eig, O::eig) == 0 &&
-      raise_smem_optin(tucker_proj_kernel<Real>, z.proj, O::proj) == 0)
+  if (raise_smem_optin(tucker_step_kernel<Real, TS>, smem_bytes<Real>(Nmax, R)) == 0) mask |= 1;
+  if (raise_smem_optin(tucker_asm_kernel<Real>, z.asm_) == 0 &&
+      raise_smem_optin(tucker_t2_kernel<Real>, z.asm_) == 0 &&
+      raise_smem_optin(tucker_gram_kernel<Real, TS>, z.gram) == 0 &&
+      raise_smem_optin(tucker_gram_small_kernel<Real>, z.gram_small) == 0 &&
+      raise_smem_optin(tucker_eig_kernel<Real>, z.eig) == 0 &&
+      raise_smem_optin(tucker_proj_kernel<Real>, z.proj) == 0)
     mask |= 2;
   return mask;
 }
@@ -2481,10 +2466,21 @@ void split_chain(const TuckerStepParams &p, const TuckerSplitBufs &b, const Spli
   for (int m = 0; m < 3; ++m) {
     const int gc = m == 0 ? kKGram0 : kKGram12;
     T(gc, true, s);
-    if (m >= 1 && p.Nmax <= 32)  // every cell's N_m <= 32: gram_seq in a light kernel
+    bool done = false;
+    if constexpr (sizeof(Real) == 4) {
+      if (m == 0 && p.tc_gram) {  // exact-split Gram on the tensor cores (gram_tc.cu)
+        const int64_t NN = (int64_t)p.N1 * p.N2 * p.N3, NC = (int64_t)p.Nmax * p.Nmax;
+        done = launch_gram_tc(reinterpret_cast<const float *>(b.X) + b.joff * NN, NN, b.cn, p.N1,
+                              p.N2 * p.N3, reinterpret_cast<float2 *>(b.C + b.joff * NC), nullptr,
+                              NC, b.disc + b.joff, p.flag, s) == 0;
+      }
+    }
+    if (done) {
+    } else if (m >= 1 && p.Nmax <= 32) {  // every cell's N_m <= 32: gram_seq in a light kernel
       tucker_gram_small_kernel<Real><<<(unsigned)b.cn, kTB, z.gram_small, s>>>(p, b, m);
-    else
+    } else {
       tucker_gram_kernel<Real, TS><<<(unsigned)b.cn, kTB, z.gram, s>>>(p, b, m);
+    }
     T(gc, false, s);
     T(kKEig, true, s);
     tucker_eig_kernel<Real><<<(unsigned)b.cn, 32, z.eig, s>>>(p, b, m);
@@ -2563,7 +2559,7 @@ template <typename Real>
 int launch_expand_T(const TuckerDev &T, int64_t c0, int64_t ncell, int N1, int N2, int N3, int R,
                     int Nmax, void *scratch, size_t stride, double *out, int grid, cudaStream_t s) {
   const size_t smem = sizeof(Real) * 3 * (size_t)Nmax * R;
-  if (raise_smem_optin(tucker_expand_kernel<Real>, smem, OptIn<Real, 0>::expand) != 0) return -1;
+  if (raise_smem_optin(tucker_expand_kernel<Real>, smem) != 0) return -1;
   tucker_expand_kernel<Real><<<grid, kTB, smem, s>>>(T, c0, ncell, N1, N2, N3, R, Nmax, scratch,
                                                      stride, out);
   return 0;
@@ -2581,7 +2577,7 @@ size_t tucker_scratch_elems(int N1, int N2, int N3, int R) {
 template <typename Real, int TS>
 int blocks_per_sm_TS(int Nmax, int R) {
   const size_t smem = smem_bytes<Real>(Nmax, R);
-  if (raise_smem_optin(tucker_step_kernel<Real, TS>, smem, OptIn<Real, TS>::step) != 0) return 1;
+  if (raise_smem_optin(tucker_step_kernel<Real, TS>, smem) != 0) return 1;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tucker_step_kernel<Real, TS>, kTB, smem) !=
       cudaSuccess) {

@@ -50,6 +50,14 @@ int ctx_finalize_dt_from_macro(dvm_ctx *C, const std::vector<double> &macro);
 
 namespace {
 
+// launch errors with the place they surfaced
+int launch_check(const char *where) {
+  const cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) return DVM_OK;
+  set_error(std::string("Tucker step (") + where + "): " + cudaGetErrorString(e));
+  return DVM_ERR_CUDA;
+}
+
 int sync_check(dvm_ctx *C) {
   DVM_CUDA_TRY(cudaGetLastError());
   DVM_CUDA_TRY(cudaStreamSynchronize(C->stream));
@@ -80,6 +88,8 @@ TuckerStepParams step_params(dvm_ctx *C) {
   p.omega = C->gas.omega;
   p.delta = std::sqrt(3.14159265358979323846) / (2.0 * C->gas.Kn);
   p.tol = C->opts.tol;
+  p.tc_gram = !S->fp64 && C->opts.gram_engine == DVM_GRAM_AUTO &&
+              gram_tc_supported(C->N[0], C->N[1] * C->N[2]);
   return p;
 }
 
@@ -231,6 +241,11 @@ int tucker_alloc(dvm_ctx *C) {
   if (rc != DVM_OK) return rc;
   DVM_CUDA_TRY(cudaMemset(S->err, 0, sizeof(double) * nc));
   S->fit = tucker_prepare_launch(S->Nmax, R, S->fp64);
+  if (!S->fp64 && C->opts.gram_engine == DVM_GRAM_AUTO &&
+      gram_tc_supported(C->N[0], C->N[1] * C->N[2]) && gram_tc_prepare(C->N[0]) != 0) {
+    set_error("tensor-core Gram kernel: shared-memory opt-in refused by the device");
+    return DVM_ERR_UNSUPPORTED;
+  }
   const int need = C->opts.variant == DVM_VARIANT_FUSED ? 1 :
                    C->opts.variant == DVM_VARIANT_PHASED ? 2 : 3;
   if (!(S->fit & need)) {
@@ -570,7 +585,9 @@ int tucker_step(dvm_ctx *C, int32_t nsteps, double *residual_out) {
         S->graph = nullptr;
       }
     }
-    int rc = autotune(C);
+    int rc = launch_check("before the autotuner");
+    if (rc == DVM_OK) rc = autotune(C);
+    if (rc == DVM_OK) rc = launch_check("autotuner");
     if (rc != DVM_OK) return rc;
   }
   TuckerStepParams p = step_params(C);
@@ -598,6 +615,7 @@ int tucker_step(dvm_ctx *C, int32_t nsteps, double *residual_out) {
       const int c0 = S->cur, s0 = S->scur;
       int rc = enqueue_one_step(C, p);
       if (rc == DVM_OK) rc = enqueue_one_step(C, p);
+      if (rc == DVM_OK) rc = launch_check("graph capture");
       S->cur = c0;  // capture does not execute: restore the parity
       S->scur = s0;
       cudaError_t e = cudaStreamEndCapture(S->gstream, &g);
@@ -625,8 +643,7 @@ int tucker_step(dvm_ctx *C, int32_t nsteps, double *residual_out) {
     if (rc != DVM_OK) return rc;
     C->steps++;
   }
-  DVM_CUDA_TRY(cudaGetLastError());
-  return DVM_OK;
+  return launch_check(use_graph ? "graph replay / last step" : "step launches");
 }
 
 int tucker_launch_info(dvm_ctx *C, int32_t *grid, float *tune_ms) {

@@ -218,13 +218,15 @@ def test_graph_replay_equals_single_steps(dvm):
 def test_launch_variants_compute_the_same_values(dvm, precision):
     """The fused persistent kernel and the phase-major variant (assembly, then per mode
     Gram / eigen-solve / projection kernels) run the same per-cell arithmetic in the
-    same order, so 12 steps of a cavity with walls, a moving lid and an inflow-free
-    interior agree bit for bit; the launch configuration reports the variant."""
+    same order (first-mode Gram on the CUDA cores in both), so 12 steps of a cavity with
+    walls, a moving lid and an inflow-free interior agree bit for bit; the launch
+    configuration reports the variant."""
     from paper_1912_04582_gb300 import _native as NAT
     wl = W.cavity(nside=6, N=16, seed=4)
     out = {}
     for v in (NAT.DVM_VARIANT_FUSED, NAT.DVM_VARIANT_PHASED):
-        s = dvm.Solver(wl, format=1, precision=precision, rank_cap=8, tol=1e-6, variant=v)
+        s = dvm.Solver(wl, format=1, precision=precision, rank_cap=8, tol=1e-6, variant=v,
+                       gram_engine=NAT.DVM_GRAM_CUDA_CORES)
         s.step(12)
         out[v] = (s.f(), s.moments(), dvm.dvm_get_ranks(s.h))
         grid, _ = dvm.dvm_get_launch_config(s.h)
@@ -283,7 +285,8 @@ def test_velocity_grids_above_32_nodes(dvm, oracle_lib, N, precision):
     fo, mo = o.f(), o.macro()
     out = {}
     for v in (NAT.DVM_VARIANT_FUSED, NAT.DVM_VARIANT_PHASED):
-        s = dvm.Solver(wl, format=1, precision=precision, rank_cap=12, tol=1e-6, variant=v)
+        s = dvm.Solver(wl, format=1, precision=precision, rank_cap=12, tol=1e-6, variant=v,
+                       gram_engine=NAT.DVM_GRAM_CUDA_CORES)
         s.step(8)
         out[v] = (s.f(), s.moments(), dvm.dvm_get_ranks(s.h))
         s.close()
@@ -371,7 +374,8 @@ def test_non_cubic_velocity_grid(dvm, oracle_lib, precision):
     fo, mo = o.f(), o.macro()
     out = {}
     for v in (NAT.DVM_VARIANT_FUSED, NAT.DVM_VARIANT_PHASED):
-        s = dvm.Solver(wl, format=1, precision=precision, rank_cap=12, tol=1e-6, variant=v)
+        s = dvm.Solver(wl, format=1, precision=precision, rank_cap=12, tol=1e-6, variant=v,
+                       gram_engine=NAT.DVM_GRAM_CUDA_CORES)
         s.step(8)
         out[v] = (s.f(), s.moments(), dvm.dvm_get_ranks(s.h))
         s.close()
@@ -399,3 +403,45 @@ def test_chunked_step_equals_single_chunk(dvm):
         assert np.array_equal(r, out[0][2])
         assert np.array_equal(f, out[0][0])
         assert np.array_equal(m, out[0][1])
+
+
+@pytest.mark.parametrize("nside,N", [(4, 32), (3, 48)])
+def test_tensor_core_gram_matches_cuda_core_gram(dvm, oracle_lib, nside, N):
+    """The phase-major mixed path with its first-mode Gram matrices on the tensor cores
+    (exact integer split) and on the CUDA cores (double-FP32): both within 1e-4 of the
+    oracle after 10 steps and within eps-level of each other (the two Gram matrices
+    differ only by rounding far below the truncation threshold, so the chosen ranks agree
+    in all but borderline cells)."""
+    from paper_1912_04582_gb300 import _native as NAT
+    wl = W.cavity(nside=nside, N=N, seed=9)
+    o = oracle_lib.FullGridOracle(wl)
+    o.step(10, o.dt())
+    fo, mo = o.f(), o.macro()
+    out = {}
+    for eng in (NAT.DVM_GRAM_AUTO, NAT.DVM_GRAM_CUDA_CORES):
+        s = dvm.Solver(wl, format=1, precision=MIXED, rank_cap=12, tol=1e-6,
+                       variant=NAT.DVM_VARIANT_PHASED, gram_engine=eng)
+        s.step(10)
+        out[eng] = (s.f(), s.moments(), dvm.dvm_get_ranks(s.h))
+        s.close()
+    for eng, (fg, mg, _) in out.items():
+        assert rel_l2(fg, fo) < 1e-4, eng
+        for k, err in macro_err(mg, mo, u_scale=0.2).items():
+            assert err < 1e-4, (eng, k, err)
+    a, b = out[NAT.DVM_GRAM_AUTO], out[NAT.DVM_GRAM_CUDA_CORES]
+    assert rel_l2(a[0], b[0]) < 2e-6
+    assert np.mean(a[2] == b[2]) > 0.98
+
+
+def test_contexts_of_different_sizes_in_one_process(dvm):
+    """The kernels' shared-memory opt-in is one setting per kernel function for the whole
+    process: a context with a small velocity grid created after a large one must not
+    lower what a later medium one needs (64, then 16, then 40 nodes; mixed precision,
+    phase-major)."""
+    from paper_1912_04582_gb300 import _native as NAT
+    for N in (64, 16, 40, 24, 48):
+        wl = W.cavity(nside=2, N=N, seed=1)
+        s = dvm.Solver(wl, format=1, precision=MIXED, rank_cap=8, tol=1e-6,
+                       variant=NAT.DVM_VARIANT_PHASED)
+        assert np.isfinite(s.step(3))
+        s.close()
