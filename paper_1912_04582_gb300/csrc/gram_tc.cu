@@ -27,12 +27,17 @@
 // accumulator lanes hold several slices) and a run of rows as B (N up to 256
 // columns hold several slices): a single instruction forms up to 4 x 5 slice
 // products.  One to three groups cover every needed pair for n <= 64; their FP32
-// accumulators live in tensor memory (TMEM).  Per CTA: 256 threads slice the next
-// chunk (from a register prefetch) while the tensor cores work on the previous ones
-// (three-stage ring, one mbarrier per stage signalled by tcgen05.commit); thread 0
-// issues the MMAs.  After a cell's last chunk the accumulators are read back
-// (tcgen05.ld) tile by tile and combined.  Every wait is bounded: on timeout the CTA
-// sets bit 1 of *flag, drains, frees its tensor memory and returns.
+// accumulators live in tensor memory (TMEM).  Per CTA (persistent, one per SM): one
+// thread streams the cell's K-chunks by 2-D TMA loads (cp.async.bulk.tensor) into a
+// four-deep ring, twice (row scales, then slicing); eight warps slice each chunk into
+// one of three bf16 stages while the tensor cores work on the previous ones (one
+// mbarrier per stage signalled by tcgen05.commit), and one of their threads issues
+// the MMAs.  After a cell's last chunk the accumulators are read back (tcgen05.ld)
+// tile by tile and combined while the next cell's chunks already load.  Every wait
+// is bounded: on timeout the CTA sets bit 1 of *flag, drains its loads and MMAs,
+// frees its tensor memory and returns.
+#include <cuda.h>
+
 #include <cstdint>
 #include <mutex>
 
@@ -42,10 +47,12 @@
 namespace dvm {
 namespace {
 
-constexpr int kTcThreads = 256;
-constexpr int kTcStages = 3;
+constexpr int kTcMaxStages = 3;     // shared-memory stages of sliced chunks (at most)
+constexpr int kTcLevels = 2 * kTcSlices - 2;  // slice-product levels k + l = 0 .. 7
 constexpr int kTcKC = 64;              // columns per chunk: one 128-byte bf16 row
 constexpr int kTcRowBytes = 128;
+constexpr int kTcRawStages = 4;              // TMA ring of FP32 chunks
+constexpr int kTcRawBytes = 64 * kTcKC * 4;  // one chunk of up to 64 rows
 constexpr int kTcWaitIters = 1 << 24;  // bound on the polls of one mbarrier phase
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -104,12 +111,14 @@ __device__ __forceinline__ void fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// bf16 of a small integer held in a float (exact), two per 32-bit word
+// bf16 of two small integers held in floats, packed (lo in the low half): a float
+// holding an integer of at most 8 significant bits has zero low 16 bits, so its bf16 is
+// its upper half, taken by a byte permute
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
-  uint32_t r;
-  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
-  return r;
+  return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
 }
+
+constexpr float kRoundMagic = 12582912.0f;  // 1.5 * 2^23
 
 }  // namespace
 
@@ -207,6 +216,13 @@ static GramTcPlan make_plan(int n) {
     rows = rb > rows ? rb : rows;
   }
   p.buf_rows = (rows + 7) / 8 * 8;
+  // three stages of sliced chunks where they fit beside the TMA ring and the level
+  // accumulators in 227 KB of shared memory, else two (n > 56)
+  const size_t fixed = 1024 + (size_t)kTcRawStages * kTcRawBytes +
+                       sizeof(int) * kTcLevels * (size_t)(n * (n + 1) / 2) + 1024;
+  p.nstages = fixed + (size_t)kTcMaxStages * p.buf_rows * kTcRowBytes <= 227 * 1024
+                  ? kTcMaxStages
+                  : kTcMaxStages - 1;
   return p;
 }
 
@@ -223,17 +239,23 @@ GramTcPlan gram_tc_plan(int n) {
   return plans[n];
 }
 
-size_t gram_tc_smem_bytes(const GramTcPlan &p) {
-  const size_t stages = (size_t)kTcStages * p.buf_rows * kTcRowBytes;
-  const size_t acc = sizeof(double) * 64 * 65 / 2;  // upper triangle, n <= 64
-  return 1024 + stages + acc + 64 * (sizeof(int) + sizeof(float)) + 64;
+// level accumulators: int32 [kTcLevels][n (n + 1) / 2]
+static size_t level_bytes(int n) { return sizeof(int) * kTcLevels * (size_t)(n * (n + 1) / 2); }
+
+static size_t smem_for(const GramTcPlan &p, int nstages) {
+  const size_t stages = (size_t)nstages * p.buf_rows * kTcRowBytes;
+  const size_t raw = (size_t)kTcRawStages * kTcRawBytes;
+  return 1024 + stages + raw + level_bytes(p.n) + 64 * (sizeof(int) + sizeof(float)) + 64;
 }
+
+size_t gram_tc_smem_bytes(const GramTcPlan &p) { return smem_for(p, p.nstages); }
 
 namespace {
 
+constexpr int kTcConsumers = 256;                  // eight slicing / MMA-issuing warps
+constexpr int kTcThreadsAll = kTcConsumers + 32;   // plus the TMA producer warp
+
 struct TcArgs {
-  const float *X;   // cell j: X + j * xstride, row-major n x K
-  int64_t xstride;
   int64_t ncell;
   int K;
   float2 *C;        // cell j: C + j * cstride, n x n double-float pairs (hi, lo), or
@@ -244,25 +266,94 @@ struct TcArgs {
   GramTcPlan plan;
 };
 
-__global__ void __launch_bounds__(kTcThreads, 1) gram_tc_kernel(TcArgs A) {
+// bounded wait on one mbarrier phase that also gives up once *abort is set
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, const volatile int *abort) {
+  uint32_t done = 0;
+  for (int it = 0; it < kTcWaitIters && !done; ++it) {
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (!done && *abort) break;
+  }
+  return done != 0;
+}
+
+// barrier of the eight consumer warps (named barrier 1) returning the AND of v
+__device__ __forceinline__ bool consumers_and(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.and.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(kTcConsumers)
+      : "memory");
+  return r != 0;
+}
+
+__device__ __forceinline__ void consumers_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kTcConsumers) : "memory");
+}
+
+__device__ __forceinline__ void bar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// 2-D tiled TMA load of one chunk (x: column, y: row) completing on bar
+__device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                         uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+      "%3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Warp 0: tensor-memory allocation and, in lane 0, the TMA producer: for each of the
+// CTA's cells, two passes over the cell's K-chunks (n rows x 64 columns of FP32, one
+// 2-D tiled load each) into a four-deep ring, each slot released by the eight
+// consumer warps.  Warps 1-8 (the consumers): pass 1 takes the row maxima (the row
+// scales of the split), pass 2 slices each chunk into a shared-memory stage and the
+// first consumer thread issues the chunk's MMAs, committed to the stage's mbarrier;
+// after a cell's last chunk the consumers read the accumulators back and combine
+// them while the producer already loads the next cell.
+__global__ void __launch_bounds__(kTcThreadsAll, 1)
+    gram_tc_kernel(const __grid_constant__ CUtensorMap xmap, TcArgs A) {
   extern __shared__ unsigned char tc_raw[];
   const GramTcPlan &P = A.plan;
   const int n = P.n, sp = P.sp, K = A.K;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   unsigned char *base = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~uintptr_t(1023));
-  const size_t stage_bytes = (size_t)P.buf_rows * kTcRowBytes;
+  const size_t stage_bytes = (size_t)P.buf_rows * kTcRowBytes;  // a multiple of 1024
+  const uint32_t NS = (uint32_t)P.nstages;
+  const int ntri = n * (n + 1) / 2;
   unsigned char *stages = base;
-  double *Sacc = reinterpret_cast<double *>(stages + kTcStages * stage_bytes);  // upper triangle
-  int *rexp = reinterpret_cast<int *>(Sacc + 64 * 65 / 2);
+  unsigned char *raw = stages + NS * stage_bytes;
+  // exact integer sums of the slice products per level k + l, upper triangle
+  int *Lacc = reinterpret_cast<int *>(raw + kTcRawStages * kTcRawBytes);
+  int *rexp = Lacc + kTcLevels * ntri;
   float *rinv = reinterpret_cast<float *>(rexp + 64);
-  __shared__ __align__(8) unsigned long long s_bar[kTcStages];
+  __shared__ __align__(8) unsigned long long s_full[kTcRawStages], s_empty[kTcRawStages];
+  __shared__ __align__(8) unsigned long long s_mma[kTcMaxStages];
   __shared__ uint32_t s_tmem;
+  __shared__ volatile int s_abort;
 
   if (tid == 0) {
-    for (int s = 0; s < kTcStages; ++s)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_bar[s])) : "memory");
+    for (int s = 0; s < kTcRawStages; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_full[s])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&s_empty[s])),
+                   "n"(kTcConsumers / 32)
+                   : "memory");
+    }
+    for (int s = 0; s < kTcMaxStages; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_mma[s])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -276,200 +367,233 @@ __global__ void __launch_bounds__(kTcThreads, 1) gram_tc_kernel(TcArgs A) {
   fence_after();
   const uint32_t tmem = s_tmem;
   const int nchunk = (K + kTcKC - 1) / kTcKC;
-  const int items = n * (kTcKC / 8);  // (row, 8-column piece) per chunk
-  uint32_t issued = 0;                // chunks committed so far (all cells of this CTA)
-  bool fail = false;
 
-  for (int64_t cell = blockIdx.x; cell < A.ncell && !fail; cell += gridDim.x) {
-    const float *X = A.X + cell * A.xstride;
-    // pass 1: row scales (exponent of the row maximum)
-    for (int a = warp; a < n; a += kTcThreads / 32) {
-      float m = 0.f;
-      for (int j = lane * 4; j < K; j += 32 * 4) {
-        const float4 v = *reinterpret_cast<const float4 *>(X + (int64_t)a * K + j);
-        m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
-      }
-      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-      if (lane == 0) {
-        int e = m > 0.f ? ilogbf(m) + 1 : 0;
-        e = e < -100 ? -100 : (e > 100 ? 100 : e);
-        rexp[a] = e;
-        rinv[a] = ldexpf(1.0f, 6 - e);
-      }
+  if (warp == 0) {
+    if (lane == 0) {  // TMA producer
+      const uint32_t bytes = (uint32_t)(n * kTcKC * 4);
+      uint32_t r = 0;
+      bool ok = true;
+      for (int64_t cell = blockIdx.x; cell < A.ncell && ok; cell += gridDim.x)
+        for (int pass = 0; pass < 2 && ok; ++pass)
+          for (int ch = 0; ch < nchunk; ++ch, ++r) {
+            const int slot = (int)(r % kTcRawStages);
+            if (r >= (uint32_t)kTcRawStages &&
+                !bar_wait(smem_addr(&s_empty[slot]), ((r / kTcRawStages) - 1) & 1, &s_abort)) {
+              ok = false;
+              break;
+            }
+            tma_load(smem_addr(raw + (size_t)slot * kTcRawBytes), &xmap, ch * kTcKC,
+                     (int)(cell * n), smem_addr(&s_full[slot]), bytes);
+          }
+      if (!ok) s_abort = 1;
+      // every load issued has landed before the block gives up its shared memory
+      for (uint32_t q = r > (uint32_t)kTcRawStages ? r - kTcRawStages : 0; q < r; ++q)
+        bar_poll(smem_addr(&s_full[q % kTcRawStages]), (q / kTcRawStages) & 1);
     }
-    for (int i = tid; i < n * (n + 1) / 2; i += kTcThreads) Sacc[i] = 0.0;
-    __syncthreads();
-    // register prefetch of a chunk's pieces (at most two per thread: n <= 64)
-    float pre[2][8];
-    auto fetch = [&](int ch) {
+    __syncwarp();
+  } else {
+    const int ct = tid - 32;
+    const int items = n * (kTcKC / 8);  // (row, 8-column piece) per chunk
+    uint32_t rc = 0, issued = 0;
+    bool fail = false;
+    for (int64_t cell = blockIdx.x; cell < A.ncell && !fail; cell += gridDim.x) {
+      // pass 1: row maxima -> row exponents
+      float mx[2] = {0.f, 0.f};
+      bool ok = true;
+      for (int ch = 0; ch < nchunk; ++ch, ++rc) {
+        const int slot = (int)(rc % kTcRawStages);
+        if (ok) ok = bar_wait(smem_addr(&s_full[slot]), (rc / kTcRawStages) & 1, &s_abort);
+        if (ok) {
+          const float *rs = reinterpret_cast<const float *>(raw + (size_t)slot * kTcRawBytes);
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const int it = tid + q * kTcThreads;
-        const int a = it >> 3, c = it & 7, j = ch * kTcKC + c * 8;
-        if (it < items && j < K) {
-          const float4 *src = reinterpret_cast<const float4 *>(X + (int64_t)a * K + j);
-          const float4 u = src[0], w = src[1];
-          pre[q][0] = u.x; pre[q][1] = u.y; pre[q][2] = u.z; pre[q][3] = u.w;
-          pre[q][4] = w.x; pre[q][5] = w.y; pre[q][6] = w.z; pre[q][7] = w.w;
-        } else {
+          for (int q = 0; q < 2; ++q) {
+            const int it = ct + q * kTcConsumers;
+            if (it < items) {
+              const float4 *p4 = reinterpret_cast<const float4 *>(rs + (it >> 3) * kTcKC + (it & 7) * 8);
+              const float4 u = p4[0], w = p4[1];
+              mx[q] = fmaxf(mx[q], fmaxf(fmaxf(fmaxf(fabsf(u.x), fabsf(u.y)), fmaxf(fabsf(u.z), fabsf(u.w))),
+                                        fmaxf(fmaxf(fabsf(w.x), fabsf(w.y)), fmaxf(fabsf(w.z), fabsf(w.w)))));
+            }
+          }
+        }
+        __syncwarp();
+        if (lane == 0) bar_arrive(smem_addr(&s_empty[slot]));
+      }
 #pragma unroll
-          for (int e = 0; e < 8; ++e) pre[q][e] = 0.f;
+      for (int q = 0; q < 2; ++q) {  // the 8 pieces of a row sit in 8 adjacent lanes
+        for (int o = 1; o < 8; o <<= 1) mx[q] = fmaxf(mx[q], __shfl_xor_sync(0xffffffffu, mx[q], o));
+        const int it = ct + q * kTcConsumers;
+        if (it < items && (it & 7) == 0) {
+          int e = mx[q] > 0.f ? ilogbf(mx[q]) + 1 : 0;
+          e = e < -100 ? -100 : (e > 100 ? 100 : e);
+          rexp[it >> 3] = e;
+          rinv[it >> 3] = ldexpf(1.0f, 6 - e);
         }
       }
-    };
-    fetch(0);
-    for (int ch = 0; ch < nchunk; ++ch, ++issued) {
-      const int st = (int)(issued % kTcStages);
-      unsigned char *buf = stages + (size_t)st * stage_bytes;
-      // the MMAs that last read this stage must be complete
-      if (issued >= (uint32_t)kTcStages) {
-        const uint32_t par = ((issued / kTcStages) - 1) & 1;
-        const bool ok = bar_poll(smem_addr(&s_bar[st]), par);
-        if (__syncthreads_or(!ok)) {
+      for (int i = ct; i < kTcLevels * ntri; i += kTcConsumers) Lacc[i] = 0;
+      if (!consumers_and(ok)) {
+        fail = true;
+        break;
+      }
+      // pass 2: slice each chunk into a stage (row k*sp + a holds slice k of row a) and
+      // issue its MMAs
+      for (int ch = 0; ch < nchunk; ++ch, ++rc, ++issued) {
+        const int slot = (int)(rc % kTcRawStages), st = (int)(issued % NS);
+        bool ok2 = bar_wait(smem_addr(&s_full[slot]), (rc / kTcRawStages) & 1, &s_abort);
+        // the MMAs that last read this stage must be complete
+        if (ok2 && issued >= NS)
+          ok2 = bar_wait(smem_addr(&s_mma[st]), ((issued / NS) - 1) & 1, &s_abort);
+        unsigned char *buf = stages + (size_t)st * stage_bytes;
+        if (ok2) {
+          const float *rs = reinterpret_cast<const float *>(raw + (size_t)slot * kTcRawBytes);
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const int it = ct + q * kTcConsumers;
+            if (it < items) {
+              const int a = it >> 3, c = it & 7;
+              const float4 *p4 = reinterpret_cast<const float4 *>(rs + a * kTcKC + c * 8);
+              const float4 u = p4[0], w = p4[1];
+              const float ra = rinv[a];
+              float y[8] = {u.x * ra, u.y * ra, u.z * ra, u.w * ra,
+                            w.x * ra, w.y * ra, w.z * ra, w.w * ra};
+#pragma unroll
+              for (int k = 0; k < kTcSlices; ++k) {
+                float s[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {  // round to nearest even: |y| <= 64 < 2^22
+                  s[e] = __fsub_rn(__fadd_rn(y[e], kRoundMagic), kRoundMagic);
+                  y[e] = __fmul_rn(__fsub_rn(y[e], s[e]), 128.0f);
+                }
+                const int row = k * sp + a;
+                uint4 v;
+                v.x = pack2(s[0], s[1]);
+                v.y = pack2(s[2], s[3]);
+                v.z = pack2(s[4], s[5]);
+                v.w = pack2(s[6], s[7]);
+                *reinterpret_cast<uint4 *>(buf + (size_t)row * kTcRowBytes + ((c ^ (row & 7)) << 4)) = v;
+              }
+            }
+          }
+        }
+        __syncwarp();
+        if (lane == 0) bar_arrive(smem_addr(&s_empty[slot]));
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (!consumers_and(ok2)) {
+          fail = true;
+          break;
+        }
+        if (ct == 0) {
+          fence_after();
+          const uint32_t b0 = smem_addr(buf);
+          for (int g = 0; g < P.ngroups; ++g) {
+            const uint32_t idesc = umma_idesc(128, P.N[g]);
+            const uint32_t da = b0 + (uint32_t)(P.a0[g] * sp) * kTcRowBytes;
+            const uint32_t db = b0 + (uint32_t)(P.b0[g] * sp) * kTcRowBytes;
+#pragma unroll
+            for (int kk = 0; kk < kTcKC / 16; ++kk)
+              mma_bf16(tmem + (uint32_t)P.col[g], umma_desc(da + kk * 32), umma_desc(db + kk * 32),
+                       idesc, (ch > 0 || kk > 0) ? 1u : 0u);
+          }
+          mma_commit(smem_addr(&s_mma[st]));
+        }
+      }
+      if (fail) break;
+      // the cell's last commit (and with it every earlier MMA) must be complete
+      {
+        const uint32_t last = issued - 1;
+        const bool okm =
+            bar_wait(smem_addr(&s_mma[last % NS]), (last / NS) & 1, &s_abort);
+        if (!consumers_and(okm)) {
           fail = true;
           break;
         }
       }
-      // slice the prefetched pieces into the stage (row k*sp + a of slice k)
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const int it = tid + q * kTcThreads;
-        if (it < items) {
-          const int a = it >> 3, c = it & 7;
-          float y[8];
-#pragma unroll
-          for (int e = 0; e < 8; ++e) y[e] = pre[q][e] * rinv[a];
-#pragma unroll
-          for (int k = 0; k < kTcSlices; ++k) {
-            float s[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-              s[e] = rintf(y[e]);
-              y[e] = (y[e] - s[e]) * 128.0f;
-            }
-            const int row = k * sp + a;
-            uint4 v;
-            v.x = pack2(s[0], s[1]);
-            v.y = pack2(s[2], s[3]);
-            v.z = pack2(s[4], s[5]);
-            v.w = pack2(s[6], s[7]);
-            *reinterpret_cast<uint4 *>(buf + (size_t)row * kTcRowBytes + ((c ^ (row & 7)) << 4)) = v;
-          }
-        }
-      }
-      if (ch + 1 < nchunk) fetch(ch + 1);
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      if (tid == 0) {
-        fence_after();
-        const uint32_t b0 = smem_addr(buf);
-        for (int g = 0; g < P.ngroups; ++g) {
-          const uint32_t idesc = umma_idesc(128, P.N[g]);
-          const uint32_t da = b0 + (uint32_t)(P.a0[g] * sp) * kTcRowBytes;
-          const uint32_t db = b0 + (uint32_t)(P.b0[g] * sp) * kTcRowBytes;
-#pragma unroll
-          for (int kk = 0; kk < kTcKC / 16; ++kk)
-            mma_bf16(tmem + (uint32_t)P.col[g], umma_desc(da + kk * 32), umma_desc(db + kk * 32),
-                     idesc, (ch > 0 || kk > 0) ? 1u : 0u);
-        }
-        mma_commit(smem_addr(&s_bar[st]));
-      }
-    }
-    if (fail) break;
-    // the cell's last commit (and with it all earlier MMAs) must be complete
-    {
-      const uint32_t last = issued - 1;
-      const bool ok = bar_poll(smem_addr(&s_bar[last % kTcStages]), (last / kTcStages) & 1);
-      if (__syncthreads_or(!ok)) {
-        fail = true;
-        break;
-      }
-    }
-    fence_after();
-    // combine: tile by tile (one B slice of one group at a time), accumulators to
-    // shared memory as exact FP32 integers, then each upper-triangle entry adds its
-    // owned products in a fixed order
-    float *tile = reinterpret_cast<float *>(stages);  // [128][sp + 1]
-    const int tw = sp + 1;
-    for (int g = 0; g < P.ngroups; ++g) {
-      for (int jb = 0; jb < P.nb[g]; ++jb) {
-        const int l = P.b0[g] + jb;
-        {
-          const int q = warp & 3, half = warp >> 2;  // lanes 32q .. 32q + 31
-          const int c0 = jb * sp + half * (sp / 2);
-          for (int cc = 0; cc < sp / 2; cc += 4) {
-            uint32_t r0, r1, r2, r3;
-            const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(P.col[g] + c0 + cc);
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];\n\t"
-                "tcgen05.wait::ld.sync.aligned;"
-                : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                : "r"(taddr)
-                : "memory");
-            float *t = tile + (32 * q + lane) * tw + half * (sp / 2) + cc;
-            t[0] = __uint_as_float(r0);
-            t[1] = __uint_as_float(r1);
-            t[2] = __uint_as_float(r2);
-            t[3] = __uint_as_float(r3);
-          }
-        }
-        fence_before();
-        __syncthreads();
+      fence_after();
+      // read the accumulators back: each warp its 32 lanes (rows of A) for half of a
+      // group's columns, and every owned slice product D^(k,l)_ij is added, as the exact
+      // integer it is, to the level k + l accumulator of entry (min(i,j), max(i,j)) (for
+      // k != l, D_ij and D_ji both belong to C_ij, so D_ii counts twice; for k == l, D is
+      // symmetric and only i <= j is taken).  Integer addition makes the order
+      // irrelevant.
+      {
+        const int q4 = warp & 3, half = (warp - 1) >> 2;  // lanes 32 q4 .. 32 q4 + 31
+        const int lrow = 32 * q4 + lane;                   // accumulator lane = row of A
         const int na = 128 / sp;
-        for (int e = tid; e < n * (n + 1) / 2; e += kTcThreads) {
-          int a = 0, t = e;  // e -> (a <= b), row-major over the upper triangle
-          while (t >= n - a) {
-            t -= n - a;
-            ++a;
+        for (int g = 0; g < P.ngroups; ++g) {
+          const int il = lrow / sp, i = lrow - il * sp, k = P.a0[g] + il;
+          const bool row_ok = il < na && i < n && k < kTcSlices;
+          const int cbeg = half * (P.N[g] / 2), cend = cbeg + P.N[g] / 2;
+          for (int c0 = cbeg; c0 < cend; c0 += 8) {
+            uint32_t r[8];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t"
+                "tcgen05.wait::ld.sync.aligned;"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                  "=r"(r[6]), "=r"(r[7])
+                : "r"(tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(P.col[g] + c0))
+                : "memory");
+            if (!row_ok) continue;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int col = c0 + u, jl = col / sp, j = col - jl * sp, l = P.b0[g] + jl;
+              if (jl >= P.nb[g] || j >= n || P.own[k * kTcSlices + l] != g + 1) continue;
+              if (k == l && i > j) continue;
+              const int lo = i < j ? i : j, hi = i < j ? j : i;
+              const int tri = lo * n - lo * (lo - 1) / 2 + (hi - lo);
+              const int d = __float2int_rn(__uint_as_float(r[u]));
+              // a diagonal entry of a k != l product is its own transpose: counted twice
+              atomicAdd(&Lacc[(k + l) * ntri + tri], (k != l && i == j) ? 2 * d : d);
+            }
           }
-          const int b = a + t;
-          double s = Sacc[e];
-          for (int i = 0; i < na; ++i) {
-            const int k = P.a0[g] + i;
-            if (k >= kTcSlices || P.own[k * kTcSlices + l] != g + 1) continue;
-            const double w = __longlong_as_double((long long)(1023 - 7 * (k + l)) << 52);
-            s += w * (double)tile[(i * sp + a) * tw + b];
-            if (k != l) s += w * (double)tile[(i * sp + b) * tw + a];
-          }
-          Sacc[e] = s;
         }
-        __syncthreads();
       }
-    }
-    // C_ab = 2^(e_a + e_b - 12) S_ab (as double-float pairs or doubles), both triangles
-    for (int e = tid; e < n * (n + 1) / 2; e += kTcThreads) {
-      int a = 0, t = e;
-      while (t >= n - a) {
-        t -= n - a;
-        ++a;
+      fence_before();
+      consumers_sync();
+      // C_ab = 2^(e_a + e_b - 12) sum_m 2^(-7 m) L_m, formed exactly in integers:
+      // T = sum_{m <= 4} L_m 2^(28 - 7m) and U = sum_{m >= 5} L_m 2^(49 - 7m) (|L_m| < 2^28,
+      // so |T| < 2^60), C_ab = 2^(e_a + e_b - 40) (T + 2^-21 U); written once rounded, as a
+      // double-float pair or a double
+      for (int e = ct; e < ntri; e += kTcConsumers) {
+        int a = 0, t = e;  // e -> (a <= b), row-major over the upper triangle
+        while (t >= n - a) {
+          t -= n - a;
+          ++a;
+        }
+        const int b = a + t;
+        long long T = 0, U = 0;
+#pragma unroll
+        for (int m = 0; m <= 4; ++m) T = T * 128 + Lacc[m * ntri + e];
+#pragma unroll
+        for (int m = 5; m < kTcLevels; ++m) U = U * 128 + Lacc[m * ntri + e];
+        const int sc = rexp[a] + rexp[b] - 40;
+        if (A.Cd) {
+          const double v = ldexp((double)T, sc) + ldexp((double)U, sc - 21);
+          double *C = A.Cd + cell * A.cstride;
+          C[a * n + b] = v;
+          C[b * n + a] = v;
+        } else {
+          const float th = __ll2float_rn(T);
+          const long long tr = T - __float2ll_rn(th);  // exact: th is an integer
+          const float tl = __fadd_rn(__ll2float_rn(tr), ldexpf(__ll2float_rn(U), -21));
+          const float hi = __fadd_rn(th, tl);
+          const float lo = __fsub_rn(tl, __fsub_rn(hi, th));
+          float2 *C = A.C + cell * A.cstride;
+          const float2 v = make_float2(ldexpf(hi, sc), ldexpf(lo, sc));
+          C[a * n + b] = v;
+          C[b * n + a] = v;
+        }
       }
-      const int b = a + t;
-      const double v = ldexp(Sacc[e], rexp[a] + rexp[b] - 12);
-      if (A.Cd) {
-        double *C = A.Cd + cell * A.cstride;
-        C[a * n + b] = v;
-        C[b * n + a] = v;
-      } else {
-        float2 *C = A.C + cell * A.cstride;
-        const float hi = (float)v;
-        const float lo = (float)(v - (double)hi);
-        C[a * n + b] = make_float2(hi, lo);
-        C[b * n + a] = make_float2(hi, lo);
-      }
+      if (ct == 0 && A.disc) A.disc[cell] = 0.0;
+      fence_before();
+      consumers_sync();  // the accumulators and the tile are free for the next cell
+      fence_after();
     }
-    if (tid == 0 && A.disc) A.disc[cell] = 0.0;
-    fence_before();
-    __syncthreads();  // the accumulators and the tile are free for the next cell
-    fence_after();
-  }
-  if (fail) {
-    if (tid == 0) atomicOr(A.flag, 2);
-    // drain (bounded) every committed group before giving up the tensor memory
-    if (issued > 0) {
-      const uint32_t last = issued - 1;
-      bar_poll(smem_addr(&s_bar[last % kTcStages]), (last / kTcStages) & 1);
+    if (fail && ct == 0) {
+      s_abort = 1;
+      atomicOr(A.flag, 2);
+      if (issued > 0)  // drain (bounded) the committed MMAs
+        bar_poll(smem_addr(&s_mma[(issued - 1) % NS]), ((issued - 1) / NS) & 1);
     }
-    __syncthreads();
   }
   fence_before();
   __syncthreads();
@@ -489,11 +613,35 @@ size_t launch_smem(const GramTcPlan &p) {
   const size_t smem = gram_tc_smem_bytes(p);
   return smem < 120 * 1024 ? 120 * 1024 : smem;
 }
+
+// cuTensorMapEncodeTiled through the driver's entry point (no link against the
+// driver library); null if unavailable
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                 const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                 const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiled encode_tiled() {
+  static EncodeTiled fn = nullptr;
+  static bool looked_up = false;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!looked_up) {
+    looked_up = true;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", reinterpret_cast<void **>(&fn),
+                                         12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      fn = nullptr;
+    }
+  }
+  return fn;
+}
 }  // namespace
 
 int gram_tc_prepare(int n) {
   const GramTcPlan p = gram_tc_plan(n);
-  if (p.ngroups == 0) return -1;
+  if (p.ngroups == 0 || !encode_tiled()) return -1;
   static std::mutex mu;
   std::lock_guard<std::mutex> lk(mu);
   const size_t smem = launch_smem(p);
@@ -515,12 +663,11 @@ bool gram_tc_supported(int n, int K) {
 int launch_gram_tc(const float *X, int64_t xstride, int64_t ncell, int n, int K, float2 *C,
                    double *Cd, int64_t cstride, double *disc, int *flag, cudaStream_t s) {
   if (ncell <= 0) return 0;
-  if (!gram_tc_supported(n, K) || (xstride % 4) != 0 ||
-      (reinterpret_cast<uintptr_t>(X) & 15) != 0)
+  // the cells' rows must form one row-major [ncell * n][K] array for the tensor map
+  if (!gram_tc_supported(n, K) || xstride != (int64_t)n * K ||
+      (reinterpret_cast<uintptr_t>(X) & 15) != 0 || ncell * n > 0x7fffffffLL)
     return -1;
   TcArgs a{};
-  a.X = X;
-  a.xstride = xstride;
   a.ncell = ncell;
   a.K = K;
   a.C = C;
@@ -535,11 +682,24 @@ int launch_gram_tc(const float *X, int64_t xstride, int64_t ncell, int n, int K,
     cudaStreamIsCapturing(s, &cap);
     if (cap != cudaStreamCaptureStatusNone || gram_tc_prepare(n) != 0) return -1;
   }
+  const EncodeTiled enc = encode_tiled();
+  if (!enc) return -1;
+  // X as a 2-D FP32 array [ncell * n][K] (K innermost), boxes of n rows x 64 columns;
+  // columns beyond K (a ragged last chunk) read as zeros
+  CUtensorMap map;
+  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)(ncell * n)};
+  const cuuint64_t strides[1] = {(cuuint64_t)K * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)kTcKC, (cuuint32_t)n};
+  const cuuint32_t estr[2] = {1, 1};
+  if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(X), dims, strides, box,
+          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return -1;
   int sms = 1, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = (int)(ncell < sms ? ncell : sms);
-  gram_tc_kernel<<<grid, kTcThreads, launch_smem(a.plan), s>>>(a);
+  gram_tc_kernel<<<grid, kTcThreadsAll, smem, s>>>(map, a);
   return 0;
 }
 

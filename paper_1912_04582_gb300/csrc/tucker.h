@@ -125,6 +125,7 @@ struct GramTcPlan {
   int col[kTcMaxGroups];         // first tensor-memory column of the group's accumulator
   int ncols;                     // tensor-memory columns allocated
   int buf_rows;                  // rows of one shared-memory stage
+  int nstages;                   // shared-memory stages of sliced chunks (2 or 3)
   signed char own[kTcSlices * kTcSlices];  // group + 1 that owns product (k, l), else 0
 };
 GramTcPlan gram_tc_plan(int n);
