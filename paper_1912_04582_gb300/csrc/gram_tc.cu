@@ -21,15 +21,18 @@
 // rounding: a relative perturbation of X below 2^-35, far under the FP32 rounding
 // the tensor already carries.
 //
-// Tensor-core mapping.  The slices of a K-chunk of 64 columns sit in shared memory
-// one after the other, sp = n rounded up to 8 rows each, as a K-major 128-byte
-// swizzled bf16 operand.  One MMA group takes 128 consecutive rows as A (the M = 128
+// Tensor-core mapping.  Slice k is stored as the bf16 value s_k 2^-7k (exact: a small
+// integer times a power of two, formed by rounding at level k directly), so the
+// accumulator of slice product (k, l) holds 2^-7(k+l) D^(k,l), still exact.  The slices
+// of a K-chunk of 64 columns sit in shared memory one after the other, sp = n rounded
+// up to 8 rows each, as a K-major 128-byte swizzled bf16 operand.  One MMA group takes 128 consecutive rows as A (the M = 128
 // accumulator lanes hold several slices) and a run of rows as B (N up to 256
 // columns hold several slices): a single instruction forms up to 4 x 5 slice
 // products.  One to three groups cover every needed pair for n <= 64; their FP32
 // accumulators live in tensor memory (TMEM).  Per CTA (persistent, one per SM): one
 // thread streams the cell's K-chunks by 2-D TMA loads (cp.async.bulk.tensor) into a
-// four-deep ring, twice (row scales, then slicing); eight warps slice each chunk into
+// four-deep ring, once when the row maxima are given (the assembly of X records them),
+// else twice (row scales, then slicing); eight warps slice each chunk into
 // one of three bf16 stages while the tensor cores work on the previous ones (one
 // mbarrier per stage signalled by tcgen05.commit), and one of their threads issues
 // the MMAs.  After a cell's last chunk the accumulators are read back (tcgen05.ld)
@@ -111,14 +114,41 @@ __device__ __forceinline__ void fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// bf16 of two small integers held in floats, packed (lo in the low half): a float
-// holding an integer of at most 8 significant bits has zero low 16 bits, so its bf16 is
+// bf16 of two floats with at most 8 significant bits (small integers times powers of
+// two), packed (lo in the low half): such a float has zero low 16 bits, so its bf16 is
 // its upper half, taken by a byte permute
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
   return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
 }
 
-constexpr float kRoundMagic = 12582912.0f;  // 1.5 * 2^23
+// 1.5 * 2^(23 - 7k): adding and removing it rounds to a multiple of 2^-7k
+__device__ constexpr float kSliceMagic[kTcSlices] = {12582912.0f, 98304.0f, 768.0f, 6.0f,
+                                                     0.046875f};
+
+// 2^7m: an accumulator of level m holds 2^-7m times an integer
+__device__ constexpr float kLevelScale[kTcLevels] = {1.0f, 128.0f, 16384.0f, 2097152.0f,
+                                                     268435456.0f, 34359738368.0f,
+                                                     4398046511104.0f, 562949953421312.0f};
+
+// paired FP32 arithmetic (two lanes of a 64-bit register), round to nearest
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
+  return (uint64_t)__float_as_uint(lo) | ((uint64_t)__float_as_uint(hi) << 32);
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
 
 }  // namespace
 
@@ -245,15 +275,15 @@ static size_t level_bytes(int n) { return sizeof(int) * kTcLevels * (size_t)(n *
 static size_t smem_for(const GramTcPlan &p, int nstages) {
   const size_t stages = (size_t)nstages * p.buf_rows * kTcRowBytes;
   const size_t raw = (size_t)kTcRawStages * kTcRawBytes;
-  return 1024 + stages + raw + level_bytes(p.n) + 64 * (sizeof(int) + sizeof(float)) + 64;
+  return 1024 + stages + raw + level_bytes(p.n) + 64 * (2 * sizeof(int) + sizeof(float)) + 64;
 }
 
 size_t gram_tc_smem_bytes(const GramTcPlan &p) { return smem_for(p, p.nstages); }
 
 namespace {
 
-constexpr int kTcConsumers = 256;                  // eight slicing / MMA-issuing warps
-constexpr int kTcThreadsAll = kTcConsumers + 32;   // plus the TMA producer warp
+constexpr int kTcConsumers = 384;                  // twelve slicing warps
+constexpr int kTcThreadsAll = kTcConsumers + 64;   // plus the TMA producer and MMA warps
 
 struct TcArgs {
   int64_t ncell;
@@ -263,6 +293,8 @@ struct TcArgs {
   int64_t cstride;
   double *disc;     // [ncell] set to 0 (no columns left out), may be null
   int *flag;
+  const float *rowmax;  // cell j: rowmax + j * rstride, each row's largest |x| (or null:
+  int64_t rstride;      // then a first pass over X finds them)
   GramTcPlan plan;
 };
 
@@ -313,14 +345,16 @@ __device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap *map, i
       : "memory");
 }
 
-// Warp 0: tensor-memory allocation and, in lane 0, the TMA producer: for each of the
-// CTA's cells, two passes over the cell's K-chunks (n rows x 64 columns of FP32, one
-// 2-D tiled load each) into a four-deep ring, each slot released by the eight
-// consumer warps.  Warps 1-8 (the consumers): pass 1 takes the row maxima (the row
-// scales of the split), pass 2 slices each chunk into a shared-memory stage and the
-// first consumer thread issues the chunk's MMAs, committed to the stage's mbarrier;
-// after a cell's last chunk the consumers read the accumulators back and combine
-// them while the producer already loads the next cell.
+// Warp roles.  Warp 0: tensor-memory allocation and, in lane 0, the TMA producer: for
+// each of the CTA's cells, the cell's K-chunks (n rows x 64 columns of FP32, one 2-D
+// tiled load each; twice when the row maxima are not given) into a four-deep ring whose
+// slots the slicing warps release.  Warp 1, lane 0: the MMA issuer: waits until the
+// slicing warps have filled a stage, issues the stage's MMAs and commits them to the
+// stage's "freed" barrier (and, after a cell's last chunk, to the "accumulators full"
+// barrier); before a cell's first chunk it waits until the previous cell's
+// accumulators have been read.  Warps 2-13: the slicing warps: row scales, slicing of
+// each chunk into a free stage, and the read-back and combination of the accumulators.
+// No CTA-wide barrier is taken per chunk: every hand-off is an mbarrier.
 __global__ void __launch_bounds__(kTcThreadsAll, 1)
     gram_tc_kernel(const __grid_constant__ CUtensorMap xmap, TcArgs A) {
   extern __shared__ unsigned char tc_raw[];
@@ -338,23 +372,33 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1)
   int *Lacc = reinterpret_cast<int *>(raw + kTcRawStages * kTcRawBytes);
   int *rexp = Lacc + kTcLevels * ntri;
   float *rinv = reinterpret_cast<float *>(rexp + 64);
+  int *rowoff = reinterpret_cast<int *>(rinv + 64);  // upper-triangle offset of each row
   __shared__ __align__(8) unsigned long long s_full[kTcRawStages], s_empty[kTcRawStages];
-  __shared__ __align__(8) unsigned long long s_mma[kTcMaxStages];
+  __shared__ __align__(8) unsigned long long s_ready[kTcMaxStages], s_freed[kTcMaxStages];
+  __shared__ __align__(8) unsigned long long s_accf, s_acce;
   __shared__ uint32_t s_tmem;
   __shared__ volatile int s_abort;
+  constexpr int kWarpsC = kTcConsumers / 32;
 
   if (tid == 0) {
-    for (int s = 0; s < kTcRawStages; ++s) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_full[s])) : "memory");
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&s_empty[s])),
-                   "n"(kTcConsumers / 32)
+    auto init = [](unsigned long long *b, int count) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count)
                    : "memory");
+    };
+    for (int s = 0; s < kTcRawStages; ++s) {
+      init(&s_full[s], 1);
+      init(&s_empty[s], kWarpsC);
     }
-    for (int s = 0; s < kTcMaxStages; ++s)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_mma[s])) : "memory");
+    for (int s = 0; s < kTcMaxStages; ++s) {
+      init(&s_ready[s], kWarpsC);
+      init(&s_freed[s], 1);
+    }
+    init(&s_accf, 1);
+    init(&s_acce, kWarpsC);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_abort = 0;
   }
+  for (int a = tid; a < 64; a += blockDim.x) rowoff[a] = a * n - a * (a - 1) / 2;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_addr(&s_tmem)),
@@ -374,7 +418,7 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1)
       uint32_t r = 0;
       bool ok = true;
       for (int64_t cell = blockIdx.x; cell < A.ncell && ok; cell += gridDim.x)
-        for (int pass = 0; pass < 2 && ok; ++pass)
+        for (int pass = A.rowmax ? 1 : 0; pass < 2 && ok; ++pass)
           for (int ch = 0; ch < nchunk; ++ch, ++r) {
             const int slot = (int)(r % kTcRawStages);
             if (r >= (uint32_t)kTcRawStages &&
@@ -391,28 +435,66 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1)
         bar_poll(smem_addr(&s_full[q % kTcRawStages]), (q / kTcRawStages) & 1);
     }
     __syncwarp();
-  } else {
-    const int ct = tid - 32;
-    const int items = n * (kTcKC / 8);  // (row, 8-column piece) per chunk
-    uint32_t rc = 0, issued = 0;
-    bool fail = false;
-    for (int64_t cell = blockIdx.x; cell < A.ncell && !fail; cell += gridDim.x) {
-      // pass 1: row maxima -> row exponents
-      float mx[2] = {0.f, 0.f};
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      uint32_t t = 0, cidx = 0;
       bool ok = true;
-      for (int ch = 0; ch < nchunk; ++ch, ++rc) {
+      for (int64_t cell = blockIdx.x; cell < A.ncell && ok; cell += gridDim.x, ++cidx) {
+        // the previous cell's accumulators must have been read back
+        if (cidx > 0 && !bar_wait(smem_addr(&s_acce), (cidx - 1) & 1, &s_abort)) {
+          ok = false;
+          break;
+        }
+        for (int ch = 0; ch < nchunk; ++ch, ++t) {
+          const uint32_t st = t % NS;
+          if (!bar_wait(smem_addr(&s_ready[st]), (t / NS) & 1, &s_abort)) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t b0 = smem_addr(stages + (size_t)st * stage_bytes);
+          for (int g = 0; g < P.ngroups; ++g) {
+            const uint32_t idesc = umma_idesc(128, P.N[g]);
+            const uint32_t da = b0 + (uint32_t)(P.a0[g] * sp) * kTcRowBytes;
+            const uint32_t db = b0 + (uint32_t)(P.b0[g] * sp) * kTcRowBytes;
+#pragma unroll
+            for (int kk = 0; kk < kTcKC / 16; ++kk)
+              mma_bf16(tmem + (uint32_t)P.col[g], umma_desc(da + kk * 32),
+                       umma_desc(db + kk * 32), idesc, (ch > 0 || kk > 0) ? 1u : 0u);
+          }
+          mma_commit(smem_addr(&s_freed[st]));
+          if (ch + 1 == nchunk) mma_commit(smem_addr(&s_accf));
+        }
+      }
+      if (!ok) s_abort = 1;
+      // every committed MMA has completed before the tensor memory is given up
+      if (t > 0) bar_poll(smem_addr(&s_freed[(t - 1) % NS]), ((t - 1) / NS) & 1);
+    }
+    __syncwarp();
+  } else {
+    const int ct = tid - 64;
+    const int items = n * (kTcKC / 4);  // (row, 4-column piece) per chunk
+    constexpr int kItems = (64 * (kTcKC / 4) + kTcConsumers - 1) / kTcConsumers;
+    uint32_t rc = 0, t = 0, cidx = 0;
+    bool fail = false;
+    for (int64_t cell = blockIdx.x; cell < A.ncell && !fail; cell += gridDim.x, ++cidx) {
+      // row scales: from the given row maxima, else from a first pass over the chunks (the
+      // 16 pieces of a row sit in 16 adjacent lanes)
+      float mx[kItems];
+#pragma unroll
+      for (int q = 0; q < kItems; ++q) mx[q] = 0.f;
+      bool ok = true;
+      for (int ch = 0; !A.rowmax && ch < nchunk; ++ch, ++rc) {
         const int slot = (int)(rc % kTcRawStages);
         if (ok) ok = bar_wait(smem_addr(&s_full[slot]), (rc / kTcRawStages) & 1, &s_abort);
         if (ok) {
           const float *rs = reinterpret_cast<const float *>(raw + (size_t)slot * kTcRawBytes);
 #pragma unroll
-          for (int q = 0; q < 2; ++q) {
+          for (int q = 0; q < kItems; ++q) {
             const int it = ct + q * kTcConsumers;
             if (it < items) {
-              const float4 *p4 = reinterpret_cast<const float4 *>(rs + (it >> 3) * kTcKC + (it & 7) * 8);
-              const float4 u = p4[0], w = p4[1];
-              mx[q] = fmaxf(mx[q], fmaxf(fmaxf(fmaxf(fabsf(u.x), fabsf(u.y)), fmaxf(fabsf(u.z), fabsf(u.w))),
-                                        fmaxf(fmaxf(fabsf(w.x), fabsf(w.y)), fmaxf(fabsf(w.z), fabsf(w.w)))));
+              const float4 u = *reinterpret_cast<const float4 *>(rs + (it >> 4) * kTcKC + (it & 15) * 4);
+              mx[q] = fmaxf(mx[q], fmaxf(fmaxf(fabsf(u.x), fabsf(u.y)), fmaxf(fabsf(u.z), fabsf(u.w))));
             }
           }
         }
@@ -420,14 +502,15 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1)
         if (lane == 0) bar_arrive(smem_addr(&s_empty[slot]));
       }
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {  // the 8 pieces of a row sit in 8 adjacent lanes
-        for (int o = 1; o < 8; o <<= 1) mx[q] = fmaxf(mx[q], __shfl_xor_sync(0xffffffffu, mx[q], o));
+      for (int q = 0; q < kItems; ++q) {
         const int it = ct + q * kTcConsumers;
-        if (it < items && (it & 7) == 0) {
+        if (A.rowmax) mx[q] = it < items ? A.rowmax[cell * A.rstride + (it >> 4)] : 0.f;
+        for (int o = 1; o < 16; o <<= 1) mx[q] = fmaxf(mx[q], __shfl_xor_sync(0xffffffffu, mx[q], o));
+        if (it < items && (it & 15) == 0) {
           int e = mx[q] > 0.f ? ilogbf(mx[q]) + 1 : 0;
           e = e < -100 ? -100 : (e > 100 ? 100 : e);
-          rexp[it >> 3] = e;
-          rinv[it >> 3] = ldexpf(1.0f, 6 - e);
+          rexp[it >> 4] = e;
+          rinv[it >> 4] = ldexpf(1.0f, 6 - e);
         }
       }
       for (int i = ct; i < kTcLevels * ntri; i += kTcConsumers) Lacc[i] = 0;
@@ -435,131 +518,125 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1)
         fail = true;
         break;
       }
-      // pass 2: slice each chunk into a stage (row k*sp + a holds slice k of row a) and
-      // issue its MMAs
-      for (int ch = 0; ch < nchunk; ++ch, ++rc, ++issued) {
-        const int slot = (int)(rc % kTcRawStages), st = (int)(issued % NS);
+      // slice each chunk into a free stage (row k*sp + a holds slice k of row a) and
+      // hand it to the MMA issuer
+      for (int ch = 0; ch < nchunk; ++ch, ++rc, ++t) {
+        const int slot = (int)(rc % kTcRawStages);
+        const uint32_t st = t % NS;
         bool ok2 = bar_wait(smem_addr(&s_full[slot]), (rc / kTcRawStages) & 1, &s_abort);
         // the MMAs that last read this stage must be complete
-        if (ok2 && issued >= NS)
-          ok2 = bar_wait(smem_addr(&s_mma[st]), ((issued / NS) - 1) & 1, &s_abort);
-        unsigned char *buf = stages + (size_t)st * stage_bytes;
-        if (ok2) {
-          const float *rs = reinterpret_cast<const float *>(raw + (size_t)slot * kTcRawBytes);
-#pragma unroll
-          for (int q = 0; q < 2; ++q) {
-            const int it = ct + q * kTcConsumers;
-            if (it < items) {
-              const int a = it >> 3, c = it & 7;
-              const float4 *p4 = reinterpret_cast<const float4 *>(rs + a * kTcKC + c * 8);
-              const float4 u = p4[0], w = p4[1];
-              const float ra = rinv[a];
-              float y[8] = {u.x * ra, u.y * ra, u.z * ra, u.w * ra,
-                            w.x * ra, w.y * ra, w.z * ra, w.w * ra};
-#pragma unroll
-              for (int k = 0; k < kTcSlices; ++k) {
-                float s[8];
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {  // round to nearest even: |y| <= 64 < 2^22
-                  s[e] = __fsub_rn(__fadd_rn(y[e], kRoundMagic), kRoundMagic);
-                  y[e] = __fmul_rn(__fsub_rn(y[e], s[e]), 128.0f);
-                }
-                const int row = k * sp + a;
-                uint4 v;
-                v.x = pack2(s[0], s[1]);
-                v.y = pack2(s[2], s[3]);
-                v.z = pack2(s[4], s[5]);
-                v.w = pack2(s[6], s[7]);
-                *reinterpret_cast<uint4 *>(buf + (size_t)row * kTcRowBytes + ((c ^ (row & 7)) << 4)) = v;
-              }
-            }
-          }
-        }
-        __syncwarp();
-        if (lane == 0) bar_arrive(smem_addr(&s_empty[slot]));
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        if (!consumers_and(ok2)) {
-          fail = true;
+        if (ok2 && t >= NS) ok2 = bar_wait(smem_addr(&s_freed[st]), ((t / NS) - 1) & 1, &s_abort);
+        ok2 = __all_sync(0xffffffffu, ok2);  // the warp leaves together (it syncs below)
+        if (!ok2) {
+          s_abort = 1;
+          ok = false;
           break;
         }
-        if (ct == 0) {
-          fence_after();
-          const uint32_t b0 = smem_addr(buf);
-          for (int g = 0; g < P.ngroups; ++g) {
-            const uint32_t idesc = umma_idesc(128, P.N[g]);
-            const uint32_t da = b0 + (uint32_t)(P.a0[g] * sp) * kTcRowBytes;
-            const uint32_t db = b0 + (uint32_t)(P.b0[g] * sp) * kTcRowBytes;
+        unsigned char *buf = stages + (size_t)st * stage_bytes;
+        const float *rs = reinterpret_cast<const float *>(raw + (size_t)slot * kTcRawBytes);
+        for (int it = ct; it < items; it += kTcConsumers) {
+          const int a = it >> 4, c4 = it & 15;
+          const float4 u = *reinterpret_cast<const float4 *>(rs + a * kTcKC + c4 * 4);
+          const float ra = rinv[a];
+          uint64_t y01 = f2_mul(f2_pack(u.x, u.y), f2_pack(ra, ra));
+          uint64_t y23 = f2_mul(f2_pack(u.z, u.w), f2_pack(ra, ra));
 #pragma unroll
-            for (int kk = 0; kk < kTcKC / 16; ++kk)
-              mma_bf16(tmem + (uint32_t)P.col[g], umma_desc(da + kk * 32), umma_desc(db + kk * 32),
-                       idesc, (ch > 0 || kk > 0) ? 1u : 0u);
+          for (int k = 0; k < kTcSlices; ++k) {
+            // v_k = y rounded to a multiple of 2^-7k (round to nearest even by adding and
+            // removing 1.5 * 2^(23 - 7k)); v_k 2^7k is an integer in [-64, 64]
+            const uint64_t M = f2_pack(kSliceMagic[k], kSliceMagic[k]);
+            const uint64_t v01 = f2_sub(f2_add(y01, M), M), v23 = f2_sub(f2_add(y23, M), M);
+            if (k + 1 < kTcSlices) {
+              y01 = f2_sub(y01, v01);
+              y23 = f2_sub(y23, v23);
+            }
+            const int row = k * sp + a;
+            uint2 w;
+            w.x = pack2(__uint_as_float((uint32_t)v01), __uint_as_float((uint32_t)(v01 >> 32)));
+            w.y = pack2(__uint_as_float((uint32_t)v23), __uint_as_float((uint32_t)(v23 >> 32)));
+            *reinterpret_cast<uint2 *>(buf + (size_t)row * kTcRowBytes +
+                                       ((((c4 >> 1) ^ (row & 7)) << 4) | ((c4 & 1) << 3))) = w;
           }
-          mma_commit(smem_addr(&s_mma[st]));
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+          bar_arrive(smem_addr(&s_empty[slot]));
+          bar_arrive(smem_addr(&s_ready[st]));
         }
       }
-      if (fail) break;
-      // the cell's last commit (and with it every earlier MMA) must be complete
-      {
-        const uint32_t last = issued - 1;
-        const bool okm =
-            bar_wait(smem_addr(&s_mma[last % NS]), (last / NS) & 1, &s_abort);
-        if (!consumers_and(okm)) {
-          fail = true;
-          break;
-        }
+      // the cell's accumulators complete
+      if (ok) ok = bar_wait(smem_addr(&s_accf), cidx & 1, &s_abort);
+      if (!consumers_and(ok)) {
+        fail = true;
+        break;
       }
       fence_after();
-      // read the accumulators back: each warp its 32 lanes (rows of A) for half of a
-      // group's columns, and every owned slice product D^(k,l)_ij is added, as the exact
-      // integer it is, to the level k + l accumulator of entry (min(i,j), max(i,j)) (for
-      // k != l, D_ij and D_ji both belong to C_ij, so D_ii counts twice; for k == l, D is
-      // symmetric and only i <= j is taken).  Integer addition makes the order
-      // irrelevant.
+      // read the accumulators back.  The three warps of a lane quarter share each
+      // group's 8-column blocks round robin, four loads in flight before one wait.  The
+      // accumulator of slice product (k, l) holds 2^-7(k+l) D with D = S_k S_l^T an
+      // integer matrix; every owned D_ij is added, as the exact integer it is, to the
+      // level k + l accumulator of entry (min(i,j), max(i,j)) (for k != l, D_ij and D_ji
+      // both belong to C_ij, so D_ii counts twice; for k == l, D is symmetric and only
+      // i <= j is taken).  Integer addition makes the order irrelevant.
       {
-        const int q4 = warp & 3, half = (warp - 1) >> 2;  // lanes 32 q4 .. 32 q4 + 31
-        const int lrow = 32 * q4 + lane;                   // accumulator lane = row of A
+        const int q4 = warp & 3, sub = (warp - 2) >> 2;  // lanes 32 q4 .. 32 q4 + 31
+        const int lrow = 32 * q4 + lane;                  // accumulator lane = row of A
         const int na = 128 / sp;
         for (int g = 0; g < P.ngroups; ++g) {
           const int il = lrow / sp, i = lrow - il * sp, k = P.a0[g] + il;
           const bool row_ok = il < na && i < n && k < kTcSlices;
-          const int cbeg = half * (P.N[g] / 2), cend = cbeg + P.N[g] / 2;
-          for (int c0 = cbeg; c0 < cend; c0 += 8) {
-            uint32_t r[8];
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t"
-                "tcgen05.wait::ld.sync.aligned;"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-                  "=r"(r[6]), "=r"(r[7])
-                : "r"(tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(P.col[g] + c0))
-                : "memory");
-            if (!row_ok) continue;
+          uint32_t ownl = 0;  // B slices l whose product (k, l) this group owns
+          if (row_ok)
+            for (int l = 0; l < kTcSlices; ++l)
+              if (P.own[k * kTcSlices + l] == g + 1) ownl |= 1u << l;
+          const int nblk = P.N[g] / 8;
+          for (int b0 = sub; b0 < nblk; b0 += 4 * 3) {
+            uint32_t r[4][8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              const int col = c0 + u, jl = col / sp, j = col - jl * sp, l = P.b0[g] + jl;
-              if (jl >= P.nb[g] || j >= n || P.own[k * kTcSlices + l] != g + 1) continue;
-              if (k == l && i > j) continue;
-              const int lo = i < j ? i : j, hi = i < j ? j : i;
-              const int tri = lo * n - lo * (lo - 1) / 2 + (hi - lo);
-              const int d = __float2int_rn(__uint_as_float(r[u]));
-              // a diagonal entry of a k != l product is its own transpose: counted twice
-              atomicAdd(&Lacc[(k + l) * ntri + tri], (k != l && i == j) ? 2 * d : d);
+            for (int q = 0; q < 4; ++q) {
+              const int b = b0 + 3 * q;
+              if (b < nblk)  // warp-uniform
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                    : "=r"(r[q][0]), "=r"(r[q][1]), "=r"(r[q][2]), "=r"(r[q][3]), "=r"(r[q][4]),
+                      "=r"(r[q][5]), "=r"(r[q][6]), "=r"(r[q][7])
+                    : "r"(tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(P.col[g] + 8 * b))
+                    : "memory");
+            }
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int b = b0 + 3 * q;
+              if (b >= nblk) continue;
+              const int jl = (8 * b) / sp, j0 = 8 * b - jl * sp, l = P.b0[g] + jl;
+              if (!row_ok || jl >= P.nb[g] || !((ownl >> l) & 1u)) continue;
+              const float scale = kLevelScale[k + l];
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                const int j = j0 + u;
+                if (j >= n || (k == l && i > j)) continue;
+                const int tri = i <= j ? rowoff[i] + (j - i) : rowoff[j] + (i - j);
+                const int d = __float2int_rn(__uint_as_float(r[q][u]) * scale);
+                // a diagonal entry of a k != l product is its own transpose: counted twice
+                atomicAdd(&Lacc[(k + l) * ntri + tri], (k != l && i == j) ? 2 * d : d);
+              }
             }
           }
         }
       }
       fence_before();
+      __syncwarp();
+      if (lane == 0) bar_arrive(smem_addr(&s_acce));  // the accumulators may be reused
       consumers_sync();
       // C_ab = 2^(e_a + e_b - 12) sum_m 2^(-7 m) L_m, formed exactly in integers:
       // T = sum_{m <= 4} L_m 2^(28 - 7m) and U = sum_{m >= 5} L_m 2^(49 - 7m) (|L_m| < 2^28,
       // so |T| < 2^60), C_ab = 2^(e_a + e_b - 40) (T + 2^-21 U); written once rounded, as a
       // double-float pair or a double
       for (int e = ct; e < ntri; e += kTcConsumers) {
-        int a = 0, t = e;  // e -> (a <= b), row-major over the upper triangle
-        while (t >= n - a) {
-          t -= n - a;
-          ++a;
-        }
-        const int b = a + t;
+        int a = 0;
+        while (a + 1 < n && rowoff[a + 1] <= e) ++a;
+        const int b = a + (e - rowoff[a]);
         long long T = 0, U = 0;
 #pragma unroll
         for (int m = 0; m <= 4; ++m) T = T * 128 + Lacc[m * ntri + e];
@@ -584,15 +661,11 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1)
         }
       }
       if (ct == 0 && A.disc) A.disc[cell] = 0.0;
-      fence_before();
-      consumers_sync();  // the accumulators and the tile are free for the next cell
-      fence_after();
+      consumers_sync();  // the level accumulators are free for the next cell
     }
     if (fail && ct == 0) {
       s_abort = 1;
       atomicOr(A.flag, 2);
-      if (issued > 0)  // drain (bounded) the committed MMAs
-        bar_poll(smem_addr(&s_mma[(issued - 1) % NS]), ((issued - 1) / NS) & 1);
     }
   }
   fence_before();
@@ -661,7 +734,8 @@ bool gram_tc_supported(int n, int K) {
 }
 
 int launch_gram_tc(const float *X, int64_t xstride, int64_t ncell, int n, int K, float2 *C,
-                   double *Cd, int64_t cstride, double *disc, int *flag, cudaStream_t s) {
+                   double *Cd, int64_t cstride, double *disc, int *flag, cudaStream_t s,
+                   const float *rowmax, int64_t rstride) {
   if (ncell <= 0) return 0;
   // the cells' rows must form one row-major [ncell * n][K] array for the tensor map
   if (!gram_tc_supported(n, K) || xstride != (int64_t)n * K ||
@@ -675,6 +749,8 @@ int launch_gram_tc(const float *X, int64_t xstride, int64_t ncell, int n, int K,
   a.cstride = cstride;
   a.disc = disc;
   a.flag = flag;
+  a.rowmax = rowmax;
+  a.rstride = rstride;
   a.plan = gram_tc_plan(n);
   const size_t smem = launch_smem(a.plan);
   if (smem > g_opted) {

@@ -57,6 +57,7 @@ struct TuckerSplitBufs {
   int asm_grid;  // assembly CTAs (persistent over the chunk)
   int64_t c0, cn;  // cells [c0, c0 + cn) of this launch
   int64_t joff;    // their first buffer index (buffers hold one chunk)
+  float *rowmax;   // [cn][Nmax] largest |X| per first-mode row (mixed path; may be null)
   double *cellpar; // [nc][kCellPar] per-cell parameters, formed at the start of the step
   double *macro;   // [nc][8] macroparameters of the current state (may be null)
 };
@@ -133,8 +134,11 @@ bool gram_tc_supported(int n, int K);
 // raise the kernel's shared-memory opt-in for n rows (outside stream captures); 0 ok
 int gram_tc_prepare(int n);
 // C (double-float pairs) or Cd (doubles), cstride elements per cell; disc[cell] = 0
+// rowmax (optional, rstride floats per cell): each row's largest magnitude, known from
+// the producer of X; without it the kernel reads X twice (row scales, then slicing)
 int launch_gram_tc(const float *X, int64_t xstride, int64_t ncell, int n, int K, float2 *C,
-                   double *Cd, int64_t cstride, double *disc, int *flag, cudaStream_t s);
+                   double *Cd, int64_t cstride, double *disc, int *flag, cudaStream_t s,
+                   const float *rowmax = nullptr, int64_t rstride = 0);
 
 size_t tucker_scratch_elems(int N1, int N2, int N3, int R);
 size_t tucker_smem_bytes(int Nmax, int R, bool fp64);

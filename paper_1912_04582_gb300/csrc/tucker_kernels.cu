@@ -1389,14 +1389,21 @@ __device__ __noinline__ void term_contract(const TuckerDev &T, int64_t cell, con
 // The assembly pass proper (see above).  The mode-2/3 contractions come either
 // from T2all / U1all (computed once per cell by tucker_t2_kernel: [cell][R][N2 N3]
 // and [cell][R][padN(N1)]) or, when T2all is null, are formed here into T2buf.
-template <typename Real>
+// kRowMax: also write the largest magnitude of each first-mode row of X to rowmax[N1]
+// (the row scales of the tensor-core Gram matrix), kept per thread while its items stay
+// in one block of rows and combined by shared-memory atomics (non-negative floats order
+// as their bit patterns)
+template <typename Real, bool kRowMax = false>
 __device__ __noinline__ void assemble(const TuckerStepParams &P, int64_t c, const int N[3],
                                       Smem<Real> &sm, const SlotDev *s_slot,
                                       const double *s_scale, Real *X, Real *T2buf,
-                                      const Real *T2all, const Real *U1all, PhaseClock &pc) {
+                                      const Real *T2all, const Real *U1all, PhaseClock &pc,
+                                      float *rowmax = nullptr) {
   __shared__ AsmTerm s_term[1 + 2 * 6];
   __shared__ int s_r1[kTerms];
+  __shared__ unsigned s_rmax[kRowMax ? 64 : 1];
   const int tid = threadIdx.x;
+  if (kRowMax && tid < 64) s_rmax[tid] = 0u;
   const int N1 = N[0], N2 = N[1], N3 = N[2], NP = N2 * N3, Nm = P.Nmax, R = P.R;
   const int N1P = padN(N1), u1slot = R * padN(Nm);
   int nsrc = 0;
@@ -1476,8 +1483,27 @@ __device__ __noinline__ void assemble(const TuckerStepParams &P, int64_t c, cons
   const Real *V0 = tabp(sm, Nm, 9), *V1 = tabp(sm, Nm, 10), *V2 = tabp(sm, Nm, 11);
   const Real *G0 = tabp(sm, Nm, 12), *G1 = tabp(sm, Nm, 13), *G2 = tabp(sm, Nm, 14);
   const int nch = N1P / kRows;
+  float rm[kRowMax ? kRows : 1];
+  int rm_ch = -1;
+  auto flush_rows = [&]() {
+    if constexpr (kRowMax) {
+      if (rm_ch >= 0) {
+#pragma unroll
+        for (int j = 0; j < kRows; ++j)
+          if (rm_ch * kRows + j < N1) atomicMax(&s_rmax[rm_ch * kRows + j], __float_as_uint(rm[j]));
+      }
+    }
+  };
   for (int item = tid; item < NP * nch; item += blockDim.x) {
     const int p = item % NP, ch = item / NP;
+    if constexpr (kRowMax) {
+      if (ch != rm_ch) {
+        flush_rows();
+        rm_ch = ch;
+#pragma unroll
+        for (int j = 0; j < kRows; ++j) rm[j] = 0.f;
+      }
+    }
     const int i2 = p / N3, i3 = p - i2 * N3;
     const int i10 = ch * kRows;  // rows i10 .. i10 + kRows - 1 (tables zero-padded)
     Real acc[kRows], sv[kRows];
@@ -1598,10 +1624,15 @@ __device__ __noinline__ void assemble(const TuckerStepParams &P, int64_t c, cons
     for (int j = 0; j < kRows; ++j) {
       const int i1 = i10 + j;
       if (i1 < N1) __stcs(X + (int64_t)i1 * NP + p, acc[j]);  // streamed past L2
+      if constexpr (kRowMax) rm[j] = fmaxf(rm[j], fabsf((float)acc[j]));
     }
     pc.mark(3);
   }
+  flush_rows();
   __syncthreads();
+  if constexpr (kRowMax) {
+    for (int i = tid; i < N1; i += blockDim.x) rowmax[i] = __uint_as_float(s_rmax[i]);
+  }
 }
 
 // The cell's parameters from its moment sums (Section 4 item 5): n, u, T, q
@@ -1812,8 +1843,15 @@ __global__ void __launch_bounds__(kAsmTB, sizeof(Real) == 8 ? 4 : 6)
     cell_prologue<Real>(P, c, N, sm, s_slot, s_scale);
     pc.mark(0);
     Real *X = reinterpret_cast<Real *>(B.X) + jb * NN;
-    assemble<Real>(P, c, N, sm, s_slot, s_scale, X, T2buf, reinterpret_cast<const Real *>(B.T2all),
-                   reinterpret_cast<const Real *>(B.U1all), pc);
+    if (sizeof(Real) == 4 && B.rowmax)
+      assemble<Real, sizeof(Real) == 4>(P, c, N, sm, s_slot, s_scale, X, T2buf,
+                                        reinterpret_cast<const Real *>(B.T2all),
+                                        reinterpret_cast<const Real *>(B.U1all), pc,
+                                        B.rowmax + jb * P.Nmax);
+    else
+      assemble<Real>(P, c, N, sm, s_slot, s_scale, X, T2buf,
+                     reinterpret_cast<const Real *>(B.T2all),
+                     reinterpret_cast<const Real *>(B.U1all), pc);
     pc.mark(3);
     if (threadIdx.x == 0) B.disc[jb] = 0.0;
   }
@@ -2472,7 +2510,8 @@ void split_chain(const TuckerStepParams &p, const TuckerSplitBufs &b, const Spli
         const int64_t NN = (int64_t)p.N1 * p.N2 * p.N3, NC = (int64_t)p.Nmax * p.Nmax;
         done = launch_gram_tc(reinterpret_cast<const float *>(b.X) + b.joff * NN, NN, b.cn, p.N1,
                               p.N2 * p.N3, reinterpret_cast<float2 *>(b.C + b.joff * NC), nullptr,
-                              NC, b.disc + b.joff, p.flag, s) == 0;
+                              NC, b.disc + b.joff, p.flag, s,
+                              b.rowmax ? b.rowmax + b.joff * p.Nmax : nullptr, p.Nmax) == 0;
       }
     }
     if (done) {
@@ -2630,7 +2669,7 @@ int tucker_prepare_launch(int Nmax, int R, bool fp64) {
 size_t tucker_split_bytes_per_cell(int N1, int N2, int N3, int R, int Nmax, bool fp64) {
   const size_t es = fp64 ? sizeof(double) : sizeof(float);
   return es * ((size_t)N1 * N2 * N3 + (size_t)R * N2 * N3 + (size_t)R * R * N3) +
-         sizeof(double) * ((size_t)Nmax * Nmax + 2);
+         sizeof(double) * ((size_t)Nmax * Nmax + 2) + sizeof(float) * (size_t)Nmax;
 }
 
 size_t tucker_split_t2all_bytes_per_cell(int N1, int N2, int N3, int R, bool fp64) {

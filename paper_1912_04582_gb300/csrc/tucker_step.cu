@@ -472,6 +472,12 @@ int alloc_split(dvm_ctx *C) {
   b.e = reinterpret_cast<double *>(q);
   q += sizeof(double) * chunk;
   b.disc = reinterpret_cast<double *>(q);
+  q += sizeof(double) * chunk;
+  // first-mode row maxima of X, for the tensor-core Gram matrices of the mixed path
+  b.rowmax = (!S->fp64 && C->opts.gram_engine == DVM_GRAM_AUTO &&
+              gram_tc_supported(C->N[0], C->N[1] * C->N[2]))
+                 ? reinterpret_cast<float *>(q)
+                 : nullptr;
   S->sb = b;
   S->chunk = chunk;
   S->split_mem = mem;
