@@ -475,6 +475,91 @@ def run_c2(P, NAT, stream, advance=200, warmup=3, steps=10):
     return out
 
 
+def c4_uneven_rank_state(wl, R, seed=42, delta=1e-4):
+    """Device-resident Tucker state for the uneven-rank step benchmark: per-cell ranks
+    drawn from U{4..20} per mode (seeded); column 0 of each factor the free stream's
+    normalised 1-D Maxwellian profile, the other columns a random orthonormal complement
+    (seeded); core entry (0,0,0) the free stream's density scale times the profiles'
+    norms, every other kept entry delta times it with a random (seeded) normal weight."""
+    import math
+    import torch
+    import workloads as W
+    nc = wl.n_cell
+    dev = torch.device("cuda")
+    ranks = torch.from_numpy(W.uniform_random_tucker_ranks(nc, 4, 20, seed)).to(dev)
+    gen = torch.Generator(device=dev).manual_seed(seed)
+    n0, T0 = float(wl.n0[0]), float(wl.T0[0])
+    facs, norms = [], []
+    for a in range(3):
+        N = int(wl.N[a])
+        i = torch.arange(N, dtype=torch.float64, device=dev)
+        xi = ((N - 1 - i) * wl.lo[a] + i * wl.hi[a]) / (N - 1)
+        prof = torch.exp(-(xi - float(wl.u0[0, a])) ** 2 / T0)
+        nrm = float(prof.norm())
+        A = torch.randn(nc, N, R, generator=gen, dtype=torch.float64, device=dev)
+        A[:, :, 0] = prof / nrm
+        Q = torch.linalg.qr(A).Q
+        Q = Q * torch.sign((Q[:, :, :1] * (prof / nrm)[None, :, None]).sum(1, keepdim=True))
+        facs.append(Q.contiguous())
+        norms.append(nrm)
+    g0 = n0 * (math.pi * T0) ** -1.5 * norms[0] * norms[1] * norms[2]
+    e = torch.arange(R ** 3, device=dev)[None, :]
+    keep = e < (ranks[:, 0] * ranks[:, 1] * ranks[:, 2]).to(torch.int64)[:, None]
+    core = delta * g0 * torch.randn(nc, R ** 3, generator=gen, dtype=torch.float64, device=dev)
+    core[:, 0] = g0
+    core = torch.where(keep, core, torch.zeros_like(core)).contiguous()
+    return ranks.contiguous(), core, facs
+
+
+def run_c4_uneven(P, NAT, wl, stream, steps=2):
+    """One timed Tucker step (mixed, cap 20, eps 1e-5) from the uneven-rank state of the C4
+    mesh, with per-class launch times."""
+    import torch
+    # the phase-major variant (the fused kernel's shared memory does not fit these ranks)
+    s = P.Solver(wl, format=NAT.DVM_FORMAT_TUCKER, precision=NAT.DVM_PREC_MIXED, rank_cap=20,
+                 tol=1e-5, stream=stream.cuda_stream, init=False,
+                 variant=NAT.DVM_VARIANT_PHASED)
+    ranks, core, facs = c4_uneven_rank_state(wl, 20)
+    rin = ranks.cpu().numpy()
+    out = {"ranks_in": {"mean": float(rin.mean()), "histogram": rank_histogram(rin)}}
+    P.dvm_init_tucker_device(s.h, ranks.data_ptr(), core.data_ptr(), [f.data_ptr() for f in facs])
+    del core, facs
+    torch.cuda.synchronize()
+    ms = []
+    for k in range(steps):  # re-set the same state before each timed step
+        if k:
+            ranks2, core2, facs2 = c4_uneven_rank_state(wl, 20)
+            P.dvm_init_tucker_device(s.h, ranks2.data_ptr(), core2.data_ptr(),
+                                     [f.data_ptr() for f in facs2])
+            del ranks2, core2, facs2
+        if k == steps - 1:
+            P.dvm_set_kernel_timing(s.h, True)
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        s.step(1, residual=False)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(ev0.elapsed_time(ev1))
+    t = P.dvm_get_kernel_timing(s.h)
+    P.dvm_set_kernel_timing(s.h, False)
+    rout = P.dvm_get_ranks(s.h)
+    g, _ = P.dvm_get_launch_config(s.h)
+    out.update({"ms_per_step_first": ms[0], "ms_per_step": ms[-1],
+                "updates_per_s": wl.n_cell * wl.nodes_per_cell / (ms[-1] / 1e3),
+                "kernel_ms": {k: v[0] for k, v in t.items() if v[1]},
+                "ranks_out": {"mean": float(rout.mean()), "histogram": rank_histogram(rout)},
+                "variant": "phase-major" if g < 0 else "fused",
+                "state": "ranks U{4..20} per mode (seed 42), free-stream Maxwellian plus 1e-4 "
+                         "random kept components (not low rank: the step keeps the cap); the "
+                         "state is set again before each step; the last is timed per kernel "
+                         "class on one stream"})
+    s.close()
+    torch.cuda.synchronize()
+    return out
+
+
 def run_c4(P, NAT, stream, advance=10, steps=3):
     """C4, Mach-3 flow past a cube on 101,888 jittered cells x 64^3, Tucker mixed cap 20,
     eps 1e-5, a few steps from the initial free stream (its full-grid FP64 state would need
@@ -488,6 +573,7 @@ def run_c4(P, NAT, stream, advance=10, steps=3):
                     2, steps, stream, snap=False)
     return {f"C4_obstacle_{c4.n_cell}x64^3": {
         "tucker_mixed": d,
+        "tucker_mixed_uneven_ranks_4_20": run_c4_uneven(P, NAT, c4, stream),
         "full_fp64": {"device_bytes_needed": need, "device_bytes_total": int(total),
                       "fits": bool(need <= total)}}}
 

@@ -185,6 +185,18 @@ def dvm_init_tucker(h, ranks, core, fac):
                                             _dp(fac[1]), _dp(fac[2]), 0), "dvm_init_tucker")
 
 
+def dvm_init_tucker_device(h, ranks_ptr, core_ptr, fac_ptrs):
+    """Set the Tucker state from device pointers (ints) in the layout of ``dvm_get_tucker``:
+    ranks int32 [nc,3], core float64 [nc,R^3], factors float64 [nc,N_a,R]."""
+    v = ctypes.c_void_p
+    return _n.check(N_lib().dvm_init_tucker(h.ptr, ctypes.cast(v(int(ranks_ptr)), _n._c_i32p),
+                                            ctypes.cast(v(int(core_ptr)), _n._c_dp),
+                                            ctypes.cast(v(int(fac_ptrs[0])), _n._c_dp),
+                                            ctypes.cast(v(int(fac_ptrs[1])), _n._c_dp),
+                                            ctypes.cast(v(int(fac_ptrs[2])), _n._c_dp), 1),
+                    "dvm_init_tucker")
+
+
 def dvm_set_kernel_timing(h, on):
     _n.check(N_lib().dvm_set_kernel_timing(h.ptr, int(bool(on))), "dvm_set_kernel_timing")
 
