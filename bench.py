@@ -515,7 +515,8 @@ def run_c4_uneven(P, NAT, wl, stream, steps=2):
     """One timed Tucker step (mixed, cap 20, eps 1e-5) from the uneven-rank state of the C4
     mesh, with per-class launch times."""
     import torch
-    # the phase-major variant (the fused kernel's shared memory does not fit these ranks)
+    # the phase-major variant, fixed so that no step includes the autotuner's trial runs
+    # of the fused kernel (seconds each at these ranks)
     s = P.Solver(wl, format=NAT.DVM_FORMAT_TUCKER, precision=NAT.DVM_PREC_MIXED, rank_cap=20,
                  tol=1e-5, stream=stream.cuda_stream, init=False,
                  variant=NAT.DVM_VARIANT_PHASED)
