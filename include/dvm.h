@@ -118,19 +118,24 @@ typedef struct {
                        * sized to 1/8 of the free device memory, at most all
                        * cells); bounds the context's memory.  Results do not
                        * depend on it.                                      */
-  int32_t gram_engine; /* mixed-precision Tucker, phase-major variant: how the
-                       * first-mode Gram matrices are formed.  DVM_GRAM_AUTO
-                       * (0): on the tensor cores (exact integer split, see
-                       * dvm_gram_tc) when N1 <= 64 and N2 N3 is a multiple
-                       * of 8 up to 4096, else on the CUDA cores;
-                       * DVM_GRAM_CUDA_CORES (1): exact FP32 products summed
-                       * in double-FP32 on the CUDA cores, as the fused
-                       * variant does (the two variants then agree bit for
-                       * bit).  Both are accurate far below FP32 rounding.  */
+  int32_t engine;     /* mixed-precision Tucker, phase-major variant: how the
+                       * dense contractions run.  DVM_ENGINE_AUTO (0): the
+                       * first-mode Gram matrices on the tensor cores (exact
+                       * integer split, see dvm_gram_tc) when N1 <= 64 and
+                       * N2 N3 is a multiple of 8 up to 4096, else on the
+                       * CUDA cores; on meshes whose faces all lie on
+                       * coordinate planes (and N <= 64), the assembly of
+                       * f^{n+1} as one small GEMM per cell of its rank-one
+                       * terms (FP32 FMAs).  DVM_ENGINE_CUDA_CORES (1): the
+                       * fused variant's arithmetic (Gram matrices from
+                       * exact FP32 products summed in double-FP32, the
+                       * assembly term by term): the two variants then
+                       * agree bit for bit.  Both are accurate to FP32
+                       * rounding of f^{n+1}.                              */
 } dvm_opts;
 
-#define DVM_GRAM_AUTO 0
-#define DVM_GRAM_CUDA_CORES 1
+#define DVM_ENGINE_AUTO 0
+#define DVM_ENGINE_CUDA_CORES 1
 
 #define DVM_VARIANT_AUTO 0
 #define DVM_VARIANT_FUSED 1

@@ -58,7 +58,7 @@ class dvm_opts(ctypes.Structure):
                 ("rank_cap", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("cfl", ctypes.c_double), ("dt", ctypes.c_double),
                 ("cuda_stream", ctypes.c_void_p), ("variant", ctypes.c_int32),
-                ("max_chunk", ctypes.c_int64), ("gram_engine", ctypes.c_int32)]
+                ("max_chunk", ctypes.c_int64), ("engine", ctypes.c_int32)]
 
 
 class dvm_request(ctypes.Structure):
@@ -72,7 +72,7 @@ class dvm_request(ctypes.Structure):
 (DVM_REQ_QUEUED, DVM_REQ_RUNNING, DVM_REQ_CONVERGED, DVM_REQ_NOT_CONVERGED, DVM_REQ_FAILED,
  DVM_REQ_CANCELLED) = range(6)
 DVM_FAULT_NONE, DVM_FAULT_ALLOC, DVM_FAULT_TIMEOUT, DVM_FAULT_ADMIT = range(4)
-DVM_GRAM_AUTO, DVM_GRAM_CUDA_CORES = range(2)
+DVM_ENGINE_AUTO, DVM_ENGINE_CUDA_CORES = range(2)
 
 _P = ctypes.c_void_p
 _PP = ctypes.POINTER(ctypes.c_void_p)

@@ -187,8 +187,8 @@ int dvm_create(dvm_ctx **out, const dvm_mesh *mesh, const dvm_vgrid *vg, const d
     set_error("dvm_create: unknown format");
     return DVM_ERR_INVALID_ARG;
   }
-  if (opts->gram_engine != DVM_GRAM_AUTO && opts->gram_engine != DVM_GRAM_CUDA_CORES) {
-    set_error("dvm_create: gram_engine must be DVM_GRAM_AUTO or DVM_GRAM_CUDA_CORES");
+  if (opts->engine != DVM_ENGINE_AUTO && opts->engine != DVM_ENGINE_CUDA_CORES) {
+    set_error("dvm_create: engine must be DVM_ENGINE_AUTO or DVM_ENGINE_CUDA_CORES");
     return DVM_ERR_INVALID_ARG;
   }
   if (opts->max_chunk < 0) {

@@ -39,6 +39,8 @@ struct TuckerStepParams {
   int N1, N2, N3, R, Nmax;
   int mode;              // 0 = time step, 1 = compress finit
   int tc_gram;           // phase-major mixed path: first-mode Gram on the tensor cores
+  int gemm_asm;          // phase-major mixed path: assembly as one GEMM per cell (all faces on
+                         // coordinate planes)
   double w, dt, Pr, omega, delta, tol;
 };
 
@@ -133,6 +135,9 @@ GramTcPlan gram_tc_plan(int n);
 bool gram_tc_supported(int n, int K);
 // raise the kernel's shared-memory opt-in for n rows (outside stream captures); 0 ok
 int gram_tc_prepare(int n);
+// raise the GEMM-form assembly kernel's shared-memory opt-in (outside stream captures);
+// 0 ok, else the form is not available for this size
+int tucker_asm_gemm_prepare(int Nmax, int N1, int R);
 // C (double-float pairs) or Cd (doubles), cstride elements per cell; disc[cell] = 0
 // rowmax (optional, rstride floats per cell): each row's largest magnitude, known from
 // the producer of X; without it the kernel reads X twice (row scales, then slicing)

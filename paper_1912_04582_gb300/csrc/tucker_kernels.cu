@@ -1857,6 +1857,296 @@ __global__ void __launch_bounds__(kAsmTB, sizeof(Real) == 8 ? 4 : 6)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Assembly of f^{n+1} in GEMM form (mixed path; meshes whose faces all lie on coordinate
+// planes).  Every term of
+//   X = dt nu f^S + sum_ghosts m_l g_l + W_self o f + sum_faces m_l o f_src(l)
+// factors into (a vector over the first-mode index i1) x (a vector over the columns
+// p = (i2, i3)), because every face weight then depends on one velocity coordinate:
+// the self term (Lemma 1) is (w0 + G0(i1) + zero-gradient inflows along axis 0) U1 T2 +
+// U1 (T2 o (G1(i2) + G2(i3) + zero-gradient inflows along axes 1, 2)); a face term is
+// (m_l(i1) U1_src) T2_src or U1_src (T2_src o m_l(i2 or i3)) (a symmetry face: the
+// cell's own tensor with one index mirrored); the Shakhov term (Proposition 1: f^M
+// times a cubic polynomial) is four rank-one products; a ghost is one.  Hence
+// X = A B^T with A [N1 x K] the row factors and B [NP x K] the column factors, K <=
+// 4 + 8 R the cell's number of rank-one terms: one small GEMM per cell, its K-term sums
+// in FP32 FMAs.  One CTA per cell: A in shared memory, then per tile of 256 columns the
+// column factors staged 32 terms at a time (every thread one column, its gathers all
+// issued before any is used) and a register tile of N1P / 4 rows x 4 columns per thread,
+// A read as broadcast float4 and B as one float4 per term.  X is written once, column-
+// coalesced, and each first-mode row's largest magnitude kept (the tensor-core Gram
+// matrix's row scales).
+constexpr int kAgThreads = 256;
+constexpr int kAgCols = 256;  // columns of X per tile: 64 groups of four
+constexpr int kAgKC = 32;     // terms per staged chunk of B
+
+struct AgTerm {
+  int64_t t2;  // Tucker terms: T2 row offset (elements), cell * R * NP + k * NP
+  int64_t u1;  // Tucker terms: U1 row offset (elements), cell * R * padN(N1) + k * padN(N1)
+  int kind;    // 0 Tucker term, 1-4 Shakhov parts, 5 ghost of face `face`
+  int refl;    // 1 / 2: second / third-mode index mirrored
+  int wsel;    // column weight: 0 none, 1 self (G1(i2) + G2(i3)), 2 face tab over i2, 3 over i3
+  int face;
+  int wa;      // row weight: 0 none, 1 self (w0 + G0(i1)), 2 face tab over i1
+  int rev;     // first-mode index mirrored
+};
+
+__host__ __device__ inline int ag_max_terms(int R) { return 4 + 8 * R; }
+
+// shared memory: cell scalars and tables, self weights, A [K][padN(N1)], the staged column
+// factors B [kAgKC][kAgCols], term list, row maxima
+__host__ __device__ inline size_t ag_smem_bytes(int Nmax, int N1, int R) {
+  const size_t NmP = padN(Nmax), K4 = (size_t)((ag_max_terms(R) + 3) & ~3);
+  return sizeof(double) * 96 + sizeof(float) * ((size_t)kTabs * NmP + 3 * NmP) +
+         sizeof(float) * K4 * padN(N1) + sizeof(float) * kAgKC * kAgCols +
+         sizeof(AgTerm) * K4 + sizeof(unsigned) * NmP + 64;
+}
+
+// X of one cell: thread (rg, cg) = (tid / 64, tid % 64) holds rows rg TR .. rg TR + TR - 1
+// and columns 4 cg .. 4 cg + 3 of each 256-column tile (TR = padN(N1) / 4)
+template <int TR>
+__device__ __forceinline__ void ag_columns(const TuckerStepParams &P, const TuckerSplitBufs &B,
+                                           int64_t jb, Smem<float> &sm, const SlotDev *s_slot,
+                                           const float *A_s, float *B_s, const AgTerm *terms,
+                                           int K, const float *colW2, const float *colW3,
+                                           unsigned *s_rmax) {
+  const int N1 = P.N1, N2 = P.N2, N3 = P.N3, NP = N2 * N3, Nm = P.Nmax, N1P = padN(N1);
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int rg = tid >> 6, cg = tid & 63, row0 = rg * TR;
+  const float *T2all = reinterpret_cast<const float *>(B.T2all);
+  const float *ghostR = P.ghostf32;
+  float *Xc = reinterpret_cast<float *>(B.X) + jb * (int64_t)N1 * NP;
+  const bool vec = (NP & 3) == 0;
+  float rm[TR];
+#pragma unroll
+  for (int r = 0; r < TR; ++r) rm[r] = 0.f;
+  for (int c0 = 0; c0 < NP; c0 += kAgCols) {
+    float acc[TR][4];
+#pragma unroll
+    for (int r = 0; r < TR; ++r)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[r][q] = 0.f;
+    for (int k0 = 0; k0 < K; k0 += kAgKC) {
+      const int kn = min(kAgKC, K - k0), kn4 = (kn + 3) & ~3;
+      {  // stage B[c0 + tid][k0 .. k0 + kn4): this thread's column, SH terms at a time
+        constexpr int SH = TR > 12 ? 8 : 16;  // gathers in flight (registers: the tile is live)
+        const int p = c0 + tid;
+        const bool pin = p < NP;
+        const int pc = pin ? p : 0, i2 = pc / N3, i3 = pc - i2 * N3;
+        const int pm2 = (N2 - 1 - i2) * N3 + i3, pm3 = i2 * N3 + (N3 - 1 - i3);
+#pragma unroll
+        for (int h = 0; h < kAgKC; h += SH) {
+          if (h >= kn4) break;  // uniform
+          float g[SH];
+#pragma unroll
+          for (int e = 0; e < SH; ++e) {
+            g[e] = 0.f;
+            if (h + e < kn && pin && terms[k0 + h + e].kind == 0) {
+              const int refl = terms[k0 + h + e].refl;
+              g[e] = __ldg(T2all + terms[k0 + h + e].t2 + (refl == 1 ? pm2 : (refl == 2 ? pm3 : pc)));
+            }
+          }
+#pragma unroll
+          for (int e = 0; e < SH; ++e) {
+            if (h + e >= kn4) break;  // uniform
+            float x = 0.f;
+            if (h + e < kn && pin) {
+              const AgTerm tm = terms[k0 + h + e];
+              if (tm.kind == 0) {
+                x = g[e];
+                if (tm.wsel == 1) x *= colW2[i2] + colW3[i3];
+                else if (tm.wsel == 2) x *= tabp(sm, Nm, 15 + tm.face)[i2];
+                else if (tm.wsel == 3) x *= tabp(sm, Nm, 15 + tm.face)[i3];
+              } else if (tm.kind == 5) {
+                const SlotDev &sl = s_slot[tm.face];
+                const float *gf = ghostR + (int64_t)sl.src * 3 * Nm;
+                x = gf[Nm + i2] * gf[2 * Nm + i3];
+                if (sl.axis == 1) x *= tabp(sm, Nm, 15 + tm.face)[i2];
+                else if (sl.axis == 2) x *= tabp(sm, Nm, 15 + tm.face)[i3];
+              } else {
+                const float fM = tabp(sm, Nm, 4)[i2] * tabp(sm, Nm, 5)[i3];
+                const float Qp = tabp(sm, Nm, 7)[i2] + tabp(sm, Nm, 8)[i3];
+                const float Vp = tabp(sm, Nm, 10)[i2] + tabp(sm, Nm, 11)[i3] - 2.5f;
+                x = tm.kind == 1 ? fM : (tm.kind == 2 ? fM * Vp : (tm.kind == 3 ? fM * Qp : fM * Qp * Vp));
+              }
+            }
+            B_s[(h + e) * kAgCols + tid] = x;
+          }
+        }
+      }
+      __syncthreads();
+      const float *a = A_s + (size_t)k0 * N1P + row0;
+      const float *bp = B_s + 4 * cg;
+#pragma unroll(TR > 12 ? 1 : 4)
+      for (int e = 0; e < kn4; ++e) {
+        float av[TR];
+#pragma unroll
+        for (int q = 0; q < TR / 4; ++q) {
+          const float4 t = *reinterpret_cast<const float4 *>(a + (size_t)e * N1P + 4 * q);
+          av[4 * q] = t.x;
+          av[4 * q + 1] = t.y;
+          av[4 * q + 2] = t.z;
+          av[4 * q + 3] = t.w;
+        }
+        const float4 bv = *reinterpret_cast<const float4 *>(bp + e * kAgCols);
+#pragma unroll
+        for (int r = 0; r < TR; ++r) {
+          acc[r][0] = fmaf(av[r], bv.x, acc[r][0]);
+          acc[r][1] = fmaf(av[r], bv.y, acc[r][1]);
+          acc[r][2] = fmaf(av[r], bv.z, acc[r][2]);
+          acc[r][3] = fmaf(av[r], bv.w, acc[r][3]);
+        }
+      }
+      __syncthreads();  // B_s is restaged next
+    }
+    // the tile of X (streamed past L2) and the row maxima
+    const int cb = c0 + 4 * cg;
+#pragma unroll
+    for (int r = 0; r < TR; ++r) {
+      const int row = row0 + r;
+      if (row >= N1 || cb >= NP) continue;
+      float *dst = Xc + (int64_t)row * NP + cb;
+      if (vec) {  // NP a multiple of 4: the four columns are in range and 16-byte aligned
+        __stcs(reinterpret_cast<float4 *>(dst), make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]));
+        rm[r] = fmaxf(rm[r], fmaxf(fmaxf(fabsf(acc[r][0]), fabsf(acc[r][1])),
+                                   fmaxf(fabsf(acc[r][2]), fabsf(acc[r][3]))));
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (cb + q < NP) {
+            __stcs(dst + q, acc[r][q]);
+            rm[r] = fmaxf(rm[r], fabsf(acc[r][q]));
+          }
+      }
+    }
+  }
+  if (B.rowmax) {  // across the warp's 32 column groups (its rows are the same), then warps
+#pragma unroll
+    for (int r = 0; r < TR; ++r) {
+      float m = rm[r];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if (lane == 0 && row0 + r < N1) atomicMax(&s_rmax[row0 + r], __float_as_uint(m));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kAgThreads, 2)
+    tucker_asm_gemm_kernel(TuckerStepParams P, TuckerSplitBufs B) {
+  extern __shared__ __align__(16) unsigned char ag_raw[];
+  const int Nm = P.Nmax, N1 = P.N1, N2 = P.N2, N3 = P.N3, NmP = padN(Nm), NP = N2 * N3;
+  const int N1P = padN(N1), R = P.R, Kmax = ag_max_terms(R), K4max = (Kmax + 3) & ~3;
+  const int N[3] = {N1, N2, N3};
+  Smem<float> sm{};
+  sm.nmax = Nm;
+  sm.par = reinterpret_cast<double *>(ag_raw);
+  sm.red = sm.par + 32;
+  sm.rt = reinterpret_cast<float *>(sm.par + 96);
+  float *rowW = sm.rt + (size_t)kTabs * NmP;        // self weight over i1
+  float *colW2 = rowW + NmP, *colW3 = colW2 + NmP;  // self weight parts over i2, i3
+  float *A_s = colW3 + NmP;                         // [K][N1P]
+  float *B_s = A_s + (size_t)K4max * N1P;           // [kAgKC][kAgCols]
+  AgTerm *terms = reinterpret_cast<AgTerm *>(B_s + kAgKC * kAgCols);
+  unsigned *s_rmax = reinterpret_cast<unsigned *>(terms + K4max);
+  __shared__ SlotDev s_slot[6];
+  __shared__ double s_scale[6];
+  __shared__ int s_K;
+  const float *U1all = reinterpret_cast<const float *>(B.U1all);
+  const float *ghostR = P.ghostf32;
+  const int tid = threadIdx.x;
+  for (int64_t j = blockIdx.x; j < B.cn; j += gridDim.x) {
+    const int64_t c = B.c0 + j, jb = B.joff + j;
+    cell_prologue<float>(P, c, N, sm, s_slot, s_scale);
+    // the cell's rank-one terms: Shakhov parts, ghosts, self (row weight), self (column
+    // weight), then each interior / symmetry face
+    if (tid == 0) {
+      int n = 0;
+      auto put = [&](const AgTerm &tm) {
+        if (n < Kmax) terms[n] = tm;
+        ++n;
+      };
+      for (int k = 1; k <= 4; ++k) put(AgTerm{0, 0, k, 0, 0, 0, 0, 0});
+      for (int l = 0; l < 6; ++l)
+        if (s_slot[l].kind == kFreeStream || s_slot[l].kind == kWall) put(AgTerm{0, 0, 5, 0, 0, l, 0, 0});
+      const int r = P.cur.rank[3 * c];
+      const int64_t oT = c * (int64_t)R * NP, oU = c * (int64_t)R * N1P;
+      for (int k = 0; k < r; ++k) put(AgTerm{oT + (int64_t)k * NP, oU + (int64_t)k * N1P, 0, 0, 0, -1, 1, 0});
+      for (int k = 0; k < r; ++k) put(AgTerm{oT + (int64_t)k * NP, oU + (int64_t)k * N1P, 0, 0, 1, -1, 0, 0});
+      for (int l = 0; l < 6; ++l) {
+        const SlotDev &sl = s_slot[l];
+        if (sl.kind != kInterior && sl.kind != kSymmetry) continue;
+        const bool sym = sl.kind == kSymmetry;
+        const int64_t src = sym ? c : (int64_t)sl.src;
+        const int rs = P.cur.rank[3 * src];
+        const int wa = sl.axis == 0 ? 2 : 0, ws = sl.axis == 1 ? 2 : (sl.axis == 2 ? 3 : 0);
+        const int rev = sym && sl.flip == 0, refl = sym ? (sl.flip == 1 ? 1 : (sl.flip == 2 ? 2 : 0)) : 0;
+        const int64_t sT = src * (int64_t)R * NP, sU = src * (int64_t)R * N1P;
+        for (int k = 0; k < rs; ++k)
+          put(AgTerm{sT + (int64_t)k * NP, sU + (int64_t)k * N1P, 0, refl, ws, l, wa, rev});
+      }
+      s_K = n;
+    }
+    // self weights (Lemma 1): w0 + G0(i1) | G1(i2) | G2(i3), plus zero-gradient inflows
+    {
+      const float w0 = (float)(1.0 - sm.par[8]);
+      for (int i = tid; i < NmP; i += blockDim.x) {
+        float a = i < N1 ? w0 + tabp(sm, Nm, 12)[i] : 0.f;
+        float b2 = i < N2 ? tabp(sm, Nm, 13)[i] : 0.f, b3 = i < N3 ? tabp(sm, Nm, 14)[i] : 0.f;
+        for (int l = 0; l < 6; ++l) {
+          if (s_slot[l].kind != kZeroGrad) continue;
+          const float *tab = tabp(sm, Nm, 15 + l);
+          if (s_slot[l].axis == 0 && i < N1) a += tab[i];
+          if (s_slot[l].axis == 1 && i < N2) b2 += tab[i];
+          if (s_slot[l].axis == 2 && i < N3) b3 += tab[i];
+        }
+        rowW[i] = a;
+        colW2[i] = b2;
+        colW3[i] = b3;
+        s_rmax[i] = 0u;
+      }
+    }
+    __syncthreads();
+    const int K = s_K;
+    if (K > Kmax) {  // more terms than 4 + 8 R: a rank above the cap (state corrupt)
+      if (tid == 0) atomicOr(P.flag, 2);
+      break;
+    }
+    // A: the row factors, [term][row], zero past N1 and up to a multiple of four terms
+    const int K4 = (K + 3) & ~3;
+    for (int idx = tid; idx < K4 * N1P; idx += blockDim.x) {
+      const int k = idx / N1P, row = idx - k * N1P;
+      float x = 0.f;
+      if (k < K && row < N1) {
+        const AgTerm tm = terms[k];
+        if (tm.kind == 0) {
+          x = U1all[tm.u1 + (tm.rev ? N1 - 1 - row : row)];
+          if (tm.wa == 1) x *= rowW[row];
+          else if (tm.wa == 2) x *= tabp(sm, Nm, 15 + tm.face)[row];
+        } else if (tm.kind == 5) {
+          const SlotDev &sl = s_slot[tm.face];
+          x = ghostR[(int64_t)sl.src * 3 * Nm + row];
+          if (sl.axis == 0) x *= tabp(sm, Nm, 15 + tm.face)[row];
+        } else {
+          const float f0 = tabp(sm, Nm, 3)[row], q0 = tabp(sm, Nm, 6)[row], v0 = tabp(sm, Nm, 9)[row];
+          x = tm.kind == 1 ? f0 * (1.f + q0 * v0) : (tm.kind == 2 ? f0 * q0 : (tm.kind == 3 ? f0 * v0 : f0));
+        }
+      }
+      A_s[idx] = x;
+    }
+    __syncthreads();
+    switch (N1P) {
+      case 16: ag_columns<4>(P, B, jb, sm, s_slot, A_s, B_s, terms, K, colW2, colW3, s_rmax); break;
+      case 32: ag_columns<8>(P, B, jb, sm, s_slot, A_s, B_s, terms, K, colW2, colW3, s_rmax); break;
+      case 48: ag_columns<12>(P, B, jb, sm, s_slot, A_s, B_s, terms, K, colW2, colW3, s_rmax); break;
+      default: ag_columns<16>(P, B, jb, sm, s_slot, A_s, B_s, terms, K, colW2, colW3, s_rmax); break;
+    }
+    __syncthreads();
+    if (B.rowmax)
+      for (int i = tid; i < N1; i += blockDim.x) B.rowmax[jb * Nm + i] = __uint_as_float(s_rmax[i]);
+    if (tid == 0) B.disc[jb] = 0.0;
+  }
+}
+
 // Mode-2/3 contraction T2 = G x2 U2 x3 U3 of every cell's current tensor and its
 // first-mode factor in the working precision (transposed, zero-padded), once per
 // step for all cells (each is used by the cell and its face neighbours).
@@ -2482,6 +2772,8 @@ int prepare_split_TS(int Nmax, int R) {
   const SplitSmem<Real, TS> z(Nmax, R);
   int mask = 0;
   if (raise_smem_optin(tucker_step_kernel<Real, TS>, smem_bytes<Real>(Nmax, R)) == 0) mask |= 1;
+  if (sizeof(Real) == 4 && Nmax <= 64)  // GEMM-form assembly (used where the mesh allows)
+    raise_smem_optin(tucker_asm_gemm_kernel, ag_smem_bytes(Nmax, Nmax, R));
   if (raise_smem_optin(tucker_asm_kernel<Real>, z.asm_) == 0 &&
       raise_smem_optin(tucker_t2_kernel<Real>, z.asm_) == 0 &&
       raise_smem_optin(tucker_gram_kernel<Real, TS>, z.gram) == 0 &&
@@ -2499,7 +2791,15 @@ void split_chain(const TuckerStepParams &p, const TuckerSplitBufs &b, const Spli
                  cudaStream_t s, const LaunchTimer &T, const TuckerMomentParams *mp) {
   const int ga = (int)(b.cn < b.asm_grid ? b.cn : b.asm_grid);
   T(kKAsm, true, s);
-  tucker_asm_kernel<Real><<<ga, kAsmTB, z.asm_, s>>>(p, b);
+  if (sizeof(Real) == 4 && p.gemm_asm) {  // one small GEMM per cell of its rank-one terms
+    int sms = 1, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int gg = (int)(b.cn < 2 * sms ? b.cn : 2 * sms);
+    tucker_asm_gemm_kernel<<<gg, kAgThreads, ag_smem_bytes(p.Nmax, p.N1, p.R), s>>>(p, b);
+  } else {
+    tucker_asm_kernel<Real><<<ga, kAsmTB, z.asm_, s>>>(p, b);
+  }
   T(kKAsm, false, s);
   for (int m = 0; m < 3; ++m) {
     const int gc = m == 0 ? kKGram0 : kKGram12;
@@ -2664,6 +2964,11 @@ int tucker_prepare_launch(int Nmax, int R, bool fp64) {
   if (fp64)
     return Nmax <= 32 ? prepare_split_TS<double, 2>(Nmax, R) : prepare_split_TS<double, 4>(Nmax, R);
   return Nmax <= 32 ? prepare_split_TS<float, 2>(Nmax, R) : prepare_split_TS<float, 4>(Nmax, R);
+}
+
+int tucker_asm_gemm_prepare(int Nmax, int N1, int R) {
+  if (Nmax > 64 || N1 > 64) return -1;  // register tiles of at most 16 rows per thread
+  return raise_smem_optin(tucker_asm_gemm_kernel, ag_smem_bytes(Nmax, N1, R));
 }
 
 size_t tucker_split_bytes_per_cell(int N1, int N2, int N3, int R, int Nmax, bool fp64) {

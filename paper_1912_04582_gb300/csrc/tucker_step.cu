@@ -34,6 +34,7 @@ struct TuckerState {
   int64_t tuned_step = 0;       // step counter at the first tuning
   float tune_ms[5] = {0, 0, 0, 0, 0};  // [0] phase-major step, [1..4] fused kernel per CTAs/SM
   bool split = false;                  // phase-major variant chosen
+  bool gemm_asm = false;               // its assembly may take the GEMM form
   int fit = 3;                         // variants whose kernels fit: 1 fused, 2 phase-major
   TuckerSplitBufs sb{};                // its work buffers (one chunk of cells)
   int64_t chunk = 0;                   // cells per chunk
@@ -88,8 +89,9 @@ TuckerStepParams step_params(dvm_ctx *C) {
   p.omega = C->gas.omega;
   p.delta = std::sqrt(3.14159265358979323846) / (2.0 * C->gas.Kn);
   p.tol = C->opts.tol;
-  p.tc_gram = !S->fp64 && C->opts.gram_engine == DVM_GRAM_AUTO &&
+  p.tc_gram = !S->fp64 && C->opts.engine == DVM_ENGINE_AUTO &&
               gram_tc_supported(C->N[0], C->N[1] * C->N[2]);
+  p.gemm_asm = S->gemm_asm && C->all_axis;
   return p;
 }
 
@@ -241,7 +243,12 @@ int tucker_alloc(dvm_ctx *C) {
   if (rc != DVM_OK) return rc;
   DVM_CUDA_TRY(cudaMemset(S->err, 0, sizeof(double) * nc));
   S->fit = tucker_prepare_launch(S->Nmax, R, S->fp64);
-  if (!S->fp64 && C->opts.gram_engine == DVM_GRAM_AUTO &&
+  // the assembly in GEMM form (used on meshes whose faces all lie on coordinate planes,
+  // known once the boundaries are set up: each face weight then depends on one velocity
+  // coordinate)
+  S->gemm_asm = !S->fp64 && C->opts.engine == DVM_ENGINE_AUTO &&
+                tucker_asm_gemm_prepare(S->Nmax, C->N[0], R) == 0;
+  if (!S->fp64 && C->opts.engine == DVM_ENGINE_AUTO &&
       gram_tc_supported(C->N[0], C->N[1] * C->N[2]) && gram_tc_prepare(C->N[0]) != 0) {
     set_error("tensor-core Gram kernel: shared-memory opt-in refused by the device");
     return DVM_ERR_UNSUPPORTED;
@@ -474,7 +481,7 @@ int alloc_split(dvm_ctx *C) {
   b.disc = reinterpret_cast<double *>(q);
   q += sizeof(double) * chunk;
   // first-mode row maxima of X, for the tensor-core Gram matrices of the mixed path
-  b.rowmax = (!S->fp64 && C->opts.gram_engine == DVM_GRAM_AUTO &&
+  b.rowmax = (!S->fp64 && C->opts.engine == DVM_ENGINE_AUTO &&
               gram_tc_supported(C->N[0], C->N[1] * C->N[2]))
                  ? reinterpret_cast<float *>(q)
                  : nullptr;
