@@ -145,14 +145,15 @@ def _peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def _traffic(kernel):
+def _traffic(kernel, source=None):
     """Per-launch DRAM bytes from the committed ncu summary, if the kernel source is
     unchanged since the capture (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(p):
         return None
-    src = os.path.join(ROOT, "paper_1912_04582_gb300", "csrc", "full_kernels.cu"
-                       if kernel in ("full", "full_step") else "tucker_kernels.cu")
+    if source is None:
+        source = "full_kernels.cu" if kernel in ("full", "full_step") else "tucker_kernels.cu"
+    src = os.path.join(ROOT, "paper_1912_04582_gb300", "csrc", source)
     if not os.path.exists(src):
         return None
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
@@ -234,12 +235,47 @@ FP32_PEAK_GOPS = 35000.0   # FP32 lane operations/s: an FMA-chain probe measured
 DF_OPS = 10                # FP32 operations of one double-float multiply-accumulate
 
 
-def _tucker_work(wl, ranks, cls):
+def gram_on_tensor_cores(N):
+    """Whether the first-mode Gram matrices of a velocity grid N run on the tensor cores
+    with the default engine (the library's rule: N1 <= 64, N2 N3 a multiple of 8 up to
+    4096)."""
+    n2n3 = int(N[1]) * int(N[2])
+    return int(N[0]) <= 64 and n2n3 % 8 == 0 and 8 <= n2n3 <= 4096
+
+
+def assembly_terms(wl, r1):
+    """Rank-one terms of each cell's assembly in GEMM form (lattice meshes with cell_ijk):
+    4 Shakhov parts, 2 r1 for the cell itself, r1 of the neighbour across each interior
+    face and one ghost per boundary face (every boundary of these workloads is a
+    Maxwellian wall or free stream)."""
+    ijk = np.asarray(wl.cell_ijk)
+    shape = ijk.max(axis=0) + 1
+    at = -np.ones(tuple(shape), dtype=np.int64)
+    at[tuple(ijk.T)] = np.arange(ijk.shape[0])
+    K = 4.0 + 2.0 * r1
+    for a in range(3):
+        for d in (-1, 1):
+            nb = ijk.copy()
+            nb[:, a] += d
+            inside = (nb[:, a] >= 0) & (nb[:, a] < shape[a])
+            idx = np.where(inside, at[tuple(np.clip(nb, 0, shape - 1).T)], -1)
+            K += np.where(idx >= 0, r1[np.maximum(idx, 0)], 1.0)
+    return K
+
+
+def _tucker_work(wl, ranks, cls, peaks=None, peak_src=None):
     """Algorithmic work of one launch of a phase-major kernel class, from the shapes and
     the current ranks: (amount, unit, bound, peak, peak_source, definition)."""
     N1, N2, N3 = wl.N
     nc = wl.n_cell
     r = ranks.astype(np.float64)
+    if cls == "tucker_gram_mode1" and gram_on_tensor_cores(wl.N) and peaks:
+        # the tensor-core Gram reads each cell's X once (the assembly gives the row
+        # scales) and writes the n x n matrix as double-float pairs
+        nbytes = nc * (4.0 * N1 * N2 * N3 + 8.0 * N1 * N1)
+        return (nbytes, "GB/s", "hbm", peaks["hbm_gbs"],
+                f"{peak_src} MEASURED_PEAKS.json hbm_gbs",
+                "4 N1 N2 N3 bytes of X read + 8 N1^2 bytes written per cell")
     if cls == "tucker_gram_mode1":
         ops = nc * (N1 * (N1 + 1) / 2) * N2 * N3 * DF_OPS
         return (ops, "GOP/s", "alu", FP32_PEAK_GOPS,
@@ -262,13 +298,13 @@ def _tucker_work(wl, ranks, cls):
         return (flops, "GFLOP/s", "alu", 2 * FP32_PEAK_GOPS,
                 "FP32 70.0 TFLOP/s FMA-chain probe on this pool",
                 "r1 r2 r3 N3 + r1 r2 N2 N3 FP32 FMAs per cell")
-    if cls == "tucker_asm":
-        # each cell assembles itself and its 6 neighbours' tensors: sum of first-mode
-        # ranks x N1 N2 N3 FMAs (interior cells; boundary faces are cheaper)
-        flops = 2.0 * 7.0 * float(r[:, 0].sum()) * N1 * N2 * N3
+    if cls == "tucker_asm" and getattr(wl, "cell_ijk", None) is not None:
+        # one GEMM per cell of its K rank-one terms: K x N1 N2 N3 FP32 FMAs
+        flops = 2.0 * float(assembly_terms(wl, r[:, 0]).sum()) * N1 * N2 * N3
         return (flops, "GFLOP/s", "alu", 2 * FP32_PEAK_GOPS,
                 "FP32 70.0 TFLOP/s FMA-chain probe on this pool",
-                "7 x r1 x N1 N2 N3 FP32 FMAs per cell (self + 6 face terms)")
+                "K x N1 N2 N3 FP32 FMAs per cell, K = 4 + 2 r1 + per face r1 of the "
+                "neighbour or 1 ghost")
     return None
 
 
@@ -284,14 +320,15 @@ def _roofline_tucker(P, s, wl, steps, peaks=None, peak_src=None):
     times = {k: {"ms_per_launch": ms / n, "launches": n, "share": ms / total}
              for k, (ms, n) in t.items() if n}
     dom = max(times, key=lambda k: t[k][0])
-    w = _tucker_work(wl, ranks, dom)
+    w = _tucker_work(wl, ranks, dom, peaks, peak_src)
     if w is None:
         return {"bound": None, "kernel": dom, "achieved": None, "peak": None, "unit": None,
                 "frac": None, "traffic": None, "kernel_times": times}
     amount, unit, bound, peak, psrc, defin = w
     achieved = amount / (times[dom]["ms_per_launch"] / 1e3) / 1e9
+    src = "gram_tc.cu" if bound == "hbm" and dom == "tucker_gram_mode1" else None
     return {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": achieved / peak, "traffic": _traffic(dom), "peak_source": psrc,
+            "frac": achieved / peak, "traffic": _traffic(dom, src), "peak_source": psrc,
             "work_per_launch": amount, "work": defin, "kernel_times": times,
             "timing": f"CUDA events around each launch over {steps} further steps"}
 
