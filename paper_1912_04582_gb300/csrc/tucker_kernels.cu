@@ -1902,6 +1902,25 @@ __host__ __device__ inline size_t ag_smem_bytes(int Nmax, int N1, int R) {
          sizeof(AgTerm) * K4 + sizeof(unsigned) * NmP + 64;
 }
 
+// the column factor at (i2, i3) of a computed term: a Shakhov part (Proposition 1: the
+// Maxwellian's (i2, i3) factor times 1, Vp, Qp or Qp Vp) or a ghost (its (i2, i3) factors,
+// weighed by the face's inflow table when the face normal is axis 1 or 2)
+__device__ __forceinline__ float ag_column(const AgTerm &tm, Smem<float> &sm, const SlotDev *s_slot,
+                                           const float *ghostR, int Nm, int i2, int i3) {
+  if (tm.kind == 5) {
+    const SlotDev &sl = s_slot[tm.face];
+    const float *gf = ghostR + (int64_t)sl.src * 3 * Nm;
+    float x = gf[Nm + i2] * gf[2 * Nm + i3];
+    if (sl.axis == 1) x *= tabp(sm, Nm, 15 + tm.face)[i2];
+    else if (sl.axis == 2) x *= tabp(sm, Nm, 15 + tm.face)[i3];
+    return x;
+  }
+  const float fM = tabp(sm, Nm, 4)[i2] * tabp(sm, Nm, 5)[i3];
+  const float Qp = tabp(sm, Nm, 7)[i2] + tabp(sm, Nm, 8)[i3];
+  const float Vp = tabp(sm, Nm, 10)[i2] + tabp(sm, Nm, 11)[i3] - 2.5f;
+  return tm.kind == 1 ? fM : (tm.kind == 2 ? fM * Vp : (tm.kind == 3 ? fM * Qp : fM * Qp * Vp));
+}
+
 // X of one cell: thread (rg, cg) = (tid / 64, tid % 64) holds rows rg TR .. rg TR + TR - 1
 // and columns 4 cg .. 4 cg + 3 of each 256-column tile (TR = padN(N1) / 4)
 template <int TR>
@@ -1916,7 +1935,9 @@ __device__ __forceinline__ void ag_columns(const TuckerStepParams &P, const Tuck
   const float *T2all = reinterpret_cast<const float *>(B.T2all);
   const float *ghostR = P.ghostf32;
   float *Xc = reinterpret_cast<float *>(B.X) + jb * (int64_t)N1 * NP;
-  const bool vec = (NP & 3) == 0;
+  // vector staging: four columns of one i2 row per thread (16-row tiles keep the scalar
+  // staging, for registers)
+  const bool vec = (NP & 3) == 0, vec4 = TR <= 12 && (N3 & 3) == 0;
   float rm[TR];
 #pragma unroll
   for (int r = 0; r < TR; ++r) rm[r] = 0.f;
@@ -1928,7 +1949,62 @@ __device__ __forceinline__ void ag_columns(const TuckerStepParams &P, const Tuck
       for (int q = 0; q < 4; ++q) acc[r][q] = 0.f;
     for (int k0 = 0; k0 < K; k0 += kAgKC) {
       const int kn = min(kAgKC, K - k0), kn4 = (kn + 3) & ~3;
-      {  // stage B[c0 + tid][k0 .. k0 + kn4): this thread's column, SH terms at a time
+      if (vec4) {
+        // N3 a multiple of four: thread (ts, cq) stages columns c0 + 4 cq .. + 3 (one i2
+        // row) of terms 8 ts .. 8 ts + 7 of the chunk: one float4 gather, weighing and
+        // store per term, the eight gathers issued before any is used
+        const int ts = tid >> 6, cq = tid & 63;
+        const int p = c0 + 4 * cq;
+        const bool pin = p < NP;  // all four columns or none (NP a multiple of four)
+        const int pc = pin ? p : 0, i2 = pc / N3, i3 = pc - i2 * N3;
+        const int pm2 = (N2 - 1 - i2) * N3 + i3, pm3 = i2 * N3 + (N3 - 4 - i3);
+        constexpr int VG = TR >= 12 ? 4 : 8;  // gathers in flight (registers: the tile is live)
+#pragma unroll
+        for (int e0 = 0; e0 < 8; e0 += VG) {
+          if (8 * ts + e0 >= kn4) break;  // warp-uniform
+          float4 g[VG];
+#pragma unroll
+          for (int e = 0; e < VG; ++e) {
+            const int kk = 8 * ts + e0 + e;
+            g[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (kk < kn && pin && terms[k0 + kk].kind == 0) {
+              const int refl = terms[k0 + kk].refl;
+              g[e] = __ldg(reinterpret_cast<const float4 *>(
+                  T2all + terms[k0 + kk].t2 + (refl == 1 ? pm2 : (refl == 2 ? pm3 : pc))));
+            }
+          }
+#pragma unroll
+          for (int e = 0; e < VG; ++e) {
+            const int kk = 8 * ts + e0 + e;
+            if (kk >= kn4) break;  // warp-uniform
+            float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (kk < kn && pin) {
+              const AgTerm tm = terms[k0 + kk];
+              if (tm.kind == 0) {
+                x = tm.refl == 2 ? make_float4(g[e].w, g[e].z, g[e].y, g[e].x) : g[e];
+                if (tm.wsel == 1) {
+                  const float w2 = colW2[i2];
+                  const float4 w3 = *reinterpret_cast<const float4 *>(colW3 + i3);
+                  x = make_float4(x.x * (w2 + w3.x), x.y * (w2 + w3.y), x.z * (w2 + w3.z),
+                                  x.w * (w2 + w3.w));
+                } else if (tm.wsel == 2) {
+                  const float w = tabp(sm, Nm, 15 + tm.face)[i2];
+                  x = make_float4(x.x * w, x.y * w, x.z * w, x.w * w);
+                } else if (tm.wsel == 3) {
+                  const float4 w = *reinterpret_cast<const float4 *>(tabp(sm, Nm, 15 + tm.face) + i3);
+                  x = make_float4(x.x * w.x, x.y * w.y, x.z * w.z, x.w * w.w);
+                }
+              } else {
+                x = make_float4(ag_column(tm, sm, s_slot, ghostR, Nm, i2, i3),
+                                ag_column(tm, sm, s_slot, ghostR, Nm, i2, i3 + 1),
+                                ag_column(tm, sm, s_slot, ghostR, Nm, i2, i3 + 2),
+                                ag_column(tm, sm, s_slot, ghostR, Nm, i2, i3 + 3));
+              }
+            }
+            *reinterpret_cast<float4 *>(B_s + kk * kAgCols + 4 * cq) = x;
+          }
+        }
+      } else {  // stage B[c0 + tid][k0 .. k0 + kn4): this thread's column, SH terms at a time
         constexpr int SH = TR > 12 ? 8 : 16;  // gathers in flight (registers: the tile is live)
         const int p = c0 + tid;
         const bool pin = p < NP;
@@ -1957,17 +2033,8 @@ __device__ __forceinline__ void ag_columns(const TuckerStepParams &P, const Tuck
                 if (tm.wsel == 1) x *= colW2[i2] + colW3[i3];
                 else if (tm.wsel == 2) x *= tabp(sm, Nm, 15 + tm.face)[i2];
                 else if (tm.wsel == 3) x *= tabp(sm, Nm, 15 + tm.face)[i3];
-              } else if (tm.kind == 5) {
-                const SlotDev &sl = s_slot[tm.face];
-                const float *gf = ghostR + (int64_t)sl.src * 3 * Nm;
-                x = gf[Nm + i2] * gf[2 * Nm + i3];
-                if (sl.axis == 1) x *= tabp(sm, Nm, 15 + tm.face)[i2];
-                else if (sl.axis == 2) x *= tabp(sm, Nm, 15 + tm.face)[i3];
               } else {
-                const float fM = tabp(sm, Nm, 4)[i2] * tabp(sm, Nm, 5)[i3];
-                const float Qp = tabp(sm, Nm, 7)[i2] + tabp(sm, Nm, 8)[i3];
-                const float Vp = tabp(sm, Nm, 10)[i2] + tabp(sm, Nm, 11)[i3] - 2.5f;
-                x = tm.kind == 1 ? fM : (tm.kind == 2 ? fM * Vp : (tm.kind == 3 ? fM * Qp : fM * Qp * Vp));
+                x = ag_column(tm, sm, s_slot, ghostR, Nm, i2, i3);
               }
             }
             B_s[(h + e) * kAgCols + tid] = x;
