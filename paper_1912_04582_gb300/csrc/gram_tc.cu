@@ -295,7 +295,28 @@ struct TcArgs {
   int *flag;
   const float *rowmax;  // cell j: rowmax + j * rstride, each row's largest |x| (or null:
   int64_t rstride;      // then a first pass over X finds them)
+  long long *phase;     // optional per-role cycle counters, slots 16-26 (null: off)
   GramTcPlan plan;
+};
+
+// cycles of one role's lane, accumulated into phase[slot] when phase is set; no effect on
+// the computation
+struct RoleClock {
+  long long *acc;
+  long long t;
+  __device__ explicit RoleClock(long long *a) {
+    acc = a;
+    t = a ? (long long)clock64() : 0;
+  }
+  __device__ void mark(int slot) {
+    if (!acc) return;
+    const long long now = (long long)clock64();
+    atomicAdd(reinterpret_cast<unsigned long long *>(acc + slot), (unsigned long long)(now - t));
+    t = now;
+  }
+  __device__ void reset() {
+    if (acc) t = (long long)clock64();
+  }
 };
 
 // bounded wait on one mbarrier phase that also gives up once *abort is set
@@ -411,6 +432,9 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1)
   fence_after();
   const uint32_t tmem = s_tmem;
   const int nchunk = (K + kTcKC - 1) / kTcKC;
+  // role timing: TMA lane (warp 0), MMA lane (warp 1), one slicing lane (warp 2)
+  RoleClock rc((A.phase && lane == 0 && warp <= 2) ? A.phase : nullptr);
+  RoleClock rtot((A.phase && tid == 0) ? A.phase : nullptr);
 
   if (warp == 0) {
     if (lane == 0) {  // TMA producer
@@ -421,11 +445,13 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1)
         for (int pass = A.rowmax ? 1 : 0; pass < 2 && ok; ++pass)
           for (int ch = 0; ch < nchunk; ++ch, ++r) {
             const int slot = (int)(r % kTcRawStages);
+            rc.reset();
             if (r >= (uint32_t)kTcRawStages &&
                 !bar_wait(smem_addr(&s_empty[slot]), ((r / kTcRawStages) - 1) & 1, &s_abort)) {
               ok = false;
               break;
             }
+            rc.mark(16);
             tma_load(smem_addr(raw + (size_t)slot * kTcRawBytes), &xmap, ch * kTcKC,
                      (int)(cell * n), smem_addr(&s_full[slot]), bytes);
           }
@@ -441,16 +467,21 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1)
       bool ok = true;
       for (int64_t cell = blockIdx.x; cell < A.ncell && ok; cell += gridDim.x, ++cidx) {
         // the previous cell's accumulators must have been read back
+        rc.reset();
         if (cidx > 0 && !bar_wait(smem_addr(&s_acce), (cidx - 1) & 1, &s_abort)) {
           ok = false;
           break;
         }
+        rc.mark(19);
+        if (A.phase) atomicAdd(reinterpret_cast<unsigned long long *>(A.phase + 25), 1ull);
         for (int ch = 0; ch < nchunk; ++ch, ++t) {
           const uint32_t st = t % NS;
+          rc.reset();
           if (!bar_wait(smem_addr(&s_ready[st]), (t / NS) & 1, &s_abort)) {
             ok = false;
             break;
           }
+          rc.mark(17);
           fence_after();
           const uint32_t b0 = smem_addr(stages + (size_t)st * stage_bytes);
           for (int g = 0; g < P.ngroups; ++g) {
@@ -464,6 +495,7 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1)
           }
           mma_commit(smem_addr(&s_freed[st]));
           if (ch + 1 == nchunk) mma_commit(smem_addr(&s_accf));
+          rc.mark(18);
         }
       }
       if (!ok) s_abort = 1;
@@ -473,6 +505,7 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1)
     __syncwarp();
   } else {
     const int ct = tid - 64;
+    RoleClock &rcl = rc;
     const int items = n * (kTcKC / 4);  // (row, 4-column piece) per chunk
     constexpr int kItems = (64 * (kTcKC / 4) + kTcConsumers - 1) / kTcConsumers;
     uint32_t rc = 0, t = 0, cidx = 0;
@@ -523,9 +556,12 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1)
       for (int ch = 0; ch < nchunk; ++ch, ++rc, ++t) {
         const int slot = (int)(rc % kTcRawStages);
         const uint32_t st = t % NS;
+        if (warp == 2) rcl.mark(22);
         bool ok2 = bar_wait(smem_addr(&s_full[slot]), (rc / kTcRawStages) & 1, &s_abort);
+        if (warp == 2) rcl.mark(20);
         // the MMAs that last read this stage must be complete
         if (ok2 && t >= NS) ok2 = bar_wait(smem_addr(&s_freed[st]), ((t / NS) - 1) & 1, &s_abort);
+        if (warp == 2) rcl.mark(21);
         ok2 = __all_sync(0xffffffffu, ok2);  // the warp leaves together (it syncs below)
         if (!ok2) {
           s_abort = 1;
@@ -566,7 +602,9 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1)
         }
       }
       // the cell's accumulators complete
+      if (warp == 2) rcl.mark(22);
       if (ok) ok = bar_wait(smem_addr(&s_accf), cidx & 1, &s_abort);
+      if (warp == 2) rcl.mark(24);
       if (!consumers_and(ok)) {
         fail = true;
         break;
@@ -662,12 +700,14 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1)
       }
       if (ct == 0 && A.disc) A.disc[cell] = 0.0;
       consumers_sync();  // the level accumulators are free for the next cell
+      if (warp == 2) rcl.mark(23);
     }
     if (fail && ct == 0) {
       s_abort = 1;
       atomicOr(A.flag, 2);
     }
   }
+  rtot.mark(26);
   fence_before();
   __syncthreads();
   if (warp == 0)
@@ -735,7 +775,7 @@ bool gram_tc_supported(int n, int K) {
 
 int launch_gram_tc(const float *X, int64_t xstride, int64_t ncell, int n, int K, float2 *C,
                    double *Cd, int64_t cstride, double *disc, int *flag, cudaStream_t s,
-                   const float *rowmax, int64_t rstride) {
+                   const float *rowmax, int64_t rstride, long long *phase) {
   if (ncell <= 0) return 0;
   // the cells' rows must form one row-major [ncell * n][K] array for the tensor map
   if (!gram_tc_supported(n, K) || xstride != (int64_t)n * K ||
@@ -751,6 +791,7 @@ int launch_gram_tc(const float *X, int64_t xstride, int64_t ncell, int n, int K,
   a.flag = flag;
   a.rowmax = rowmax;
   a.rstride = rstride;
+  a.phase = phase;
   a.plan = gram_tc_plan(n);
   const size_t smem = launch_smem(a.plan);
   if (smem > g_opted) {

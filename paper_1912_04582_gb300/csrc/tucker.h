@@ -29,7 +29,7 @@ struct TuckerStepParams {
   const double *xi[3];
   const double *finit;   // mode 1: [nc][N^3] tensors to compress
   double *err;           // [nc] relative truncation error of the last rounding (may be null)
-  long long *phase;      // [16] optional per-phase cycle counters (null: off)
+  long long *phase;      // [32] optional per-phase cycle counters (null: off)
   const double *cellpar; // [nc][kCellPar] per-cell parameters of the assembly (null: the
                          // assembly forms them from the sums)
   int *flag;
@@ -143,7 +143,8 @@ int tucker_asm_gemm_prepare(int Nmax, int N1, int R);
 // the producer of X; without it the kernel reads X twice (row scales, then slicing)
 int launch_gram_tc(const float *X, int64_t xstride, int64_t ncell, int n, int K, float2 *C,
                    double *Cd, int64_t cstride, double *disc, int *flag, cudaStream_t s,
-                   const float *rowmax = nullptr, int64_t rstride = 0);
+                   const float *rowmax = nullptr, int64_t rstride = 0,
+                   long long *phase = nullptr);
 
 size_t tucker_scratch_elems(int N1, int N2, int N3, int R);
 size_t tucker_smem_bytes(int Nmax, int R, bool fp64);

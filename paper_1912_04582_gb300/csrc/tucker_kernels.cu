@@ -2878,7 +2878,8 @@ void split_chain(const TuckerStepParams &p, const TuckerSplitBufs &b, const Spli
         done = launch_gram_tc(reinterpret_cast<const float *>(b.X) + b.joff * NN, NN, b.cn, p.N1,
                               p.N2 * p.N3, reinterpret_cast<float2 *>(b.C + b.joff * NC), nullptr,
                               NC, b.disc + b.joff, p.flag, s,
-                              b.rowmax ? b.rowmax + b.joff * p.Nmax : nullptr, p.Nmax) == 0;
+                              b.rowmax ? b.rowmax + b.joff * p.Nmax : nullptr, p.Nmax,
+                              p.phase) == 0;
       }
     }
     if (done) {

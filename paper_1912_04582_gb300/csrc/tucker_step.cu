@@ -261,9 +261,9 @@ int tucker_alloc(dvm_ctx *C) {
     return DVM_ERR_UNSUPPORTED;
   }
   if (std::getenv("DVM_TUCKER_PHASES")) {
-    rc = ctx_malloc(C, reinterpret_cast<void **>(&S->phase), sizeof(long long) * 16);
+    rc = ctx_malloc(C, reinterpret_cast<void **>(&S->phase), sizeof(long long) * 32);
     if (rc != DVM_OK) return rc;
-    DVM_CUDA_TRY(cudaMemset(S->phase, 0, sizeof(long long) * 16));
+    DVM_CUDA_TRY(cudaMemset(S->phase, 0, sizeof(long long) * 32));
   }
   return DVM_OK;
 }
@@ -292,15 +292,17 @@ void tucker_free(dvm_ctx *C) {
   if (S->ghostf32) cudaFree(S->ghostf32);
   if (S->err) cudaFree(S->err);
   if (S->phase) {
-    long long h[16] = {0};
+    long long h[32] = {0};
     if (cudaMemcpy(h, S->phase, sizeof h, cudaMemcpyDeviceToHost) == cudaSuccess) {
-      // fused kernel / eigen-solve kernel
-      static const char *names[16] = {"prologue",    "reseeds",    "retries",    "assemble|asm_terms",
-                                      "energy|setup", "gram|asm_eq",      "eig_init",   "rank",
-                                      "project|retry", "eig_cq32", "eig_orth32", "eig_cq64",
-                                      "eig_orth64",  "contract",   "rayleigh",   "sort"};
-      std::fprintf(stderr, "tucker phases (SM cycles summed over CTAs; reseeds, retries: counts):");
-      for (int i = 0; i < 16; ++i) std::fprintf(stderr, " %s=%lld", names[i], h[i]);
+      // fused kernel / eigen-solve kernel; 16-26: the tensor-core Gram kernel's roles
+      static const char *names[32] = {
+          "prologue", "reseeds", "retries", "assemble|asm_terms", "energy|setup", "gram|asm_eq",
+          "eig_init", "rank", "project|retry", "eig_cq32", "eig_orth32", "eig_cq64", "eig_orth64",
+          "contract", "rayleigh", "sort", "gtc_tma_wait", "gtc_mma_wait_ready", "gtc_mma_issue",
+          "gtc_mma_wait_readback", "gtc_slice_wait_load", "gtc_slice_wait_freed", "gtc_slice",
+          "gtc_readback", "gtc_wait_accum", "gtc_cells", "gtc_total", "", "", "", "", ""};
+      std::fprintf(stderr, "tucker phases (SM cycles summed over CTAs; reseeds, retries, cells: counts):");
+      for (int i = 0; i < 27; ++i) std::fprintf(stderr, " %s=%lld", names[i], h[i]);
       std::fprintf(stderr, "\n");
     }
     cudaFree(S->phase);
