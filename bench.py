@@ -54,7 +54,9 @@ def _args():
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--rank-cap", type=int, default=None)
     ap.add_argument("--tol", type=float, default=None)
-    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "cavity_small", "sod"])
+    ap.add_argument("--workload", default="c3",
+                    choices=["c3", "c3_small", "c2", "cavity_small", "sod"],
+                    help="c3_small: the C3 velocity grid on 12^3 cells (kernel profiles)")
     ap.add_argument("--variant", default="auto", choices=["auto", "fused", "phased"],
                     help="Tucker launch variant (auto: the autotuner times both)")
     ap.add_argument("--advance", type=int, default=200,
@@ -72,6 +74,8 @@ def make_workload(name):
     import workloads as W
     if name == "c3":
         return W.cavity(nside=32, N=48)
+    if name == "c3_small":
+        return W.cavity(nside=12, N=48)
     if name in ("c2", "cavity"):
         return W.cavity()
     if name == "cavity_small":
