@@ -344,14 +344,39 @@ __device__ double gram_trace(Smem<Real> &sm, int n) {
 }
 
 
+// Double-float (hi, lo) += (h2, l2), renormalised (fast two-sum of the high parts)
+__device__ __forceinline__ void df_add_into(float &hi, float &lo, float h2, float l2) {
+  const float s = __fadd_rn(hi, h2);
+  const float bb = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(h2, bb));
+  const float t = __fadd_rn(__fadd_rn(lo, l2), err);
+  hi = __fadd_rn(s, t);
+  lo = __fsub_rn(t, __fsub_rn(hi, s));
+}
+
+// Gram matrix of the mode-m unfolding by TS x TS output blocks on or above the diagonal.
+// The nb (nb + 1) / 2 blocks (nb = ceil(n / TS)) are numbered row by row; with fewer
+// blocks than threads the columns of every staged chunk are split into S segments, thread
+// t owning block t mod nblk and segment t / nblk; the segments' partial sums are then added
+// into the result in segment order (a fixed order: the same sums in either launch variant).
+// Each chunk's loop stops at the last real column.
 template <typename Real, int TS>
 __device__ void gram_tiled(const Real *T, const int D[3], int m, Smem<Real> &sm) {
   const int n = D[m];
   const int cols = (D[0] * D[1] * D[2]) / n;
-  // thread (ta, tb) of a 16 x 16 grid owns the TS x TS output block at
-  // rows ta*TS.., columns tb*TS..; only blocks on or above the diagonal work
-  const int ta = threadIdx.x >> 4, tb = threadIdx.x & 15;
-  const bool active = (ta <= tb) && (ta * TS < n) && (tb * TS < n);
+  const int nb = (n + TS - 1) / TS, nblk = nb * (nb + 1) / 2;
+  const int S = nblk >= (int)blockDim.x ? 1 : min(4, (int)blockDim.x / nblk);
+  const int seg = threadIdx.x / nblk;
+  int ta = 0, tb = 0;
+  {
+    int b = threadIdx.x - seg * nblk;
+    while (ta < nb && b >= nb - ta) {
+      b -= nb - ta;
+      ++ta;
+    }
+    tb = ta + b;
+  }
+  const bool active = seg < S && ta < nb;
   Real hi[TS][TS], lo[TS][TS];
 #pragma unroll
   for (int i = 0; i < TS; ++i)
@@ -377,8 +402,10 @@ __device__ void gram_tiled(const Real *T, const int D[3], int m, Smem<Real> &sm)
     }
     __syncthreads();
     if (active) {
+      const int len = min(kKC, cols - j0);
+      const int k0 = seg * len / S, k1 = (seg + 1) * len / S;
 #pragma unroll 4
-      for (int kk = 0; kk < kKC; ++kk) {
+      for (int kk = k0; kk < k1; ++kk) {
         Real xa[TS], xb[TS];
 #pragma unroll
         for (int i = 0; i < TS; ++i) {
@@ -410,19 +437,31 @@ __device__ void gram_tiled(const Real *T, const int D[3], int m, Smem<Real> &sm)
     }
     __syncthreads();
   }
-  if (active) {
+  for (int sg = 0; sg < S; ++sg) {  // the segments' partial sums, in order
+    if (active && seg == sg) {
 #pragma unroll
-    for (int i = 0; i < TS; ++i)
+      for (int i = 0; i < TS; ++i)
 #pragma unroll
-      for (int j = 0; j < TS; ++j) {
-        const int a = ta * TS + i, b = tb * TS + j;
-        if (a < n && b < n) {
-          gram_store<Real>(sm.C, a * n + b, hi[i][j], lo[i][j]);
-          gram_store<Real>(sm.C, b * n + a, hi[i][j], lo[i][j]);
+        for (int j = 0; j < TS; ++j) {
+          const int a = ta * TS + i, b = tb * TS + j;
+          // a diagonal block holds entry (a, b) twice, as (i, j) and (j, i): take it once
+          if (a < n && b < n && (ta < tb || i <= j)) {
+            Real h = hi[i][j], l = lo[i][j];
+            if (sg > 0) {
+              if constexpr (sizeof(Real) == 8) {
+                h += sm.C[a * n + b];
+              } else {
+                const float2 c = reinterpret_cast<const float2 *>(sm.C)[a * n + b];
+                df_add_into(h, l, c.x, c.y);
+              }
+            }
+            gram_store<Real>(sm.C, a * n + b, h, l);
+            gram_store<Real>(sm.C, b * n + a, h, l);
+          }
         }
-      }
+    }
+    __syncthreads();
   }
-  __syncthreads();
 }
 
 // Double-float (hi, lo) sum of two pairs (Knuth's two-sum of the high parts,
