@@ -158,6 +158,13 @@ __device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
 // slice product with the fewest tensor-memory columns (the MMA work is proportional to
 // them), found by exhaustive search; each product is owned by the first group that
 // forms it.
+// words of row a of a level accumulator (the packed upper triangle: n - a entries), padded
+// to 2 mod 32 when pad is set
+__host__ __device__ inline int level_row_words(int n, int a, int pad) {
+  const int len = n - a;
+  return pad ? len + (((2 - len) % 32) + 32) % 32 : len;
+}
+
 static GramTcPlan make_plan(int n) {
   GramTcPlan p{};
   if (n < 1 || n > 64) return p;
@@ -253,6 +260,19 @@ static GramTcPlan make_plan(int n) {
   p.nstages = fixed + (size_t)kTcMaxStages * p.buf_rows * kTcRowBytes <= 227 * 1024
                   ? kTcMaxStages
                   : kTcMaxStages - 1;
+  // level accumulators: the packed upper triangle, row a at rowoff[a].  Where it fits
+  // beside the same stages, every row is padded to a length of 2 mod 32 words, so that the
+  // read-back's lanes (consecutive rows a, one column b) hit consecutive banks on both
+  // sides of the diagonal (rowoff[a] - a then steps by 1 mod 32)
+  p.ltri = n * (n + 1) / 2;
+  p.lpad = 0;
+  int padded = 0;
+  for (int a = 0; a < n; ++a) padded += level_row_words(n, a, 1);
+  if (fixed - sizeof(int) * kTcLevels * (size_t)p.ltri + sizeof(int) * kTcLevels * (size_t)padded +
+          (size_t)p.nstages * p.buf_rows * kTcRowBytes <= 227 * 1024) {
+    p.lpad = 1;
+    p.ltri = padded;
+  }
   return p;
 }
 
@@ -269,13 +289,13 @@ GramTcPlan gram_tc_plan(int n) {
   return plans[n];
 }
 
-// level accumulators: int32 [kTcLevels][n (n + 1) / 2]
-static size_t level_bytes(int n) { return sizeof(int) * kTcLevels * (size_t)(n * (n + 1) / 2); }
+// level accumulators: int32 [kTcLevels][ltri]
+static size_t level_bytes(const GramTcPlan &p) { return sizeof(int) * kTcLevels * (size_t)p.ltri; }
 
 static size_t smem_for(const GramTcPlan &p, int nstages) {
   const size_t stages = (size_t)nstages * p.buf_rows * kTcRowBytes;
   const size_t raw = (size_t)kTcRawStages * kTcRawBytes;
-  return 1024 + stages + raw + level_bytes(p.n) + 64 * (2 * sizeof(int) + sizeof(float)) + 64;
+  return 1024 + stages + raw + level_bytes(p) + 64 * (2 * sizeof(int) + sizeof(float)) + 64;
 }
 
 size_t gram_tc_smem_bytes(const GramTcPlan &p) { return smem_for(p, p.nstages); }
@@ -308,13 +328,13 @@ struct RoleClock {
     acc = a;
     t = a ? (long long)clock64() : 0;
   }
-  __device__ void mark(int slot) {
+  __device__ __forceinline__ void mark(int slot) {
     if (!acc) return;
     const long long now = (long long)clock64();
     atomicAdd(reinterpret_cast<unsigned long long *>(acc + slot), (unsigned long long)(now - t));
     t = now;
   }
-  __device__ void reset() {
+  __device__ __forceinline__ void reset() {
     if (acc) t = (long long)clock64();
   }
 };
@@ -376,6 +396,7 @@ __device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap *map, i
 // accumulators have been read.  Warps 2-13: the slicing warps: row scales, slicing of
 // each chunk into a free stage, and the read-back and combination of the accumulators.
 // No CTA-wide barrier is taken per chunk: every hand-off is an mbarrier.
+template <bool kTimed>
 __global__ void __launch_bounds__(kTcThreadsAll, 1)
     gram_tc_kernel(const __grid_constant__ CUtensorMap xmap, TcArgs A) {
   extern __shared__ unsigned char tc_raw[];
@@ -386,12 +407,12 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1)
       (reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~uintptr_t(1023));
   const size_t stage_bytes = (size_t)P.buf_rows * kTcRowBytes;  // a multiple of 1024
   const uint32_t NS = (uint32_t)P.nstages;
-  const int ntri = n * (n + 1) / 2;
+  const int ntri = n * (n + 1) / 2, ltri = P.ltri;
   unsigned char *stages = base;
   unsigned char *raw = stages + NS * stage_bytes;
   // exact integer sums of the slice products per level k + l, upper triangle
   int *Lacc = reinterpret_cast<int *>(raw + kTcRawStages * kTcRawBytes);
-  int *rexp = Lacc + kTcLevels * ntri;
+  int *rexp = Lacc + kTcLevels * ltri;
   float *rinv = reinterpret_cast<float *>(rexp + 64);
   int *rowoff = reinterpret_cast<int *>(rinv + 64);  // upper-triangle offset of each row
   __shared__ __align__(8) unsigned long long s_full[kTcRawStages], s_empty[kTcRawStages];
@@ -419,7 +440,13 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_abort = 0;
   }
-  for (int a = tid; a < 64; a += blockDim.x) rowoff[a] = a * n - a * (a - 1) / 2;
+  if (tid == 0) {  // row starts of the level accumulators (padded rows where P.lpad)
+    int o = 0;
+    for (int a = 0; a < 64; ++a) {
+      rowoff[a] = o;
+      if (a < n) o += level_row_words(n, a, P.lpad);
+    }
+  }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_addr(&s_tmem)),
@@ -433,8 +460,8 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1)
   const uint32_t tmem = s_tmem;
   const int nchunk = (K + kTcKC - 1) / kTcKC;
   // role timing: TMA lane (warp 0), MMA lane (warp 1), one slicing lane (warp 2)
-  RoleClock rc((A.phase && lane == 0 && warp <= 2) ? A.phase : nullptr);
-  RoleClock rtot((A.phase && tid == 0) ? A.phase : nullptr);
+  RoleClock rc((kTimed && lane == 0 && warp <= 2) ? A.phase : nullptr);
+  RoleClock rtot((kTimed && tid == 0) ? A.phase : nullptr);
 
   if (warp == 0) {
     if (lane == 0) {  // TMA producer
@@ -473,7 +500,7 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1)
           break;
         }
         rc.mark(19);
-        if (A.phase) atomicAdd(reinterpret_cast<unsigned long long *>(A.phase + 25), 1ull);
+        if (kTimed) atomicAdd(reinterpret_cast<unsigned long long *>(A.phase + 25), 1ull);
         for (int ch = 0; ch < nchunk; ++ch, ++t) {
           const uint32_t st = t % NS;
           rc.reset();
@@ -546,7 +573,7 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1)
           rinv[it >> 4] = ldexpf(1.0f, 6 - e);
         }
       }
-      for (int i = ct; i < kTcLevels * ntri; i += kTcConsumers) Lacc[i] = 0;
+      for (int i = ct; i < kTcLevels * ltri; i += kTcConsumers) Lacc[i] = 0;
       if (!consumers_and(ok)) {
         fail = true;
         break;
@@ -657,7 +684,7 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1)
                 const int tri = i <= j ? rowoff[i] + (j - i) : rowoff[j] + (i - j);
                 const int d = __float2int_rn(__uint_as_float(r[q][u]) * scale);
                 // a diagonal entry of a k != l product is its own transpose: counted twice
-                atomicAdd(&Lacc[(k + l) * ntri + tri], (k != l && i == j) ? 2 * d : d);
+                atomicAdd(&Lacc[(k + l) * ltri + tri], (k != l && i == j) ? 2 * d : d);
               }
             }
           }
@@ -672,14 +699,17 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1)
       // so |T| < 2^60), C_ab = 2^(e_a + e_b - 40) (T + 2^-21 U); written once rounded, as a
       // double-float pair or a double
       for (int e = ct; e < ntri; e += kTcConsumers) {
-        int a = 0;
-        while (a + 1 < n && rowoff[a + 1] <= e) ++a;
-        const int b = a + (e - rowoff[a]);
+        int a = 0, ea = 0;  // entry e of the upper triangle, row by row: (a, b)
+        while (a + 1 < n && ea + (n - a) <= e) {
+          ea += n - a;
+          ++a;
+        }
+        const int b = a + (e - ea), w = rowoff[a] + (b - a);
         long long T = 0, U = 0;
 #pragma unroll
-        for (int m = 0; m <= 4; ++m) T = T * 128 + Lacc[m * ntri + e];
+        for (int m = 0; m <= 4; ++m) T = T * 128 + Lacc[m * ltri + w];
 #pragma unroll
-        for (int m = 5; m < kTcLevels; ++m) U = U * 128 + Lacc[m * ntri + e];
+        for (int m = 5; m < kTcLevels; ++m) U = U * 128 + Lacc[m * ltri + w];
         const int sc = rexp[a] + rexp[b] - 40;
         if (A.Cd) {
           const double v = ldexp((double)T, sc) + ldexp((double)U, sc - 21);
@@ -759,7 +789,9 @@ int gram_tc_prepare(int n) {
   std::lock_guard<std::mutex> lk(mu);
   const size_t smem = launch_smem(p);
   if (smem <= g_opted) return 0;
-  if (cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncSetAttribute(gram_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess ||
+      cudaFuncSetAttribute(gram_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return -1;
@@ -816,7 +848,10 @@ int launch_gram_tc(const float *X, int64_t xstride, int64_t ncell, int n, int K,
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = (int)(ncell < sms ? ncell : sms);
-  gram_tc_kernel<<<grid, kTcThreadsAll, smem, s>>>(map, a);
+  if (phase)
+    gram_tc_kernel<true><<<grid, kTcThreadsAll, smem, s>>>(map, a);
+  else
+    gram_tc_kernel<false><<<grid, kTcThreadsAll, smem, s>>>(map, a);
   return 0;
 }
 

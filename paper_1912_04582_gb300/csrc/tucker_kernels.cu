@@ -810,11 +810,20 @@ __device__ void mat_cq(const T *__restrict__ C, const T *Q, T *W, int n, int k) 
 // W = C_hi Q in FP32 (the mixed path's orthogonal iterations), C_hi the leading
 // float of every double-float Gram entry, read by columns like mat_cq
 __device__ void mat_cq_hi(const float2 *__restrict__ C, const float *Q, float *W, int n, int k) {
-  for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) {
-    const int i = idx / k, j = idx - i * k;
-    float s = 0.f;
-    for (int t = 0; t < n; ++t) s = fmaf(C[t * n + i].x, Q[t * k + j], s);
-    W[idx] = s;
+  // four columns of a row at a time (independent chains; each entry's sum in t order)
+  const int ng = (k + 3) >> 2;
+  for (int idx = threadIdx.x; idx < n * ng; idx += blockDim.x) {
+    const int i = idx / ng, j0 = 4 * (idx - i * ng), nq = min(4, k - j0);
+    float s[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int t = 0; t < n; ++t) {
+      const float c = C[t * n + i].x;
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (q < nq) s[q] = fmaf(c, Q[t * k + j0 + q], s[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (q < nq) W[i * k + j0 + q] = s[q];
   }
   __syncthreads();
 }
@@ -823,22 +832,40 @@ __device__ void mat_cq_hi(const float2 *__restrict__ C, const float *Q, float *W
 // leading products (fma) and a two-sum accumulation: about 2^-48 relative.  c_t
 // is read at c[t * cstride] (a column of the symmetric Gram matrix, so that the
 // lanes of a warp, one row each, read consecutive entries).
+// one term of it: (hi, lo) += (ct.x + ct.y) (h + l)
+__device__ __forceinline__ void df_mac(float2 ct, float h, float l, float &hi, float &lo) {
+  const float p = __fmul_rn(ct.x, h);
+  const float pe = __fmaf_rn(ct.x, h, -p);
+  const float s = __fadd_rn(hi, p);
+  const float bb = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(err, __fmaf_rn(ct.x, l, __fmaf_rn(ct.y, h, pe))));
+}
+
 __device__ __forceinline__ double df_dot(const float2 *c, int cstride, const float *vh,
                                          const float *vl, int stride, int n) {
   float hi = 0.f, lo = 0.f;
-  for (int t = 0; t < n; ++t) {
-    const float2 ct = c[t * cstride];
-    const float h = vh[t * stride];
-    const float l = vl ? vl[t * stride] : 0.f;
-    const float p = __fmul_rn(ct.x, h);
-    const float pe = __fmaf_rn(ct.x, h, -p);
-    const float s = __fadd_rn(hi, p);
-    const float bb = __fsub_rn(s, hi);
-    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-    hi = s;
-    lo = __fadd_rn(lo, __fadd_rn(err, __fmaf_rn(ct.x, l, __fmaf_rn(ct.y, h, pe))));
-  }
+  for (int t = 0; t < n; ++t)
+    df_mac(c[t * cstride], vh[t * stride], vl ? vl[t * stride] : 0.f, hi, lo);
   return (double)hi + (double)lo;
+}
+
+// df_dot of row i of the symmetric double-float matrix C (n x n, read by columns) with up
+// to four columns j0 .. j0 + 3 of V (n x k, hi parts vh, lo parts vl or none) at once: the
+// same operations per product as df_dot, four independent chains
+__device__ __forceinline__ void df_dot4(const float2 *C, int n, int i, const float *vh,
+                                        const float *vl, int k, int j0, double (&out)[4]) {
+  float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+  const int nq = min(4, k - j0);
+  for (int t = 0; t < n; ++t) {
+    const float2 ct = C[t * n + i];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (q < nq) df_mac(ct, vh[t * k + j0 + q], vl ? vl[t * k + j0 + q] : 0.f, hi[q], lo[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) out[q] = (double)hi[q] + (double)lo[q];
 }
 
 constexpr int kOrthMax = 24;  // largest number of basis columns
@@ -1076,9 +1103,14 @@ __device__ __noinline__ int leading_eigs(Smem<Real> &sm, int n, int k, const WT 
     float *V = reinterpret_cast<float *>(sm.Vr);
     for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) V[idx] = sm.Q32[idx];
     __syncthreads();
-    for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) {
-      const int i = idx / k, j = idx - i * k;
-      sm.Q[idx] = df_dot(Cdf + i, n, V + j, nullptr, k, n);
+    const int ng = (k + 3) >> 2;  // groups of four columns
+    for (int idx = threadIdx.x; idx < n * ng; idx += blockDim.x) {
+      const int i = idx / ng, j0 = 4 * (idx - i * ng);
+      double w[4];
+      df_dot4(Cdf, n, i, V, nullptr, k, j0, w);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (j0 + q < k) sm.Q[i * k + j0 + q] = w[q];
     }
     __syncthreads();
     pc.mark(11);
@@ -1114,12 +1146,22 @@ __device__ __noinline__ int leading_eigs(Smem<Real> &sm, int n, int k, const WT 
       ql[idx] = (float)(q - (double)h);
     }
     __syncthreads();
-    for (int j = warp; j < k; j += nwarp) {
-      double d = 0.0;
-      for (int i = lane; i < n; i += 32)
-        d = fma(sm.Q[i * k + j], df_dot(Cdf + i, n, qh + j, ql + j, k, n), d);
-      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-      if (lane == 0) sm.cs[j] = sm.cs[j] == 0.0 ? -1.0 : d;  // zeroed columns sort last
+    // four columns at a time (each lane's rows in order, then the shuffle tree: the same
+    // sums as one column at a time)
+    for (int j0 = 4 * warp; j0 < k; j0 += 4 * nwarp) {
+      double d[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int i = lane; i < n; i += 32) {
+        double w[4];
+        df_dot4(Cdf, n, i, qh, ql, k, j0, w);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (j0 + q < k) d[q] = fma(sm.Q[i * k + j0 + q], w[q], d[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        for (int o = 16; o > 0; o >>= 1) d[q] += __shfl_xor_sync(0xffffffffu, d[q], o);
+        if (lane == 0 && j0 + q < k) sm.cs[j0 + q] = sm.cs[j0 + q] == 0.0 ? -1.0 : d[q];
+      }
     }
   }
   __syncthreads();
