@@ -2032,8 +2032,9 @@ __device__ __forceinline__ void ag_columns(const TuckerStepParams &P, const Tuck
       const int kn = min(kAgKC, K - k0), kn4 = (kn + 3) & ~3;
       if (vec4) {
         // N3 a multiple of four: thread (ts, cq) stages columns c0 + 4 cq .. + 3 (one i2
-        // row) of terms 8 ts .. 8 ts + 7 of the chunk: one float4 gather, weighing and
-        // store per term, the eight gathers issued before any is used
+        // row) of terms ts, ts + 4, ..., ts + 28 of the chunk (dealt round robin, so the
+        // four groups share a short chunk evenly): one float4 gather, weighing and store
+        // per term, the gathers of a batch issued before any is used
         const int ts = tid >> 6, cq = tid & 63;
         const int p = c0 + 4 * cq;
         const bool pin = p < NP;  // all four columns or none (NP a multiple of four)
@@ -2042,11 +2043,11 @@ __device__ __forceinline__ void ag_columns(const TuckerStepParams &P, const Tuck
         constexpr int VG = TR >= 12 ? 4 : 8;  // gathers in flight (registers: the tile is live)
 #pragma unroll
         for (int e0 = 0; e0 < 8; e0 += VG) {
-          if (8 * ts + e0 >= kn4) break;  // warp-uniform
+          if (ts + 4 * e0 >= kn4) break;  // warp-uniform
           float4 g[VG];
 #pragma unroll
           for (int e = 0; e < VG; ++e) {
-            const int kk = 8 * ts + e0 + e;
+            const int kk = ts + 4 * (e0 + e);
             g[e] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (kk < kn && pin && terms[k0 + kk].kind == 0) {
               const int refl = terms[k0 + kk].refl;
@@ -2056,7 +2057,7 @@ __device__ __forceinline__ void ag_columns(const TuckerStepParams &P, const Tuck
           }
 #pragma unroll
           for (int e = 0; e < VG; ++e) {
-            const int kk = 8 * ts + e0 + e;
+            const int kk = ts + 4 * (e0 + e);
             if (kk >= kn4) break;  // warp-uniform
             float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
             if (kk < kn && pin) {
@@ -2198,13 +2199,19 @@ __global__ void __launch_bounds__(kAgThreads, 2)
   unsigned *s_rmax = reinterpret_cast<unsigned *>(terms + K4max);
   __shared__ SlotDev s_slot[6];
   __shared__ double s_scale[6];
-  __shared__ int s_K;
+  __shared__ int s_K, s_rk[7];
   const float *U1all = reinterpret_cast<const float *>(B.U1all);
   const float *ghostR = P.ghostf32;
   const int tid = threadIdx.x;
   for (int64_t j = blockIdx.x; j < B.cn; j += gridDim.x) {
     const int64_t c = B.c0 + j, jb = B.joff + j;
     cell_prologue<float>(P, c, N, sm, s_slot, s_scale);
+    // first-mode ranks of the cell and of each face's source, loaded side by side
+    if (tid < 7) {
+      const SlotDev *sl = tid > 0 ? &s_slot[tid - 1] : nullptr;
+      s_rk[tid] = P.cur.rank[3 * ((sl && sl->kind == kInterior) ? (int64_t)sl->src : c)];
+    }
+    __syncthreads();
     // the cell's rank-one terms: Shakhov parts, ghosts, self (row weight), self (column
     // weight), then each interior / symmetry face
     if (tid == 0) {
@@ -2216,7 +2223,7 @@ __global__ void __launch_bounds__(kAgThreads, 2)
       for (int k = 1; k <= 4; ++k) put(AgTerm{0, 0, k, 0, 0, 0, 0, 0});
       for (int l = 0; l < 6; ++l)
         if (s_slot[l].kind == kFreeStream || s_slot[l].kind == kWall) put(AgTerm{0, 0, 5, 0, 0, l, 0, 0});
-      const int r = P.cur.rank[3 * c];
+      const int r = s_rk[0];
       const int64_t oT = c * (int64_t)R * NP, oU = c * (int64_t)R * N1P;
       for (int k = 0; k < r; ++k) put(AgTerm{oT + (int64_t)k * NP, oU + (int64_t)k * N1P, 0, 0, 0, -1, 1, 0});
       for (int k = 0; k < r; ++k) put(AgTerm{oT + (int64_t)k * NP, oU + (int64_t)k * N1P, 0, 0, 1, -1, 0, 0});
@@ -2225,7 +2232,7 @@ __global__ void __launch_bounds__(kAgThreads, 2)
         if (sl.kind != kInterior && sl.kind != kSymmetry) continue;
         const bool sym = sl.kind == kSymmetry;
         const int64_t src = sym ? c : (int64_t)sl.src;
-        const int rs = P.cur.rank[3 * src];
+        const int rs = s_rk[l + 1];
         const int wa = sl.axis == 0 ? 2 : 0, ws = sl.axis == 1 ? 2 : (sl.axis == 2 ? 3 : 0);
         const int rev = sym && sl.flip == 0, refl = sym ? (sl.flip == 1 ? 1 : (sl.flip == 2 ? 2 : 0)) : 0;
         const int64_t sT = src * (int64_t)R * NP, sU = src * (int64_t)R * N1P;
