@@ -1976,11 +1976,34 @@ __host__ __device__ inline int ag_max_terms(int R) { return 4 + 8 * R; }
 
 // shared memory: cell scalars and tables, self weights, A [K][padN(N1)], the staged column
 // factors B [kAgKC][kAgCols], term list, row maxima
-__host__ __device__ inline size_t ag_smem_bytes(int Nmax, int N1, int R) {
+__host__ __device__ inline size_t ag_smem_bytes(int Nmax, int N1, int R, int nbuf = 1) {
   const size_t NmP = padN(Nmax), K4 = (size_t)((ag_max_terms(R) + 3) & ~3);
   return sizeof(double) * 96 + sizeof(float) * ((size_t)kTabs * NmP + 3 * NmP) +
-         sizeof(float) * K4 * padN(N1) + sizeof(float) * kAgKC * kAgCols +
+         sizeof(float) * K4 * padN(N1) + sizeof(float) * kAgKC * kAgCols * nbuf +
          sizeof(AgTerm) * K4 + sizeof(unsigned) * NmP + 64;
+}
+
+// B stages: two (the next unit's column factors copied in while the current one's FMAs
+// run) where the four-column staging applies (N3 a multiple of four, tiles of at most 12
+// rows) and two CTAs per SM still fit, else one
+__host__ __device__ inline int ag_nbuf(int Nmax, int N1, int N3, int R) {
+  return (padN(N1) <= 48 && (N3 & 3) == 0 &&
+          2 * (ag_smem_bytes(Nmax, N1, R, 2) + 1024) <= 228 * 1024)
+             ? 2
+             : 1;
+}
+
+__device__ __forceinline__ void cp_async16(float *smem_dst, const float *gmem_src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst))),
+               "l"(gmem_src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 // the column factor at (i2, i3) of a computed term: a Shakhov part (Proposition 1: the
@@ -2180,6 +2203,151 @@ __device__ __forceinline__ void ag_columns(const TuckerStepParams &P, const Tuck
   }
 }
 
+// ag_columns with two B stages (N3 a multiple of four, TR <= 12): the units (tile, chunk
+// of 32 terms) run in order; the Tucker columns of unit u + 1 are copied from T2 straight
+// into the other stage (16-byte asynchronous copies, thread (ts, cq) its four columns of
+// terms ts, ts + 4, ...) while unit u's FMAs run, and each thread then weighs its own
+// entries in place (the computed columns and the zero padding written there too): one
+// barrier per unit.  The same sums as ag_columns.
+template <int TR>
+__device__ __forceinline__ void ag_columns_pipe(const TuckerStepParams &P, const TuckerSplitBufs &B,
+                                                int64_t jb, Smem<float> &sm, const SlotDev *s_slot,
+                                                const float *A_s, float *B_s, const AgTerm *terms,
+                                                int K, const float *colW2, const float *colW3,
+                                                unsigned *s_rmax) {
+  const int N1 = P.N1, N2 = P.N2, N3 = P.N3, NP = N2 * N3, Nm = P.Nmax, N1P = padN(N1);
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int rg = tid >> 6, cg = tid & 63, row0 = rg * TR;
+  const int ts = tid >> 6, cq = tid & 63;
+  const float *T2all = reinterpret_cast<const float *>(B.T2all);
+  const float *ghostR = P.ghostf32;
+  float *Xc = reinterpret_cast<float *>(B.X) + jb * (int64_t)N1 * NP;
+  const int nchunk = (K + kAgKC - 1) / kAgKC, ntile = (NP + kAgCols - 1) / kAgCols;
+  const int nunit = nchunk * ntile;
+  constexpr int kStage = kAgKC * kAgCols;
+  // copies of unit u's Tucker columns into stage u & 1 (one commit group per unit)
+  auto issue = [&](int u) {
+    const int tile = u / nchunk, k0 = (u - tile * nchunk) * kAgKC, kn = min(kAgKC, K - k0);
+    const int p = tile * kAgCols + 4 * cq;
+    if (p < NP) {
+      const int i2 = p / N3, i3 = p - i2 * N3;
+      const int pm2 = (N2 - 1 - i2) * N3 + i3, pm3 = i2 * N3 + (N3 - 4 - i3);
+      float *buf = B_s + (u & 1) * kStage + 4 * cq;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int kk = ts + 4 * e;
+        if (kk >= kn) break;  // warp-uniform
+        const AgTerm &tm = terms[k0 + kk];
+        if (tm.kind == 0)
+          cp_async16(buf + kk * kAgCols, T2all + tm.t2 + (tm.refl == 1 ? pm2 : (tm.refl == 2 ? pm3 : p)));
+      }
+    }
+    cp_async_commit();
+  };
+  float rm[TR];
+#pragma unroll
+  for (int r = 0; r < TR; ++r) rm[r] = 0.f;
+  float acc[TR][4];
+  if (nunit > 0) issue(0);
+  for (int u = 0; u < nunit; ++u) {
+    const int tile = u / nchunk, ch = u - tile * nchunk, k0 = ch * kAgKC;
+    const int kn = min(kAgKC, K - k0), kn4 = (kn + 3) & ~3, c0 = tile * kAgCols;
+    float *buf = B_s + (u & 1) * kStage;
+    cp_async_wait_all();  // this thread's copies of unit u have landed
+    {  // weigh this thread's entries of unit u in place
+      const int p = c0 + 4 * cq;
+      const bool pin = p < NP;
+      const int pc = pin ? p : 0, i2 = pc / N3, i3 = pc - i2 * N3;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int kk = ts + 4 * e;
+        if (kk >= kn4) break;  // warp-uniform
+        float4 *dst = reinterpret_cast<float4 *>(buf + kk * kAgCols + 4 * cq);
+        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (kk < kn && pin) {
+          const AgTerm tm = terms[k0 + kk];
+          if (tm.kind == 0) {
+            x = *dst;
+            if (tm.refl == 2) x = make_float4(x.w, x.z, x.y, x.x);
+            if (tm.wsel == 1) {
+              const float w2 = colW2[i2];
+              const float4 w3 = *reinterpret_cast<const float4 *>(colW3 + i3);
+              x = make_float4(x.x * (w2 + w3.x), x.y * (w2 + w3.y), x.z * (w2 + w3.z), x.w * (w2 + w3.w));
+            } else if (tm.wsel == 2) {
+              const float w = tabp(sm, Nm, 15 + tm.face)[i2];
+              x = make_float4(x.x * w, x.y * w, x.z * w, x.w * w);
+            } else if (tm.wsel == 3) {
+              const float4 w = *reinterpret_cast<const float4 *>(tabp(sm, Nm, 15 + tm.face) + i3);
+              x = make_float4(x.x * w.x, x.y * w.y, x.z * w.z, x.w * w.w);
+            }
+          } else {
+            x = make_float4(ag_column(tm, sm, s_slot, ghostR, Nm, i2, i3),
+                            ag_column(tm, sm, s_slot, ghostR, Nm, i2, i3 + 1),
+                            ag_column(tm, sm, s_slot, ghostR, Nm, i2, i3 + 2),
+                            ag_column(tm, sm, s_slot, ghostR, Nm, i2, i3 + 3));
+          }
+        }
+        *dst = x;
+      }
+    }
+    __syncthreads();  // unit u staged; every thread is past unit u - 1's FMAs
+    if (u + 1 < nunit) issue(u + 1);
+    if (ch == 0) {
+#pragma unroll
+      for (int r = 0; r < TR; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[r][q] = 0.f;
+    }
+    const float *a = A_s + (size_t)k0 * N1P + row0;
+    const float *bp = buf + 4 * cg;
+#pragma unroll 4
+    for (int e = 0; e < kn4; ++e) {
+      float av[TR];
+#pragma unroll
+      for (int q = 0; q < TR / 4; ++q) {
+        const float4 t = *reinterpret_cast<const float4 *>(a + (size_t)e * N1P + 4 * q);
+        av[4 * q] = t.x;
+        av[4 * q + 1] = t.y;
+        av[4 * q + 2] = t.z;
+        av[4 * q + 3] = t.w;
+      }
+      const float4 bv = *reinterpret_cast<const float4 *>(bp + e * kAgCols);
+#pragma unroll
+      for (int r = 0; r < TR; ++r) {
+        acc[r][0] = fmaf(av[r], bv.x, acc[r][0]);
+        acc[r][1] = fmaf(av[r], bv.y, acc[r][1]);
+        acc[r][2] = fmaf(av[r], bv.z, acc[r][2]);
+        acc[r][3] = fmaf(av[r], bv.w, acc[r][3]);
+      }
+    }
+    if (ch + 1 == nchunk) {  // the tile of X (NP a multiple of four) and the row maxima
+      const int cb = c0 + 4 * cg;
+      if (cb < NP) {
+#pragma unroll
+        for (int r = 0; r < TR; ++r) {
+          const int row = row0 + r;
+          if (row >= N1) continue;
+          __stcs(reinterpret_cast<float4 *>(Xc + (int64_t)row * NP + cb),
+                 make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]));
+          rm[r] = fmaxf(rm[r], fmaxf(fmaxf(fabsf(acc[r][0]), fabsf(acc[r][1])),
+                                     fmaxf(fabsf(acc[r][2]), fabsf(acc[r][3]))));
+        }
+      }
+    }
+  }
+  if (B.rowmax) {  // across the warp's 32 column groups (its rows are the same), then warps
+#pragma unroll
+    for (int r = 0; r < TR; ++r) {
+      float m = rm[r];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if (lane == 0 && row0 + r < N1) atomicMax(&s_rmax[row0 + r], __float_as_uint(m));
+    }
+  }
+}
+
+// TR rows of X per thread (padN(N1) / 4), kPipe: two B stages (ag_nbuf = 2)
+template <int TR, bool kPipe>
 __global__ void __launch_bounds__(kAgThreads, 2)
     tucker_asm_gemm_kernel(TuckerStepParams P, TuckerSplitBufs B) {
   extern __shared__ __align__(16) unsigned char ag_raw[];
@@ -2194,8 +2362,8 @@ __global__ void __launch_bounds__(kAgThreads, 2)
   float *rowW = sm.rt + (size_t)kTabs * NmP;        // self weight over i1
   float *colW2 = rowW + NmP, *colW3 = colW2 + NmP;  // self weight parts over i2, i3
   float *A_s = colW3 + NmP;                         // [K][N1P]
-  float *B_s = A_s + (size_t)K4max * N1P;           // [kAgKC][kAgCols]
-  AgTerm *terms = reinterpret_cast<AgTerm *>(B_s + kAgKC * kAgCols);
+  float *B_s = A_s + (size_t)K4max * N1P;           // [1 or 2][kAgKC][kAgCols]
+  AgTerm *terms = reinterpret_cast<AgTerm *>(B_s + (kPipe ? 2 : 1) * kAgKC * kAgCols);
   unsigned *s_rmax = reinterpret_cast<unsigned *>(terms + K4max);
   __shared__ SlotDev s_slot[6];
   __shared__ double s_scale[6];
@@ -2289,17 +2457,29 @@ __global__ void __launch_bounds__(kAgThreads, 2)
       A_s[idx] = x;
     }
     __syncthreads();
-    switch (N1P) {
-      case 16: ag_columns<4>(P, B, jb, sm, s_slot, A_s, B_s, terms, K, colW2, colW3, s_rmax); break;
-      case 32: ag_columns<8>(P, B, jb, sm, s_slot, A_s, B_s, terms, K, colW2, colW3, s_rmax); break;
-      case 48: ag_columns<12>(P, B, jb, sm, s_slot, A_s, B_s, terms, K, colW2, colW3, s_rmax); break;
-      default: ag_columns<16>(P, B, jb, sm, s_slot, A_s, B_s, terms, K, colW2, colW3, s_rmax); break;
-    }
+    if constexpr (kPipe)
+      ag_columns_pipe<TR>(P, B, jb, sm, s_slot, A_s, B_s, terms, K, colW2, colW3, s_rmax);
+    else
+      ag_columns<TR>(P, B, jb, sm, s_slot, A_s, B_s, terms, K, colW2, colW3, s_rmax);
     __syncthreads();
     if (B.rowmax)
       for (int i = tid; i < N1; i += blockDim.x) B.rowmax[jb * Nm + i] = __uint_as_float(s_rmax[i]);
     if (tid == 0) B.disc[jb] = 0.0;
   }
+}
+
+// the GEMM-form assembly kernel for a first mode padded to N1P rows and 1 or 2 B stages
+using AgKernel = void (*)(TuckerStepParams, TuckerSplitBufs);
+inline AgKernel ag_kernel(int N1P, int nbuf) {
+  if (nbuf == 2) {
+    if (N1P == 16) return tucker_asm_gemm_kernel<4, true>;
+    if (N1P == 32) return tucker_asm_gemm_kernel<8, true>;
+    return tucker_asm_gemm_kernel<12, true>;
+  }
+  if (N1P == 16) return tucker_asm_gemm_kernel<4, false>;
+  if (N1P == 32) return tucker_asm_gemm_kernel<8, false>;
+  if (N1P == 48) return tucker_asm_gemm_kernel<12, false>;
+  return tucker_asm_gemm_kernel<16, false>;
 }
 
 // Mode-2/3 contraction T2 = G x2 U2 x3 U3 of every cell's current tensor and its
@@ -2928,7 +3108,7 @@ int prepare_split_TS(int Nmax, int R) {
   int mask = 0;
   if (raise_smem_optin(tucker_step_kernel<Real, TS>, smem_bytes<Real>(Nmax, R)) == 0) mask |= 1;
   if (sizeof(Real) == 4 && Nmax <= 64)  // GEMM-form assembly (used where the mesh allows)
-    raise_smem_optin(tucker_asm_gemm_kernel, ag_smem_bytes(Nmax, Nmax, R));
+    tucker_asm_gemm_prepare(Nmax, Nmax, R);
   if (raise_smem_optin(tucker_asm_kernel<Real>, z.asm_) == 0 &&
       raise_smem_optin(tucker_t2_kernel<Real>, z.asm_) == 0 &&
       raise_smem_optin(tucker_gram_kernel<Real, TS>, z.gram) == 0 &&
@@ -2951,7 +3131,8 @@ void split_chain(const TuckerStepParams &p, const TuckerSplitBufs &b, const Spli
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int gg = (int)(b.cn < 2 * sms ? b.cn : 2 * sms);
-    tucker_asm_gemm_kernel<<<gg, kAgThreads, ag_smem_bytes(p.Nmax, p.N1, p.R), s>>>(p, b);
+    const int nbuf = ag_nbuf(p.Nmax, p.N1, p.N3, p.R);
+    ag_kernel(padN(p.N1), nbuf)<<<gg, kAgThreads, ag_smem_bytes(p.Nmax, p.N1, p.R, nbuf), s>>>(p, b);
   } else {
     tucker_asm_kernel<Real><<<ga, kAsmTB, z.asm_, s>>>(p, b);
   }
@@ -3124,7 +3305,12 @@ int tucker_prepare_launch(int Nmax, int R, bool fp64) {
 
 int tucker_asm_gemm_prepare(int Nmax, int N1, int R) {
   if (Nmax > 64 || N1 > 64) return -1;  // register tiles of at most 16 rows per thread
-  return raise_smem_optin(tucker_asm_gemm_kernel, ag_smem_bytes(Nmax, N1, R));
+  for (int nbuf = 1; nbuf <= 2; ++nbuf) {
+    const size_t smem = ag_smem_bytes(Nmax, N1, R, nbuf);
+    if (nbuf == 2 && smem > 227 * 1024) break;  // then only one stage is ever used
+    if (raise_smem_optin(ag_kernel(padN(N1), nbuf), smem) != 0) return -1;
+  }
+  return 0;
 }
 
 size_t tucker_split_bytes_per_cell(int N1, int N2, int N3, int R, int Nmax, bool fp64) {
