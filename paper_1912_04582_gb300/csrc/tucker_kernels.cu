@@ -2568,7 +2568,6 @@ __host__ __device__ inline size_t smem_eig_bytes(int Nmax, int R) {
   const int K = sub_k(Nmax, R);
   size_t b = sizeof(double) * (64 + 2 * (size_t)Nmax * K + (size_t)K * K + 2 * K + 2);
   b += sizeof(Real) * (size_t)Nmax * K + 16;
-  b += sizeof(double) * (size_t)Nmax * Nmax;  // the staged Gram matrix
   b += sizeof(int) * (2 * (size_t)K + 2);
   return b + 64;
 }
@@ -2674,7 +2673,6 @@ __global__ void __launch_bounds__(kEigTB, 13) tucker_eig_kernel(TuckerStepParams
   Smem<Real> sm{};
   sm.nmax = Nm;
   sm.kdim = K;
-  double *Cs;  // the Gram matrix staged in shared memory
   {
     size_t off = 0;
     auto takeD = [&](size_t n) {
@@ -2692,8 +2690,6 @@ __global__ void __launch_bounds__(kEigTB, 13) tucker_eig_kernel(TuckerStepParams
     sm.Vr = reinterpret_cast<Real *>(smem_raw + off);
     off += sizeof(Real) * (size_t)Nm * K;
     off = (off + 15) & ~size_t(15);
-    Cs = reinterpret_cast<double *>(smem_raw + off);
-    off += sizeof(double) * (size_t)Nm * Nm;
     sm.Q32 = reinterpret_cast<float *>(sm.W);
     sm.W32 = sm.Q32 + (size_t)Nm * K;
     sm.pairs = reinterpret_cast<int *>(smem_raw + off);
@@ -2704,17 +2700,16 @@ __global__ void __launch_bounds__(kEigTB, 13) tucker_eig_kernel(TuckerStepParams
   const int N[3] = {P.N1, P.N2, P.N3};
   const int64_t c = B.c0 + blockIdx.x, j = B.joff + blockIdx.x;  // j: buffer index
   const int n = N[m];
-  // the Gram matrix and the previous factor (the warm start) to shared memory; the
-  // factor goes to a block the eigen-solver fills only after reading it (sm.Q on the
-  // mixed path, where the FP32 basis lives in sm.W; sm.W on the FP64 path)
+  // the previous factor (the warm start) to shared memory, into a block the eigen-solver
+  // fills only after reading it (sm.Q on the mixed path, where the FP32 basis lives in
+  // sm.W; sm.W on the FP64 path).  The Gram matrix is read where the Gram kernel left it
+  // (L2 / L1): without a shared copy of it more cells fit on an SM at once.
   double *Ws = sizeof(Real) == 4 ? sm.Q : sm.W;
   {
-    const StagePiece pcs[2] = {
-        {Cs, B.C + j * (int64_t)Nm * Nm, 8u * (unsigned)(n * n)},
-        {Ws, P.cur.fac[m] + c * (int64_t)n * R, 8u * (unsigned)(n * R)}};
-    if (!stage_to_shared(pcs, 2, P.flag)) return;  // timed out: step reported failed
+    const StagePiece pcs[1] = {{Ws, P.cur.fac[m] + c * (int64_t)n * R, 8u * (unsigned)(n * R)}};
+    if (!stage_to_shared(pcs, 1, P.flag)) return;  // timed out: step reported failed
   }
-  sm.Cg = Cs;
+  sm.Cg = B.C + j * (int64_t)Nm * Nm;
   const double tr = gram_trace<Real>(sm, n);
   // ||X||^2 = trace of the first Gram matrix + the columns it left out (B.disc)
   if (m == 0 && threadIdx.x == 0) B.e[j] = tr + B.disc[j];
