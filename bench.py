@@ -61,6 +61,8 @@ def _args():
                     help="Tucker launch variant (auto: the autotuner times both)")
     ap.add_argument("--advance", type=int, default=200,
                     help="untimed steps that develop the flow (and the Tucker ranks) first")
+    ap.add_argument("--c4-advance", type=int, default=10,
+                    help="untimed C4 steps before its timed ones (ranks develop with the flow)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
@@ -783,7 +785,7 @@ def run_gpu(args, rank, world):
             line["configs"] = {}
             if args.workload != "c2":
                 line["configs"]["C2_cavity_16^3x32^3"] = run_c2(P, NAT, stream)
-            line["configs"].update(run_c4(P, NAT, stream))
+            line["configs"].update(run_c4(P, NAT, stream, advance=args.c4_advance))
             line["serving"] = run_serving(P)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(wl)
