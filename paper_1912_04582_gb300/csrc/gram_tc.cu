@@ -158,12 +158,8 @@ __device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
 // slice product with the fewest tensor-memory columns (the MMA work is proportional to
 // them), found by exhaustive search; each product is owned by the first group that
 // forms it.
-// words of row a of a level accumulator (the packed upper triangle: n - a entries), padded
-// to 2 mod 32 when pad is set
-__host__ __device__ inline int level_row_words(int n, int a, int pad) {
-  const int len = n - a;
-  return pad ? len + (((2 - len) % 32) + 32) % 32 : len;
-}
+// offset of row a in the packed upper triangle of an n x n matrix (row a: entries (a, a..n-1))
+__host__ __device__ inline int tri_row(int n, int a) { return a * n - ((a * (a - 1)) >> 1); }
 
 static GramTcPlan make_plan(int n) {
   GramTcPlan p{};
@@ -260,19 +256,7 @@ static GramTcPlan make_plan(int n) {
   p.nstages = fixed + (size_t)kTcMaxStages * p.buf_rows * kTcRowBytes <= 227 * 1024
                   ? kTcMaxStages
                   : kTcMaxStages - 1;
-  // level accumulators: the packed upper triangle, row a at rowoff[a].  Where it fits
-  // beside the same stages, every row is padded to a length of 2 mod 32 words, so that the
-  // read-back's lanes (consecutive rows a, one column b) hit consecutive banks on both
-  // sides of the diagonal (rowoff[a] - a then steps by 1 mod 32)
-  p.ltri = n * (n + 1) / 2;
-  p.lpad = 0;
-  int padded = 0;
-  for (int a = 0; a < n; ++a) padded += level_row_words(n, a, 1);
-  if (fixed - sizeof(int) * kTcLevels * (size_t)p.ltri + sizeof(int) * kTcLevels * (size_t)padded +
-          (size_t)p.nstages * p.buf_rows * kTcRowBytes <= 227 * 1024) {
-    p.lpad = 1;
-    p.ltri = padded;
-  }
+  p.ltri = n * (n + 1) / 2;  // level accumulators: the packed upper triangle
   return p;
 }
 
@@ -414,7 +398,7 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1)
   int *Lacc = reinterpret_cast<int *>(raw + kTcRawStages * kTcRawBytes);
   int *rexp = Lacc + kTcLevels * ltri;
   float *rinv = reinterpret_cast<float *>(rexp + 64);
-  int *rowoff = reinterpret_cast<int *>(rinv + 64);  // upper-triangle offset of each row
+
   __shared__ __align__(8) unsigned long long s_full[kTcRawStages], s_empty[kTcRawStages];
   __shared__ __align__(8) unsigned long long s_ready[kTcMaxStages], s_freed[kTcMaxStages];
   __shared__ __align__(8) unsigned long long s_accf, s_acce;
@@ -440,13 +424,7 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_abort = 0;
   }
-  if (tid == 0) {  // row starts of the level accumulators (padded rows where P.lpad)
-    int o = 0;
-    for (int a = 0; a < 64; ++a) {
-      rowoff[a] = o;
-      if (a < n) o += level_row_words(n, a, P.lpad);
-    }
-  }
+
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_addr(&s_tmem)),
@@ -681,7 +659,7 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1)
               for (int u = 0; u < 8; ++u) {
                 const int j = j0 + u;
                 if (j >= n || (k == l && i > j)) continue;
-                const int tri = i <= j ? rowoff[i] + (j - i) : rowoff[j] + (i - j);
+                const int tri = i <= j ? tri_row(n, i) + (j - i) : tri_row(n, j) + (i - j);
                 const int d = __float2int_rn(__uint_as_float(r[q][u]) * scale);
                 // a diagonal entry of a k != l product is its own transpose: counted twice
                 atomicAdd(&Lacc[(k + l) * ltri + tri], (k != l && i == j) ? 2 * d : d);
@@ -699,12 +677,9 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1)
       // so |T| < 2^60), C_ab = 2^(e_a + e_b - 40) (T + 2^-21 U); written once rounded, as a
       // double-float pair or a double
       for (int e = ct; e < ntri; e += kTcConsumers) {
-        int a = 0, ea = 0;  // entry e of the upper triangle, row by row: (a, b)
-        while (a + 1 < n && ea + (n - a) <= e) {
-          ea += n - a;
-          ++a;
-        }
-        const int b = a + (e - ea), w = rowoff[a] + (b - a);
+        int a = 0;  // entry e of the upper triangle, row by row: (a, b)
+        while (a + 1 < n && tri_row(n, a + 1) <= e) ++a;
+        const int b = a + (e - tri_row(n, a)), w = e;
         long long T = 0, U = 0;
 #pragma unroll
         for (int m = 0; m <= 4; ++m) T = T * 128 + Lacc[m * ltri + w];

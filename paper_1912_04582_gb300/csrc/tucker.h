@@ -129,7 +129,6 @@ struct GramTcPlan {
   int ncols;                     // tensor-memory columns allocated
   int buf_rows;                  // rows of one shared-memory stage
   int nstages;                   // shared-memory stages of sliced chunks (2 or 3)
-  int lpad;                      // 1: rows of the level accumulators padded to 2 mod 32 words
   int ltri;                      // words of one level accumulator (the packed upper triangle)
   signed char own[kTcSlices * kTcSlices];  // group + 1 that owns product (k, l), else 0
 };
