@@ -267,7 +267,6 @@ __device__ void expand(const TuckerDev &T, int64_t cell, const int N[3], int R, 
   // out[i1][p] (+)= w * sum_k1 U1[i1][k1] T2[k1][p]
   const int NP = N2 * N3;
   for (int p = tid; p < NP; p += blockDim.x) {
-    const int i2 = p / N3, i3 = p - i2 * N3;
     for (int i0 = 0; i0 < N1; i0 += 8) {
       Real a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
       for (int k1 = 0; k1 < r1; ++k1) {
@@ -828,11 +827,9 @@ __device__ void mat_cq_hi(const float2 *__restrict__ C, const float *Q, float *W
   __syncthreads();
 }
 
-// Double-float inner product sum_t (c_t.hi + c_t.lo) (vh_t + vl_t) with exact
-// leading products (fma) and a two-sum accumulation: about 2^-48 relative.  c_t
-// is read at c[t * cstride] (a column of the symmetric Gram matrix, so that the
-// lanes of a warp, one row each, read consecutive entries).
-// one term of it: (hi, lo) += (ct.x + ct.y) (h + l)
+// One term of a double-float inner product sum_t (c_t.hi + c_t.lo) (vh_t + vl_t):
+// (hi, lo) += (ct.x + ct.y) (h + l), the leading product exact (fma) and a two-sum
+// accumulation: about 2^-48 relative over the sum.
 __device__ __forceinline__ void df_mac(float2 ct, float h, float l, float &hi, float &lo) {
   const float p = __fmul_rn(ct.x, h);
   const float pe = __fmaf_rn(ct.x, h, -p);
@@ -843,17 +840,10 @@ __device__ __forceinline__ void df_mac(float2 ct, float h, float l, float &hi, f
   lo = __fadd_rn(lo, __fadd_rn(err, __fmaf_rn(ct.x, l, __fmaf_rn(ct.y, h, pe))));
 }
 
-__device__ __forceinline__ double df_dot(const float2 *c, int cstride, const float *vh,
-                                         const float *vl, int stride, int n) {
-  float hi = 0.f, lo = 0.f;
-  for (int t = 0; t < n; ++t)
-    df_mac(c[t * cstride], vh[t * stride], vl ? vl[t * stride] : 0.f, hi, lo);
-  return (double)hi + (double)lo;
-}
-
-// df_dot of row i of the symmetric double-float matrix C (n x n, read by columns) with up
-// to four columns j0 .. j0 + 3 of V (n x k, hi parts vh, lo parts vl or none) at once: the
-// same operations per product as df_dot, four independent chains
+// Double-float inner products of row i of the symmetric double-float matrix C (n x n, read
+// by columns: the lanes of a warp, one row each, read consecutive entries) with up to four
+// columns j0 .. j0 + 3 of V (n x k, hi parts vh, lo parts vl or none) at once: each sum in
+// t order by df_mac, four independent chains
 __device__ __forceinline__ void df_dot4(const float2 *C, int n, int i, const float *vh,
                                         const float *vl, int k, int j0, double (&out)[4]) {
   float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
@@ -1837,7 +1827,6 @@ __global__ void __launch_bounds__(kTB, MinBlocks<Real>::value) tucker_step_kerne
   const int N[3] = {P.N1, P.N2, P.N3};
   const int N1 = P.N1, N2 = P.N2, N3 = P.N3, NP = N2 * N3;
   const int NN = N1 * NP;
-  const int Nm = P.Nmax;
   const int tid = threadIdx.x;
   Real *X = reinterpret_cast<Real *>(P.scratch) + (size_t)blockIdx.x * P.scratch_stride;
   Real *T2buf = X + NN;  // assembly: mode-2/3 contractions; rounding: its work space
@@ -2928,7 +2917,7 @@ __global__ void __launch_bounds__(128) tucker_moments_kernel(TuckerMomentParams 
   }
   // S_a^(p)[k] = sum_i U_a[i][k] (xi_a,i - r_a)^p
   for (int idx = tid; idx < 12 * R; idx += blockDim.x) {
-    const int k = idx % R, ap = idx / R, p = ap % 4, a = ap / 4;
+    const int k = idx % R, ap = idx / R, a = ap / 4;
     double s = 0.0;
     if (k < r[a]) {
       const double *U = Uc[a], *w = Pw + ap * Nx;
