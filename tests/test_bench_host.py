@@ -57,3 +57,35 @@ def test_job_value_counts_every_rank(world, steps, ms):
     upd = 4096 * 32 ** 3
     v = bench.job_value(world, upd, steps, ms)
     assert v == pytest.approx(world * upd * steps / (ms / 1e3), rel=1e-12)
+
+
+def test_assembly_terms_count_the_rank_one_terms_of_each_cell():
+    """The GEMM-form assembly's work model: K = 4 Shakhov parts + 2 r1 for the cell + per
+    face r1 of the neighbour or one ghost.  On a 4^3 cavity with every rank 2: corner cells
+    (3 walls) 4 + 4 + 3*2 + 3 = 17, edge cells 18, face cells 19, interior cells 20, in the
+    counts 8 / 24 / 24 / 8; with rank 1 in one interior cell its six neighbours lose 1."""
+    import numpy as np
+    import workloads as W
+    wl = W.cavity(nside=4, N=8, seed=3)
+    r = np.full(wl.n_cell, 2.0)
+    K = bench.assembly_terms(wl, r)
+    assert sorted(np.unique(K).tolist()) == [17, 18, 19, 20]
+    assert [int((K == v).sum()) for v in (17, 18, 19, 20)] == [8, 24, 24, 8]
+    ijk = np.asarray(wl.cell_ijk)
+    c = int(np.flatnonzero((ijk == [1, 1, 1]).all(axis=1))[0])
+    r2 = r.copy()
+    r2[c] = 1.0
+    d = K - bench.assembly_terms(wl, r2)
+    assert d[c] == 2  # its own 2 r1
+    nb = [int(np.flatnonzero((ijk == ijk[c] + e).all(axis=1))[0])
+          for e in np.vstack([np.eye(3, dtype=int), -np.eye(3, dtype=int)])]
+    assert all(d[q] == 1 for q in nb) and d.sum() == 2 + 6
+
+
+@pytest.mark.parametrize("N,tc", [((48, 48, 48), True), ((64, 64, 64), True),
+                                  ((32, 24, 20), True), ((40, 13, 7), False),
+                                  ((72, 16, 16), False)])
+def test_gram_on_tensor_cores_follows_the_library_rule(N, tc):
+    """N1 <= 64 and N2 N3 a multiple of 8 up to 4096 (64^3: N2 N3 = 4096 is allowed; 40 x 13 x
+    7: 91 columns, not a multiple of 8; 72 first-mode rows: too many)."""
+    assert bench.gram_on_tensor_cores(N) == tc
