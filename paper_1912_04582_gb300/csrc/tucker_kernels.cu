@@ -1088,11 +1088,9 @@ __device__ __noinline__ int leading_eigs(Smem<Real> &sm, int n, int k, const WT 
       orthonormalise<float, float>(sm.Q32, n, k, G32, d32, kF32Passes, 1e-5, kDepNone);
       pc.mark(10);
     }
-    // one power step with the accurate Gram matrix: W = C Q32 in double-float
-    // (the FP32 basis moves out of sm.W's space first)
-    float *V = reinterpret_cast<float *>(sm.Vr);
-    for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) V[idx] = sm.Q32[idx];
-    __syncthreads();
+    // one power step with the accurate Gram matrix: Q = C Q32 in double-float (Q32, in
+    // sm.W's space, is read in place: nothing writes sm.W before the Rayleigh quotients)
+    const float *V = sm.Q32;
     const int ng = (k + 3) >> 2;  // groups of four columns
     for (int idx = threadIdx.x; idx < n * ng; idx += blockDim.x) {
       const int i = idx / ng, j0 = 4 * (idx - i * ng);
@@ -2556,8 +2554,8 @@ template <typename Real>
 __host__ __device__ inline size_t smem_eig_bytes(int Nmax, int R) {
   const int K = sub_k(Nmax, R);
   size_t b = sizeof(double) * (64 + 2 * (size_t)Nmax * K + (size_t)K * K + 2 * K + 2);
-  b += sizeof(Real) * (size_t)Nmax * K + 16;
-  b += sizeof(int) * (2 * (size_t)K + 2);
+  if (sizeof(Real) == 8) b += sizeof(Real) * (size_t)Nmax * K;  // the retry start (FP64 path)
+  b += 16 + sizeof(int) * (2 * (size_t)K + 2);
   return b + 64;
 }
 
@@ -2651,11 +2649,12 @@ __device__ __noinline__ bool stage_to_shared(const StagePiece (&pc)[NP], int np,
 // mode 3).
 // threads per eigen-solve CTA (one warp per cell).  The solver's loops are block-size
 // generic (the fused kernel runs the same routines with 256 threads and gets the same
-// sums); four warps per cell were measured 9% slower on the C3 cavity.
+// sums); four warps per cell were measured 9% slower on the C3 cavity.  Up to 16 cells per
+// SM (the mixed path's ~13 KB of shared memory a cell, 128 registers a thread).
 constexpr int kEigTB = 32;
 
 template <typename Real>
-__global__ void __launch_bounds__(kEigTB, 13) tucker_eig_kernel(TuckerStepParams P, TuckerSplitBufs B,
+__global__ void __launch_bounds__(kEigTB, 16) tucker_eig_kernel(TuckerStepParams P, TuckerSplitBufs B,
                                                              int m) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int Nm = P.Nmax, R = P.R, K = sub_k(Nm, R);
@@ -2676,8 +2675,12 @@ __global__ void __launch_bounds__(kEigTB, 13) tucker_eig_kernel(TuckerStepParams
     sm.B = takeD((size_t)K * K);
     sm.Z = takeD(K);
     sm.cs = takeD(K + 2);
-    sm.Vr = reinterpret_cast<Real *>(smem_raw + off);
-    off += sizeof(Real) * (size_t)Nm * K;
+    if (sizeof(Real) == 8) {  // the FP64 path's retry start (the mixed path starts from sm.Q)
+      sm.Vr = reinterpret_cast<Real *>(smem_raw + off);
+      off += sizeof(Real) * (size_t)Nm * K;
+    } else {
+      sm.Vr = nullptr;
+    }
     off = (off + 15) & ~size_t(15);
     sm.Q32 = reinterpret_cast<float *>(sm.W);
     sm.W32 = sm.Q32 + (size_t)Nm * K;
@@ -2716,10 +2719,18 @@ __global__ void __launch_bounds__(kEigTB, 13) tucker_eig_kernel(TuckerStepParams
   bool met;
   int r = choose_rank<Real>(sm, n, k, thr, R, &met, tr);
   pc.mark(7);
-  if (!met && k < kmax) {
-    for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) sm.Vr[idx] = (Real)sm.W[idx];
-    __syncthreads();
-    k = leading_eigs<Real, Real>(sm, n, kmax, sm.Vr, k, k, pc, kDepReseed);
+  if (!met && k < kmax) {  // the k columns found start a solve with kmax columns
+    if constexpr (sizeof(Real) == 4) {
+      // mixed path: from sm.Q, which the solver reads into its FP32 basis (in sm.W's
+      // space) before it writes sm.Q again
+      for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) sm.Q[idx] = sm.W[idx];
+      __syncthreads();
+      k = leading_eigs<Real, double>(sm, n, kmax, sm.Q, k, k, pc, kDepReseed);
+    } else {
+      for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) sm.Vr[idx] = (Real)sm.W[idx];
+      __syncthreads();
+      k = leading_eigs<Real, Real>(sm, n, kmax, sm.Vr, k, k, pc, kDepReseed);
+    }
     r = choose_rank<Real>(sm, n, k, thr, R, &met, tr);
     pc.mark(8);
     pc.count(2, 1);
