@@ -354,10 +354,11 @@ __device__ __forceinline__ void df_add_into(float &hi, float &lo, float h2, floa
 }
 
 // Gram matrix of the mode-m unfolding by TS x TS output blocks on or above the diagonal.
-// The nb (nb + 1) / 2 blocks (nb = ceil(n / TS)) are numbered row by row; with fewer
-// blocks than threads the columns of every staged chunk are split into S segments, thread
-// t owning block t mod nblk and segment t / nblk; the segments' partial sums are then added
-// into the result in segment order (a fixed order: the same sums in either launch variant).
+// The nb (nb + 1) / 2 blocks (nb = ceil(n / TS)) are numbered row by row; every block needs
+// a thread (the callers launch at least as many threads as blocks); with fewer blocks than
+// threads the columns of every staged chunk are split into S segments, thread t owning
+// block t mod nblk and segment t / nblk; the segments' partial sums are then added into
+// the result in segment order (a fixed order: the same sums in either launch variant).
 // Each chunk's loop stops at the last real column.
 template <typename Real, int TS>
 __device__ void gram_tiled(const Real *T, const int D[3], int m, Smem<Real> &sm) {
@@ -3155,7 +3156,14 @@ void split_chain(const TuckerStepParams &p, const TuckerSplitBufs &b, const Spli
     } else if (m >= 1 && p.Nmax <= 32) {  // every cell's N_m <= 32: gram_seq in a light kernel
       tucker_gram_small_kernel<Real><<<(unsigned)b.cn, kTB, z.gram_small, s>>>(p, b, m);
     } else {
-      tucker_gram_kernel<Real, TS><<<(unsigned)b.cn, kTB, z.gram, s>>>(p, b, m);
+      // engine AUTO (mixed path): second/third modes with half the threads, so that twice
+      // as many cells run per SM (their unfoldings have few columns), where every 4 x 4
+      // output block still gets a thread (gram_tiled gives each thread one block: at most
+      // 128 blocks, i.e. Nmax <= 60); the CUDA-core engine keeps the fused variant's block
+      // size, and with it the same sums
+      const int nbk = (p.Nmax + 3) / 4;
+      const int tb = (m >= 1 && p.tc_gram && nbk * (nbk + 1) / 2 <= kTB / 2) ? kTB / 2 : kTB;
+      tucker_gram_kernel<Real, TS><<<(unsigned)b.cn, tb, z.gram, s>>>(p, b, m);
     }
     T(gc, false, s);
     T(kKEig, true, s);

@@ -506,11 +506,14 @@ def test_gemm_form_assembly_many_terms(dvm, oracle_lib):
     assert out[NAT.DVM_ENGINE_AUTO][2][:, 0].max() >= 8
 
 
-@pytest.mark.parametrize("N", [(12, 10, 9), (20, 14, 11), (40, 24, 20), (64, 16, 12)])
+@pytest.mark.parametrize("N", [(12, 10, 9), (20, 14, 11), (40, 24, 20), (64, 16, 12),
+                               (20, 60, 36), (24, 64, 40)])
 def test_gemm_form_assembly_grid_shapes(dvm, oracle_lib, N):
-    """Velocity grids whose first mode pads to 16, 32, 48 and 64 rows (register tiles of
-    4, 8, 12, 16 rows a thread), with N2 N3 not a multiple of four (scalar stores, a
-    ragged last tile of columns) or spanning two tiles."""
+    """Engine AUTO on velocity grids whose first mode pads to 16, 32, 48 and 64 rows
+    (register tiles of 4, 8, 12, 16 rows a thread), with N2 N3 not a multiple of four
+    (scalar stores, a ragged last tile of columns) or spanning two tiles; and on both sides
+    of the second/third-mode Gram's half-size launch (a 60-node second mode: 120 output
+    blocks on 128 threads; a 64-node second mode: 136 blocks, the full-size launch)."""
     wl = W.cavity(nside=3, N=max(N), seed=6)
     wl.N = N
     wl.lo = tuple(-5.0 - 0.02 * n for n in N)
