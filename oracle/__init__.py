@@ -70,6 +70,9 @@ def _load():
     L.orc_dt.restype = ctypes.c_double
     L.orc_dt.argtypes = [P, ctypes.c_double]
     L.orc_step.argtypes = [P, ctypes.c_int32, ctypes.c_double, dp]
+    L.orc_step_lusgs.argtypes = [P, ctypes.c_int32, ctypes.c_double, dp]
+    L.orc_rhs.argtypes = [P, dp]
+    L.orc_lusgs_diag.argtypes = [P, ctypes.c_double, dp]
     L.orc_cell_shakhov.argtypes = [P, dp, dp, dp]
     L.orc_shakhov_from_macro.argtypes = [P, dp, dp]
     L.orc_maxwellian.argtypes = [P, ctypes.c_double, dp, ctypes.c_double, dp]
@@ -156,6 +159,25 @@ class FullGridOracle:
         r = ctypes.c_double(0.0)
         self.L.orc_step(self.h, int(nsteps), float(dt), ctypes.byref(r))
         return r.value
+
+    def step_lusgs(self, nsteps, dt):
+        """Implicit steps (linear-system equation of Section 3), one LU-SGS pass
+        each over the cells in index order; returns the last residual."""
+        r = ctypes.c_double(0.0)
+        self.L.orc_step_lusgs(self.h, int(nsteps), float(dt), ctypes.byref(r))
+        return r.value
+
+    def rhs(self):
+        """R^n of every cell: the explicit right-hand side of Algorithm 1."""
+        out = np.empty((self.n_cell,) + tuple(int(v) for v in self.wl.N))
+        self.L.orc_rhs(self.h, _dp(out))
+        return out
+
+    def lusgs_diag(self, dt):
+        """The diagonal tensors D_i of the implicit system (diagonal_term equation)."""
+        out = np.empty((self.n_cell,) + tuple(int(v) for v in self.wl.N))
+        self.L.orc_lusgs_diag(self.h, float(dt), _dp(out))
+        return out
 
     def geometry(self):
         nf = self.L.orc_num_faces(self.h)

@@ -13,7 +13,9 @@
  *               diffuse-wall / symmetry / free-stream boundary conditions;
  *   Section 3   velocity grid and quadrature, finite-volume form (ode_system),
  *               CIR upwind flux (exact-flux), explicit Euler (expl-scheme-final),
- *               Algorithm 1 (time step) and Algorithm 2 (computeJ).
+ *               Algorithm 1 (time step) and Algorithm 2 (computeJ);
+ *               the implicit scheme (linear-system, diagonal_term): one LU-SGS
+ *               pass per step over the cells in index order.
  *
  * Readings of points the paper leaves open (each is also listed with its
  * reason in the design notes):
@@ -514,10 +516,9 @@ static void conserved(const orc *P, const double *f, double U[5]) {
   for (int k = 0; k < 5; ++k) U[k] = P->w * ks_val(&s[k]);
 }
 
-/* Algorithm 1: one explicit time step (returns the residual) */
-static double one_step(orc *P, double dt) {
+/* boundary conditions: wall density from impermeability (Section 2) */
+static void set_wall_density(orc *P) {
   const int64_t nn = P->nnode;
-  /* set boundary conditions: wall density from impermeability (Section 2) */
 #pragma omp parallel for schedule(dynamic, 8)
   for (int64_t j = 0; j < P->nf; ++j) {
     orc_face *F = &P->face[j];
@@ -535,6 +536,12 @@ static double one_step(orc *P, double dt) {
         }
     P->ghost_scale[j] = -ks_val(&out) / ks_val(&in);
   }
+}
+
+/* Algorithm 1: one explicit time step (returns the residual) */
+static double one_step(orc *P, double dt) {
+  const int64_t nn = P->nnode;
+  set_wall_density(P);
   double num = 0.0, den = 0.0;
   /* cell loop: R_i = J(f_i) - sum_l sign(i,l) |A_j| / |V_i| F_j ;  f_i += dt R_i */
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : num, den)
@@ -609,5 +616,147 @@ double orc_weight(const orc *P) { return P->w; }
 /* wall densities n_w of the last step, per face (0 for non-wall faces) */
 int orc_wall_density(const orc *P, double *out) {
   for (int64_t j = 0; j < P->nf; ++j) out[j] = P->ghost_scale[j];
+  return 0;
+}
+
+/* ----------------------------------------------------------------------- */
+/* Implicit step, Section 3 (linear-system and diagonal_term equations): the
+ * right-hand side of the explicit scheme is taken at t^{n+1} and linearised,
+ *   [I/dt - dR/df] (f^{n+1} - f^n) = R^n,
+ * and the system is solved approximately by one symmetric Gauss-Seidel pass
+ * (LU-SGS) over the cells in their index order.  With e_l outward from cell i
+ * and the upwind flux xn^+ f_i + xn^- f_nb of Algorithm 1, the blocks are
+ *   diagonal    D_i  = 1/dt + nu_i + (1/(2|V_i|)) sum_l |A_l| |xi.e_l|
+ *                      (the diagonal_term equation; f^S held fixed),
+ *   off-diagonal M_ij = (|A_l| / |V_i|) (xi.e_l)^-    (interior face l to j),
+ * and boundary ghost values stay at their t^n values (they enter R^n only).
+ *   forward : for i = 0 .. nc-1   D_i g_i   = R_i - sum_{j<i} M_ij g_j
+ *   backward: for i = nc-1 .. 0   df_i      = g_i - D_i^{-1} sum_{j>i} M_ij df_j
+ *   f^{n+1} = f^n + df.
+ * Every operation is a node-by-node one, so the division by D_i is exact here
+ * (the full-grid format). */
+
+/* R^n of one cell at every node (Algorithm 1 without the Euler update) */
+static void cell_rhs(const orc *P, int64_t c, double *R) {
+  const int64_t nn = P->nnode;
+  const double *fc = P->f + c * nn;
+  double a[8];
+  macro(P, fc, a);
+  double nu = collision_nu(P, a[0], a[4]);
+  shakhov(P, a, R); /* R temporarily holds f^S */
+  int64_t idx = 0;
+  for (int i1 = 0; i1 < P->N[0]; ++i1)
+    for (int i2 = 0; i2 < P->N[1]; ++i2)
+      for (int i3 = 0; i3 < P->N[2]; ++i3, ++idx) {
+        double r = nu * (R[idx] - fc[idx]);
+        for (int l = 0; l < 6; ++l) {
+          int64_t j = P->cell_face[6 * c + l];
+          double Fj = face_flux(P, j, P->f, i1, i2, i3, idx);
+          r -= (double)P->cell_sign[6 * c + l] * P->face[j].area / P->vol[c] * Fj;
+        }
+        R[idx] = r;
+      }
+}
+
+/* the neighbour blocks of cell c on one side of it:
+ *   out = sum over interior faces l with (nb < c) == lower of M_c,nb x[nb]      */
+static void offdiag_sum(const orc *P, int64_t c, const double *x, int lower, double *out) {
+  const int64_t nn = P->nnode;
+  for (int64_t k = 0; k < nn; ++k) out[k] = 0.0;
+  for (int l = 0; l < 6; ++l) {
+    int64_t j = P->cell_face[6 * c + l];
+    const orc_face *F = &P->face[j];
+    if (F->nb < 0) continue;
+    int64_t nb = F->owner == c ? F->nb : F->owner;
+    if ((nb < c) != (lower != 0)) continue;
+    double s = (double)P->cell_sign[6 * c + l], k = F->area / P->vol[c];
+    const double *xn_ = x + nb * nn;
+    int64_t idx = 0;
+    for (int i1 = 0; i1 < P->N[0]; ++i1)
+      for (int i2 = 0; i2 < P->N[1]; ++i2)
+        for (int i3 = 0; i3 < P->N[2]; ++i3, ++idx) {
+          double xn = s * (F->e[0] * P->xi[0][i1] + F->e[1] * P->xi[1][i2] +
+                           F->e[2] * P->xi[2][i3]);
+          if (xn < 0.0) out[idx] += k * xn * xn_[idx];
+        }
+  }
+}
+
+/* the diagonal tensor D_i (diagonal_term equation) */
+static void cell_diag(const orc *P, int64_t c, double dt, double *D) {
+  double a[8];
+  macro(P, P->f + c * P->nnode, a);
+  double nu = collision_nu(P, a[0], a[4]);
+  int64_t idx = 0;
+  for (int i1 = 0; i1 < P->N[0]; ++i1)
+    for (int i2 = 0; i2 < P->N[1]; ++i2)
+      for (int i3 = 0; i3 < P->N[2]; ++i3, ++idx) {
+        double s = 0.0;
+        for (int l = 0; l < 6; ++l) {
+          const orc_face *F = &P->face[P->cell_face[6 * c + l]];
+          double xn = F->e[0] * P->xi[0][i1] + F->e[1] * P->xi[1][i2] + F->e[2] * P->xi[2][i3];
+          s += F->area * fabs(xn);
+        }
+        D[idx] = 1.0 / dt + nu + s / (2.0 * P->vol[c]);
+      }
+}
+
+static double one_step_lusgs(orc *P, double dt) {
+  const int64_t nn = P->nnode, nc = P->nc;
+  set_wall_density(P);
+  double *g = P->fnew; /* R, then g, then df */
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t c = 0; c < nc; ++c) cell_rhs(P, c, g + c * nn);
+  double *D = (double *)malloc(sizeof(double) * nn);
+  double *S = (double *)malloc(sizeof(double) * nn);
+  for (int64_t c = 0; c < nc; ++c) { /* forward sweep */
+    cell_diag(P, c, dt, D);
+    offdiag_sum(P, c, g, 1, S);
+    double *gc = g + c * nn;
+    for (int64_t k = 0; k < nn; ++k) gc[k] = (gc[k] - S[k]) / D[k];
+  }
+  for (int64_t c = nc - 1; c >= 0; --c) { /* backward sweep */
+    cell_diag(P, c, dt, D);
+    offdiag_sum(P, c, g, 0, S);
+    double *gc = g + c * nn;
+    for (int64_t k = 0; k < nn; ++k) gc[k] -= S[k] / D[k];
+  }
+  free(D);
+  free(S);
+  double num = 0.0, den = 0.0;
+  for (int64_t c = 0; c < nc; ++c) {
+    double *fc = P->f + c * nn, *dc = g + c * nn;
+    double U0[5], U1[5];
+    conserved(P, fc, U0);
+    for (int64_t k = 0; k < nn; ++k) dc[k] = fc[k] + dc[k]; /* f^{n+1} */
+    conserved(P, dc, U1);
+    for (int k = 0; k < 5; ++k) {
+      num += P->vol[c] * (U1[k] - U0[k]) * (U1[k] - U0[k]);
+      den += P->vol[c] * U0[k] * U0[k];
+    }
+  }
+  double *t = P->f;
+  P->f = P->fnew;
+  P->fnew = t;
+  return sqrt(num) / (dt * sqrt(den));
+}
+
+int orc_step_lusgs(orc *P, int32_t nsteps, double dt, double *residual) {
+  double r = 0.0;
+  for (int s = 0; s < nsteps; ++s) r = one_step_lusgs(P, dt);
+  if (residual) *residual = r;
+  return 0;
+}
+
+/* R^n of every cell (the explicit right-hand side), for the pin tests */
+int orc_rhs(orc *P, double *out) {
+  set_wall_density(P);
+  for (int64_t c = 0; c < P->nc; ++c) cell_rhs(P, c, out + c * P->nnode);
+  return 0;
+}
+
+/* D_i of every cell (diagonal_term equation), for the pin tests */
+int orc_lusgs_diag(const orc *P, double dt, double *out) {
+  for (int64_t c = 0; c < P->nc; ++c) cell_diag(P, c, dt, out + c * P->nnode);
   return 0;
 }

@@ -169,6 +169,35 @@ def shakhov_rank4(xi, a, Pr):
     return G, U
 
 
+def speed_bound(xi):
+    """The coarse bound |xi_n| <= |xi| = sqrt(xi_1^2 + xi_2^2 + xi_3^2) of every face's
+    normal speed (Section 5, xin-one-rank-approx), as a full N1 x N2 x N3 array."""
+    return np.sqrt(xi[0][:, None, None] ** 2 + xi[1][None, :, None] ** 2
+                   + xi[2][None, None, :] ** 2)
+
+
+def diag_estimate_rank1(xi, a, b):
+    """D_i^est of the implicit scheme (Section 5, diagonal_term with the bound of
+    xin-one-rank-approx): the tensor a + b |xi| with a = 1/dt + nu_i and
+    b = sum_l |A_l| / (2 |V_i|), approximated with ranks (1, 1, 1) by the truncated
+    HOSVD.  The tensor is positive, so its leading singular vectors can be taken
+    positive (Perron-Frobenius); returns three positive vectors d_a whose outer
+    product is D^est (the core is folded into d_1)."""
+    X = a + b * speed_bound(xi)
+    (G, U), _ = hosvd(X, eps=0.0, cap=1)
+    d = [U[k][:, 0] * np.sign(U[k][0, 0]) for k in range(3)]
+    g = float(np.einsum("ijk,i,j,k->", X, d[0], d[1], d[2]))   # projection onto d1 d2 d3
+    return d[0] * g, d[1], d[2]
+
+
+def divide_rank1(t, d):
+    """Element-wise division of a Tucker tensor by a rank-1 positive tensor
+    d_1 (x) d_2 (x) d_3 (Section 5, one_rank_division): each factor row i of mode a is
+    divided by d_a(i); the core and the ranks are unchanged, O(n r) work."""
+    G, U = t
+    return G, tuple(U[k] / np.asarray(d[k])[:, None] for k in range(3))
+
+
 def compression(r, N):
     """C = (r1 r2 r3 + N (r1 + r2 + r3)) / N^3 (Section 7)."""
     r1, r2, r3 = r

@@ -5,6 +5,7 @@ operations on full tensors; the rank-1 Maxwellian, Lemma 1 and the low-rank Shak
 function must equal their pointwise definitions (the Shakhov one against the C oracle's
 full-grid f^S, which is pinned separately); HOSVD must respect its error bound.
 """
+import math
 import os
 
 import numpy as np
@@ -142,3 +143,55 @@ def test_compression_ratio_formula():
     """C = (r1 r2 r3 + N (r1 + r2 + r3)) / N^3 (Section 7)."""
     assert tk.compression((1, 1, 1), 64) == (1 + 64 * 3) / 64 ** 3
     assert tk.compression((64, 64, 64), 64) == 1.0 + 3.0 / 64
+
+
+def _rand_tucker(rng, N, r):
+    G = rng.standard_normal(r)
+    U = tuple(rng.standard_normal((N[k], r[k])) for k in range(3))
+    return G, U
+
+
+def test_rank1_division_is_elementwise_division():
+    """one_rank_division (Section 5): dividing the factor rows equals dividing the
+    expanded tensor element by element, for any ranks."""
+    rng = np.random.default_rng(3)
+    for N, r in (((7, 5, 6), (3, 2, 4)), ((12, 12, 12), (5, 5, 5)), ((4, 9, 3), (1, 6, 2))):
+        t = _rand_tucker(rng, N, r)
+        d = [rng.uniform(0.3, 2.0, N[k]) for k in range(3)]
+        B = tk.full(tk.divide_rank1(t, d))
+        ref = tk.full(t) / (d[0][:, None, None] * d[1][None, :, None] * d[2][None, None, :])
+        assert tk.ranks(tk.divide_rank1(t, d)) == r
+        assert np.max(np.abs(B - ref)) < 1e-13 * np.max(np.abs(ref))
+
+
+def test_speed_bound_bounds_every_normal_speed():
+    """xin-one-rank-approx: |xi . e| <= |xi| for every unit normal e (Cauchy-Schwarz),
+    with equality on the axis planes' normals at nodes on that axis."""
+    rng = np.random.default_rng(5)
+    xi = [np.linspace(-4, 4, 8), np.linspace(-3, 5, 6), np.linspace(-6, 6, 10)]
+    S = tk.speed_bound(xi)
+    for _ in range(20):
+        e = rng.standard_normal(3)
+        e /= np.linalg.norm(e)
+        xn = (e[0] * xi[0][:, None, None] + e[1] * xi[1][None, :, None]
+              + e[2] * xi[2][None, None, :])
+        assert np.all(np.abs(xn) <= S * (1 + 1e-15))
+    brute = np.array([[[math.sqrt(a * a + b * b + c * c) for c in xi[2]] for b in xi[1]]
+                      for a in xi[0]])
+    assert np.max(np.abs(S - brute)) < 1e-14
+
+
+def test_rank1_diag_estimate_positive_and_exact_for_constants():
+    xi = [np.linspace(-5, 5, 12)] * 3
+    d = tk.diag_estimate_rank1(xi, 3.0, 0.0)        # b = 0: the constant tensor, rank 1
+    D = np.einsum("i,j,k->ijk", *d)
+    assert np.max(np.abs(D - 3.0)) < 1e-12
+    d = tk.diag_estimate_rank1(xi, 2.0, 1.5)
+    assert all(np.all(v > 0) for v in d)
+    D = np.einsum("i,j,k->ijk", *d)
+    X = 2.0 + 1.5 * tk.speed_bound(xi)
+    # best rank-1 approximation: its error is below the one of the constant fit
+    # with the mean (another rank-1 tensor), and the residual is orthogonal to D
+    err = np.linalg.norm(D - X)
+    assert err < np.linalg.norm(X - X.mean())
+    assert abs(np.sum((X - D) * D)) < 1e-10 * np.sum(D * D)
