@@ -132,10 +132,32 @@ typedef struct {
                        * assembly term by term): the two variants then
                        * agree bit for bit.  Both are accurate to FP32
                        * rounding of f^{n+1}.                              */
+  int32_t scheme;     /* time stepping (Section 3): DVM_SCHEME_EXPLICIT (0),
+                       * the explicit Euler step of Algorithm 1, or
+                       * DVM_SCHEME_LUSGS (1, full format only), the implicit
+                       * step of the linear-system equation, [I/dt - dR/df]
+                       * (f^{n+1} - f^n) = R^n, solved by one LU-SGS pass: a
+                       * forward sweep over the cells in increasing index
+                       * order, D_i g_i = R_i - sum_{j<i} M_ij g_j, then a
+                       * backward sweep in decreasing order, df_i = g_i -
+                       * D_i^{-1} sum_{j>i} M_ij df_j, with the diagonal of
+                       * the diagonal_term equation D_i = 1/dt + nu_i +
+                       * sum_l |A_l| |xi.e_l| / (2 |V_i|), evaluated as
+                       * sum_l |A_l| (xi.e_l)^+ / |V_i| (the same on a closed
+                       * cell; f^S and boundary ghosts held at t^n), and
+                       * M_ij = |A_l| (xi.e_l)^- / |V_i| for the face l shared
+                       * with cell j.  The result depends
+                       * on the cell numbering (it fixes the sweep order), not
+                       * on how the work is scheduled: cells of one wavefront
+                       * of the sweep run in parallel.  Its time step is not
+                       * bound by the explicit limit: set cfl (> 0.5) or dt.  */
 } dvm_opts;
 
 #define DVM_ENGINE_AUTO 0
 #define DVM_ENGINE_CUDA_CORES 1
+
+#define DVM_SCHEME_EXPLICIT 0
+#define DVM_SCHEME_LUSGS 1
 
 #define DVM_VARIANT_AUTO 0
 #define DVM_VARIANT_FUSED 1
@@ -404,6 +426,23 @@ int dvm_gram_tc(const float *X, int64_t ncell, int32_t n, int32_t K, double *C,
 #define DVM_FAULT_TIMEOUT 2
 #define DVM_FAULT_ADMIT 3
 int dvm_fault_inject(int32_t kind, int64_t count);
+
+/* The schedule of one sweep of the implicit LU-SGS step (DVM_SCHEME_LUSGS; Section 3,
+ * linear-system equation), a host computation with no device work.  The forward
+ * sweep visits the cells in increasing index order and the backward sweep in
+ * decreasing order; a cell's wavefront is 0 if none of its neighbours comes before
+ * it in the sweep, else one more than the largest wavefront of those that do.  The
+ * cells of one wavefront depend only on earlier ones, so the step updates them in
+ * parallel (one launch per wavefront) with the result of the sequential sweep.
+ *   nb       host, [n_cell][6] neighbour cell across each face, -1 on the boundary
+ *            (each entry -1 or in [0, n_cell), else INVALID_ARG)
+ *   forward  1 forward sweep, 0 backward sweep
+ *   order    host, [n_cell] out: the cells by wavefront, increasing index within one
+ *   offsets  host, [n_cell + 1] out: wavefront w is order[offsets[w] .. offsets[w+1])
+ *   n_waves  out: the number of wavefronts (offsets[0 .. n_waves] are written)
+ * Errors: INVALID_ARG (n_cell < 0, null pointers, a neighbour out of range). */
+int dvm_lusgs_wavefronts(int64_t n_cell, const int32_t *nb, int32_t forward, int32_t *order,
+                         int64_t *offsets, int64_t *n_waves);
 
 void dvm_destroy(dvm_ctx *ctx);
 

@@ -11,5 +11,5 @@ from .api import (  # noqa: F401
     dvm_get_num_faces, dvm_get_ranks, dvm_get_step_count, dvm_init_f, dvm_init_maxwellian,
     dvm_last_error, dvm_load, dvm_memory, dvm_moments, dvm_save, dvm_set_bc,
     dvm_set_kernel_timing, dvm_solve, dvm_step, dvm_fault_inject, dvm_server_cancel,
-    dvm_gram_tc, dvm_init_tucker_device,
+    dvm_gram_tc, dvm_init_tucker_device, dvm_lusgs_wavefronts,
 )

@@ -58,7 +58,8 @@ class dvm_opts(ctypes.Structure):
                 ("rank_cap", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("cfl", ctypes.c_double), ("dt", ctypes.c_double),
                 ("cuda_stream", ctypes.c_void_p), ("variant", ctypes.c_int32),
-                ("max_chunk", ctypes.c_int64), ("engine", ctypes.c_int32)]
+                ("max_chunk", ctypes.c_int64), ("engine", ctypes.c_int32),
+                ("scheme", ctypes.c_int32)]
 
 
 class dvm_request(ctypes.Structure):
@@ -73,6 +74,7 @@ class dvm_request(ctypes.Structure):
  DVM_REQ_CANCELLED) = range(6)
 DVM_FAULT_NONE, DVM_FAULT_ALLOC, DVM_FAULT_TIMEOUT, DVM_FAULT_ADMIT = range(4)
 DVM_ENGINE_AUTO, DVM_ENGINE_CUDA_CORES = range(2)
+DVM_SCHEME_EXPLICIT, DVM_SCHEME_LUSGS = range(2)
 
 _P = ctypes.c_void_p
 _PP = ctypes.POINTER(ctypes.c_void_p)
@@ -115,6 +117,8 @@ SIGNATURES = {
     "dvm_server_error": (ctypes.c_char_p, [_P, ctypes.c_int64]),
     "dvm_server_cancel": (ctypes.c_int, [_P, ctypes.c_int64]),
     "dvm_fault_inject": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64]),
+    "dvm_lusgs_wavefronts": (ctypes.c_int, [ctypes.c_int64, _c_i32p, ctypes.c_int32, _c_i32p,
+                                            _c_i64p, _c_i64p]),
     "dvm_gram_tc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "dvm_server_destroy": (None, [_P]),

@@ -39,7 +39,7 @@ class Handle:
 
 def dvm_create(xyz, hex8, bface, bface_group, N, lo, hi, Pr, omega, Kn, format=0,
                precision=0, rank_cap=8, tol=1e-5, cfl=0.5, dt=0.0, stream=0, variant=0,
-               max_chunk=0, engine=0):
+               max_chunk=0, engine=0, scheme=0):
     L = N_lib()
     xyz = np.ascontiguousarray(xyz, dtype=np.float64)
     hex8 = np.ascontiguousarray(hex8, dtype=np.int64)
@@ -53,7 +53,7 @@ def dvm_create(xyz, hex8, bface, bface_group, N, lo, hi, Pr, omega, Kn, format=0
     gas = _n.dvm_gas(float(Pr), float(omega), float(Kn))
     opts = _n.dvm_opts(int(format), int(precision), int(rank_cap), float(tol), float(cfl),
                       float(dt), ctypes.c_void_p(int(stream)), int(variant), int(max_chunk),
-                      int(engine))
+                      int(engine), int(scheme))
     out = ctypes.c_void_p()
     _n.check(L.dvm_create(ctypes.byref(out), ctypes.byref(mesh), ctypes.byref(vg),
                          ctypes.byref(gas), ctypes.byref(opts)), "dvm_create")
@@ -253,14 +253,16 @@ class Solver:
 
     def __init__(self, wl, format=_n.DVM_FORMAT_FULL, precision=_n.DVM_PREC_FP64,
                  rank_cap=None, tol=None, dt=0.0, stream=0, init=True,
-                 variant=_n.DVM_VARIANT_AUTO, max_chunk=0, engine=_n.DVM_ENGINE_AUTO):
+                 variant=_n.DVM_VARIANT_AUTO, max_chunk=0, engine=_n.DVM_ENGINE_AUTO,
+                 scheme=_n.DVM_SCHEME_EXPLICIT, cfl=None):
         self.wl = wl
         self.h = dvm_create(wl.xyz, wl.hex8, wl.bface, wl.bgroup, wl.N, wl.lo, wl.hi, wl.Pr,
                             wl.omega, wl.Kn, format=format, precision=precision,
                             rank_cap=wl.rank_cap if rank_cap is None else rank_cap,
-                            tol=wl.tol if tol is None else tol, cfl=wl.cfl, dt=dt,
+                            tol=wl.tol if tol is None else tol,
+                            cfl=wl.cfl if cfl is None else cfl, dt=dt,
                             stream=stream, variant=variant, max_chunk=max_chunk,
-                            engine=engine)
+                            engine=engine, scheme=scheme)
         for g, t, p in wl.bcs:
             dvm_set_bc(self.h, g, t, p)
         if init:
@@ -313,7 +315,8 @@ def _request(wl, format, precision, rank_cap, tol, res_tol, max_steps, check_eve
                              (ctypes.c_double * 3)(*[float(v) for v in wl.hi]))
     req.gas = _n.dvm_gas(float(wl.Pr), float(wl.omega), float(wl.Kn))
     req.opts = _n.dvm_opts(int(format), int(precision), int(rank_cap), float(tol), float(wl.cfl),
-                           0.0, None, _n.DVM_VARIANT_AUTO, 0, _n.DVM_ENGINE_AUTO)
+                           0.0, None, _n.DVM_VARIANT_AUTO, 0, _n.DVM_ENGINE_AUTO,
+                           _n.DVM_SCHEME_EXPLICIT)
     req.n_bc = len(wl.bcs)
     req.bc_group, req.bc_type, req.bc_params = _i32p(groups), _i32p(types), _dp(params)
     req.n0, req.u0, req.T0 = _dp(n0), _dp(u0), _dp(T0)
@@ -434,3 +437,17 @@ def dvm_gram_tc(x_ptr, ncell, n, K, c_ptr, status_ptr, stream=0):
 def dvm_fault_inject(kind, count=0):
     """Arm a host-side injected failure (``_native.DVM_FAULT_*``); see include/dvm.h."""
     return _n.check(N_lib().dvm_fault_inject(int(kind), int(count)), "dvm_fault_inject")
+
+
+def dvm_lusgs_wavefronts(nb, forward=True):
+    """Schedule of one sweep of the implicit LU-SGS step (host only): ``nb`` is the
+    [n_cell, 6] neighbour table (-1 on the boundary).  Returns (order, offsets): the
+    cells by wavefront and the wavefront boundaries; see include/dvm.h."""
+    nb = np.ascontiguousarray(nb, dtype=np.int32).reshape(-1, 6)
+    n = nb.shape[0]
+    order = np.empty(n, dtype=np.int32)
+    off = np.empty(n + 1, dtype=np.int64)
+    nw = ctypes.c_int64(0)
+    _n.check(N_lib().dvm_lusgs_wavefronts(n, _i32p(nb), 1 if forward else 0, _i32p(order),
+                                          _i64p(off), ctypes.byref(nw)), "dvm_lusgs_wavefronts")
+    return order, off[:nw.value + 1].copy()

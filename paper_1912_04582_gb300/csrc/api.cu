@@ -191,6 +191,14 @@ int dvm_create(dvm_ctx **out, const dvm_mesh *mesh, const dvm_vgrid *vg, const d
     set_error("dvm_create: engine must be DVM_ENGINE_AUTO or DVM_ENGINE_CUDA_CORES");
     return DVM_ERR_INVALID_ARG;
   }
+  if (opts->scheme != DVM_SCHEME_EXPLICIT && opts->scheme != DVM_SCHEME_LUSGS) {
+    set_error("dvm_create: scheme must be DVM_SCHEME_EXPLICIT or DVM_SCHEME_LUSGS");
+    return DVM_ERR_INVALID_ARG;
+  }
+  if (opts->scheme == DVM_SCHEME_LUSGS && opts->format != DVM_FORMAT_FULL) {
+    set_error("dvm_create: the LU-SGS scheme is implemented for the full format only");
+    return DVM_ERR_UNSUPPORTED;
+  }
   if (opts->max_chunk < 0) {
     set_error("dvm_create: max_chunk must be >= 0");
     return DVM_ERR_INVALID_ARG;
@@ -502,6 +510,24 @@ void dvm_destroy(dvm_ctx *C) {
   if (!C) return;
   ctx_free(C);
   delete C;
+}
+
+int dvm_lusgs_wavefronts(int64_t n_cell, const int32_t *nb, int32_t forward, int32_t *order,
+                         int64_t *offsets, int64_t *n_waves) {
+  if (n_cell < 0 || n_cell > INT32_MAX || (n_cell > 0 && (!nb || !order)) || !offsets || !n_waves) {
+    set_error("dvm_lusgs_wavefronts: bad arguments");
+    return DVM_ERR_INVALID_ARG;
+  }
+  for (int64_t k = 0; k < 6 * n_cell; ++k)
+    if (nb[k] < -1 || nb[k] >= n_cell) {
+      set_error("dvm_lusgs_wavefronts: neighbour index out of range");
+      return DVM_ERR_INVALID_ARG;
+    }
+  std::vector<int64_t> off;
+  lusgs_wavefronts(n_cell, nb, forward != 0, order, off);
+  for (size_t w = 0; w < off.size(); ++w) offsets[w] = off[w];
+  *n_waves = (int64_t)off.size() - 1;
+  return DVM_OK;
 }
 
 }  // extern "C"

@@ -82,6 +82,15 @@ int ctx_alloc_state(dvm_ctx *C) {
   if (C->opts.format == DVM_FORMAT_FULL) {
     const size_t fb = sizeof(double) * (size_t)nc * (size_t)C->nn;
     for (int k = 0; k < 2; ++k) CTX_MALLOC(C->d_f[k], fb);
+    if (C->opts.scheme == DVM_SCHEME_LUSGS) {
+      std::vector<int32_t> order(2 * nc);
+      for (int s = 0; s < 2; ++s)
+        lusgs_wavefronts(nc, C->slot_nb.data(), s == 0, order.data() + s * nc, C->wave_off[s]);
+      CTX_MALLOC(C->d_wave, sizeof(int32_t) * 2 * nc);
+      DVM_CUDA_TRY(cudaMemcpy(C->d_wave, order.data(), sizeof(int32_t) * 2 * nc,
+                              cudaMemcpyHostToDevice));
+      CTX_MALLOC(C->d_dtnu, sizeof(double) * nc);
+    }
   } else {
     int rc = tucker_alloc(C);
     if (rc != DVM_OK) return rc;
@@ -137,7 +146,7 @@ void ctx_free(dvm_ctx *C) {
   if (C->tucker) tucker_free(C);
   void *ptrs[] = {C->d_xi[0], C->d_xi[1], C->d_xi[2], C->d_vol, C->d_slot, C->d_ghost,
                   C->d_f[0], C->d_f[1], C->d_sums[0], C->d_sums[1], C->d_uref, C->d_respart,
-                  C->d_res, C->d_macro, C->d_flag};
+                  C->d_res, C->d_macro, C->d_flag, C->d_wave, C->d_dtnu};
   for (void *p : ptrs)
     if (p) cudaFree(p);
 }
@@ -430,6 +439,60 @@ static int read_residual(dvm_ctx *C, double *residual_out) {
   return DVM_OK;
 }
 
+// Wavefronts of one LU-SGS sweep over the cells in increasing (forward) or
+// decreasing (backward) index order: a cell's wavefront is one more than the
+// largest wavefront of its neighbours that come before it in the sweep, so the
+// cells of one wavefront depend only on earlier wavefronts and can be updated
+// in parallel with the result of the sequential sweep.  order[] lists the cells
+// by wavefront (increasing index within one), off[w] .. off[w+1] is wavefront w.
+void lusgs_wavefronts(int64_t nc, const int32_t *nb, bool forward, int32_t *order,
+                      std::vector<int64_t> &off) {
+  std::vector<int32_t> wave(nc, 0);
+  int32_t nw = 0;
+  for (int64_t k = 0; k < nc; ++k) {
+    const int64_t i = forward ? k : nc - 1 - k;
+    int32_t w = 0;
+    for (int l = 0; l < 6; ++l) {
+      const int64_t j = nb[6 * i + l];
+      if (j >= 0 && (forward ? j < i : j > i)) w = std::max(w, wave[j] + 1);
+    }
+    wave[i] = w;
+    nw = std::max(nw, w + 1);
+  }
+  off.assign((size_t)nw + 1, 0);
+  for (int64_t i = 0; i < nc; ++i) off[wave[i] + 1]++;
+  for (int32_t w = 0; w < nw; ++w) off[w + 1] += off[w];
+  std::vector<int64_t> pos(off.begin(), off.end() - 1);
+  for (int64_t i = 0; i < nc; ++i) order[pos[wave[i]]++] = (int32_t)i;
+}
+
+// One implicit step (LU-SGS): right-hand side, forward and backward sweeps by
+// wavefront, then f^{n+1} = f^n + df with its moment sums.
+static void lusgs_step(dvm_ctx *C, FullParams &P) {
+  const LaunchTimer lt = C->timer();
+  lt(kKFullStep, true, C->stream);
+  P.dtnu = C->d_dtnu;
+  launch_full_rhs(P, C->stream);
+  LusgsParams L{};
+  L.g = P.fnew;
+  L.dtnu = C->d_dtnu;
+  L.slot = C->d_slot;
+  for (int a = 0; a < 3; ++a) L.xi[a] = C->d_xi[a];
+  L.N1 = C->N[0];
+  L.N2 = C->N[1];
+  L.N3 = C->N[2];
+  L.all_axis = C->all_axis ? 1 : 0;
+  for (int s = 0; s < 2; ++s) {
+    const std::vector<int64_t> &off = C->wave_off[s];
+    for (size_t w = 0; w + 1 < off.size(); ++w) {
+      L.cells = C->d_wave + s * C->nc + off[w];
+      launch_lusgs_sweep(L, (int)(off[w + 1] - off[w]), s == 0, C->stream);
+    }
+  }
+  launch_lusgs_apply(P, C->stream);
+  lt(kKFullStep, false, C->stream);
+}
+
 // A new state starts with no device error recorded (the flag is sticky until then).
 int ctx_clear_flag(dvm_ctx *C) {
   DVM_CUDA_TRY(cudaMemsetAsync(C->d_flag, 0, sizeof(int) * 4, C->stream));
@@ -469,10 +532,14 @@ int ctx_step(dvm_ctx *C, int32_t nsteps, double *residual_out) {
     P.fnew = C->d_f[1 - C->cur];
     P.sums = C->d_sums[C->cur];
     P.sums_new = C->d_sums[1 - C->cur];
-    const LaunchTimer lt = C->timer();
-    lt(kKFullStep, true, C->stream);
-    launch_full_step(P, C->stream);
-    lt(kKFullStep, false, C->stream);
+    if (C->opts.scheme == DVM_SCHEME_LUSGS) {
+      lusgs_step(C, P);
+    } else {
+      const LaunchTimer lt = C->timer();
+      lt(kKFullStep, true, C->stream);
+      launch_full_step(P, C->stream);
+      lt(kKFullStep, false, C->stream);
+    }
     C->cur = 1 - C->cur;
     C->steps++;
   }

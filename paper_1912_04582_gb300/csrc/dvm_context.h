@@ -60,6 +60,12 @@ struct dvm_ctx {
 
   TuckerState *tucker = nullptr;
 
+  // implicit full-format step (LU-SGS): the cells of the forward sweep's
+  // wavefronts, then the backward sweep's, in launch order; per-cell dt nu
+  int32_t *d_wave = nullptr;         // [2][nc]
+  std::vector<int64_t> wave_off[2];  // wavefront w of sweep s: [wave_off[s][w], wave_off[s][w+1])
+  double *d_dtnu = nullptr;          // [nc]
+
   // optional per-launch event timing (dvm_set_kernel_timing)
   struct Timing {
     bool on = false;
@@ -92,6 +98,9 @@ int ctx_save(dvm_ctx *C, const char *path);
 int ctx_load(dvm_ctx *C, const char *path);
 int ctx_malloc(dvm_ctx *C, void **p, size_t bytes);
 int ctx_finalize_dt_from_macro(dvm_ctx *C, const std::vector<double> &macro);
+// wavefronts of one LU-SGS sweep (see dvm_lusgs_wavefronts)
+void lusgs_wavefronts(int64_t nc, const int32_t *nb, bool forward, int32_t *order,
+                      std::vector<int64_t> &off);
 
 namespace dvm {
 int build_topology(dvm_ctx *C, const dvm_mesh *m);

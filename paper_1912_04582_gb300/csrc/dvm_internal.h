@@ -67,6 +67,19 @@ struct FullParams {
   double w;              // quadrature weight
   double dt;
   double Pr, omega, delta;  // delta = sqrt(pi) / (2 Kn)
+  double *dtnu;          // [nc] dt nu of f^n (written by the implicit step's right-hand side)
+};
+
+// One wavefront of an LU-SGS sweep of the implicit full-grid step.
+struct LusgsParams {
+  double *g;             // [nc][nn] dt R^n before the forward sweep, the increment after
+                         // the backward sweep
+  const double *dtnu;    // [nc] dt nu of f^n
+  const SlotDev *slot;   // [nc][6]
+  const double *xi[3];
+  const int32_t *cells;  // the cells of this wavefront
+  int N1, N2, N3;
+  int all_axis;
 };
 
 // moments-only launch (initialisation / reference velocity refresh)
@@ -81,6 +94,11 @@ struct MomentParams {
 };
 
 void launch_full_step(const FullParams &p, cudaStream_t s);
+// implicit step (LU-SGS): dt R^n into p.fnew and dt nu into p.dtnu; one sweep
+// wavefront; f^{n+1} = f^n + df into p.fnew with the moment sums and residual parts
+void launch_full_rhs(const FullParams &p, cudaStream_t s);
+void launch_lusgs_sweep(const LusgsParams &p, int ncell, bool forward, cudaStream_t s);
+void launch_lusgs_apply(const FullParams &p, cudaStream_t s);
 void launch_full_moments(const MomentParams &p, cudaStream_t s);
 void launch_macro_from_sums(const double *sums, double *macro, int64_t nc, double w,
                             cudaStream_t s);

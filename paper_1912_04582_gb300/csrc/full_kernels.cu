@@ -75,8 +75,10 @@ __device__ __forceinline__ void fold_column(double (&acc)[kRawSums], double P0, 
 }
 
 // ------------------------------------------------------------------------
-// Fused explicit step: f^{n+1} and the moment sums of f^{n+1}.
-template <int B, bool ALL_AXIS>
+// Fused explicit step: f^{n+1} and the moment sums of f^{n+1}.  With kIncr the
+// kernel writes the increment dt R^n of the explicit scheme instead (the
+// right-hand side of the implicit step) and the cell's dt nu, without moments.
+template <int B, bool ALL_AXIS, bool kIncr>
 __global__ void __launch_bounds__(B) full_step_kernel(const FullParams P) {
   extern __shared__ double tab[];
   __shared__ SlotDev s_slot[6];
@@ -127,6 +129,7 @@ __global__ void __launch_bounds__(B) full_step_kernel(const FullParams P) {
     s_par[9] = 1.6 * (1.0 - P.Pr) / (m.n * m.T * m.T);  // Shakhov A (R_g = 1/2, m = 1)
     s_par[10] = cbrt(m.n) / sqrt(kPi * m.T);            // per-axis Maxwellian amplitude
     s_par[11] = P.dt * nu;
+    if (kIncr) P.dtnu[c] = s_par[11];
   }
   __syncthreads();
 
@@ -144,7 +147,7 @@ __global__ void __launch_bounds__(B) full_step_kernel(const FullParams P) {
     tV2[i] = v * v;
     tV3[i] = v * v * v;
     tX1[i] = x;
-    double c0 = 1.0 - dtnu;
+    double c0 = (kIncr ? 0.0 : 1.0) - dtnu;
 #pragma unroll
     for (int l = 0; l < 6; ++l) {
       const SlotDev &sl = s_slot[l];
@@ -247,6 +250,7 @@ __global__ void __launch_bounds__(B) full_step_kernel(const FullParams P) {
       }
       const double fn = fma(c0, fc, a);
       fout[off + p] = fn;
+      if (kIncr) continue;
       P0 += fn;
       P1 = fma(tV1[i1], fn, P1);
       P2 = fma(tV2[i1], fn, P2);
@@ -263,10 +267,12 @@ __global__ void __launch_bounds__(B) full_step_kernel(const FullParams P) {
         }
       }
     }
+    if (kIncr) continue;
     fold_column(acc, P0, P1, P2, P3, v2, v3);
 #pragma unroll
     for (int l = 0; l < 6; ++l) acc[13 + l] += O[l] + ow[l] * P0;
   }
+  if (kIncr) return;
 
   warp_block_reduce<B>(acc, s_red, s_tot);
 
@@ -456,12 +462,209 @@ size_t step_smem_bytes(int N1, int N2, int N3) {
 }
 
 template <int B>
-void launch_step_B(const FullParams &p, bool all_axis, cudaStream_t s) {
+void launch_step_B(const FullParams &p, bool all_axis, bool incr, cudaStream_t s) {
   const size_t smem = step_smem_bytes(p.N1, p.N2, p.N3);
-  if (all_axis)
-    full_step_kernel<B, true><<<(unsigned)p.nc, B, smem, s>>>(p);
-  else
-    full_step_kernel<B, false><<<(unsigned)p.nc, B, smem, s>>>(p);
+  if (incr) {
+    if (all_axis)
+      full_step_kernel<B, true, true><<<(unsigned)p.nc, B, smem, s>>>(p);
+    else
+      full_step_kernel<B, false, true><<<(unsigned)p.nc, B, smem, s>>>(p);
+  } else if (all_axis) {
+    full_step_kernel<B, true, false><<<(unsigned)p.nc, B, smem, s>>>(p);
+  } else {
+    full_step_kernel<B, false, false><<<(unsigned)p.nc, B, smem, s>>>(p);
+  }
+}
+
+// ------------------------------------------------------------------------
+// LU-SGS sweeps of the implicit step (Section 3, linear-system equation),
+// scaled by dt: with c_l = dt |A_l| / |V_i| and e_l outward from cell i,
+//   D~_i(xi) = 1 + dt nu_i + sum_l c_l (xi.e_l)^+      (all six faces),
+//   M~_l(xi) = c_l (xi.e_l)^-                           (interior face l to cell j),
+//   forward : g_i  = (g_i - sum_{l: j<i} M~_l g_j) / D~_i   (g_i = dt R_i on entry)
+//   backward: df_i = g_i - (sum_{l: j>i} M~_l df_j) / D~_i
+// One CTA per cell of one wavefront: every neighbour it reads belongs to an
+// earlier wavefront of the same sweep, so the launch order of the wavefronts
+// reproduces the sequential sweep exactly.  Thread layout and tables as in the
+// explicit step: columns p = (i2, i3) per thread, i1 walked, axis-1 face
+// weights in shared memory.
+template <int B, bool ALL_AXIS, bool FWD>
+__global__ void __launch_bounds__(B) lusgs_sweep_kernel(const LusgsParams P) {
+  extern __shared__ double tab[];
+  __shared__ SlotDev s_slot[6];
+  __shared__ int s_act;
+  const int64_t c = P.cells[blockIdx.x];
+  const int tid = threadIdx.x;
+  const int N1 = P.N1, N2 = P.N2, N3 = P.N3;
+  const int NP = N2 * N3;
+  const int64_t nn = (int64_t)N1 * NP;
+  double *tD1 = tab;        // [N1] 1 + dt nu + sum_{axis-1 faces} c max(s xi1, 0)
+  double *tX1 = tD1 + N1;   // [N1] xi1
+  double *tM = tX1 + N1;    // [6][N1] c min(s xi1, 0) of axis-1 faces
+
+  if (tid < 6) s_slot[tid] = P.slot[c * 6 + tid];
+  __syncthreads();
+  if (tid == 0) {
+    int m = 0;
+    for (int l = 0; l < 6; ++l) {
+      const SlotDev &sl = s_slot[l];
+      if (sl.kind == kInterior && (FWD ? (int64_t)sl.src < c : (int64_t)sl.src > c)) m |= 1 << l;
+    }
+    s_act = m;
+  }
+  const double d0 = 1.0 + P.dtnu[c];
+  for (int i = tid; i < N1; i += B) {
+    const double x = P.xi[0][i];
+    double d = d0;
+#pragma unroll
+    for (int l = 0; l < 6; ++l) {
+      const SlotDev &sl = s_slot[l];
+      double m = 0.0;
+      if (sl.axis == 0) {
+        const double sx = sl.sgn * x;
+        d = fma(sl.c, fmax(sx, 0.0), d);
+        m = sl.c * fmin(sx, 0.0);
+      }
+      tM[l * N1 + i] = m;
+    }
+    tD1[i] = d;
+    tX1[i] = x;
+  }
+  __syncthreads();
+  const int act = s_act;
+
+  double *__restrict__ gc = P.g + c * nn;
+  for (int p = tid; p < NP; p += B) {
+    const int i2 = p / N3, i3 = p - i2 * N3;
+    const double x2 = P.xi[1][i2], x3 = P.xi[2][i3];
+    double D23 = 0.0;
+    double pm[6];  // axis-2/3 faces: M~ weight; generic faces: e2 xi2 + e3 xi3
+    const double *src[6];
+#pragma unroll
+    for (int l = 0; l < 6; ++l) {
+      const SlotDev &sl = s_slot[l];
+      pm[l] = 0.0;
+      if (sl.axis == 1 || sl.axis == 2) {
+        const double sx = sl.sgn * (sl.axis == 1 ? x2 : x3);
+        D23 = fma(sl.c, fmax(sx, 0.0), D23);
+        pm[l] = sl.c * fmin(sx, 0.0);
+      } else if (!ALL_AXIS && sl.axis < 0) {
+        pm[l] = sl.e[1] * x2 + sl.e[2] * x3;
+      }
+      src[l] = ((act >> l) & 1) ? P.g + (int64_t)sl.src * nn + p : gc + p;
+    }
+    for (int i1 = 0; i1 < N1; ++i1) {
+      const int64_t off = (int64_t)i1 * NP;
+      double D = tD1[i1] + D23;
+      double S = 0.0;
+#pragma unroll
+      for (int l = 0; l < 6; ++l) {
+        const SlotDev &sl = s_slot[l];
+        const bool on = (act >> l) & 1;
+        if (sl.axis == 0) {
+          if (on) S = fma(tM[l * N1 + i1], src[l][off], S);
+        } else if (ALL_AXIS || sl.axis > 0) {
+          if (on) S = fma(pm[l], src[l][off], S);
+        } else {
+          const double x = sl.c * fma(sl.e[0], tX1[i1], pm[l]);
+          D += fmax(x, 0.0);
+          if (on) S = fma(fmin(x, 0.0), src[l][off], S);
+        }
+      }
+      const double g = gc[off + p];
+      gc[off + p] = FWD ? (g - S) / D : g - S / D;
+    }
+  }
+}
+
+// f^{n+1} = f^n + df (in place over df) and the moment sums of f^{n+1} about the
+// cell's velocity u^n, the wall outflow sums and the residual parts, as in the
+// epilogue of the explicit step.
+template <int B>
+__global__ void __launch_bounds__(B) lusgs_apply_kernel(const FullParams P) {
+  extern __shared__ double tab[];
+  __shared__ SlotDev s_slot[6];
+  __shared__ double s_red[B / 32][kRawSums];
+  __shared__ double s_tot[kRawSums];
+  __shared__ double s_u[3];
+  const int64_t c = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int N1 = P.N1, N2 = P.N2, N3 = P.N3;
+  const int NP = N2 * N3;
+  const int64_t nn = (int64_t)N1 * NP;
+  double *tV1 = tab, *tV2 = tV1 + N1, *tV3 = tV2 + N1, *tX1 = tV3 + N1;
+  const double *S = P.sums + c * kSums;
+  if (tid < 6) s_slot[tid] = P.slot[c * 6 + tid];
+  if (tid == 0) {
+    CellMacro m;
+    macro_from_sums(S, P.w, m);
+    s_u[0] = m.u[0];
+    s_u[1] = m.u[1];
+    s_u[2] = m.u[2];
+  }
+  __syncthreads();
+  const double r0 = s_u[0], r1 = s_u[1], r2 = s_u[2];
+  for (int i = tid; i < N1; i += B) {
+    const double x = P.xi[0][i], v = x - r0;
+    tV1[i] = v;
+    tV2[i] = v * v;
+    tV3[i] = v * v * v;
+    tX1[i] = x;
+  }
+  __syncthreads();
+  double acc[kRawSums];
+#pragma unroll
+  for (int k = 0; k < kRawSums; ++k) acc[k] = 0.0;
+  const double *__restrict__ fc = P.f + c * nn;
+  double *__restrict__ fo = P.fnew + c * nn;
+  for (int p = tid; p < NP; p += B) {
+    const int i2 = p / N3, i3 = p - i2 * N3;
+    const double x2 = P.xi[1][i2], x3 = P.xi[2][i3];
+    double P0 = 0.0, P1 = 0.0, P2 = 0.0, P3 = 0.0;
+    double O[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int i1 = 0; i1 < N1; ++i1) {
+      const int64_t off = (int64_t)i1 * NP + p;
+      const double g = __ldg(fc + off) + fo[off];
+      fo[off] = g;
+      P0 += g;
+      P1 = fma(tV1[i1], g, P1);
+      P2 = fma(tV2[i1], g, P2);
+      P3 = fma(tV3[i1], g, P3);
+#pragma unroll
+      for (int l = 0; l < 6; ++l) {
+        const SlotDev &sl = s_slot[l];
+        if (sl.kind == kWall) {
+          const double x = sl.e[0] * tX1[i1] + sl.e[1] * x2 + sl.e[2] * x3;
+          O[l] = fma(fmax(x, 0.0), g, O[l]);
+        }
+      }
+    }
+    fold_column(acc, P0, P1, P2, P3, x2 - r1, x3 - r2);
+#pragma unroll
+    for (int l = 0; l < 6; ++l) acc[13 + l] += O[l];
+  }
+  warp_block_reduce<B>(acc, s_red, s_tot);
+  if (tid == 0) {
+    double *Sn = P.sums_new + c * kSums;
+    Sn[0] = r0;
+    Sn[1] = r1;
+    Sn[2] = r2;
+    for (int k = 0; k < kRawSums; ++k) Sn[3 + k] = s_tot[k];
+    Sn[22] = 0.0;
+    Sn[23] = 0.0;
+    if (P.respart) {
+      double U0[5], U1[5];
+      conserved_from_sums(S, P.w, U0);
+      conserved_from_sums(Sn, P.w, U1);
+      double num = 0.0, den = 0.0;
+      for (int k = 0; k < 5; ++k) {
+        num += (U1[k] - U0[k]) * (U1[k] - U0[k]);
+        den += U0[k] * U0[k];
+      }
+      P.respart[2 * c] = P.vol[c] * num;
+      P.respart[2 * c + 1] = P.vol[c] * den;
+    }
+  }
 }
 
 }  // namespace
@@ -476,9 +679,45 @@ static int pick_block(int NP) {
 void launch_full_step(const FullParams &p, cudaStream_t s) {
   const bool all_axis = p.all_axis != 0;
   switch (pick_block(p.N2 * p.N3)) {
-    case 256: launch_step_B<256>(p, all_axis, s); break;
-    case 128: launch_step_B<128>(p, all_axis, s); break;
-    default: launch_step_B<64>(p, all_axis, s); break;
+    case 256: launch_step_B<256>(p, all_axis, false, s); break;
+    case 128: launch_step_B<128>(p, all_axis, false, s); break;
+    default: launch_step_B<64>(p, all_axis, false, s); break;
+  }
+}
+
+void launch_full_rhs(const FullParams &p, cudaStream_t s) {
+  const bool all_axis = p.all_axis != 0;
+  switch (pick_block(p.N2 * p.N3)) {
+    case 256: launch_step_B<256>(p, all_axis, true, s); break;
+    case 128: launch_step_B<128>(p, all_axis, true, s); break;
+    default: launch_step_B<64>(p, all_axis, true, s); break;
+  }
+}
+
+template <int B, bool FWD>
+static void launch_sweep_B(const LusgsParams &p, int ncell, cudaStream_t s) {
+  const size_t smem = sizeof(double) * 8 * (size_t)p.N1;
+  if (p.all_axis)
+    lusgs_sweep_kernel<B, true, FWD><<<(unsigned)ncell, B, smem, s>>>(p);
+  else
+    lusgs_sweep_kernel<B, false, FWD><<<(unsigned)ncell, B, smem, s>>>(p);
+}
+
+void launch_lusgs_sweep(const LusgsParams &p, int ncell, bool forward, cudaStream_t s) {
+  if (ncell <= 0) return;
+  switch (pick_block(p.N2 * p.N3)) {
+    case 256: forward ? launch_sweep_B<256, true>(p, ncell, s) : launch_sweep_B<256, false>(p, ncell, s); break;
+    case 128: forward ? launch_sweep_B<128, true>(p, ncell, s) : launch_sweep_B<128, false>(p, ncell, s); break;
+    default: forward ? launch_sweep_B<64, true>(p, ncell, s) : launch_sweep_B<64, false>(p, ncell, s); break;
+  }
+}
+
+void launch_lusgs_apply(const FullParams &p, cudaStream_t s) {
+  const size_t smem = sizeof(double) * 4 * (size_t)p.N1;
+  switch (pick_block(p.N2 * p.N3)) {
+    case 256: lusgs_apply_kernel<256><<<(unsigned)p.nc, 256, smem, s>>>(p); break;
+    case 128: lusgs_apply_kernel<128><<<(unsigned)p.nc, 128, smem, s>>>(p); break;
+    default: lusgs_apply_kernel<64><<<(unsigned)p.nc, 64, smem, s>>>(p); break;
   }
 }
 
