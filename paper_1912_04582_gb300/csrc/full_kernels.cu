@@ -483,98 +483,46 @@ void launch_step_B(const FullParams &p, bool all_axis, bool incr, cudaStream_t s
 //   M~_l(xi) = c_l (xi.e_l)^-                           (interior face l to cell j),
 //   forward : g_i  = (g_i - sum_{l: j<i} M~_l g_j) / D~_i   (g_i = dt R_i on entry)
 //   backward: df_i = g_i - (sum_{l: j>i} M~_l df_j) / D~_i
-// One CTA per cell of one wavefront: every neighbour it reads belongs to an
-// earlier wavefront of the same sweep, so the launch order of the wavefronts
-// reproduces the sequential sweep exactly.  Thread layout and tables as in the
-// explicit step: columns p = (i2, i3) per thread, i1 walked, axis-1 face
-// weights in shared memory.
+// Every node is independent within a sweep, so a CTA takes B consecutive nodes
+// (i2, i3) of one row i1 of one cell of the wavefront: grid (cells, N1 x column
+// blocks), coalesced loads of the cell's and its neighbours' rows.  Every
+// neighbour a cell reads belongs to an earlier wavefront of the same sweep, so
+// the launch order of the wavefronts reproduces the sequential sweep exactly.
 template <int B, bool ALL_AXIS, bool FWD>
 __global__ void __launch_bounds__(B) lusgs_sweep_kernel(const LusgsParams P) {
-  extern __shared__ double tab[];
   __shared__ SlotDev s_slot[6];
-  __shared__ int s_act;
   const int64_t c = P.cells[blockIdx.x];
   const int tid = threadIdx.x;
-  const int N1 = P.N1, N2 = P.N2, N3 = P.N3;
-  const int NP = N2 * N3;
-  const int64_t nn = (int64_t)N1 * NP;
-  double *tD1 = tab;        // [N1] 1 + dt nu + sum_{axis-1 faces} c max(s xi1, 0)
-  double *tX1 = tD1 + N1;   // [N1] xi1
-  double *tM = tX1 + N1;    // [6][N1] c min(s xi1, 0) of axis-1 faces
-
+  const int N3 = P.N3;
+  const int NP = P.N2 * N3;
+  const int64_t nn = (int64_t)P.N1 * NP;
+  const int nyb = (NP + B - 1) / B;
+  const int i1 = blockIdx.y / nyb;
+  const int p = (blockIdx.y - i1 * nyb) * B + tid;
   if (tid < 6) s_slot[tid] = P.slot[c * 6 + tid];
   __syncthreads();
-  if (tid == 0) {
-    int m = 0;
-    for (int l = 0; l < 6; ++l) {
-      const SlotDev &sl = s_slot[l];
-      if (sl.kind == kInterior && (FWD ? (int64_t)sl.src < c : (int64_t)sl.src > c)) m |= 1 << l;
-    }
-    s_act = m;
-  }
-  const double d0 = 1.0 + P.dtnu[c];
-  for (int i = tid; i < N1; i += B) {
-    const double x = P.xi[0][i];
-    double d = d0;
+  if (p >= NP) return;
+  const int i2 = p / N3, i3 = p - i2 * N3;
+  const double x1 = P.xi[0][i1], x2 = P.xi[1][i2], x3 = P.xi[2][i3];
+  const int64_t idx = (int64_t)i1 * NP + p;
+  double D = 1.0 + P.dtnu[c];
+  double S = 0.0;
 #pragma unroll
-    for (int l = 0; l < 6; ++l) {
-      const SlotDev &sl = s_slot[l];
-      double m = 0.0;
-      if (sl.axis == 0) {
-        const double sx = sl.sgn * x;
-        d = fma(sl.c, fmax(sx, 0.0), d);
-        m = sl.c * fmin(sx, 0.0);
-      }
-      tM[l * N1 + i] = m;
-    }
-    tD1[i] = d;
-    tX1[i] = x;
+  for (int l = 0; l < 6; ++l) {
+    const SlotDev &sl = s_slot[l];
+    double xn;  // xi . e_l
+    if (ALL_AXIS || sl.axis >= 0)
+      xn = sl.sgn * (sl.axis == 0 ? x1 : (sl.axis == 1 ? x2 : x3));
+    else
+      xn = fma(sl.e[0], x1, fma(sl.e[1], x2, sl.e[2] * x3));
+    const double x = sl.c * xn;
+    D += fmax(x, 0.0);
+    if (sl.kind == kInterior && (FWD ? (int64_t)sl.src < c : (int64_t)sl.src > c))
+      S = fma(fmin(x, 0.0), P.g[(int64_t)sl.src * nn + idx], S);
   }
-  __syncthreads();
-  const int act = s_act;
-
-  double *__restrict__ gc = P.g + c * nn;
-  for (int p = tid; p < NP; p += B) {
-    const int i2 = p / N3, i3 = p - i2 * N3;
-    const double x2 = P.xi[1][i2], x3 = P.xi[2][i3];
-    double D23 = 0.0;
-    double pm[6];  // axis-2/3 faces: M~ weight; generic faces: e2 xi2 + e3 xi3
-    const double *src[6];
-#pragma unroll
-    for (int l = 0; l < 6; ++l) {
-      const SlotDev &sl = s_slot[l];
-      pm[l] = 0.0;
-      if (sl.axis == 1 || sl.axis == 2) {
-        const double sx = sl.sgn * (sl.axis == 1 ? x2 : x3);
-        D23 = fma(sl.c, fmax(sx, 0.0), D23);
-        pm[l] = sl.c * fmin(sx, 0.0);
-      } else if (!ALL_AXIS && sl.axis < 0) {
-        pm[l] = sl.e[1] * x2 + sl.e[2] * x3;
-      }
-      src[l] = ((act >> l) & 1) ? P.g + (int64_t)sl.src * nn + p : gc + p;
-    }
-    for (int i1 = 0; i1 < N1; ++i1) {
-      const int64_t off = (int64_t)i1 * NP;
-      double D = tD1[i1] + D23;
-      double S = 0.0;
-#pragma unroll
-      for (int l = 0; l < 6; ++l) {
-        const SlotDev &sl = s_slot[l];
-        const bool on = (act >> l) & 1;
-        if (sl.axis == 0) {
-          if (on) S = fma(tM[l * N1 + i1], src[l][off], S);
-        } else if (ALL_AXIS || sl.axis > 0) {
-          if (on) S = fma(pm[l], src[l][off], S);
-        } else {
-          const double x = sl.c * fma(sl.e[0], tX1[i1], pm[l]);
-          D += fmax(x, 0.0);
-          if (on) S = fma(fmin(x, 0.0), src[l][off], S);
-        }
-      }
-      const double g = gc[off + p];
-      gc[off + p] = FWD ? (g - S) / D : g - S / D;
-    }
-  }
+  double *gp = P.g + c * nn + idx;
+  const double g = *gp;
+  *gp = FWD ? (g - S) / D : g - S / D;
 }
 
 // f^{n+1} = f^n + df (in place over df) and the moment sums of f^{n+1} about the
@@ -696,11 +644,12 @@ void launch_full_rhs(const FullParams &p, cudaStream_t s) {
 
 template <int B, bool FWD>
 static void launch_sweep_B(const LusgsParams &p, int ncell, cudaStream_t s) {
-  const size_t smem = sizeof(double) * 8 * (size_t)p.N1;
+  const int NP = p.N2 * p.N3;
+  const dim3 grid((unsigned)ncell, (unsigned)(p.N1 * ((NP + B - 1) / B)));
   if (p.all_axis)
-    lusgs_sweep_kernel<B, true, FWD><<<(unsigned)ncell, B, smem, s>>>(p);
+    lusgs_sweep_kernel<B, true, FWD><<<grid, B, 0, s>>>(p);
   else
-    lusgs_sweep_kernel<B, false, FWD><<<(unsigned)ncell, B, smem, s>>>(p);
+    lusgs_sweep_kernel<B, false, FWD><<<grid, B, 0, s>>>(p);
 }
 
 void launch_lusgs_sweep(const LusgsParams &p, int ncell, bool forward, cudaStream_t s) {
