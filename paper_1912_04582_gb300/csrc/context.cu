@@ -90,6 +90,7 @@ int ctx_alloc_state(dvm_ctx *C) {
       DVM_CUDA_TRY(cudaMemcpy(C->d_wave, order.data(), sizeof(int32_t) * 2 * nc,
                               cudaMemcpyHostToDevice));
       CTX_MALLOC(C->d_dtnu, sizeof(double) * nc);
+      CTX_MALLOC(C->d_rD, fb);
     }
   } else {
     int rc = tucker_alloc(C);
@@ -146,7 +147,7 @@ void ctx_free(dvm_ctx *C) {
   if (C->tucker) tucker_free(C);
   void *ptrs[] = {C->d_xi[0], C->d_xi[1], C->d_xi[2], C->d_vol, C->d_slot, C->d_ghost,
                   C->d_f[0], C->d_f[1], C->d_sums[0], C->d_sums[1], C->d_uref, C->d_respart,
-                  C->d_res, C->d_macro, C->d_flag, C->d_wave, C->d_dtnu};
+                  C->d_res, C->d_macro, C->d_flag, C->d_wave, C->d_dtnu, C->d_rD};
   for (void *p : ptrs)
     if (p) cudaFree(p);
 }
@@ -475,6 +476,7 @@ static void lusgs_step(dvm_ctx *C, FullParams &P) {
   launch_full_rhs(P, C->stream);
   LusgsParams L{};
   L.g = P.fnew;
+  L.rD = C->d_rD;
   L.dtnu = C->d_dtnu;
   L.slot = C->d_slot;
   for (int a = 0; a < 3; ++a) L.xi[a] = C->d_xi[a];

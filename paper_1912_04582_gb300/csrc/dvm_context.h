@@ -65,6 +65,7 @@ struct dvm_ctx {
   int32_t *d_wave = nullptr;         // [2][nc]
   std::vector<int64_t> wave_off[2];  // wavefront w of sweep s: [wave_off[s][w], wave_off[s][w+1])
   double *d_dtnu = nullptr;          // [nc]
+  double *d_rD = nullptr;            // [nc][nn] 1 / D~ of the current step
 
   // optional per-launch event timing (dvm_set_kernel_timing)
   struct Timing {

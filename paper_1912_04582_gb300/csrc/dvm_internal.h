@@ -74,6 +74,7 @@ struct FullParams {
 struct LusgsParams {
   double *g;             // [nc][nn] dt R^n before the forward sweep, the increment after
                          // the backward sweep
+  double *rD;            // [nc][nn] 1 / D~ (written by the forward sweep, read by the backward)
   const double *dtnu;    // [nc] dt nu of f^n
   const SlotDev *slot;   // [nc][6]
   const double *xi[3];

@@ -19,6 +19,7 @@
 // velocity u^n (so the heat flux of the next step needs no second pass and no
 // large cancellation), plus the wall outflow sums that fix the wall density of
 // the next step (impermeability condition, Section 2).
+#include <algorithm>
 #include <cmath>
 
 #include "dvm_device.cuh"
@@ -483,46 +484,114 @@ void launch_step_B(const FullParams &p, bool all_axis, bool incr, cudaStream_t s
 //   M~_l(xi) = c_l (xi.e_l)^-                           (interior face l to cell j),
 //   forward : g_i  = (g_i - sum_{l: j<i} M~_l g_j) / D~_i   (g_i = dt R_i on entry)
 //   backward: df_i = g_i - (sum_{l: j>i} M~_l df_j) / D~_i
-// Every node is independent within a sweep, so a CTA takes B consecutive nodes
-// (i2, i3) of one row i1 of one cell of the wavefront: grid (cells, N1 x column
-// blocks), coalesced loads of the cell's and its neighbours' rows.  Every
-// neighbour a cell reads belongs to an earlier wavefront of the same sweep, so
-// the launch order of the wavefronts reproduces the sequential sweep exactly.
+// Every node is independent within a sweep: a CTA takes one row i1 of one cell
+// of the wavefront (grid: cells x N1), its threads the columns (i2, i3) of that
+// row with coalesced loads of the cell's and its neighbours' rows.  FP64 issue
+// bounds the sweep, so on meshes whose faces all lie on coordinate planes the
+// face weights are looked up, not recomputed per node: the axis-1 faces' weights
+// are CTA scalars, the axis-2/3 faces' sit in shared-memory tables over i2 / i3,
+// and D~ = d0(i1) + d2(i2) + d3(i3).  The forward sweep stores 1/D~ for the
+// backward sweep.  Every neighbour a cell reads belongs to an earlier wavefront
+// of the same sweep, so the launch order of the wavefronts reproduces the
+// sequential sweep exactly.
 template <int B, bool ALL_AXIS, bool FWD>
 __global__ void __launch_bounds__(B) lusgs_sweep_kernel(const LusgsParams P) {
+  extern __shared__ double tab[];
   __shared__ SlotDev s_slot[6];
+  __shared__ double s_d0;     // 1 + dt nu + sum_{axis-1 faces} c max(s xi1, 0) at this row
+  __shared__ double s_m0[6];  // axis-1 faces: c min(s xi1, 0) at this row
   const int64_t c = P.cells[blockIdx.x];
+  const int i1 = blockIdx.y;
   const int tid = threadIdx.x;
-  const int N3 = P.N3;
-  const int NP = P.N2 * N3;
+  const int N2 = P.N2, N3 = P.N3;
+  const int NP = N2 * N3;
+  const int Nm = N2 > N3 ? N2 : N3;
   const int64_t nn = (int64_t)P.N1 * NP;
-  const int nyb = (NP + B - 1) / B;
-  const int i1 = blockIdx.y / nyb;
-  const int p = (blockIdx.y - i1 * nyb) * B + tid;
+  double *tD = tab;            // [N2 + N3] axis-2 / axis-3 faces' sum of c max(s xi, 0)
+  double *tM = tD + N2 + N3;   // [6][Nm] c min(s xi, 0) of face l over its axis
   if (tid < 6) s_slot[tid] = P.slot[c * 6 + tid];
   __syncthreads();
-  if (p >= NP) return;
-  const int i2 = p / N3, i3 = p - i2 * N3;
-  const double x1 = P.xi[0][i1], x2 = P.xi[1][i2], x3 = P.xi[2][i3];
-  const int64_t idx = (int64_t)i1 * NP + p;
-  double D = 1.0 + P.dtnu[c];
-  double S = 0.0;
+  const double x1 = P.xi[0][i1];
+  if (tid == 0) {
+    double d = 1.0 + P.dtnu[c];
+    for (int l = 0; l < 6; ++l) {
+      const SlotDev &sl = s_slot[l];
+      s_m0[l] = 0.0;
+      if (ALL_AXIS && sl.axis == 0) {
+        const double sx = sl.sgn * x1;
+        d = fma(sl.c, fmax(sx, 0.0), d);
+        s_m0[l] = sl.c * fmin(sx, 0.0);
+      }
+    }
+    s_d0 = d;
+  }
+  if (ALL_AXIS) {
+    for (int k = tid; k < N2 + N3; k += B) {
+      const int ax = k < N2 ? 1 : 2;
+      const int i = k < N2 ? k : k - N2;
+      const double x = (k < N2 ? P.xi[1] : P.xi[2])[i];
+      double d = 0.0;
+#pragma unroll
+      for (int l = 0; l < 6; ++l) {
+        const SlotDev &sl = s_slot[l];
+        if (sl.axis == ax) {
+          const double sx = sl.sgn * x;
+          d = fma(sl.c, fmax(sx, 0.0), d);
+          tM[l * Nm + i] = sl.c * fmin(sx, 0.0);
+        }
+      }
+      tD[k] = d;
+    }
+  }
+  __syncthreads();
+  const int64_t row = (int64_t)i1 * NP;
+  const double *nbp[6];  // this row of the neighbour across face l, if face l couples
+  int ax[6];             // on this sweep's side: the axis of face l, else -1
+  double m0[6];
 #pragma unroll
   for (int l = 0; l < 6; ++l) {
     const SlotDev &sl = s_slot[l];
-    double xn;  // xi . e_l
-    if (ALL_AXIS || sl.axis >= 0)
-      xn = sl.sgn * (sl.axis == 0 ? x1 : (sl.axis == 1 ? x2 : x3));
-    else
-      xn = fma(sl.e[0], x1, fma(sl.e[1], x2, sl.e[2] * x3));
-    const double x = sl.c * xn;
-    D += fmax(x, 0.0);
-    if (sl.kind == kInterior && (FWD ? (int64_t)sl.src < c : (int64_t)sl.src > c))
-      S = fma(fmin(x, 0.0), P.g[(int64_t)sl.src * nn + idx], S);
+    const bool on = sl.kind == kInterior && (FWD ? (int64_t)sl.src < c : (int64_t)sl.src > c);
+    nbp[l] = P.g + (on ? (int64_t)sl.src : c) * nn + row;
+    ax[l] = on ? (ALL_AXIS ? sl.axis : 3) : -1;
+    m0[l] = s_m0[l];
   }
-  double *gp = P.g + c * nn + idx;
-  const double g = *gp;
-  *gp = FWD ? (g - S) / D : g - S / D;
+  const double d0 = s_d0;
+  double *__restrict__ gc = P.g + c * nn + row;
+  double *__restrict__ rc = P.rD + c * nn + row;
+  for (int p = tid; p < NP; p += B) {
+    const int i2 = p / N3, i3 = p - i2 * N3;
+    double D, S = 0.0;
+    if (ALL_AXIS) {
+      D = d0 + tD[i2] + tD[N2 + i3];
+#pragma unroll
+      for (int l = 0; l < 6; ++l) {
+        if (ax[l] >= 0) {
+          const double m = ax[l] == 0 ? m0[l] : tM[l * Nm + (ax[l] == 1 ? i2 : i3)];
+          S = fma(m, nbp[l][p], S);
+        }
+      }
+    } else {
+      const double x2 = P.xi[1][i2], x3 = P.xi[2][i3];
+      D = d0;
+#pragma unroll
+      for (int l = 0; l < 6; ++l) {
+        const SlotDev &sl = s_slot[l];
+        const double xn = sl.axis >= 0 ? sl.sgn * (sl.axis == 0 ? x1 : (sl.axis == 1 ? x2 : x3))
+                                       : fma(sl.e[0], x1, fma(sl.e[1], x2, sl.e[2] * x3));
+        const double x = sl.c * xn;
+        D += fmax(x, 0.0);
+        if (ax[l] >= 0) S = fma(fmin(x, 0.0), nbp[l][p], S);
+      }
+    }
+    if (FWD) {
+      const double r = 1.0 / D;
+      rc[p] = r;
+      gc[p] = (gc[p] - S) * r;
+    } else {
+      gc[p] = fma(-S, rc[p], gc[p]);
+    }
+  }
 }
 
 // f^{n+1} = f^n + df (in place over df) and the moment sums of f^{n+1} about the
@@ -644,10 +713,10 @@ void launch_full_rhs(const FullParams &p, cudaStream_t s) {
 
 template <int B, bool FWD>
 static void launch_sweep_B(const LusgsParams &p, int ncell, cudaStream_t s) {
-  const int NP = p.N2 * p.N3;
-  const dim3 grid((unsigned)ncell, (unsigned)(p.N1 * ((NP + B - 1) / B)));
+  const dim3 grid((unsigned)ncell, (unsigned)p.N1);
+  const size_t smem = sizeof(double) * (size_t)(p.N2 + p.N3 + 6 * std::max(p.N2, p.N3));
   if (p.all_axis)
-    lusgs_sweep_kernel<B, true, FWD><<<grid, B, 0, s>>>(p);
+    lusgs_sweep_kernel<B, true, FWD><<<grid, B, smem, s>>>(p);
   else
     lusgs_sweep_kernel<B, false, FWD><<<grid, B, 0, s>>>(p);
 }
