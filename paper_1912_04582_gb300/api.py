@@ -294,7 +294,8 @@ class Solver:
 # --------------------------------------------------------------------------
 # Serving (continuous batching of steady-state solves)
 
-def _request(wl, format, precision, rank_cap, tol, res_tol, max_steps, check_every, keep):
+def _request(wl, format, precision, rank_cap, tol, res_tol, max_steps, check_every, keep,
+             scheme=_n.DVM_SCHEME_EXPLICIT, cfl=None):
     xyz = np.ascontiguousarray(wl.xyz, dtype=np.float64)
     hex8 = np.ascontiguousarray(wl.hex8, dtype=np.int64)
     bface = np.ascontiguousarray(wl.bface, dtype=np.int64).reshape(-1, 2)
@@ -314,9 +315,9 @@ def _request(wl, format, precision, rank_cap, tol, res_tol, max_steps, check_eve
                              (ctypes.c_double * 3)(*[float(v) for v in wl.lo]),
                              (ctypes.c_double * 3)(*[float(v) for v in wl.hi]))
     req.gas = _n.dvm_gas(float(wl.Pr), float(wl.omega), float(wl.Kn))
-    req.opts = _n.dvm_opts(int(format), int(precision), int(rank_cap), float(tol), float(wl.cfl),
-                           0.0, None, _n.DVM_VARIANT_AUTO, 0, _n.DVM_ENGINE_AUTO,
-                           _n.DVM_SCHEME_EXPLICIT)
+    req.opts = _n.dvm_opts(int(format), int(precision), int(rank_cap), float(tol),
+                           float(wl.cfl if cfl is None else cfl), 0.0, None,
+                           _n.DVM_VARIANT_AUTO, 0, _n.DVM_ENGINE_AUTO, int(scheme))
     req.n_bc = len(wl.bcs)
     req.bc_group, req.bc_type, req.bc_params = _i32p(groups), _i32p(types), _dp(params)
     req.n0, req.u0, req.T0 = _dp(n0), _dp(u0), _dp(T0)
@@ -326,9 +327,9 @@ def _request(wl, format, precision, rank_cap, tol, res_tol, max_steps, check_eve
     return req
 
 
-def dvm_estimate_memory(wl, format=0, precision=0, rank_cap=8, tol=1e-5):
+def dvm_estimate_memory(wl, format=0, precision=0, rank_cap=8, tol=1e-5, scheme=0):
     keep = []
-    req = _request(wl, format, precision, rank_cap, tol, 1e-6, 1, 1, keep)
+    req = _request(wl, format, precision, rank_cap, tol, 1e-6, 1, 1, keep, scheme=scheme)
     b = ctypes.c_size_t(0)
     _n.check(N_lib().dvm_estimate_memory(ctypes.byref(req), ctypes.byref(b)),
              "dvm_estimate_memory")
@@ -345,10 +346,10 @@ class Server:
                                            int(max_slots)), "dvm_server_create")
 
     def submit(self, wl, format=0, precision=0, rank_cap=8, tol=1e-5, res_tol=1e-6,
-               max_steps=10000, check_every=10):
+               max_steps=10000, check_every=10, scheme=0, cfl=None):
         keep = []
         req = _request(wl, format, precision, rank_cap, tol, res_tol, max_steps, check_every,
-                       keep)
+                       keep, scheme=scheme, cfl=cfl)
         t = ctypes.c_int64(0)
         _n.check(N_lib().dvm_server_submit(self.ptr, ctypes.byref(req), ctypes.byref(t)),
                  "dvm_server_submit")

@@ -74,6 +74,9 @@ size_t estimate(const dvm_request *q) {
              sizeof(SlotDev) * 6 * (size_t)nc + sizeof(double) * (size_t)nghost * nn;
   if (q->opts.format == DVM_FORMAT_FULL) {
     b += 2 * sizeof(double) * (size_t)nc * nn;
+    // implicit step: 1/D~ at every node, per-cell dt nu, the two sweeps' cell lists
+    if (q->opts.scheme == DVM_SCHEME_LUSGS)
+      b += sizeof(double) * (size_t)nc * (nn + 1) + sizeof(int32_t) * 2 * (size_t)nc;
   } else {
     const int64_t R = q->opts.rank_cap;
     b += 2 * (sizeof(double) * (size_t)nc * (R * R * R + sumN * R) + sizeof(int) * 3 * nc);

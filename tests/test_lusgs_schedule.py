@@ -129,3 +129,15 @@ def test_create_rejects_lusgs_on_tucker_and_unknown_schemes(api):
     with pytest.raises(_native.DvmError) as e:
         api.dvm_create(*args, scheme=7)
     assert e.value.code == _native.DVM_ERR_INVALID_ARG
+
+
+def test_serving_estimate_counts_the_implicit_buffers(api):
+    """Admission by memory: an implicit full-grid request also holds 1/D at every node
+    (a third N^3 array per cell) besides the two state copies."""
+    from paper_1912_04582_gb300 import _native
+    wl = W.cavity(nside=4, N=12)
+    e0 = api.dvm_estimate_memory(wl)
+    e1 = api.dvm_estimate_memory(wl, scheme=_native.DVM_SCHEME_LUSGS)
+    nn = wl.n_cell * int(np.prod(wl.N))
+    assert e1 - e0 >= 8 * nn
+    assert e0 >= 16 * nn
