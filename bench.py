@@ -55,8 +55,10 @@ def _args():
     ap.add_argument("--rank-cap", type=int, default=None)
     ap.add_argument("--tol", type=float, default=None)
     ap.add_argument("--workload", default="c3",
-                    choices=["c3", "c3_small", "c2", "cavity_small", "sod"],
-                    help="c3_small: the C3 velocity grid on 12^3 cells (kernel profiles)")
+                    choices=["c3", "c3_small", "c2", "cavity_small", "sod", "cylinder"],
+                    help="c3_small: the C3 velocity grid on 12^3 cells (kernel profiles); "
+                         "cylinder: the Mach-10 cylinder stand-in, 1600 cells x 64^3 (with "
+                         "--tol 1e-3 / 1e-4 / 1e-5 the compression study of Section 7)")
     ap.add_argument("--variant", default="auto", choices=["auto", "fused", "phased"],
                     help="Tucker launch variant (auto: the autotuner times both)")
     ap.add_argument("--advance", type=int, default=200,
@@ -84,6 +86,8 @@ def make_workload(name):
         return W.cavity(nside=8, N=24)
     if name == "sod":
         return W.sod_row()
+    if name == "cylinder":
+        return W.cylinder()
     raise SystemExit(f"unknown workload {name}")
 
 

@@ -387,6 +387,101 @@ def channel(n_cell_target=2000, N=24, vmax=6.0, Kn=0.1, kind="poiseuille", rank_
         rank_cap=rank_cap, tol=tol, h=h)
 
 
+# Section 7 free stream (argon) in the units of these workloads: speeds in
+# sqrt(2 R T_inf), R = 8.314 / 0.039948 J/(kg K), T_inf = 200 K.
+_AR_R = 8.314462618 / 0.039948
+_C_UNIT = math.sqrt(2.0 * _AR_R * 200.0)          # m/s per speed unit
+
+
+def cylinder(n_theta=40, n_r=40, N=64, r_out=8.0, dr1=0.05, Kn=0.552, Tw=5.0,
+             u_inf=2630.0 / _C_UNIT, vmax=6400.0 / _C_UNIT, rank_cap=16, tol=1e-5,
+             seed=None):
+    """Hypersonic flow past a circular cylinder, the shape of Section 7's test problem
+    (its mesh is not available, so this O-grid stands in for it).
+
+    Half of the flow (y >= 0) around a unit-radius cylinder (lengths in radii), solved
+    as 3D with one cell along z: n_theta cells over the half circle (theta = 0 is the
+    downstream axis), n_r cells radially with geometric growth from dr1 at the wall to
+    the outer radius r_out; 1600 cells at the defaults, as in Section 7.  Groups:
+    0 free stream on the outer boundary (n = 1, T = 1, u = (u_inf, 0, 0)), 1 the diffuse
+    wall at Tw (Section 7: Tw = 5 T_inf), 2 symmetry on the y = 0 plane and on both z
+    planes.  Free stream v0 = 2630 m/s, T0 = 200 K of argon: u_inf = 9.12 (Mach 10),
+    the velocity box +-6400 m/s = +-22.2, N = 64 nodes per axis as in Section 7;
+    viscosity exponent 0.734; Kn = 0.552 is the printed Kn ~ 0.56 in the collision
+    frequency of these units.  Cells are numbered radius-fastest (or shuffled with seed).
+    """
+    g = _growth(dr1, r_out - 1.0, n_r)
+    r = np.concatenate([[1.0], 1.0 + dr1 * np.cumsum(g ** np.arange(n_r))])
+    r[-1] = r_out
+    th = math.pi * np.arange(n_theta + 1) / n_theta
+    hz = math.pi / n_theta
+    # vertex (i_theta, j_r, k_z), k fastest; y = 0 exactly on the symmetry line
+    xyz = np.empty(((n_theta + 1) * (n_r + 1) * 2, 3))
+    vid = lambda i, j, k: (i * (n_r + 1) + j) * 2 + k  # noqa: E731
+    for i in range(n_theta + 1):
+        c, sn = math.cos(th[i]), math.sin(th[i])
+        if i == 0 or i == n_theta:
+            sn = 0.0
+            c = 1.0 if i == 0 else -1.0
+        for j in range(n_r + 1):
+            for k in range(2):
+                xyz[vid(i, j, k)] = (r[j] * c, r[j] * sn, k * hz)
+    # local hex axes (x, y, z) = (radius, theta, z): right-handed, positive volumes
+    cells = [(i, j) for i in range(n_theta) for j in range(n_r)]
+    hex8 = np.empty((len(cells), 8), dtype=np.int64)
+    for q, (i, j) in enumerate(cells):
+        for v in range(8):
+            dx, dy, dz = _CORNER[v]
+            hex8[q, v] = vid(i + dy, j + dx, dz)
+    bface, bgroup = [], []
+    for q, (i, j) in enumerate(cells):
+        if j == 0:
+            bface.append((q, 0)); bgroup.append(1)          # wall (local x-)
+        if j == n_r - 1:
+            bface.append((q, 1)); bgroup.append(0)          # outer free stream (local x+)
+        if i == 0:
+            bface.append((q, 2)); bgroup.append(2)          # theta = 0 line (local y-)
+        if i == n_theta - 1:
+            bface.append((q, 3)); bgroup.append(2)          # theta = pi line (local y+)
+        bface.append((q, 4)); bgroup.append(2)              # z planes
+        bface.append((q, 5)); bgroup.append(2)
+    bface = np.array(bface, dtype=np.int64)
+    bgroup = np.array(bgroup, dtype=np.int32)
+    ijk = np.array([(i, j, 0) for i, j in cells], dtype=np.int64)
+    if seed is not None:
+        rng = np.random.default_rng(seed)
+        perm = rng.permutation(hex8.shape[0])
+        inv = np.empty_like(perm)
+        inv[perm] = np.arange(perm.size)
+        hex8, ijk = hex8[perm], ijk[perm]
+        bface[:, 0] = inv[bface[:, 0]]
+    nc = hex8.shape[0]
+    u0 = np.tile([u_inf, 0.0, 0.0], (nc, 1))
+    return Workload(
+        name=f"cylinder_{nc}x{N}^3", xyz=xyz, hex8=hex8, bface=bface, bgroup=bgroup,
+        N=(N, N, N), lo=(-vmax,) * 3, hi=(vmax,) * 3, Pr=2.0 / 3.0, omega=0.734, Kn=Kn,
+        bcs=[(0, BC_FREESTREAM, _params(n=1.0, u=(u_inf, 0.0, 0.0), T=1.0)),
+             (1, BC_WALL, _params(Tw=Tw)),
+             (2, BC_SYMMETRY, np.zeros(8))],
+        n0=np.ones(nc), u0=u0, T0=np.ones(nc), cell_ijk=ijk, steps=4000,
+        rank_cap=rank_cap, tol=tol, h=(dr1, hz, hz))
+
+
+def _growth(d1, length, n):
+    """Ratio q of the geometric series d1 (1 + q + ... + q^(n-1)) = length (bisection)."""
+    if abs(d1 * n - length) < 1e-12 * length:
+        return 1.0
+    lo, hi = (1.0, 10.0) if d1 * n < length else (1e-6, 1.0)
+    for _ in range(200):
+        q = 0.5 * (lo + hi)
+        s = d1 * (q ** n - 1.0) / (q - 1.0)
+        if (s < length) == (d1 * n < length):
+            lo = q
+        else:
+            hi = q
+    return 0.5 * (lo + hi)
+
+
 def uniform_random_tucker_ranks(n_cell, lo=4, hi=20, seed=42):
     """Per-cell Tucker ranks drawn uniformly from {lo..hi} in each mode (seeded)."""
     rng = np.random.default_rng(seed)
