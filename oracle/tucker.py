@@ -202,3 +202,77 @@ def compression(r, N):
     """C = (r1 r2 r3 + N (r1 + r2 + r3)) / N^3 (Section 7)."""
     r1, r2, r3 = r
     return (r1 * r2 * r3 + N * (r1 + r2 + r3)) / float(N) ** 3
+
+
+def lusgs_step_tucker(o, dt, eps, cap=None, diag="rank1"):
+    """One implicit step of Section 5 in the Tucker format's arithmetic, on the state held
+    by the full-grid oracle ``o`` (a FullGridOracle), which it advances.
+
+    The linear-system equation [I/dt - dR/df] (f^{n+1} - f^n) = R^n is solved by one
+    LU-SGS pass over the cells in index order (the same sweeps as the full-grid oracle),
+    with the Tucker format's two departures:
+      * the division by the diagonal uses D_i^est, the rank-1 approximation of
+        1/dt + nu_i + sum_l |A_l| |xi| / (2 |V_i|) (diagonal_term with the bound of
+        xin-one-rank-approx), so it is exact in the Tucker format (one_rank_division);
+        diag="exact" divides by the full-grid diagonal instead (a cross-check);
+      * every sum of Tucker tensors is rounded to eps (and cap): the forward sweep's
+        R_i - sum_{j<i} M_ij g_j, the backward sweep's g_i - D^-1 sum_{j>i} M_ij df_j and
+        f^n + df.  eps = 0 keeps every sum exact.
+    Tensors are held expanded; a rounding is the truncated HOSVD of the exact sum, which
+    is what rounding a Tucker sum computes.  The off-diagonal blocks are the exact
+    (xi.e)^- weights.  Returns the residual of the step (the oracle's definition)."""
+    f = o.f()
+    R = o.rhs()
+    vol, fcell, fgeo = o.geometry()
+    xi = o.nodes()
+    m = o.macro()
+    nc = f.shape[0]
+    X = [xi[0][:, None, None], xi[1][None, :, None], xi[2][None, None, :]]
+
+    def rnd(A):
+        return full(hosvd(A, eps, cap)[0]) if eps > 0 else A
+
+    nbrs = [[] for _ in range(nc)]           # (j, |A_l| / |V_i| * (xi.e_out)^-)
+    area = np.zeros(nc)
+    for jf in range(fcell.shape[0]):
+        a, b = int(fcell[jf, 0]), int(fcell[jf, 1])
+        e = fgeo[jf, 1:]
+        xn = e[0] * X[0] + e[1] * X[1] + e[2] * X[2]
+        area[a] += fgeo[jf, 0]
+        if b >= 0:
+            area[b] += fgeo[jf, 0]
+            nbrs[a].append((b, fgeo[jf, 0] / vol[a] * np.minimum(xn, 0.0)))
+            nbrs[b].append((a, fgeo[jf, 0] / vol[b] * np.minimum(-xn, 0.0)))
+    if diag == "exact":
+        D = o.lusgs_diag(dt)
+    else:
+        D = np.empty_like(f)
+        for i in range(nc):
+            nu = o.nu(m[i, 0], m[i, 4])
+            d = diag_estimate_rank1(xi, 1.0 / dt + nu, area[i] / (2.0 * vol[i]))
+            D[i] = np.einsum("i,j,k->ijk", *d)
+    g = np.empty_like(f)
+    for i in range(nc):                      # forward sweep
+        A = R[i].copy()
+        for j, M in nbrs[i]:
+            if j < i:
+                A -= M * g[j]
+        g[i] = rnd(A) / D[i]
+    df = np.empty_like(f)
+    for i in range(nc - 1, -1, -1):          # backward sweep
+        B = np.zeros_like(f[i])
+        for j, M in nbrs[i]:
+            if j > i:
+                B += M * df[j]
+        df[i] = rnd(g[i] - B / D[i])
+    fn = np.stack([rnd(f[i] + df[i]) for i in range(nc)])
+    o.init_f(fn)
+    w = o.weight()
+    x2 = X[0] ** 2 + X[1] ** 2 + X[2] ** 2
+
+    def U(t):
+        return np.array([t.sum(), (X[0] * t).sum(), (X[1] * t).sum(), (X[2] * t).sum(),
+                         (x2 * t).sum()]) * w
+    num = sum(vol[i] * np.sum((U(fn[i]) - U(f[i])) ** 2) for i in range(nc))
+    den = sum(vol[i] * np.sum(U(f[i]) ** 2) for i in range(nc))
+    return math.sqrt(num) / (dt * math.sqrt(den))

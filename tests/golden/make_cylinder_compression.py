@@ -11,9 +11,10 @@ velocity box, run towards its steady state with the oracle's implicit LU-SGS ste
 HOSVD (Section 4, the per-mode rule with eps) and records, per eps, the mean
 compression ratio, the rank distribution, the mean largest rank by radial band, and the
 error in T of the compressed state (a one-time rounding error, not the paper's solution
-difference Delta T).
+difference Delta T), and the map of each cell's largest rank (rows: theta from the
+downstream axis, 0, to the stagnation line, pi; columns: wall to outer boundary).
 
-Run: python tests/golden/make_cylinder_compression.py  (about 10 minutes on 8 cores).
+Run: python tests/golden/make_cylinder_compression.py  (about 7 minutes on 8 cores).
 """
 import json
 import math
@@ -31,7 +32,7 @@ from oracle import tucker as tk  # noqa: E402
 import workloads as W  # noqa: E402
 
 SHAPE = dict(n_theta=16, n_r=12, N=40, dr1=0.1)
-STEPS, DT_FACTOR, EPS = 300, 20.0, (1e-3, 1e-4, 1e-5)
+STEPS, DT_FACTOR, EPS = 400, 20.0, (1e-3, 1e-4, 1e-5)
 
 
 def temperature(o, f):
@@ -70,12 +71,15 @@ def main(out=os.path.join(HERE, "cylinder_compression.json")):
             dT.append(abs(temperature(o, tk.full(t)) - m[c, 4]) / m[c, 4])
         ranks = np.array(ranks)
         rmax = ranks.max(axis=1)
+        rmap = np.zeros((SHAPE["n_theta"], SHAPE["n_r"]), dtype=int)
+        rmap[wl.cell_ijk[:, 0], wl.cell_ijk[:, 1]] = rmax
         res["eps"][f"{eps:g}"] = {
             "mean_compression": float(np.mean(C)),
             "rank_mean": float(ranks.mean()), "rank_max": int(ranks.max()),
             "max_rank_histogram": {int(v): int(np.sum(rmax == v)) for v in np.unique(rmax)},
             "mean_max_rank_by_band": {k: float(rmax[b].mean()) for k, b in bands.items()},
             "T_rounding_error_rel_max": float(np.max(dT)),
+            "rank_map_theta_by_radius": rmap.tolist(),
         }
         print(eps, res["eps"][f"{eps:g}"]["mean_compression"], flush=True)
     with open(out, "w") as fp:

@@ -165,3 +165,73 @@ def test_lusgs_reaches_steady_state_in_fewer_steps(oracle_lib):
     assert r_i < 0.3 * r_e, (r_i, r_e)
     m = oi.macro()
     assert np.all(m[:, 0] > 0.0) and np.all(m[:, 4] > 0.0)
+
+
+# ---------------------------------------------------------------------------
+# The Tucker format's implicit step (Section 5): division by the rank-1 estimate
+# D^est and rounding of every Tucker sum (oracle.tucker.lusgs_step_tucker).
+
+def test_tucker_lusgs_machinery_equals_the_full_grid_step(oracle_lib):
+    """With the exact diagonal and no rounding, the Tucker reference's sweeps are the
+    full-grid LU-SGS step (two independent codings of the same sweeps)."""
+    from oracle import tucker as tk
+    wl = W.cavity(nside=3, N=6, vmax=4.0, Kn=0.3, seed=2)
+    a = oracle_lib.FullGridOracle(wl)
+    b = oracle_lib.FullGridOracle(wl)
+    a.step(2, a.dt())
+    b.step(2, b.dt())
+    dt = 5.0 * a.dt()
+    ra = a.step_lusgs(1, dt)
+    rb = tk.lusgs_step_tucker(b, dt, 0.0, diag="exact")
+    assert np.max(np.abs(a.f() - b.f())) < 1e-14 * np.max(np.abs(a.f()))
+    assert abs(ra - rb) < 1e-12 * ra
+
+
+def test_tucker_lusgs_small_dt_is_the_explicit_step(oracle_lib):
+    """D^est = (1/dt) (1 + O(dt)): the rank-1 step is consistent with the explicit one."""
+    from oracle import tucker as tk
+    wl = W.cavity(nside=3, N=8, vmax=4.0, Kn=0.3, seed=2)
+    errs = []
+    for dt in (1e-3, 1e-4):
+        o = oracle_lib.FullGridOracle(wl)
+        o.step(3, o.dt())
+        f1, R = o.f(), o.rhs()
+        tk.lusgs_step_tucker(o, dt, 0.0)
+        errs.append(np.max(np.abs((o.f() - f1) / dt - R)) / np.max(np.abs(R)))
+    assert errs[0] < 0.05 and errs[1] < errs[0] / 8.0, errs
+
+
+def test_tucker_lusgs_rounding_stays_within_eps(oracle_lib):
+    """Three roundings per cell (forward sum, backward sum, f + df), each within eps of
+    its operand (Section 4, HOSVD bound): the rounded step stays within a few eps of the
+    exact one in every cell."""
+    from oracle import tucker as tk
+    wl = W.cavity(nside=3, N=8, vmax=4.0, Kn=0.3, seed=2)
+    out = {}
+    for eps in (0.0, 1e-4, 1e-6):
+        o = oracle_lib.FullGridOracle(wl)
+        o.step(3, o.dt())
+        tk.lusgs_step_tucker(o, 5.0 * o.dt(), eps)
+        out[eps] = o.f()
+    for eps in (1e-4, 1e-6):
+        d = np.sqrt(np.sum((out[eps] - out[0.0]) ** 2, axis=(1, 2, 3))
+                    / np.sum(out[0.0] ** 2, axis=(1, 2, 3)))
+        assert np.all(d <= 3.0 * eps), (eps, d.max())
+        assert d.max() > 0.01 * eps           # the rounding really truncates
+
+
+def test_tucker_lusgs_rank1_diagonal_still_converges_faster(oracle_lib):
+    """Section 5: the rank-1 estimate of the diagonal is rough, yet the implicit step
+    approaches the steady state faster than the explicit one (here at 20 x its step,
+    rounding to eps = 1e-6)."""
+    from oracle import tucker as tk
+    wl = W.cavity(nside=4, N=6, vmax=4.0, Kn=0.5, lid=0.3, seed=None)
+    oe = oracle_lib.FullGridOracle(wl)
+    dt = oe.dt()
+    oe.step(40, dt)
+    oi = oracle_lib.FullGridOracle(wl)
+    for _ in range(40):
+        tk.lusgs_step_tucker(oi, 20.0 * dt, 1e-6)
+    r_e = np.sqrt(np.mean(oe.rhs() ** 2))
+    r_i = np.sqrt(np.mean(oi.rhs() ** 2))
+    assert r_i < 0.5 * r_e, (r_i, r_e)
