@@ -93,6 +93,12 @@ def test_specular_box_with_walls(dvm, oracle_lib):
     _pair(dvm, oracle_lib, wl, 6, 6.0)
 
 
+def test_cavity_at_the_benchmark_size(dvm, oracle_lib):
+    """C2 as the benchmark times it: 16^3 cells x 32^3 nodes (46 wavefronts per sweep,
+    256-thread rows), one step at 5 x the explicit step."""
+    _pair(dvm, oracle_lib, W.cavity(), 1, 5.0)
+
+
 def test_lusgs_converges_faster_than_explicit(dvm):
     """Section 3: at 20 x the explicit step the implicit solve gets closer to the
     steady state in the same number of steps (the steady-state residual R^n, read
