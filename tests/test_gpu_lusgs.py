@@ -56,7 +56,6 @@ def _pair(dvm, oracle_lib, wl, steps, dt_factor, f0=None):
     for k, v in _macro_err(s.moments(), o.macro()).items():
         assert v <= TOL, f"{k}: {v}"
     assert abs(rg - ro) <= 1e-10 * ro
-    # the implicit step really differs from the explicit one at this dt
     s.close()
     return fo
 
