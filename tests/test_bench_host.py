@@ -89,3 +89,77 @@ def test_gram_on_tensor_cores_follows_the_library_rule(N, tc):
     """N1 <= 64 and N2 N3 a multiple of 8 up to 4096 (64^3: N2 N3 = 4096 is allowed; 40 x 13 x
     7: 91 columns, not a multiple of 8; 72 first-mode rows: too many)."""
     assert bench.gram_on_tensor_cores(N) == tc
+
+
+class _FakeEvent:
+    def __init__(self, **kw):
+        pass
+
+    def record(self, stream=None):
+        pass
+
+    def elapsed_time(self, other):
+        return 100.0
+
+
+class _FakeSolver:
+    """Counts steps; its 'residual' shrinks with the steps taken."""
+
+    def __init__(self, wl, **kw):
+        self.n = 0
+        self.h = self
+        self.kw = kw
+
+    def step(self, n=1, residual=True):
+        self.n += n
+        return 1.0 / (1 + self.n)
+
+    def f(self):
+        return self.n
+
+    def close(self):
+        pass
+
+
+def test_lusgs_extra_reports_step_time_and_convergence(monkeypatch):
+    """The implicit-step extra of the C2 configuration: step time against the explicit
+    step, and both schemes' steady residual at the same step counts."""
+    import types
+    import torch
+    monkeypatch.setattr(torch.cuda, "Event", _FakeEvent)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda: None)
+    made = []
+
+    def solver(wl, **kw):
+        s = _FakeSolver(wl, **kw)
+        made.append(s)
+        return s
+    P = types.SimpleNamespace(Solver=solver,
+                              api=types.SimpleNamespace(dvm_init_f=lambda h, f: None))
+    NAT = types.SimpleNamespace(DVM_SCHEME_LUSGS=1)
+    out = bench.run_lusgs(P, NAT, types.SimpleNamespace(cuda_stream=0), full_ms=7.0)
+    assert "error" not in out
+    assert out["ms_per_step"] == 10.0 and abs(out["vs_explicit_step"] - 10.0 / 7.0) < 1e-12
+    hist = out["steady_residual_after_steps"]
+    assert [k for k, _ in hist["explicit_cfl0.5"]] == [100, 200, 300]
+    assert [k for k, _ in hist["lusgs_cfl20"]] == [100, 200, 300]
+    lus = [s for s in made if s.kw.get("scheme") == 1]
+    assert len(lus) == 1 and lus[0].n == 300 and lus[0].kw["cfl"] == 20.0
+
+
+def test_lusgs_extra_survives_a_failure(monkeypatch):
+    import types
+    import torch
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda: None)
+
+    def solver(wl, **kw):
+        raise RuntimeError("no device")
+    P = types.SimpleNamespace(Solver=solver, api=None)
+    out = bench.run_lusgs(P, types.SimpleNamespace(DVM_SCHEME_LUSGS=1),
+                          types.SimpleNamespace(cuda_stream=0), full_ms=7.0)
+    assert out["error"].startswith("no device")
+
+
+def test_cylinder_workload_option():
+    wl = bench.make_workload("cylinder")
+    assert wl.n_cell == 1600 and wl.N == (64, 64, 64)
