@@ -55,10 +55,13 @@ def _args():
     ap.add_argument("--rank-cap", type=int, default=None)
     ap.add_argument("--tol", type=float, default=None)
     ap.add_argument("--workload", default="c3",
-                    choices=["c3", "c3_small", "c2", "cavity_small", "sod", "cylinder"],
+                    choices=["c3", "c3_small", "c2", "cavity_small", "sod", "cylinder",
+                             "cylinder_ogrid"],
                     help="c3_small: the C3 velocity grid on 12^3 cells (kernel profiles); "
-                         "cylinder: the Mach-10 cylinder stand-in, 1600 cells x 64^3 (with "
-                         "--tol 1e-3 / 1e-4 / 1e-5 the compression study of Section 7)")
+                         "cylinder: the Mach-10 cylinder stand-in with a staircase wall, "
+                         "1606 cells x 64^3 (with --tol 1e-3 / 1e-4 / 1e-5 the compression "
+                         "study of Section 7); cylinder_ogrid: its body-fitted O-grid, 1600 "
+                         "cells (curved wall: full format only, --path full)")
     ap.add_argument("--variant", default="auto", choices=["auto", "fused", "phased"],
                     help="Tucker launch variant (auto: the autotuner times both)")
     ap.add_argument("--advance", type=int, default=200,
@@ -87,6 +90,8 @@ def make_workload(name):
     if name == "sod":
         return W.sod_row()
     if name == "cylinder":
+        return W.cylinder_staircase()
+    if name == "cylinder_ogrid":
         return W.cylinder()
     raise SystemExit(f"unknown workload {name}")
 

@@ -160,6 +160,7 @@ def test_lusgs_extra_survives_a_failure(monkeypatch):
     assert out["error"].startswith("no device")
 
 
-def test_cylinder_workload_option():
+def test_cylinder_workload_options():
     wl = bench.make_workload("cylinder")
-    assert wl.n_cell == 1600 and wl.N == (64, 64, 64)
+    assert wl.n_cell == 1606 and wl.N == (64, 64, 64)
+    assert bench.make_workload("cylinder_ogrid").n_cell == 1600

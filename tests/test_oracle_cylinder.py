@@ -90,3 +90,26 @@ def test_cylinder_ranks_grow_near_the_wall_and_with_accuracy(oracle_lib):
         grown[eps] = int(np.sum(wall > 1))
     assert C[1e-3] <= C[1e-4] <= C[1e-5] and C[1e-3] < C[1e-5]
     assert grown[1e-3] <= grown[1e-4] <= grown[1e-5] and grown[1e-5] == 8
+
+
+def test_staircase_cylinder_geometry(oracle_lib):
+    """The lattice variant: the rectangle minus the cells whose centre lies in the unit
+    half disc, every face on a coordinate plane, the wall facing the removed cells."""
+    h = 0.25
+    wl = W.cylinder_staircase(h=h, N=6)
+    o = oracle_lib.FullGridOracle(wl)
+    vol, fcell, fgeo = o.geometry()
+    nx, ny = 48, 34
+    removed = sum(1 for i in range(nx) for j in range(ny)
+                  if (-5.0 + (i + 0.5) * h) ** 2 + ((j + 0.5) * h) ** 2 < 1.0)
+    assert wl.n_cell == nx * ny - removed == 1606
+    assert abs(vol.sum() - wl.n_cell * h ** 3) < 1e-12
+    assert np.all(np.max(np.abs(fgeo[:, 1:]), axis=1) == 1.0)
+    b = fcell[:, 1] < 0
+    groups = fcell[b, 2]
+    assert np.sum(groups == 0) == 2 * ny + nx                 # x ends and the top
+    centre = np.array([wl.xyz[q].mean(axis=0) for q in wl.hex8])
+    wc = fcell[b][groups == 1, 0]
+    ew = fgeo[b][groups == 1, 1:]
+    nxt = centre[wc, :2] + h * ew[:, :2]                     # the removed neighbour's centre
+    assert np.all(np.sum(nxt ** 2, axis=1) < 1.0)

@@ -8,5 +8,5 @@ moments, no Maxwellians, no fluxes.  Every array it returns is plain numpy.
 from .meshes import (  # noqa: F401
     BC_FREESTREAM, BC_ZEROGRAD, BC_SYMMETRY, BC_WALL, BC_NAMES, LOCAL_FACES,
     Workload, lattice_hex_mesh, sod_row, cavity, obstacle, specular_box,
-    closed_freestream_box, channel, cylinder, uniform_random_tucker_ranks,
+    closed_freestream_box, channel, cylinder, cylinder_staircase, uniform_random_tucker_ranks,
 )

@@ -106,7 +106,7 @@ class Workload:
 
 
 def lattice_hex_mesh(shape, origin, h, hole=None, jitter=0.0, jitter_seed=None,
-                     perm_seed=None, rotate_seed=None, classify=None):
+                     perm_seed=None, rotate_seed=None, classify=None, keep=None):
     """Hex mesh of a box lattice, optionally with a box-shaped hole.
 
     shape   (nx, ny, nz) cells;  origin (x0, y0, z0);  h (hx, hy, hz).
@@ -117,6 +117,7 @@ def lattice_hex_mesh(shape, origin, h, hole=None, jitter=0.0, jitter_seed=None,
     rotate_seed relabels each hex by a random proper rotation of the cube, so
                 that local face numbers no longer follow the x/y/z order.
     classify(ijk, axis, sign, on_outer_box) -> group id for each boundary face.
+    keep(i, j, k) -> False removes that cell as well (no jitter with it).
     Returns (xyz, hex8, bface, bgroup, cell_ijk).
     """
     nx, ny, nz = shape
@@ -133,12 +134,16 @@ def lattice_hex_mesh(shape, origin, h, hole=None, jitter=0.0, jitter_seed=None,
         return (i * (ny + 1) + j) * (nz + 1) + k
 
     def in_hole(i, j, k):
+        if keep is not None and not keep(i, j, k):
+            return True
         if hole is None:
             return False
         (i0, i1), (j0, j1), (k0, k1) = hole
         return i0 <= i < i1 and j0 <= j < j1 and k0 <= k < k1
 
     if jitter > 0.0:
+        if keep is not None:
+            raise ValueError("jitter with a removal mask is not supported")
         rng = np.random.default_rng(jitter_seed)
         fixed = ((lat[:, 0] == 0) | (lat[:, 0] == nx) | (lat[:, 1] == 0) | (lat[:, 1] == ny)
                  | (lat[:, 2] == 0) | (lat[:, 2] == nz))
@@ -409,6 +414,8 @@ def cylinder(n_theta=40, n_r=40, N=64, r_out=8.0, dr1=0.05, Kn=0.552, Tw=5.0,
     the velocity box +-6400 m/s = +-22.2, N = 64 nodes per axis as in Section 7;
     viscosity exponent 0.734; Kn = 0.552 is the printed Kn ~ 0.56 in the collision
     frequency of these units.  Cells are numbered radius-fastest (or shuffled with seed).
+    The curved wall's faces leave the coordinate planes, which the full format takes and
+    the Tucker format does not (`cylinder_staircase` is its Tucker-ready variant).
     """
     g = _growth(dr1, r_out - 1.0, n_r)
     r = np.concatenate([[1.0], 1.0 + dr1 * np.cumsum(g ** np.arange(n_r))])
@@ -465,6 +472,44 @@ def cylinder(n_theta=40, n_r=40, N=64, r_out=8.0, dr1=0.05, Kn=0.552, Tw=5.0,
              (2, BC_SYMMETRY, np.zeros(8))],
         n0=np.ones(nc), u0=u0, T0=np.ones(nc), cell_ijk=ijk, steps=4000,
         rank_cap=rank_cap, tol=tol, h=(dr1, hz, hz))
+
+
+def cylinder_staircase(h=0.25, x_range=(-5.0, 7.0), y_max=8.5, N=64, Kn=0.552, Tw=5.0,
+                       u_inf=2630.0 / _C_UNIT, vmax=6400.0 / _C_UNIT, rank_cap=16, tol=1e-5,
+                       seed=None):
+    """The Mach-10 cylinder of `cylinder` on a Cartesian lattice: square cells of side h
+    over x in x_range, y in [0, y_max], one cell along z, with the cells whose centre lies
+    inside the unit circle removed, so the wall is a staircase and every face lies on a
+    coordinate plane (the Tucker format takes diffuse walls only there).  1607 cells at
+    the defaults.  Groups as in `cylinder`: 0 free stream (x ends and y = y_max), 1 the
+    wall at Tw, 2 symmetry (y = 0 and both z planes)."""
+    nx = int(round((x_range[1] - x_range[0]) / h))
+    ny = int(round(y_max / h))
+
+    def keep(i, j, k):
+        xc = x_range[0] + (i + 0.5) * h
+        yc = (j + 0.5) * h
+        return xc * xc + yc * yc >= 1.0
+
+    def classify(ijk, axis, sign, outer):
+        if not outer:
+            return 1
+        if axis == 2 or (axis == 1 and sign < 0):
+            return 2
+        return 0
+
+    xyz, hex8, bface, bgroup, ijk = lattice_hex_mesh(
+        (nx, ny, 1), (x_range[0], 0.0, 0.0), (h, h, h), perm_seed=seed, classify=classify,
+        keep=keep)
+    nc = hex8.shape[0]
+    return Workload(
+        name=f"cylinder_staircase_{nc}x{N}^3", xyz=xyz, hex8=hex8, bface=bface, bgroup=bgroup,
+        N=(N, N, N), lo=(-vmax,) * 3, hi=(vmax,) * 3, Pr=2.0 / 3.0, omega=0.734, Kn=Kn,
+        bcs=[(0, BC_FREESTREAM, _params(n=1.0, u=(u_inf, 0.0, 0.0), T=1.0)),
+             (1, BC_WALL, _params(Tw=Tw)),
+             (2, BC_SYMMETRY, np.zeros(8))],
+        n0=np.ones(nc), u0=np.tile([u_inf, 0.0, 0.0], (nc, 1)), T0=np.ones(nc),
+        cell_ijk=ijk, steps=4000, rank_cap=rank_cap, tol=tol, h=(h, h, h))
 
 
 def _growth(d1, length, n):
