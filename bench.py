@@ -444,12 +444,14 @@ def run_path(P, NAT, wl, fmt, prec, cap, tol, advance, warmup, steps, stream, sn
 
 
 def run_serving(P, n_req=12, seed=7, mean_gap_s=0.25, budget_gb=64, slots=8, res_tol=1e-4,
-                max_steps=4000):
+                max_steps=4000, implicit=False):
     """Seeded Poisson arrivals of steady channel solves (Poiseuille / thermal
     transpiration), Tucker mixed format, each run to the residual res_tol (scaled-down
     version of the 64-request mix so that it ends within the bench's time).  Latency
     percentiles and solves/hour count the converged solves only; the others are
-    reported by state."""
+    reported by state.  implicit: the same requests in the full format (FP64) with the
+    implicit LU-SGS step at cfl 20 (Section 3), which the Tucker format has no GPU path
+    for."""
     import workloads as W
     rng = np.random.default_rng(seed)
     reqs = []
@@ -471,19 +473,24 @@ def run_serving(P, n_req=12, seed=7, mean_gap_s=0.25, budget_gb=64, slots=8, res
         now = time.perf_counter() - t0
         while k < n_req and reqs[k][0] <= now:
             _, wl, cap = reqs[k]
-            tickets.append((srv.submit(wl, format=1, precision=1, rank_cap=cap, tol=1e-6,
-                                       res_tol=res_tol, max_steps=max_steps, check_every=25),
-                            wl))
+            if implicit:
+                tk = srv.submit(wl, format=0, precision=0, res_tol=res_tol, max_steps=max_steps,
+                                check_every=25, scheme=1, cfl=20.0)
+            else:
+                tk = srv.submit(wl, format=1, precision=1, rank_cap=cap, tol=1e-6,
+                                res_tol=res_tol, max_steps=max_steps, check_every=25)
+            tickets.append((tk, wl))
             k += 1
         pending = srv.run(0.02)
         if k == n_req and pending == 0:
             break
     total = time.perf_counter() - t0
-    lat, conv, upd, states, errors = [], 0, 0, {}, set()
+    lat, conv, upd, states, errors, steps_conv = [], 0, 0, {}, set(), []
     for tk, wl in tickets:
         st = srv.poll(tk)
         if st["state"] == 2:
             lat.append(st["latency_s"])
+            steps_conv.append(st["steps"])
             conv += 1
         states[st["state"]] = states.get(st["state"], 0) + 1
         if st["state"] == 4:
@@ -499,11 +506,14 @@ def run_serving(P, n_req=12, seed=7, mean_gap_s=0.25, budget_gb=64, slots=8, res
             "p50_latency_s": float(np.percentile(lat, 50)) if conv else None,
             "p99_latency_s": float(np.percentile(lat, 99)) if conv else None,
             "latency_over": "converged solves only (submission to converged residual)",
+            "median_steps_to_converge": float(np.median(steps_conv)) if conv else None,
             "updates_per_s": upd / total,
             "mix": f"{n_req} channel Poiseuille/transpiration solves, 256-1024 cells, "
-                   "12^3-16^3 nodes, Kn 0.3-10, Tucker mixed eps 1e-6 cap 6-12, residual "
-                   f"{res_tol:g} (at most {max_steps} steps), Poisson arrivals (mean gap "
-                   f"{mean_gap_s} s, seed {seed}), {slots} slots"}
+                   "12^3-16^3 nodes, Kn 0.3-10, "
+                   + ("full grid FP64, implicit LU-SGS at cfl 20" if implicit else
+                      "Tucker mixed eps 1e-6 cap 6-12")
+                   + f", residual {res_tol:g} (at most {max_steps} steps), Poisson arrivals "
+                   f"(mean gap {mean_gap_s} s, seed {seed}), {slots} slots"}
 
 
 def run_c2(P, NAT, stream, advance=200, warmup=3, steps=10):
@@ -833,6 +843,10 @@ def run_gpu(args, rank, world):
                 line["configs"]["C2_cavity_16^3x32^3"] = run_c2(P, NAT, stream)
             line["configs"].update(run_c4(P, NAT, stream, advance=args.c4_advance))
             line["serving"] = run_serving(P)
+            try:
+                line["serving_implicit_full"] = run_serving(P, implicit=True)
+            except Exception as e:  # a failed extra does not void the headline line
+                line["serving_implicit_full"] = {"error": str(e)[:200]}
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(wl)
         print(json.dumps(line), flush=True)

@@ -164,3 +164,48 @@ def test_cylinder_workload_options():
     wl = bench.make_workload("cylinder")
     assert wl.n_cell == 1606 and wl.N == (64, 64, 64)
     assert bench.make_workload("cylinder_ogrid").n_cell == 1600
+
+
+class _FakeServer:
+    def __init__(self, budget, slots):
+        self.sub = []
+
+    def submit(self, wl, **kw):
+        self.sub.append(kw)
+        return len(self.sub) - 1
+
+    def run(self, seconds):
+        return 0
+
+    def poll(self, t):
+        return {"state": 2 if t % 2 == 0 else 3, "steps": 100 + t, "residual": 1e-5,
+                "latency_s": 0.5 + t}
+
+    def error(self, t):
+        return ""
+
+    def close(self):
+        pass
+
+
+@pytest.mark.parametrize("implicit", [False, True])
+def test_serving_mix_reports_converged_solves_only(monkeypatch, implicit):
+    import types
+    made = []
+
+    def server(b, s):
+        made.append(_FakeServer(b, s))
+        return made[-1]
+    monkeypatch.setattr(bench.time, "perf_counter",
+                        iter(float(x) for x in range(10 ** 6)).__next__)
+    P = types.SimpleNamespace(Server=server)
+    out = bench.run_serving(P, n_req=6, implicit=implicit)
+    assert out["requests"] == 6 and out["converged"] == 3 and out["not_converged"] == 3
+    assert out["median_steps_to_converge"] == 102.0
+    kw = made[0].sub
+    assert len(kw) == 6
+    if implicit:
+        assert all(k["scheme"] == 1 and k["format"] == 0 and k["cfl"] == 20.0 for k in kw)
+        assert "implicit LU-SGS" in out["mix"]
+    else:
+        assert all(k["format"] == 1 and "scheme" not in k for k in kw)
