@@ -6,10 +6,12 @@ path (no shared code, headers, tables or helpers); the only thing both sides con
 is the seeded input from ``workloads``.
 
 * ``FullGridOracle`` wraps ``dvm_oracle.c``: the plain FP64 full-grid method
-  (Algorithms 1 and 2 of Section 3) on an unstructured hex mesh.
+  (Algorithms 1 and 2 of Section 3) on an unstructured hex mesh, and its implicit step
+  (Section 3, linear-system equation: one LU-SGS pass over the cells in index order).
 * ``oracle.tucker`` holds the Tucker-format reference operations of Sections 4-5 in
   numpy (expansion, HOSVD, sum, Hadamard product, weighted convolution, rank-1
-  Maxwellian, Lemma 1, the low-rank Shakhov function) used to pin the Tucker path.
+  Maxwellian, Lemma 1, the low-rank Shakhov function, the rank-1 diagonal estimate and
+  division, the Tucker format's implicit step) used to pin the Tucker path.
 """
 from __future__ import annotations
 
