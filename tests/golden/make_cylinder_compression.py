@@ -14,7 +14,11 @@ error in T of the compressed state (a one-time rounding error, not the paper's s
 difference Delta T), and the map of each cell's largest rank (rows: theta from the
 downstream axis, 0, to the stagnation line, pi; columns: wall to outer boundary).
 
-Run: python tests/golden/make_cylinder_compression.py  (about 7 minutes on 8 cores).
+With --staircase the same study runs on the lattice variant (cylinder_staircase, h = 0.5,
+402 cells), which the Tucker format can take, into cylinder_staircase_compression.json.
+
+Run: python tests/golden/make_cylinder_compression.py [--staircase]  (about 7 / 10 minutes
+on 8 cores).
 """
 import json
 import math
@@ -32,6 +36,7 @@ from oracle import tucker as tk  # noqa: E402
 import workloads as W  # noqa: E402
 
 SHAPE = dict(n_theta=16, n_r=12, N=40, dr1=0.1)
+STAIRCASE = dict(h=0.5, N=40)   # the Tucker-ready lattice variant, 402 cells
 STEPS, DT_FACTOR, EPS = 400, 20.0, (1e-3, 1e-4, 1e-5)
 
 
@@ -41,8 +46,13 @@ def temperature(o, f):
     return a[4]
 
 
-def main(out=os.path.join(HERE, "cylinder_compression.json")):
-    wl = W.cylinder(**SHAPE)
+def main(staircase=False):
+    if staircase:
+        wl = W.cylinder_staircase(**STAIRCASE)
+        out = os.path.join(HERE, "cylinder_staircase_compression.json")
+    else:
+        wl = W.cylinder(**SHAPE)
+        out = os.path.join(HERE, "cylinder_compression.json")
     o = oracle.FullGridOracle(wl)
     dt = DT_FACTOR * o.dt()
     hist, t0 = [], time.time()
@@ -53,10 +63,17 @@ def main(out=os.path.join(HERE, "cylinder_compression.json")):
     f = o.f()
     m = o.macro()
     N = wl.N[0]
-    j_r = wl.cell_ijk[:, 1]
-    bands = {"wall (first cell)": j_r == 0, "near wall (cells 1-3)": (j_r >= 1) & (j_r <= 3),
-             "middle": (j_r >= 4) & (j_r <= 8), "outer (last 3 cells)": j_r >= SHAPE["n_r"] - 3}
-    res = {"workload": wl.name, "shape": SHAPE, "velocity_box": [wl.lo[0], wl.hi[0]],
+    centre = np.array([wl.xyz[q].mean(axis=0) for q in wl.hex8])
+    rad = np.hypot(centre[:, 0], centre[:, 1])
+    if staircase:     # radial bands by distance from the axis
+        bands = {"wall (r < 1.5)": rad < 1.5, "near wall (1.5-2.5)": (rad >= 1.5) & (rad < 2.5),
+                 "middle (2.5-5)": (rad >= 2.5) & (rad < 5.0), "outer (r >= 5)": rad >= 5.0}
+    else:
+        j_r = wl.cell_ijk[:, 1]
+        bands = {"wall (first cell)": j_r == 0, "near wall (cells 1-3)": (j_r >= 1) & (j_r <= 3),
+                 "middle": (j_r >= 4) & (j_r <= 8), "outer (last 3 cells)": j_r >= SHAPE["n_r"] - 3}
+    res = {"workload": wl.name, "shape": STAIRCASE if staircase else SHAPE,
+           "velocity_box": [wl.lo[0], wl.hi[0]],
            "Kn": wl.Kn, "omega": wl.omega, "Tw": 5.0, "u_inf": wl.u0[0, 0],
            "implicit_steps": STEPS, "dt": dt, "residual_history": hist,
            "T_range": [float(m[:, 4].min()), float(m[:, 4].max())],
@@ -71,7 +88,8 @@ def main(out=os.path.join(HERE, "cylinder_compression.json")):
             dT.append(abs(temperature(o, tk.full(t)) - m[c, 4]) / m[c, 4])
         ranks = np.array(ranks)
         rmax = ranks.max(axis=1)
-        rmap = np.zeros((SHAPE["n_theta"], SHAPE["n_r"]), dtype=int)
+        nx, ny = wl.cell_ijk[:, 0].max() + 1, wl.cell_ijk[:, 1].max() + 1
+        rmap = np.zeros((nx, ny), dtype=int)    # removed lattice cells stay 0
         rmap[wl.cell_ijk[:, 0], wl.cell_ijk[:, 1]] = rmax
         res["eps"][f"{eps:g}"] = {
             "mean_compression": float(np.mean(C)),
@@ -79,7 +97,7 @@ def main(out=os.path.join(HERE, "cylinder_compression.json")):
             "max_rank_histogram": {int(v): int(np.sum(rmax == v)) for v in np.unique(rmax)},
             "mean_max_rank_by_band": {k: float(rmax[b].mean()) for k, b in bands.items()},
             "T_rounding_error_rel_max": float(np.max(dT)),
-            "rank_map_theta_by_radius": rmap.tolist(),
+            ("rank_map_x_by_y" if staircase else "rank_map_theta_by_radius"): rmap.tolist(),
         }
         print(eps, res["eps"][f"{eps:g}"]["mean_compression"], flush=True)
     with open(out, "w") as fp:
@@ -88,4 +106,4 @@ def main(out=os.path.join(HERE, "cylinder_compression.json")):
 
 
 if __name__ == "__main__":
-    main()
+    main(staircase="--staircase" in sys.argv)
