@@ -113,3 +113,47 @@ def test_staircase_cylinder_geometry(oracle_lib):
     ew = fgeo[b][groups == 1, 1:]
     nxt = centre[wc, :2] + h * ew[:, :2]                     # the removed neighbour's centre
     assert np.all(np.sum(nxt ** 2, axis=1) < 1.0)
+
+
+def _closed_annulus(Tw_outer=1.0, Tw_inner=1.0, N=12, vmax=5.0):
+    """The O-grid with the outer circle turned into a diffuse wall too: a closed annulus
+    bounded by curved walls and the symmetry planes, gas at rest."""
+    wl = W.cylinder(n_theta=8, n_r=4, N=N, r_out=3.0, dr1=0.4, Kn=0.5, u_inf=0.0, vmax=vmax)
+    wl.bcs = [(0, W.BC_WALL, np.array([0, 0, 0, 0, Tw_outer, 0, 0, 0], float)),
+              (1, W.BC_WALL, np.array([0, 0, 0, 0, Tw_inner, 0, 0, 0], float)),
+              (2, W.BC_SYMMETRY, np.zeros(8))]
+    return wl
+
+
+def test_curved_walls_are_impermeable(oracle_lib):
+    """Section 2 (wall-bc-f): the wall density from the discrete impermeability sum makes
+    the mass flux through every wall face zero, on faces off the coordinate planes as on
+    them, so a closed annulus keeps its mass (a hot inner wall drives the gas).  The
+    velocity grid is fine enough (spacing 0.4) that the collision term's quadrature defect
+    is far below round-off."""
+    wl = _closed_annulus(Tw_outer=1.0, Tw_inner=3.0, N=32, vmax=6.2)
+    o = oracle_lib.FullGridOracle(wl)
+    vol, _, _ = o.geometry()
+
+    def mass():
+        return float(np.sum(vol * o.macro()[:, 0]))
+    m0 = mass()
+    o.step(10, o.dt())
+    assert abs(mass() - m0) < 1e-13 * m0
+    assert np.max(np.abs(o.macro()[:, 4] - 1.0)) > 1e-3      # the hot wall heated the gas
+
+
+def test_curved_wall_density_equals_gas_density_at_equilibrium(oracle_lib):
+    """Gas at rest at the wall temperature: on a velocity grid symmetric under xi -> -xi
+    the outgoing and incoming half-range sums pair up node by node for any normal, so the
+    reflected density equals the gas density on curved faces too."""
+    wl = _closed_annulus()
+    wl.n0 = np.full(wl.n_cell, 0.8)
+    o = oracle_lib.FullGridOracle(wl)
+    o.step(1, 1e-4)
+    nw = o.wall_density()
+    _, fcell, fgeo = o.geometry()
+    wall = fcell[:, 1] < 0
+    wall &= np.isin(fcell[:, 2], (0, 1))
+    assert np.sum(np.max(np.abs(fgeo[wall, 1:]), axis=1) < 0.999) > 8   # curved faces
+    assert np.max(np.abs(nw[wall] - 0.8)) < 1e-13
