@@ -17,8 +17,11 @@ downstream axis, 0, to the stagnation line, pi; columns: wall to outer boundary)
 With --staircase the same study runs on the lattice variant (cylinder_staircase, h = 0.5,
 402 cells), which the Tucker format can take, into cylinder_staircase_compression.json.
 
-Run: python tests/golden/make_cylinder_compression.py [--staircase]  (about 7 / 10 minutes
-on 8 cores).
+With --staircase --N=64 it runs at the paper's velocity grid (cylinder_staircase_N64_
+compression.json; about an hour on 8 cores).
+
+Run: python tests/golden/make_cylinder_compression.py [--staircase [--N=64]]  (about 7 / 15
+minutes on 8 cores without --N).
 """
 import json
 import math
@@ -46,10 +49,12 @@ def temperature(o, f):
     return a[4]
 
 
-def main(staircase=False):
+def main(staircase=False, N=None):
     if staircase:
-        wl = W.cylinder_staircase(**STAIRCASE)
-        out = os.path.join(HERE, "cylinder_staircase_compression.json")
+        kw = dict(STAIRCASE, **({"N": N} if N else {}))
+        wl = W.cylinder_staircase(**kw)
+        tag = f"_N{N}" if N else ""
+        out = os.path.join(HERE, f"cylinder_staircase{tag}_compression.json")
     else:
         wl = W.cylinder(**SHAPE)
         out = os.path.join(HERE, "cylinder_compression.json")
@@ -72,7 +77,7 @@ def main(staircase=False):
         j_r = wl.cell_ijk[:, 1]
         bands = {"wall (first cell)": j_r == 0, "near wall (cells 1-3)": (j_r >= 1) & (j_r <= 3),
                  "middle": (j_r >= 4) & (j_r <= 8), "outer (last 3 cells)": j_r >= SHAPE["n_r"] - 3}
-    res = {"workload": wl.name, "shape": STAIRCASE if staircase else SHAPE,
+    res = {"workload": wl.name, "shape": kw if staircase else SHAPE,
            "velocity_box": [wl.lo[0], wl.hi[0]],
            "Kn": wl.Kn, "omega": wl.omega, "Tw": 5.0, "u_inf": wl.u0[0, 0],
            "implicit_steps": STEPS, "dt": dt, "residual_history": hist,
@@ -106,4 +111,5 @@ def main(staircase=False):
 
 
 if __name__ == "__main__":
-    main(staircase="--staircase" in sys.argv)
+    n_arg = [int(a.split("=")[1]) for a in sys.argv if a.startswith("--N=")]
+    main(staircase="--staircase" in sys.argv, N=n_arg[0] if n_arg else None)
