@@ -100,7 +100,8 @@ def main(staircase=False, N=None):
             "mean_compression": float(np.mean(C)),
             "rank_mean": float(ranks.mean()), "rank_max": int(ranks.max()),
             "max_rank_histogram": {int(v): int(np.sum(rmax == v)) for v in np.unique(rmax)},
-            "mean_max_rank_by_band": {k: float(rmax[b].mean()) for k, b in bands.items()},
+            "mean_max_rank_by_band": {k: float(rmax[b].mean()) if b.any() else None
+                                      for k, b in bands.items()},
             "T_rounding_error_rel_max": float(np.max(dT)),
             ("rank_map_x_by_y" if staircase else "rank_map_theta_by_radius"): rmap.tolist(),
         }

@@ -157,3 +157,28 @@ def test_curved_wall_density_equals_gas_density_at_equilibrium(oracle_lib):
     wall &= np.isin(fcell[:, 2], (0, 1))
     assert np.sum(np.max(np.abs(fgeo[wall, 1:]), axis=1) < 0.999) > 8   # curved faces
     assert np.max(np.abs(nw[wall] - 0.8)) < 1e-13
+
+
+def test_compression_study_script_runs(oracle_lib, tmp_path, monkeypatch):
+    """The script that wrote tests/golden/cylinder*_compression.json, on a tiny case:
+    its output has the fields the stored tables were read from."""
+    import importlib.util
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "make_cylinder_compression.py")
+    spec = importlib.util.spec_from_file_location("make_cylinder_compression", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    monkeypatch.setattr(mod, "HERE", str(tmp_path))
+    monkeypatch.setattr(mod, "STEPS", 10)
+    monkeypatch.setattr(mod, "SHAPE", dict(n_theta=6, n_r=5, N=12, dr1=0.3))
+    monkeypatch.setattr(mod, "STAIRCASE", dict(h=1.0, N=12))
+    for stair in (False, True):
+        res = mod.main(staircase=stair)
+        name = "cylinder_staircase_compression.json" if stair else "cylinder_compression.json"
+        stored = json.load(open(tmp_path / name))
+        assert stored["residual_history"][-1][0] == 10
+        C = [stored["eps"][k]["mean_compression"] for k in ("0.001", "0.0001", "1e-05")]
+        assert C[0] <= C[1] <= C[2]
+        key = "rank_map_x_by_y" if stair else "rank_map_theta_by_radius"
+        assert all(key in v for v in res["eps"].values())
