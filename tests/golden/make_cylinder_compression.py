@@ -17,10 +17,10 @@ downstream axis, 0, to the stagnation line, pi; columns: wall to outer boundary)
 With --staircase the same study runs on the lattice variant (cylinder_staircase, h = 0.5,
 402 cells), which the Tucker format can take, into cylinder_staircase_compression.json.
 
-With --staircase --N=64 it runs at the paper's velocity grid (cylinder_staircase_N64_
-compression.json; about an hour on 8 cores).
+With --N=64 either mesh runs at the paper's velocity grid (cylinder[_staircase]_N64_
+compression.json; about 35 / 50 minutes on 8 cores).
 
-Run: python tests/golden/make_cylinder_compression.py [--staircase [--N=64]]  (about 7 / 15
+Run: python tests/golden/make_cylinder_compression.py [--staircase] [--N=64]  (about 7 / 15
 minutes on 8 cores without --N).
 """
 import json
@@ -56,8 +56,10 @@ def main(staircase=False, N=None):
         tag = f"_N{N}" if N else ""
         out = os.path.join(HERE, f"cylinder_staircase{tag}_compression.json")
     else:
-        wl = W.cylinder(**SHAPE)
-        out = os.path.join(HERE, "cylinder_compression.json")
+        kw = dict(SHAPE, **({"N": N} if N else {}))
+        wl = W.cylinder(**kw)
+        tag = f"_N{N}" if N else ""
+        out = os.path.join(HERE, f"cylinder{tag}_compression.json")
     o = oracle.FullGridOracle(wl)
     dt = DT_FACTOR * o.dt()
     hist, t0 = [], time.time()
@@ -76,8 +78,8 @@ def main(staircase=False, N=None):
     else:
         j_r = wl.cell_ijk[:, 1]
         bands = {"wall (first cell)": j_r == 0, "near wall (cells 1-3)": (j_r >= 1) & (j_r <= 3),
-                 "middle": (j_r >= 4) & (j_r <= 8), "outer (last 3 cells)": j_r >= SHAPE["n_r"] - 3}
-    res = {"workload": wl.name, "shape": kw if staircase else SHAPE,
+                 "middle": (j_r >= 4) & (j_r <= 8), "outer (last 3 cells)": j_r >= kw["n_r"] - 3}
+    res = {"workload": wl.name, "shape": kw,
            "velocity_box": [wl.lo[0], wl.hi[0]],
            "Kn": wl.Kn, "omega": wl.omega, "Tw": 5.0, "u_inf": wl.u0[0, 0],
            "implicit_steps": STEPS, "dt": dt, "residual_history": hist,
